@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Throughput of the batched many-particle CTQW propagation on GB300.
+
+One bench step is one pass of the hot path over one batch: write the initial
+states of all realizations, then propagate them n_steps Taylor steps (order K)
+while sampling P(x) (ensemble-averaged), norms and energies every obs_every
+steps.  Default workload: bosons_n256_u2 (2 bosons, open chain N=256, U=2,
+eps ~ U[-1,1], J = 1 + U[-0.25,0.25], dt = 0.02, K = 16, 2500 steps, 1024
+realizations, complex FP32 with compensated update).  Metric: site-updates/s
+= N^m * K * steps * realizations / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank drives one GPU and owns its own block of
+realizations (weak scaling); the ranks' ensemble means are combined once per
+step in FP64.  --impl reference times the FP64 CPU oracle on the host cores
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import ctqw_workloads as cw  # noqa: E402
+
+METRIC = "site-updates/s (dim x K x steps x realizations)"
+UNIT = "site-updates/s"
+FP32_FMA_LANES_PER_SM = 128      # FP32 FMA lanes per SM
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+# ---------------------------------------------------------------- oracle (CPU) legs
+def _oracle_chunk(args):
+    """Propagate one realization of a workload with the oracle (runs in a worker)."""
+    name, r, n_steps = args
+    import numpy as np  # noqa: F401
+
+    import oracle
+
+    w = cw.get(name)
+    N = int(w.sizes()[r])
+    ue, uj = cw.uniform_draws(w.seed, [r], [N])
+    eps, J = oracle.workload_parameters(w, ue[0], uj[0], N)
+    H = oracle.many_particle_hamiltonian(oracle.single_particle_hamiltonian(eps, J, w.periodic), w.m, w.U)
+    psi = oracle.initial_state(N, w.m, w.initial_sites(N), w.statistics)
+    t0 = time.perf_counter()
+    res = oracle.propagate(H, psi, N, w.m, w.dt, n_steps, w.obs_every, "taylor", w.K)
+    dt = time.perf_counter() - t0
+    return float(N ** w.m) * w.K * n_steps, dt, float(res["norm"][-1])
+
+
+def oracle_sample(name: str, cores: int, n_steps: int, first: int = 0):
+    """Site-updates/s of the oracle over `cores` realizations run in parallel."""
+    ctx = mp.get_context("spawn")
+    jobs = [(name, first + k, n_steps) for k in range(cores)]
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_chunk, [(name, 0, 1)] * cores)   # import warm-up in every worker
+        t0 = time.perf_counter()
+        out = pool.map(_oracle_chunk, jobs)
+        wall = time.perf_counter() - t0
+    units = sum(o[0] for o in out)
+    return units / wall, units, wall
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sms, maxs, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs),
+                "reasons": sorted(reasons), "samples": len(sms),
+                "power_w_median": statistics.median(power) if power else None}
+
+
+# ---------------------------------------------------------------- helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def visible_gpu_id(local_rank: int) -> str:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return str(local_rank)
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = cw.get(args.workload)
+    cores = host_cores()
+    steps_per_sample = args.ref_steps
+    for _ in range(args.warmup):
+        oracle_sample(w.name, cores, steps_per_sample)
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        v, units, wall = oracle_sample(w.name, cores, steps_per_sample)
+        vals.append((units, wall))
+    units = sum(u for u, _ in vals)
+    wall = sum(t for _, t in vals)
+    value = units / wall
+    sample = (f"{cores} realizations (one per host core) x {steps_per_sample} of "
+              f"{w.n_steps} steps of {w.name} per bench step, K={w.K}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.name, "m": w.m, "N": w.N, "R": w.R,
+                                         "K": w.K, "dt": w.dt, "n_steps": w.n_steps},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.perf_counter() - t_all,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1612_00746_gb300 import ctqw
+    from paper_1612_00746_gb300.ensemble import combine_means, max_over_ranks
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctqw.load()
+
+    w = cw.get(args.workload)
+    # cpu baseline first (spawned workers, before heavy GPU use), rank 0 at N=1 only
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cores = host_cores()
+        v, units, wall = oracle_sample(w.name, cores, args.cpu_steps)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{cores} realizations (one per host core) x {args.cpu_steps} of "
+                         f"{w.n_steps} steps of {w.name}, K={w.K}, FP64 ({wall:.1f} s)"}
+
+    # realizations of this rank: its own block of the (weakly scaled) ensemble
+    realizations = list(range(rank * w.R, (rank + 1) * w.R))
+    u_eps, u_J, sizes, _ = cw.packed_draws(w, realizations)
+    dtype = w.dtype
+    stream = torch.cuda.current_stream()
+    h = ctqw.Hamiltonian(w.m, w.statistics, w.periodic, sizes, w.J0, w.U, w.eps_halfwidth,
+                         w.J_halfwidth, u_eps, u_J)
+    sites = ctqw.initial_sites(w, h)
+    psi = h.new_state(dtype, dev)
+    n_obs = h.n_obs(w.n_steps, w.obs_every)
+    P = torch.empty((n_obs, h.p_width), dtype=torch.float64, device=dev)
+    nr = torch.empty((n_obs, h.R), dtype=torch.float64, device=dev)
+    en = torch.empty((n_obs, h.R), dtype=torch.float64, device=dev)
+    ws = h.workspace(dtype, ctqw.TAYLOR, 0, dev)
+    counts = torch.tensor(np.repeat(h.group_count, h.group_sizes), dtype=torch.float64, device=dev)
+    D = float(np.sum(sizes.astype(np.float64) ** w.m))
+    units_per_step = D * w.K * w.n_steps
+    launches_per_step = 2   # init_state kernel + fused propagation kernel
+
+    prop_events = []
+
+    def step(record=False):
+        ctqw.ctqw_init_state(h, psi, sites, dtype)
+        if record:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        ctqw.ctqw_propagate_taylor(h, psi, dtype, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en, 0, ws)
+        if record:
+            e1.record(stream)
+            prop_events.append((e0, e1))
+        if world > 1:
+            combine_means(P, counts)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(visible_gpu_id(local))
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(record=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    ms = t0.elapsed_time(t1) / args.steps
+    ms_max = max_over_ranks(ms, dev)
+    value = world * units_per_step / (ms_max / 1000.0)
+    kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in prop_events)
+
+    # accuracy self-check of this run (rank 0's realizations): norm drift
+    norm_drift = float((nr - 1.0).abs().max().item())
+
+    # end to end: host draws -> build (H2D) -> init -> propagate -> D2H results
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    ue_p, uj_p = pin(u_eps), pin(u_J)
+    h2d = ue_p.numel() * 8 + uj_p.numel() * 8 + sites.size * 4
+    d2h = (P.numel() + nr.numel() + en.numel()) * 8
+    P_host = torch.empty(P.shape, dtype=P.dtype).pin_memory()
+    n_host = torch.empty(nr.shape, dtype=nr.dtype).pin_memory()
+    e_host = torch.empty(en.shape, dtype=en.dtype).pin_memory()
+
+    def e2e_step():
+        h2 = ctqw.Hamiltonian(w.m, w.statistics, w.periodic, sizes, w.J0, w.U, w.eps_halfwidth,
+                              w.J_halfwidth, ue_p.numpy(), uj_p.numpy())
+        ctqw.ctqw_init_state(h2, psi, sites, dtype)
+        ctqw.ctqw_propagate_taylor(h2, psi, dtype, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en, 0, ws)
+        P_host.copy_(P, non_blocking=True)
+        n_host.copy_(nr, non_blocking=True)
+        e_host.copy_(en, non_blocking=True)
+        torch.cuda.synchronize()
+        h2.close()
+
+    e2e_steps = max(1, min(args.steps, 3))
+    e2e_step()
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = max_over_ranks((time.perf_counter() - te) / e2e_steps, dev)
+    e2e_value = world * units_per_step / e2e_s
+
+    # plain per-term FP64 path on a subset (the comparison path of the metric)
+    fp64 = None
+    if not args.no_fp64_plain and rank == 0:
+        sub = list(range(args.fp64_realizations))
+        ue_s, uj_s, sz_s, _ = cw.packed_draws(w, sub)
+        hs = ctqw.Hamiltonian(w.m, w.statistics, w.periodic, sz_s, w.J0, w.U, w.eps_halfwidth,
+                              w.J_halfwidth, ue_s, uj_s)
+        psi64 = hs.new_state(ctqw.C128, dev)
+        ws64 = hs.workspace(ctqw.C128, ctqw.TAYLOR, ctqw.FLAG_PLAIN, dev)
+        steps64 = args.fp64_steps
+        nobs64 = hs.n_obs(steps64, w.obs_every)
+        P64 = torch.empty((nobs64, hs.p_width), dtype=torch.float64, device=dev)
+        sites_s = ctqw.initial_sites(w, hs)
+        ctqw.ctqw_init_state(hs, psi64, sites_s, ctqw.C128)
+        ctqw.ctqw_propagate_taylor(hs, psi64, ctqw.C128, w.dt, w.K, 2, w.obs_every, None, None,
+                                   None, ctqw.FLAG_PLAIN, ws64)
+        torch.cuda.synchronize()
+        ctqw.ctqw_init_state(hs, psi64, sites_s, ctqw.C128)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        ctqw.ctqw_propagate_taylor(hs, psi64, ctqw.C128, w.dt, w.K, steps64, w.obs_every, P64,
+                                   None, None, ctqw.FLAG_PLAIN, ws64)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a0.elapsed_time(a1)
+        units64 = float(np.sum(sz_s.astype(np.float64) ** w.m)) * w.K * steps64
+        # same subset, same steps, fused FP32: agreement of the ensemble mean
+        psi32 = hs.new_state(ctqw.C64, dev)
+        P32 = torch.empty_like(P64)
+        ctqw.ctqw_init_state(hs, psi32, sites_s, ctqw.C64)
+        ctqw.ctqw_propagate_taylor(hs, psi32, ctqw.C64, w.dt, w.K, steps64, w.obs_every, P32,
+                                   None, None, 0, None)
+        torch.cuda.synchronize()
+        dP = float((P32 - P64).abs().max().item())
+        fp64 = {"value": units64 / (ms64 / 1000.0), "unit": UNIT,
+                "sample": f"{len(sub)} realizations x {steps64} steps, plain per-term FP64 kernels",
+                "fp32_speedup": value / world / (units64 / (ms64 / 1000.0)),
+                "max_abs_dP_fp32_vs_fp64": dP}
+        hs.close()
+
+    peaks = measured_peaks()
+    flops_per_unit = 8 * w.m + 4
+    achieved = units_per_step * flops_per_unit / (kernel_ms / 1000.0) / 1e12
+    peak = SM_COUNT * FP32_FMA_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "m": w.m, "N": w.N, "R_per_gpu": w.R, "K": w.K,
+                   "dt": w.dt, "n_steps": w.n_steps, "obs_every": w.obs_every,
+                   "statistics": "bosons" if w.statistics == cw.BOSONS else "distinguishable",
+                   "precision": "complex FP32, compensated state update, FP64 reductions",
+                   "l2": "inputs larger than L2 (states %.0f MB per GPU)" % (D * 8 / 1e6),
+                   "parallelism": f"realizations sharded, {world} rank(s)"},
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "taylor_fused_kernel", "kernel_ms": kernel_ms,
+                     "flops_per_site_update": flops_per_unit,
+                     "peak_basis": "152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz (derived)",
+                     "hbm_gbs_measured": peaks.get("hbm_gbs")},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "cpu_baseline": cpu,
+        "fp64_plain": fp64,
+        "norm_drift": norm_drift,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="bosons_n256_u2")
+    ap.add_argument("--cpu-steps", type=int, default=120, help="steps per realization of the CPU baseline")
+    ap.add_argument("--ref-steps", type=int, default=60, help="steps per realization per reference step")
+    ap.add_argument("--fp64-realizations", type=int, default=16)
+    ap.add_argument("--fp64-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-plain", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

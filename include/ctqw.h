@@ -1,0 +1,203 @@
+/*
+ * ctqw.h - C ABI of the GB300 library for many-particle continuous-time
+ * quantum walks on noisy lattices (Piccinini et al., arXiv:1612.00746).
+ *
+ * The library propagates the state vectors of m = 2 or 3 particles on a 1D
+ * tight-binding chain or ring, one noise realization per state, with the
+ * truncated Taylor series of the evolution operator (Sec. 2.3, Algorithm 3)
+ * or fourth-order Runge-Kutta (Sec. 2.2, Algorithm 2), and reduces the
+ * diagonal of the ensemble density matrix <rho> = (1/R) sum_i |Psi_i><Psi_i|
+ * (Sec. 2) to site occupations P(x) averaged over the realizations.
+ *
+ * Conventions (hbar = 1, sites 0-based):
+ *   H1 = sum_i eps_i |i><i| - sum_b J_b (|b><b+1 mod N| + h.c.)
+ *   H  = sum_j H1 acting on particle j + U * #{pairs j<l with x_j = x_l}
+ *   Open chains have bonds b = 0..N-2; rings add the bond (N-1, 0).
+ *   State of a realization: psi[x_1][x_2] (x_2 fastest) or psi[x_1][x_2][x_3],
+ *   interleaved complex (float2 for CTQW_C64, double2 for CTQW_C128).  The
+ *   states of all realizations are packed back to back; realization r starts
+ *   at amplitude offset st_off[r] (see ctqw_state_size).
+ *   P(x) = (1/m) sum_j sum_{states with x_j = x} |psi|^2  (normalised to the norm).
+ *
+ * Pointers named *_dev are device pointers, *_host host pointers.  All
+ * device work is enqueued on the caller's stream (a cudaStream_t passed as
+ * void*; NULL is the legacy default stream) and nothing synchronizes
+ * implicitly unless stated.  Every entry point validates its arguments before
+ * launching anything and returns a ctqw_status; ctqw_last_error() gives the
+ * message of the last failure on the calling thread.  No entry point aborts,
+ * traps or exits the process.
+ */
+#ifndef CTQW_H
+#define CTQW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define CTQW_OK 0
+#define CTQW_EINVAL 1          /* bad argument (null pointer, size, range)      */
+#define CTQW_ENOMEM 2          /* a device allocation failed                     */
+#define CTQW_ECUDA 3           /* a CUDA runtime call or kernel launch failed    */
+#define CTQW_EUNSUPPORTED 4    /* valid request the library does not implement  */
+
+/* Particle statistics (initial-state symmetry). */
+#define CTQW_DISTINGUISHABLE 0
+#define CTQW_BOSONS 1
+#define CTQW_FERMIONS 2
+
+/* Amplitude types. */
+#define CTQW_C64 0             /* complex float  (float2)  */
+#define CTQW_C128 1            /* complex double (double2) */
+
+/* Propagation flags. */
+#define CTQW_FLAG_PLAIN 0x1            /* force the per-term path (one launch per Taylor term) */
+#define CTQW_FLAG_NO_COMPENSATION 0x2  /* c64 fused path: plain FP32 state update (no carried error term) */
+
+typedef struct ctqw_hamiltonian ctqw_hamiltonian;   /* opaque, owned by the library */
+
+/*
+ * Lattice and disorder description (Eq. (Hij): every entry is a deterministic
+ * part c plus a stochastic part xi, tunnelling between nearest neighbours).
+ *
+ * Realization r has n_sites[r] sites (or n_sites_uniform for all when n_sites
+ * is NULL).  Its disorder is built from uniform draws u in [0, 1) supplied by
+ * the caller, packed back to back (realization r at offset sum_{q<r} N_q):
+ *   eps_{r,i} = eps_mean[i] + eps_halfwidth * (2 u_eps - 1)
+ *   J_{r,b}   = J_mean[b]   + J_halfwidth   * (2 u_J   - 1)
+ * with eps_mean = 0 and J_mean = J0 when the arrays are NULL.  When
+ * round_to_f32 is nonzero every value is rounded to the nearest float32 so
+ * that FP32 and FP64 propagation see identical Hamiltonians.
+ */
+typedef struct {
+    int32_t n_particles;        /* m: 2 or 3                                        */
+    int32_t statistics;         /* CTQW_DISTINGUISHABLE / BOSONS / FERMIONS          */
+    int32_t periodic;           /* 0 open chain, 1 ring                              */
+    int32_t n_realizations;     /* R >= 1                                           */
+    const int32_t *n_sites;     /* host [R] sites per realization, or NULL           */
+    int32_t n_sites_uniform;    /* used when n_sites is NULL                         */
+    int32_t round_to_f32;       /* nonzero: round disorder to float32 values         */
+    double J0;                  /* mean hopping when J_mean is NULL                  */
+    double U;                   /* on-site interaction per coinciding pair           */
+    double eps_halfwidth;       /* on-site disorder half width                       */
+    double J_halfwidth;         /* hopping disorder half width                       */
+    const double *eps_mean;     /* host [max N] per-site means, or NULL              */
+    const double *J_mean;       /* host [max N] per-bond means, or NULL              */
+    const double *u_eps_host;   /* host [sum_r N_r] uniform draws for eps            */
+    const double *u_J_host;     /* host [sum_r N_r] uniform draws for J (entry N-1 of an open chain unused) */
+} ctqw_lattice_desc;
+
+/*
+ * Build the stochastic Hamiltonians of all realizations (Sec. 2, Eq. (Hij)).
+ * Allocates the handle and its device parameter arrays (O(sum_r N_r)), copies
+ * the draws to the device and builds eps, J on the device on `stream`.  The
+ * handle is usable once the stream reaches that point.  Sizes: 2 <= N <= 65536
+ * for m = 2, 2 <= N <= 2048 for m = 3, and sum_r N_r^m < 2^40.
+ * Errors: EINVAL for null pointers or sizes out of range, ENOMEM, ECUDA.
+ */
+int ctqw_build_hamiltonian(const ctqw_lattice_desc *desc, void *stream, ctqw_hamiltonian **out);
+
+/* Free the handle and its device arrays (waits for the device first).  NULL is a no-op. */
+int ctqw_destroy_hamiltonian(ctqw_hamiltonian *h);
+
+/*
+ * Copy the built parameters back to the host (synchronizes the device).
+ * eps_host and J_host are [sum_r N_r] doubles; J entry N_r-1 of an open chain
+ * is 0 (the absent wrap bond).  Either pointer may be NULL.
+ */
+int ctqw_get_params(const ctqw_hamiltonian *h, double *eps_host, double *J_host);
+
+/*
+ * Amplitudes of all realizations, sum_r N_r^m, and optionally the per-
+ * realization start offsets st_off_host [R+1] (host, int64).
+ */
+int ctqw_state_size(const ctqw_hamiltonian *h, int64_t *amplitudes_total, int64_t *st_off_host);
+
+/*
+ * Layout of averaged outputs.  Realizations are grouped by size (groups in
+ * ascending N); P_mean rows hold the groups' averages back to back, so a row
+ * has p_width = sum_g N_g doubles.  group_sizes_host [n_groups] (optional)
+ * receives the N of each group, group_count_host [n_groups] (optional) the
+ * number of realizations in it.
+ */
+int ctqw_output_layout(const ctqw_hamiltonian *h, int64_t *p_width, int32_t *n_groups,
+                       int32_t *group_sizes_host, int32_t *group_count_host);
+
+/*
+ * Write the localised initial state of every realization into psi_dev
+ * (zeroing everything else).  sites_host is [R][m] (host, int32), the
+ * occupied sites of each realization.  Bosons: normalised sum over all
+ * permutations; fermions: normalised signed sum (EINVAL if two sites
+ * coincide); distinguishable: |x_1..x_m>.
+ */
+int ctqw_init_state(const ctqw_hamiltonian *h, const int32_t *sites_host, int32_t dtype,
+                    void *psi_dev, void *stream);
+
+/*
+ * Workspace bytes ctqw_propagate_taylor / ctqw_propagate_rk4 need for the
+ * given dtype and flags (method 0 = Taylor, 1 = RK4).  0 means none.
+ */
+int ctqw_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t method, uint32_t flags,
+                        size_t *bytes);
+
+/*
+ * Advance every realization by n_steps steps of the order-K truncated Taylor
+ * series of exp(-i H dt) (Sec. 2.3, Algorithm 3):
+ *   Phi^(0) = Psi, Phi^(j) = -(i dt / j) H Phi^(j-1), Psi(t+dt) = sum_{j<=K} Phi^(j).
+ * psi_dev (in/out) holds all states in `dtype`.  When obs_every > 0, the
+ * observables are sampled at steps 0, obs_every, 2 obs_every, ... <= n_steps
+ * (n_obs = n_steps / obs_every + 1 samples) into, when not NULL:
+ *   P_mean_dev [n_obs][p_width] FP64: per size group, (1/R_g) sum_r P_r(x)
+ *   norm_dev   [n_obs][R] FP64:  <Psi_r|Psi_r>
+ *   energy_dev [n_obs][R] FP64:  <Psi_r|H_r|Psi_r>
+ * The outputs are overwritten (zeroed on the stream first).  K in 1..30.
+ * Precision: CTQW_C128 propagates in FP64; CTQW_C64 propagates in FP32 and,
+ * on the fused path, carries the rounding error of every state update in a
+ * second FP32 word (compensated summation) kept on chip for the whole call.
+ * Path: m = 2 chains with N a multiple of 64 up to 256 in CTQW_C64 run the
+ * fused cluster kernel (every Taylor term of every step on chip); everything
+ * else, or CTQW_FLAG_PLAIN, runs one launch per Taylor term and needs the
+ * workspace of ctqw_workspace_size (3 states).  Asynchronous.
+ */
+int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
+                          int32_t K, int64_t n_steps, int32_t obs_every, double *P_mean_dev,
+                          double *norm_dev, double *energy_dev, uint32_t flags,
+                          void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/*
+ * Same as ctqw_propagate_taylor with the classical fourth-order Runge-Kutta
+ * step of Sec. 2.2 (Algorithm 2): K^(1) = -iH Psi, K^(2) = -iH(Psi + dt/2 K^(1)),
+ * K^(3) = -iH(Psi + dt/2 K^(2)), K^(4) = -iH(Psi + dt K^(3)),
+ * Psi(t+dt) = Psi + dt/6 (K^(1) + 2K^(2) + 2K^(3) + K^(4)).  The norm is not
+ * corrected.  Needs the workspace of ctqw_workspace_size(method = 1).
+ */
+int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
+                       int64_t n_steps, int32_t obs_every, double *P_mean_dev, double *norm_dev,
+                       double *energy_dev, uint32_t flags, void *workspace_dev,
+                       size_t workspace_bytes, void *stream);
+
+/*
+ * One sample of the observables of the current states (the diagonal of
+ * <rho>, Sec. 2): P_mean_dev [p_width], norm_dev [R], energy_dev [R] as in
+ * ctqw_propagate_taylor, and for m = 2 optionally P_joint_dev: per size group,
+ * (1/R_g) sum_r |psi_r(x1, x2)|^2 as [N_g][N_g] blocks back to back
+ * (sum_g N_g^2 doubles).  Any output may be NULL; outputs are overwritten.
+ */
+int ctqw_ensemble_observables(const ctqw_hamiltonian *h, int32_t dtype, const void *psi_dev,
+                              double *P_mean_dev, double *P_joint_dev, double *norm_dev,
+                              double *energy_dev, void *stream);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *ctqw_last_error(void);
+
+/* Library version string. */
+const char *ctqw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTQW_H */

@@ -35,7 +35,7 @@ __all__ = [
     "exact_evolution", "site_occupation", "pair_correlation", "norm", "energy",
     "propagate", "ensemble_run", "workload_parameters", "n_samples",
     "taylor_truncation_bound", "hamiltonian_norm_bound", "loss_and_adjoint_gradient",
-    "occupation_weights",
+    "occupation_weights", "noninteracting_evolution",
 ]
 
 
@@ -187,6 +187,28 @@ def exact_evolution(H, psi0, times):
     E, W = np.linalg.eigh(Hd)
     c = W.T @ psi0
     return np.stack([W @ (np.exp(-1j * E * t) * c) for t in times])
+
+
+def noninteracting_evolution(eps, J, periodic, m, psi0, times):
+    """exp(-i H t) psi0 for U = 0, where H is the Kronecker sum of H1.
+
+    Then exp(-iHt) = exp(-iH1 t) (x) ... (x) exp(-iH1 t), and exp(-iH1 t) comes
+    from Eq. (evolPsi) applied to the N x N one-particle matrix, so any state
+    of an N^m tile is propagated exactly by applying it along every axis.
+    Returns [len(times), N^m].
+    """
+    H1 = single_particle_hamiltonian(eps, J, periodic)
+    N = H1.shape[0]
+    E, W = np.linalg.eigh(H1)
+    psi0 = np.asarray(psi0, dtype=np.complex128).reshape((N,) * m)
+    out = []
+    for t in times:
+        G = (W * np.exp(-1j * E * t)) @ W.T
+        psi = psi0
+        for axis in range(m):
+            psi = np.moveaxis(np.tensordot(G, psi, axes=([1], [axis])), 0, axis)
+        out.append(psi.reshape(-1))
+    return np.stack(out)
 
 
 # ---------------------------------------------------------------- observables

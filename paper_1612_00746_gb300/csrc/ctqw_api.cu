@@ -1,0 +1,391 @@
+// C ABI of libctqw: argument checking, the realization table, and the host
+// loops that sequence the kernels of the propagation paths.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+
+#include "ctqw_internal.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+size_t elem_bytes(int dtype) { return dtype == CTQW_C64 ? sizeof(float2) : sizeof(double2); }
+
+int64_t n_samples(int64_t n_steps, int obs_every) {
+    return obs_every > 0 ? n_steps / obs_every + 1 : 0;
+}
+
+void free_device(ctqw_hamiltonian *h) {
+    void *ptrs[] = {h->eps32, h->J32, h->eps64, h->J64, h->sizes_d, h->group_of_d, h->par_off_d,
+                    h->st_off_d, h->group_off_d, h->joint_off_d, h->inv_count_d};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+template <typename T>
+int upload(T **dst, const std::vector<T> &src, cudaStream_t s) {
+    if (cudaMalloc((void **)dst, std::max<size_t>(1, src.size()) * sizeof(T)) != cudaSuccess) {
+        ctqw_set_error("cudaMalloc of %zu bytes failed", src.size() * sizeof(T));
+        return CTQW_ENOMEM;
+    }
+    if (!src.empty())
+        CTQW_CUDA_TRY(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T),
+                                      cudaMemcpyHostToDevice, s));
+    return CTQW_OK;
+}
+
+int zero_outputs(const ctqw_hamiltonian *h, int64_t n_obs, double *P_mean, double *norm,
+                 double *energy, cudaStream_t s) {
+    if (n_obs <= 0) return CTQW_OK;
+    if (P_mean) CTQW_CUDA_TRY(cudaMemsetAsync(P_mean, 0, sizeof(double) * n_obs * h->p_width, s));
+    if (norm) CTQW_CUDA_TRY(cudaMemsetAsync(norm, 0, sizeof(double) * n_obs * h->R, s));
+    if (energy) CTQW_CUDA_TRY(cudaMemsetAsync(energy, 0, sizeof(double) * n_obs * h->R, s));
+    return CTQW_OK;
+}
+
+int check_common(const ctqw_hamiltonian *h, int dtype, const void *psi, double dt,
+                 int64_t n_steps, int obs_every) {
+    if (!h) { ctqw_set_error("null handle"); return CTQW_EINVAL; }
+    if (dtype != CTQW_C64 && dtype != CTQW_C128) { ctqw_set_error("dtype %d", dtype); return CTQW_EINVAL; }
+    if (!psi) { ctqw_set_error("null psi"); return CTQW_EINVAL; }
+    if (!std::isfinite(dt) || dt == 0.0) { ctqw_set_error("dt must be finite and nonzero"); return CTQW_EINVAL; }
+    if (n_steps < 0) { ctqw_set_error("n_steps < 0"); return CTQW_EINVAL; }
+    if (obs_every < 0) { ctqw_set_error("obs_every < 0"); return CTQW_EINVAL; }
+    return CTQW_OK;
+}
+
+#define CTQW_TRY(expr)              \
+    do {                            \
+        int _st = (expr);           \
+        if (_st != CTQW_OK) return _st; \
+    } while (0)
+
+}  // namespace
+
+void ctqw_set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int ctqw_cuda_fail(cudaError_t e, const char *what) {
+    ctqw_set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? CTQW_ENOMEM : CTQW_ECUDA;
+}
+
+extern "C" {
+
+const char *ctqw_last_error(void) { return g_err; }
+
+const char *ctqw_version(void) { return "ctqw-gb300 0.1 (sm_103a)"; }
+
+int ctqw_build_hamiltonian(const ctqw_lattice_desc *d, void *stream, ctqw_hamiltonian **out) {
+    if (!d || !out) { ctqw_set_error("null desc/out"); return CTQW_EINVAL; }
+    *out = nullptr;
+    if (d->n_particles != 2 && d->n_particles != 3) {
+        ctqw_set_error("n_particles must be 2 or 3 (got %d)", d->n_particles);
+        return CTQW_EINVAL;
+    }
+    if (d->statistics < 0 || d->statistics > 2) { ctqw_set_error("statistics %d", d->statistics); return CTQW_EINVAL; }
+    if (d->n_realizations < 1 || d->n_realizations > 65535) {
+        ctqw_set_error("n_realizations must be in 1..65535 (got %d)", d->n_realizations);
+        return CTQW_EINVAL;
+    }
+    if (!d->u_eps_host || !d->u_J_host) { ctqw_set_error("null uniform draws"); return CTQW_EINVAL; }
+    if (!std::isfinite(d->J0) || !std::isfinite(d->U) || !std::isfinite(d->eps_halfwidth) ||
+        !std::isfinite(d->J_halfwidth)) {
+        ctqw_set_error("non-finite lattice parameter");
+        return CTQW_EINVAL;
+    }
+    auto *h = new ctqw_hamiltonian();
+    h->m = d->n_particles;
+    h->statistics = d->statistics;
+    h->periodic = d->periodic ? 1 : 0;
+    h->R = d->n_realizations;
+    h->round_to_f32 = d->round_to_f32 ? 1 : 0;
+    h->J0 = d->J0;
+    h->U = d->U;
+    const int nmax_allowed = h->m == 2 ? 65536 : 2048;
+    h->sizes.resize(h->R);
+    for (int r = 0; r < h->R; ++r) {
+        int n = d->n_sites ? d->n_sites[r] : d->n_sites_uniform;
+        if (n < 2 || n > nmax_allowed) {
+            ctqw_set_error("realization %d: N=%d outside 2..%d", r, n, nmax_allowed);
+            delete h;
+            return CTQW_EINVAL;
+        }
+        h->sizes[r] = n;
+    }
+    h->Nmax = *std::max_element(h->sizes.begin(), h->sizes.end());
+    h->uniform = std::all_of(h->sizes.begin(), h->sizes.end(), [&](int n) { return n == h->Nmax; });
+    h->par_off.assign(h->R + 1, 0);
+    h->st_off.assign(h->R + 1, 0);
+    for (int r = 0; r < h->R; ++r) {
+        int64_t D = 1;
+        for (int j = 0; j < h->m; ++j) D *= h->sizes[r];
+        h->par_off[r + 1] = h->par_off[r] + h->sizes[r];
+        h->st_off[r + 1] = h->st_off[r] + D;
+    }
+    h->total_par = h->par_off[h->R];
+    h->total_amp = h->st_off[h->R];
+    if (h->total_amp >= (int64_t(1) << 40)) {
+        ctqw_set_error("total amplitudes %lld too large", (long long)h->total_amp);
+        delete h;
+        return CTQW_EINVAL;
+    }
+    std::map<int, int> gidx;
+    for (int n : h->sizes) gidx[n] = 0;
+    int G = 0;
+    for (auto &kv : gidx) {
+        kv.second = G++;
+        h->group_N.push_back(kv.first);
+    }
+    h->group_count.assign(G, 0);
+    h->group_of.resize(h->R);
+    for (int r = 0; r < h->R; ++r) {
+        h->group_of[r] = gidx[h->sizes[r]];
+        h->group_count[h->group_of[r]]++;
+    }
+    h->group_off.assign(G + 1, 0);
+    h->joint_off.assign(G + 1, 0);
+    std::vector<double> inv(G);
+    for (int g = 0; g < G; ++g) {
+        h->group_off[g + 1] = h->group_off[g] + h->group_N[g];
+        h->joint_off[g + 1] = h->joint_off[g] + (int64_t)h->group_N[g] * h->group_N[g];
+        inv[g] = 1.0 / h->group_count[g];
+    }
+    h->p_width = h->group_off[G];
+    h->joint_width = h->joint_off[G];
+
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = CTQW_OK;
+    double *u_eps_d = nullptr, *u_J_d = nullptr, *em_d = nullptr, *jm_d = nullptr;
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(s);
+        for (void *p : {(void *)u_eps_d, (void *)u_J_d, (void *)em_d, (void *)jm_d})
+            if (p) cudaFree(p);
+        free_device(h);
+        delete h;
+        return code;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) { ctqw_set_error("no CUDA device"); return fail(CTQW_ECUDA); }
+    const size_t pb = sizeof(double) * h->total_par;
+    if (cudaMalloc(&h->eps32, sizeof(float) * h->total_par) != cudaSuccess ||
+        cudaMalloc(&h->J32, sizeof(float) * h->total_par) != cudaSuccess ||
+        cudaMalloc(&h->eps64, pb) != cudaSuccess || cudaMalloc(&h->J64, pb) != cudaSuccess ||
+        cudaMalloc(&u_eps_d, pb) != cudaSuccess || cudaMalloc(&u_J_d, pb) != cudaSuccess) {
+        ctqw_set_error("cudaMalloc of the parameter arrays failed");
+        return fail(CTQW_ENOMEM);
+    }
+    if ((st = upload(&h->sizes_d, h->sizes, s)) || (st = upload(&h->par_off_d, h->par_off, s)) ||
+        (st = upload(&h->st_off_d, h->st_off, s)) || (st = upload(&h->group_of_d, h->group_of, s)) ||
+        (st = upload(&h->group_off_d, h->group_off, s)) ||
+        (st = upload(&h->joint_off_d, h->joint_off, s)) || (st = upload(&h->inv_count_d, inv, s)))
+        return fail(st);
+    if (cudaMemcpyAsync(u_eps_d, d->u_eps_host, pb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(u_J_d, d->u_J_host, pb, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        ctqw_set_error("copy of the uniform draws failed");
+        return fail(CTQW_ECUDA);
+    }
+    if (d->eps_mean) {
+        if (cudaMalloc(&em_d, sizeof(double) * h->Nmax) != cudaSuccess) return fail(CTQW_ENOMEM);
+        if (cudaMemcpyAsync(em_d, d->eps_mean, sizeof(double) * h->Nmax, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(CTQW_ECUDA);
+    }
+    if (d->J_mean) {
+        if (cudaMalloc(&jm_d, sizeof(double) * h->Nmax) != cudaSuccess) return fail(CTQW_ENOMEM);
+        if (cudaMemcpyAsync(jm_d, d->J_mean, sizeof(double) * h->Nmax, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(CTQW_ECUDA);
+    }
+    if ((st = launch_build_params(h, u_eps_d, u_J_d, em_d, jm_d, d->eps_halfwidth, d->J_halfwidth,
+                                  d->J0, s)))
+        return fail(st);
+    cudaError_t e = cudaStreamSynchronize(s);
+    for (void *p : {(void *)u_eps_d, (void *)u_J_d, (void *)em_d, (void *)jm_d})
+        if (p) cudaFree(p);
+    u_eps_d = u_J_d = em_d = jm_d = nullptr;
+    if (e != cudaSuccess) {
+        ctqw_cuda_fail(e, "parameter build");
+        free_device(h);
+        delete h;
+        return CTQW_ECUDA;
+    }
+    *out = h;
+    return CTQW_OK;
+}
+
+int ctqw_destroy_hamiltonian(ctqw_hamiltonian *h) {
+    if (!h) return CTQW_OK;
+    cudaDeviceSynchronize();
+    free_device(h);
+    delete h;
+    return CTQW_OK;
+}
+
+int ctqw_get_params(const ctqw_hamiltonian *h, double *eps_host, double *J_host) {
+    if (!h) { ctqw_set_error("null handle"); return CTQW_EINVAL; }
+    CTQW_CUDA_TRY(cudaDeviceSynchronize());
+    if (eps_host)
+        CTQW_CUDA_TRY(cudaMemcpy(eps_host, h->eps64, sizeof(double) * h->total_par, cudaMemcpyDeviceToHost));
+    if (J_host)
+        CTQW_CUDA_TRY(cudaMemcpy(J_host, h->J64, sizeof(double) * h->total_par, cudaMemcpyDeviceToHost));
+    return CTQW_OK;
+}
+
+int ctqw_state_size(const ctqw_hamiltonian *h, int64_t *amplitudes_total, int64_t *st_off_host) {
+    if (!h) { ctqw_set_error("null handle"); return CTQW_EINVAL; }
+    if (amplitudes_total) *amplitudes_total = h->total_amp;
+    if (st_off_host) std::copy(h->st_off.begin(), h->st_off.end(), st_off_host);
+    return CTQW_OK;
+}
+
+int ctqw_output_layout(const ctqw_hamiltonian *h, int64_t *p_width, int32_t *n_groups,
+                       int32_t *group_sizes_host, int32_t *group_count_host) {
+    if (!h) { ctqw_set_error("null handle"); return CTQW_EINVAL; }
+    if (p_width) *p_width = h->p_width;
+    if (n_groups) *n_groups = (int32_t)h->group_N.size();
+    if (group_sizes_host) std::copy(h->group_N.begin(), h->group_N.end(), group_sizes_host);
+    if (group_count_host) std::copy(h->group_count.begin(), h->group_count.end(), group_count_host);
+    return CTQW_OK;
+}
+
+int ctqw_init_state(const ctqw_hamiltonian *h, const int32_t *sites_host, int32_t dtype,
+                    void *psi_dev, void *stream) {
+    if (!h || !sites_host || !psi_dev) { ctqw_set_error("null argument"); return CTQW_EINVAL; }
+    if (dtype != CTQW_C64 && dtype != CTQW_C128) { ctqw_set_error("dtype %d", dtype); return CTQW_EINVAL; }
+    for (int r = 0; r < h->R; ++r) {
+        for (int j = 0; j < h->m; ++j) {
+            int x = sites_host[r * h->m + j];
+            if (x < 0 || x >= h->sizes[r]) {
+                ctqw_set_error("realization %d: site %d outside 0..%d", r, x, h->sizes[r] - 1);
+                return CTQW_EINVAL;
+            }
+            if (h->statistics == CTQW_FERMIONS)
+                for (int l = 0; l < j; ++l)
+                    if (sites_host[r * h->m + l] == x) {
+                        ctqw_set_error("realization %d: fermions on the same site %d", r, x);
+                        return CTQW_EINVAL;
+                    }
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t *sites_d = nullptr;
+    const size_t bytes = sizeof(int32_t) * h->R * h->m;
+    CTQW_CUDA_TRY(cudaMallocAsync((void **)&sites_d, bytes, s));
+    CTQW_CUDA_TRY(cudaMemcpyAsync(sites_d, sites_host, bytes, cudaMemcpyHostToDevice, s));
+    int st = launch_init_state(h, sites_d, dtype, psi_dev, s);
+    cudaFreeAsync(sites_d, s);
+    return st;
+}
+
+int ctqw_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t method, uint32_t flags,
+                        size_t *bytes) {
+    if (!h || !bytes) { ctqw_set_error("null argument"); return CTQW_EINVAL; }
+    if (dtype != CTQW_C64 && dtype != CTQW_C128) { ctqw_set_error("dtype %d", dtype); return CTQW_EINVAL; }
+    const bool fused = method == 0 && !(flags & CTQW_FLAG_PLAIN) && fused_taylor_supported(h, dtype);
+    *bytes = fused ? 0 : 3 * (size_t)h->total_amp * elem_bytes(dtype);
+    return CTQW_OK;
+}
+
+int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
+                          int32_t K, int64_t n_steps, int32_t obs_every, double *P_mean_dev,
+                          double *norm_dev, double *energy_dev, uint32_t flags,
+                          void *workspace_dev, size_t workspace_bytes, void *stream) {
+    CTQW_TRY(check_common(h, dtype, psi_dev, dt, n_steps, obs_every));
+    if (K < 1 || K > 30) { ctqw_set_error("K must be in 1..30 (got %d)", K); return CTQW_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n_obs = n_samples(n_steps, obs_every);
+    const bool fused = !(flags & CTQW_FLAG_PLAIN) && fused_taylor_supported(h, dtype);
+    if (!fused) {
+        const size_t need = 3 * (size_t)h->total_amp * elem_bytes(dtype);
+        if (!workspace_dev || workspace_bytes < need) {
+            ctqw_set_error("plain path needs a workspace of %zu bytes (got %zu)", need, workspace_bytes);
+            return CTQW_EINVAL;
+        }
+    }
+    CTQW_TRY(zero_outputs(h, n_obs, P_mean_dev, norm_dev, energy_dev, s));
+    if (fused)
+        return launch_taylor_fused(h, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
+                                   energy_dev, (flags & CTQW_FLAG_NO_COMPENSATION) ? 0 : 1, 0, s);
+
+    const size_t sb = (size_t)h->total_amp * elem_bytes(dtype);
+    char *ws = (char *)workspace_dev;
+    void *cur = psi_dev, *acc = ws, *phi1 = ws + sb, *phi2 = ws + 2 * sb;
+    int64_t obs = 0;
+    for (int64_t step = 0; step <= n_steps; ++step) {
+        if (obs_every > 0 && step % obs_every == 0) {
+            CTQW_TRY(launch_observables(h, dtype, cur, P_mean_dev ? P_mean_dev + obs * h->p_width : nullptr,
+                                        nullptr, norm_dev ? norm_dev + obs * h->R : nullptr,
+                                        energy_dev ? energy_dev + obs * h->R : nullptr, s));
+            ++obs;
+        }
+        if (step == n_steps) break;
+        const void *in = cur;
+        void *out = phi1;
+        for (int j = 1; j <= K; ++j) {
+            CTQW_TRY(launch_taylor_term(h, dtype, in, out, cur, acc, dt / j, j == 1, s));
+            in = out;
+            out = (out == phi1) ? phi2 : phi1;
+        }
+        std::swap(cur, acc);
+    }
+    if (cur != psi_dev) CTQW_CUDA_TRY(cudaMemcpyAsync(psi_dev, cur, sb, cudaMemcpyDeviceToDevice, s));
+    return CTQW_OK;
+}
+
+int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
+                       int64_t n_steps, int32_t obs_every, double *P_mean_dev, double *norm_dev,
+                       double *energy_dev, uint32_t flags, void *workspace_dev,
+                       size_t workspace_bytes, void *stream) {
+    (void)flags;
+    CTQW_TRY(check_common(h, dtype, psi_dev, dt, n_steps, obs_every));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t sb = (size_t)h->total_amp * elem_bytes(dtype);
+    if (!workspace_dev || workspace_bytes < 3 * sb) {
+        ctqw_set_error("RK4 needs a workspace of %zu bytes (got %zu)", 3 * sb, workspace_bytes);
+        return CTQW_EINVAL;
+    }
+    const int64_t n_obs = n_samples(n_steps, obs_every);
+    CTQW_TRY(zero_outputs(h, n_obs, P_mean_dev, norm_dev, energy_dev, s));
+    char *ws = (char *)workspace_dev;
+    void *cur = psi_dev, *acc = ws, *t1 = ws + sb, *t2 = ws + 2 * sb;
+    int64_t obs = 0;
+    for (int64_t step = 0; step <= n_steps; ++step) {
+        if (obs_every > 0 && step % obs_every == 0) {
+            CTQW_TRY(launch_observables(h, dtype, cur, P_mean_dev ? P_mean_dev + obs * h->p_width : nullptr,
+                                        nullptr, norm_dev ? norm_dev + obs * h->R : nullptr,
+                                        energy_dev ? energy_dev + obs * h->R : nullptr, s));
+            ++obs;
+        }
+        if (step == n_steps) break;
+        // K1 = -iH psi: next = psi + dt/2 K1, acc = psi + dt/6 K1
+        CTQW_TRY(launch_rk4_stage(h, dtype, cur, t1, cur, acc, 0.5 * dt, dt / 6.0, 1, s));
+        // K2 = -iH(psi + dt/2 K1): next = psi + dt/2 K2, acc += dt/3 K2
+        CTQW_TRY(launch_rk4_stage(h, dtype, t1, t2, cur, acc, 0.5 * dt, dt / 3.0, 0, s));
+        // K3 = -iH(psi + dt/2 K2): next = psi + dt K3, acc += dt/3 K3
+        CTQW_TRY(launch_rk4_stage(h, dtype, t2, t1, cur, acc, dt, dt / 3.0, 0, s));
+        // K4 = -iH(psi + dt K3): acc += dt/6 K4
+        CTQW_TRY(launch_rk4_stage(h, dtype, t1, nullptr, cur, acc, 0.0, dt / 6.0, 0, s));
+        std::swap(cur, acc);
+    }
+    if (cur != psi_dev) CTQW_CUDA_TRY(cudaMemcpyAsync(psi_dev, cur, sb, cudaMemcpyDeviceToDevice, s));
+    return CTQW_OK;
+}
+
+int ctqw_ensemble_observables(const ctqw_hamiltonian *h, int32_t dtype, const void *psi_dev,
+                              double *P_mean_dev, double *P_joint_dev, double *norm_dev,
+                              double *energy_dev, void *stream) {
+    if (!h || !psi_dev) { ctqw_set_error("null argument"); return CTQW_EINVAL; }
+    if (dtype != CTQW_C64 && dtype != CTQW_C128) { ctqw_set_error("dtype %d", dtype); return CTQW_EINVAL; }
+    if (P_joint_dev && h->m != 2) { ctqw_set_error("P_joint needs m = 2"); return CTQW_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    CTQW_TRY(zero_outputs(h, 1, P_mean_dev, norm_dev, energy_dev, s));
+    if (P_joint_dev) CTQW_CUDA_TRY(cudaMemsetAsync(P_joint_dev, 0, sizeof(double) * h->joint_width, s));
+    return launch_observables(h, dtype, psi_dev, P_mean_dev, P_joint_dev, norm_dev, energy_dev, s);
+}
+
+}  // extern "C"

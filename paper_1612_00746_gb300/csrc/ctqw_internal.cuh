@@ -1,0 +1,104 @@
+// Internal declarations shared by the translation units of libctqw.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ctqw.h"
+
+// Library-owned description of all realizations (opaque to callers).
+struct ctqw_hamiltonian {
+    int m = 0, statistics = 0, periodic = 0, R = 0, round_to_f32 = 1;
+    double J0 = 1.0, U = 0.0;
+    int Nmax = 0;
+    bool uniform = true;
+    int device = 0;
+    std::vector<int32_t> sizes;                 // N_r
+    std::vector<int64_t> par_off;               // [R+1] offsets of eps/J (sum N)
+    std::vector<int64_t> st_off;                // [R+1] amplitude offsets (sum N^m)
+    std::vector<int32_t> group_of;              // [R] size group of each realization
+    std::vector<int32_t> group_N, group_count;  // [G]
+    std::vector<int64_t> group_off;             // [G+1] offsets in a P_mean row
+    std::vector<int64_t> joint_off;             // [G+1] offsets of the m=2 pair blocks
+    int64_t total_amp = 0, total_par = 0, p_width = 0, joint_width = 0;
+    // device arrays
+    float *eps32 = nullptr, *J32 = nullptr;
+    double *eps64 = nullptr, *J64 = nullptr;
+    int32_t *sizes_d = nullptr, *group_of_d = nullptr;
+    int64_t *par_off_d = nullptr, *st_off_d = nullptr, *group_off_d = nullptr,
+            *joint_off_d = nullptr;
+    double *inv_count_d = nullptr;  // [G] 1 / R_g
+};
+
+// Per-launch view of the realization table (passed by value to kernels).
+struct RealTable {
+    const int32_t *N;
+    const int64_t *par_off;
+    const int64_t *st_off;
+    const int32_t *group_of;
+    const int64_t *group_off;
+    const int64_t *joint_off;
+    const double *inv_count;
+    int R;
+    int m;
+    int periodic;
+    double U;
+};
+
+inline RealTable real_table(const ctqw_hamiltonian *h) {
+    RealTable t;
+    t.N = h->sizes_d;
+    t.par_off = h->par_off_d;
+    t.st_off = h->st_off_d;
+    t.group_of = h->group_of_d;
+    t.group_off = h->group_off_d;
+    t.joint_off = h->joint_off_d;
+    t.inv_count = h->inv_count_d;
+    t.R = h->R;
+    t.m = h->m;
+    t.periodic = h->periodic;
+    t.U = h->U;
+    return t;
+}
+
+// Error reporting (thread-local message, see ctqw_last_error).
+void ctqw_set_error(const char *fmt, ...);
+int ctqw_cuda_fail(cudaError_t e, const char *what);
+
+#define CTQW_CUDA_TRY(call)                                  \
+    do {                                                     \
+        cudaError_t _e = (call);                             \
+        if (_e != cudaSuccess) return ctqw_cuda_fail(_e, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------- launchers
+// Parameter build (a1): eps/J of every realization from the uniform draws.
+int launch_build_params(const ctqw_hamiltonian *h, const double *u_eps_d, const double *u_J_d,
+                        const double *eps_mean_d, const double *J_mean_d, double eps_hw,
+                        double J_hw, double J0, cudaStream_t s);
+
+// Initial state (a2).  sites_d: [R][m] int32 on the device.
+int launch_init_state(const ctqw_hamiltonian *h, const int32_t *sites_d, int dtype, void *psi,
+                      cudaStream_t s);
+
+// Per-term Taylor launch (a3, plain path): out = -(i dt/j) H in; acc (= psi if first) += out.
+int launch_taylor_term(const ctqw_hamiltonian *h, int dtype, const void *in, void *out,
+                       const void *psi, void *acc, double coef, int first, cudaStream_t s);
+
+// RK4 stage (a4): k = -i H in; next = psi + a k (if next); acc (= psi if first) += b k.
+int launch_rk4_stage(const ctqw_hamiltonian *h, int dtype, const void *in, void *next,
+                     const void *psi, void *acc, double a, double b, int first, cudaStream_t s);
+
+// Observables (a5, a6, a6b) of one sample: adds into P_mean [p_width], norm [R],
+// energy [R], P_joint [joint_width]; any may be null.  Outputs must be zeroed.
+int launch_observables(const ctqw_hamiltonian *h, int dtype, const void *psi, double *P_mean,
+                       double *P_joint, double *norm, double *energy, cudaStream_t s);
+
+// Fused cluster-resident Taylor propagation (m = 2, c64).
+bool fused_taylor_supported(const ctqw_hamiltonian *h, int dtype);
+int launch_taylor_fused(const ctqw_hamiltonian *h, void *psi, double dt, int K, int64_t n_steps,
+                        int obs_every, double *P_mean, double *norm, double *energy,
+                        int compensated, int cta_threads, cudaStream_t s);

@@ -1,0 +1,434 @@
+// Fused, cluster-resident Taylor propagation for two particles in complex FP32.
+//
+// Algorithm 3 (Sec. 2.3) applies the order-K polynomial of -i H dt to every
+// state once per step.  Here one thread-block cluster owns one realization
+// for the whole call: the N x N amplitude tile is split into row slabs, one
+// per CTA, and each warp keeps an 8-row x 64-column block of the current
+// Taylor term in registers.  Per term only the two edge rows of every warp
+// band (and the edge columns of every warp) move, through shared memory or
+// distributed shared memory of the neighbouring CTA, behind one cluster
+// barrier.  psi is read from HBM once and written once per call, so the
+// K * n_steps stencil applications run at on-chip speed.
+//
+// Arithmetic: the same order-K polynomial as Algorithm 3, evaluated in
+// Horner form with A = -i dt H (a real stencil applied to re and im alike):
+//   w_K = psi + (A/K) psi,  w_j = psi + (A/j) w_{j+1}  (j = K-1 .. 2),
+//   psi(t+dt) = psi + A w_2.
+// Forward summation psi + sum_j A^j psi / j! in FP32 drops every term below
+// half an ulp of the running sum (j >~ 7 at |A| ~ 0.2), which truncates the
+// series per amplitude and biases the norm by ~x^8/7! per step; Horner keeps
+// each term at its own scale.  The final increment A w_2 is added to the
+// state with its rounding error carried in a second FP32 word (lo, in shared
+// memory): hi + lo holds the state to ~2^-48 relative across all steps.
+#include <cooperative_groups.h>
+
+#include "ctqw_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr int RL = 8;        // rows per warp band
+constexpr int kMaxK = 30;
+
+struct FusedArgs {
+    const double *eps;       // exact parameter values (FP64 copies of the float32-rounded draws)
+    const double *J;
+    RealTable tab;
+    float2 *psi;
+    int N;
+    double dt;
+    float inv_dt;
+    int K;
+    long long n_steps;
+    int obs_every;
+    long long p_width;
+    double *P_mean, *norm, *energy;
+    int compensated;
+    float inv_j[kMaxK + 1];  // 1 / j
+};
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_barrier() {
+    __syncwarp();
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float2 ffma2(float a, float2 b, float2 c) {
+    return __ffma2_rn(make_float2(a, a), b, c);
+}
+
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// Modes of one stencil application y = (dt H) P on the warp's 8 x 64 block.
+enum { kHorner = 0, kFinal = 1, kEnergyOnly = 2 };
+
+// up/dn: the rows above and below the block; seam: the column beyond the
+// block's left edge (used by lane 31) or right edge (used by lane 0).
+//   kHorner:     P <- Q + (-i/j) y      (Q = psi of this step)
+//   kFinal:      P <- -i y              (the increment A w_2)
+//   kEnergyOnly: P unchanged
+// ENERGY adds sum Re(conj(P) y) (= dt <psi|H|psi> when P = psi) into e.
+template <int MODE, bool ENERGY>
+__device__ __forceinline__ void stencil_term(float2 (&P)[RL][2], const float2 (&Q)[RL][2],
+                                             const float (&V)[RL][2], const float (&nJr)[RL + 1],
+                                             const float (&nJc)[3], float2 up0, float2 up1,
+                                             float2 dn0, float2 dn1, const float2 *__restrict__ seam,
+                                             int lane, float inv_j, float &e) {
+    float2 prev0 = up0, prev1 = up1;
+    const int from_left = (lane + 31) & 31, from_right = (lane + 1) & 31;
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+        const float2 c0 = P[i][0], c1 = P[i][1];
+        const float2 n0 = (i < RL - 1) ? P[i + 1][0] : dn0;
+        const float2 n1 = (i < RL - 1) ? P[i + 1][1] : dn1;
+        const float2 sv = seam[i];
+        const float2 lft = shfl2(lane == 31 ? sv : c1, from_left);
+        const float2 rgt = shfl2(lane == 0 ? sv : c0, from_right);
+        float2 y0 = make_float2(V[i][0] * c0.x, V[i][0] * c0.y);
+        y0 = ffma2(nJr[i], prev0, y0);
+        y0 = ffma2(nJr[i + 1], n0, y0);
+        y0 = ffma2(nJc[0], lft, y0);
+        y0 = ffma2(nJc[1], c1, y0);
+        float2 y1 = make_float2(V[i][1] * c1.x, V[i][1] * c1.y);
+        y1 = ffma2(nJr[i], prev1, y1);
+        y1 = ffma2(nJr[i + 1], n1, y1);
+        y1 = ffma2(nJc[1], c0, y1);
+        y1 = ffma2(nJc[2], rgt, y1);
+        if (ENERGY) e += c0.x * y0.x + c0.y * y0.y + c1.x * y1.x + c1.y * y1.y;
+        if (MODE == kHorner) {
+            P[i][0] = make_float2(fmaf(inv_j, y0.y, Q[i][0].x), fmaf(-inv_j, y0.x, Q[i][0].y));
+            P[i][1] = make_float2(fmaf(inv_j, y1.y, Q[i][1].x), fmaf(-inv_j, y1.x, Q[i][1].y));
+        } else if (MODE == kFinal) {
+            P[i][0] = make_float2(y0.y, -y0.x);
+            P[i][1] = make_float2(y1.y, -y1.x);
+        }
+        prev0 = c0;
+        prev1 = c1;
+    }
+}
+
+// hi + lo + s rounded back into (hi, lo): TwoSum then FastTwoSum.
+__device__ __forceinline__ void compensated_add(float &hi, float &lo, float s) {
+    const float t = __fadd_rn(hi, s);
+    const float bb = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(s, bb));
+    const float l = __fadd_rn(err, lo);
+    const float h2 = __fadd_rn(t, l);
+    lo = __fsub_rn(l, __fsub_rn(h2, t));
+    hi = h2;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// N sites, BPC warp bands per CTA (compile-time so that every offset is an
+// immediate); WB = N/64 warps side by side per band, C = N/(8 BPC) CTAs per cluster.
+template <int N, int BPC, int MINB>
+__global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
+    taylor_fused_kernel(const __grid_constant__ FusedArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int WB = N / 64;
+    constexpr int SR = RL * BPC;      // slab rows of this CTA
+    constexpr int C = N / SR;         // CTAs per cluster
+    constexpr int W = WB * BPC;       // warps
+    static_assert(N % 64 == 0 && N % SR == 0 && C <= 16, "unsupported fused shape");
+    float2 *hi = reinterpret_cast<float2 *>(smem_raw);
+    float2 *lo = hi + SR * N;
+    float2 *edge = lo + SR * N;                  // [2][BPC][2][N]
+    float2 *seamb = edge + 2 * BPC * 2 * N;      // [2][W][2][RL]
+    float *pacc = reinterpret_cast<float *>(seamb + 2 * W * 2 * RL);   // [N]
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster_rank();
+    const int r = blockIdx.x / C;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int band = warp / WB, wc = warp % WB;
+    const int lrow0 = band * RL;                 // first local row of the warp band
+    const int x1_0 = rank * SR + lrow0;          // its global row
+    const int x2_0 = wc * 64 + 2 * lane;         // first of the lane's two columns
+
+    // ---- coefficients of dt H (rounded once from FP64)
+    const int64_t po = a.tab.par_off[r];
+    const double *eps = a.eps + po;
+    const double *J = a.J + po;
+    const double dt = a.dt, U = a.tab.U;
+    float V[RL][2], nJr[RL + 1], nJc[3];
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+        const int x1 = x1_0 + i;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int x2 = x2_0 + c;
+            V[i][c] = (float)(dt * (eps[x1] + eps[x2] + (x1 == x2 ? U : 0.0)));
+        }
+    }
+#pragma unroll
+    for (int i = 0; i <= RL; ++i) nJr[i] = (float)(-dt * J[(x1_0 + i - 1 + N) % N]);
+    nJc[0] = (float)(-dt * J[(x2_0 - 1 + N) % N]);
+    nJc[1] = (float)(-dt * J[x2_0]);
+    nJc[2] = (float)(-dt * J[x2_0 + 1]);
+
+    // ---- load the state (one HBM read per call)
+    float2 *gpsi = a.psi + a.tab.st_off[r];
+    float2 P[RL][2], Q[RL][2];   // current Horner iterate, psi of this step
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+        const float4 v = *reinterpret_cast<const float4 *>(gpsi + (size_t)(x1_0 + i) * N + x2_0);
+        P[i][0] = Q[i][0] = make_float2(v.x, v.y);
+        P[i][1] = Q[i][1] = make_float2(v.z, v.w);
+        *reinterpret_cast<float4 *>(hi + (lrow0 + i) * N + x2_0) = v;
+        *reinterpret_cast<float4 *>(lo + (lrow0 + i) * N + x2_0) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int x = threadIdx.x; x < N; x += blockDim.x) pacc[x] = 0.f;
+
+    const int rank_up = (rank + C - 1) % C, rank_dn = (rank + 1) % C;
+    float2 *edge_up = cluster.map_shared_rank(edge, rank_up);
+    float2 *edge_dn = cluster.map_shared_rank(edge, rank_dn);
+    const int w_left = band * WB + (wc + WB - 1) % WB;
+    const int w_right = band * WB + (wc + 1) % WB;
+    const int g = a.tab.group_of[r];
+    const double pscale = a.tab.inv_count[g] * 0.5;
+    double *Pg = a.P_mean ? a.P_mean + a.tab.group_off[g] : nullptr;
+
+    cluster_barrier();   // every CTA of the cluster is running and initialised
+
+    int parity = 0;
+    long long obs = 0;
+    const long long n_steps = a.n_steps;
+    for (long long step = 0; step <= n_steps; ++step) {
+        const bool sample = a.obs_every > 0 && (step % a.obs_every) == 0;
+        if (sample) {
+            // P(x) = (row sums + column sums) / 2, norm = sum |psi|^2 (state = hi)
+            float colp[2] = {0.f, 0.f}, nrm = 0.f;
+#pragma unroll
+            for (int i = 0; i < RL; ++i) {
+                const float p0 = P[i][0].x * P[i][0].x + P[i][0].y * P[i][0].y;
+                const float p1 = P[i][1].x * P[i][1].x + P[i][1].y * P[i][1].y;
+                colp[0] += p0;
+                colp[1] += p1;
+                const float rs = warp_sum(p0 + p1);
+                nrm += rs;
+                if (lane == 0 && Pg) atomicAdd(pacc + x1_0 + i, rs);
+            }
+            if (Pg) {
+                atomicAdd(pacc + x2_0, colp[0]);
+                atomicAdd(pacc + x2_0 + 1, colp[1]);
+            }
+            if (lane == 0 && a.norm) atomicAdd(a.norm + obs * a.tab.R + r, (double)nrm);
+            __syncthreads();
+            if (Pg) {
+                for (int x = threadIdx.x; x < N; x += blockDim.x) {
+                    const float v = pacc[x];
+                    if (v != 0.f) atomicAdd(Pg + obs * a.p_width + x, (double)v * pscale);
+                    pacc[x] = 0.f;
+                }
+            }
+        }
+        const bool last = step == n_steps;
+        if (last && !(sample && a.energy)) break;
+
+        const int K = a.K;
+        const int j_end = last ? K : 1;   // the energy-only pass is one stencil
+        for (int j = K; j >= j_end; --j) {
+            // publish this warp's edge rows and edge columns
+            float2 *eb = edge + parity * (BPC * 2 * N) + band * (2 * N);
+            *reinterpret_cast<float4 *>(eb + x2_0) = make_float4(P[0][0].x, P[0][0].y, P[0][1].x, P[0][1].y);
+            *reinterpret_cast<float4 *>(eb + N + x2_0) =
+                make_float4(P[RL - 1][0].x, P[RL - 1][0].y, P[RL - 1][1].x, P[RL - 1][1].y);
+            float2 *sb = seamb + parity * (W * 2 * RL) + warp * (2 * RL);
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < RL; ++i) sb[i] = P[i][0];
+            } else if (lane == 31) {
+#pragma unroll
+                for (int i = 0; i < RL; ++i) sb[RL + i] = P[i][1];
+            }
+            cluster_barrier();
+            // gather halos
+            const float2 *up_src = (band > 0)
+                ? edge + parity * (BPC * 2 * N) + (band - 1) * (2 * N) + N
+                : edge_up + parity * (BPC * 2 * N) + (BPC - 1) * (2 * N) + N;
+            const float2 *dn_src = (band < BPC - 1)
+                ? edge + parity * (BPC * 2 * N) + (band + 1) * (2 * N)
+                : edge_dn + parity * (BPC * 2 * N);
+            const float4 u4 = *reinterpret_cast<const float4 *>(up_src + x2_0);
+            const float4 d4 = *reinterpret_cast<const float4 *>(dn_src + x2_0);
+            // lane 0 reads the right neighbour warp's first column, the others
+            // the left neighbour warp's last column (only lane 31 uses it)
+            const float2 *seam = seamb + parity * (W * 2 * RL) +
+                                 (lane == 0 ? w_right * (2 * RL) : w_left * (2 * RL) + RL);
+            const float2 up0 = make_float2(u4.x, u4.y), up1 = make_float2(u4.z, u4.w);
+            const float2 dn0 = make_float2(d4.x, d4.y), dn1 = make_float2(d4.z, d4.w);
+            const float inv_j = a.inv_j[j];
+            const bool first = j == K;
+            const bool en = first && sample && a.energy;
+            float e = 0.f;
+            if (last) {
+                stencil_term<kEnergyOnly, true>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
+            } else if (j == 1) {
+                if (en)
+                    stencil_term<kFinal, true>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
+                else
+                    stencil_term<kFinal, false>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
+            } else if (en) {
+                stencil_term<kHorner, true>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
+            } else {
+                stencil_term<kHorner, false>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
+            }
+            if (en || last) {
+                const float es = warp_sum(e);
+                if (lane == 0) atomicAdd(a.energy + obs * a.tab.R + r, (double)es * (double)a.inv_dt);
+            }
+            parity ^= 1;
+        }
+        if (sample) ++obs;
+        if (last) break;
+
+        // psi(t+dt) = psi + A w_2 (now in P), with the rounding error carried in lo
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            float4 *hp = reinterpret_cast<float4 *>(hi + (lrow0 + i) * N + x2_0);
+            float4 *lp = reinterpret_cast<float4 *>(lo + (lrow0 + i) * N + x2_0);
+            float4 h4 = *hp, l4 = *lp;
+            if (a.compensated) {
+                compensated_add(h4.x, l4.x, P[i][0].x);
+                compensated_add(h4.y, l4.y, P[i][0].y);
+                compensated_add(h4.z, l4.z, P[i][1].x);
+                compensated_add(h4.w, l4.w, P[i][1].y);
+                *lp = l4;
+            } else {
+                h4.x += P[i][0].x;
+                h4.y += P[i][0].y;
+                h4.z += P[i][1].x;
+                h4.w += P[i][1].y;
+            }
+            *hp = h4;
+            P[i][0] = Q[i][0] = make_float2(h4.x, h4.y);
+            P[i][1] = Q[i][1] = make_float2(h4.z, h4.w);
+        }
+    }
+
+    // ---- write the state back (one HBM write per call)
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+        const float4 h4 = *reinterpret_cast<const float4 *>(hi + (lrow0 + i) * N + x2_0);
+        *reinterpret_cast<float4 *>(gpsi + (size_t)(x1_0 + i) * N + x2_0) = h4;
+    }
+    cluster_barrier();   // no CTA leaves while a neighbour may still read its shared memory
+}
+
+using FusedKernel = void (*)(FusedArgs);
+
+struct FusedShape {
+    int BPC, C, threads;
+    size_t smem;
+    FusedKernel kern;
+};
+
+template <int N, int BPC, int MINB>
+FusedShape make_shape() {
+    FusedShape f;
+    constexpr int WB = N / 64, SR = RL * BPC, W = WB * BPC;
+    f.BPC = BPC;
+    f.C = N / SR;
+    f.threads = 32 * W;
+    f.smem = sizeof(float2) * ((size_t)2 * SR * N + (size_t)2 * BPC * 2 * N + (size_t)2 * W * 2 * RL) +
+             sizeof(float) * (size_t)N;
+    f.kern = taylor_fused_kernel<N, BPC, MINB>;
+    return f;
+}
+
+// Shapes compiled in: (N, warp bands per CTA).  cta_threads picks among the
+// shapes of one N (0 = the default, listed first).
+bool fused_shape(int N, int cta_threads, FusedShape &f) {
+    FusedShape opts[2];
+    int n = 0;
+    switch (N) {
+        case 64: opts[n++] = make_shape<64, 8, 2>(); opts[n++] = make_shape<64, 4, 2>(); break;
+        case 128: opts[n++] = make_shape<128, 4, 2>(); opts[n++] = make_shape<128, 2, 2>(); break;
+        case 192: opts[n++] = make_shape<192, 2, 2>(); opts[n++] = make_shape<192, 4, 1>(); break;
+        case 256: opts[n++] = make_shape<256, 2, 2>(); opts[n++] = make_shape<256, 4, 1>(); break;
+        default: return false;
+    }
+    f = opts[0];
+    for (int i = 0; i < n; ++i)
+        if (opts[i].threads == cta_threads) f = opts[i];
+    return true;
+}
+
+}  // namespace
+
+bool fused_taylor_supported(const ctqw_hamiltonian *h, int dtype) {
+    FusedShape f;
+    return dtype == CTQW_C64 && h->m == 2 && h->uniform && fused_shape(h->Nmax, 0, f);
+}
+
+int launch_taylor_fused(const ctqw_hamiltonian *h, void *psi, double dt, int K, int64_t n_steps,
+                        int obs_every, double *P_mean, double *norm, double *energy,
+                        int compensated, int cta_threads, cudaStream_t s) {
+    FusedShape f;
+    if (!fused_shape(h->Nmax, cta_threads, f)) {
+        ctqw_set_error("fused path: unsupported size N=%d", h->Nmax);
+        return CTQW_EUNSUPPORTED;
+    }
+    if (K > kMaxK) {
+        ctqw_set_error("fused path: K=%d above %d", K, kMaxK);
+        return CTQW_EUNSUPPORTED;
+    }
+    FusedArgs a;
+    a.eps = h->eps64;
+    a.J = h->J64;
+    a.tab = real_table(h);
+    a.psi = (float2 *)psi;
+    a.N = h->Nmax;
+    a.dt = dt;
+    a.inv_dt = (float)(1.0 / dt);
+    a.K = K;
+    a.n_steps = n_steps;
+    a.obs_every = obs_every;
+    a.p_width = h->p_width;
+    a.P_mean = P_mean;
+    a.norm = norm;
+    a.energy = energy;
+    a.compensated = compensated;
+    a.inv_j[0] = 0.f;
+    for (int j = 1; j <= kMaxK; ++j) a.inv_j[j] = (float)(1.0 / j);
+    FusedKernel kern = f.kern;
+    CTQW_CUDA_TRY(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)f.smem));
+    if (f.C > 8)
+        CTQW_CUDA_TRY(cudaFuncSetAttribute((const void *)kern,
+                                           cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(h->R * f.C));
+    cfg.blockDim = dim3((unsigned)f.threads);
+    cfg.dynamicSmemBytes = f.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)f.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    CTQW_CUDA_TRY(cudaOccupancyMaxActiveClusters(&clusters, (const void *)kern, &cfg));
+    if (clusters < 1) {
+        ctqw_set_error("fused path: no cluster of %d CTAs x %d threads fits", f.C, f.threads);
+        return CTQW_EUNSUPPORTED;
+    }
+    CTQW_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
+    return CTQW_OK;
+}

@@ -1,0 +1,285 @@
+"""ctypes binding of libctqw (argument marshalling only).
+
+Every entry point of include/ctqw.h has a function of the same name here;
+all compute runs in the CUDA library.  PyTorch provides device memory and
+streams.  Loading fails loudly when libctqw.so is missing: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libctqw.so")
+
+CTQW_OK, CTQW_EINVAL, CTQW_ENOMEM, CTQW_ECUDA, CTQW_EUNSUPPORTED = 0, 1, 2, 3, 4
+DISTINGUISHABLE, BOSONS, FERMIONS = 0, 1, 2
+C64, C128 = 0, 1
+FLAG_PLAIN = 0x1
+FLAG_NO_COMPENSATION = 0x2
+TAYLOR, RK4 = 0, 1
+
+EXPORTED = (
+    "ctqw_build_hamiltonian", "ctqw_destroy_hamiltonian", "ctqw_get_params", "ctqw_state_size",
+    "ctqw_output_layout", "ctqw_init_state", "ctqw_workspace_size", "ctqw_propagate_taylor",
+    "ctqw_propagate_rk4", "ctqw_ensemble_observables", "ctqw_last_error", "ctqw_version",
+)
+
+
+class CtqwError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libctqw status {status}: {msg}")
+        self.status = status
+
+
+class LatticeDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_particles", ctypes.c_int32), ("statistics", ctypes.c_int32),
+        ("periodic", ctypes.c_int32), ("n_realizations", ctypes.c_int32),
+        ("n_sites", ctypes.POINTER(ctypes.c_int32)), ("n_sites_uniform", ctypes.c_int32),
+        ("round_to_f32", ctypes.c_int32), ("J0", ctypes.c_double), ("U", ctypes.c_double),
+        ("eps_halfwidth", ctypes.c_double), ("J_halfwidth", ctypes.c_double),
+        ("eps_mean", ctypes.POINTER(ctypes.c_double)), ("J_mean", ctypes.POINTER(ctypes.c_double)),
+        ("u_eps_host", ctypes.POINTER(ctypes.c_double)), ("u_J_host", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load libctqw.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64, dbl, u32, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double,
+                                  ctypes.c_uint32, ctypes.c_size_t)
+    pd = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "ctqw_build_hamiltonian": [ctypes.POINTER(LatticeDesc), vp, ctypes.POINTER(vp)],
+        "ctqw_destroy_hamiltonian": [vp],
+        "ctqw_get_params": [vp, pd, pd],
+        "ctqw_state_size": [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)],
+        "ctqw_output_layout": [vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                               ctypes.POINTER(i32)],
+        "ctqw_init_state": [vp, ctypes.POINTER(i32), i32, vp, vp],
+        "ctqw_workspace_size": [vp, i32, i32, u32, ctypes.POINTER(sz)],
+        "ctqw_propagate_taylor": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, u32, vp, sz, vp],
+        "ctqw_propagate_rk4": [vp, i32, vp, dbl, i64, i32, vp, vp, vp, u32, vp, sz, vp],
+        "ctqw_ensemble_observables": [vp, i32, vp, vp, vp, vp, vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.ctqw_last_error.restype = ctypes.c_char_p
+    lib.ctqw_last_error.argtypes = []
+    lib.ctqw_version.restype = ctypes.c_char_p
+    lib.ctqw_version.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _check(status: int) -> None:
+    if status != CTQW_OK:
+        raise CtqwError(status, load().ctqw_last_error().decode())
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def torch_dtype(dtype: int):
+    return torch.complex64 if dtype == C64 else torch.complex128
+
+
+class Hamiltonian:
+    """Handle of the stochastic Hamiltonians of all realizations (ctqw_build_hamiltonian)."""
+
+    def __init__(self, m: int, statistics: int, periodic: bool, sizes: Sequence[int], J0: float,
+                 U: float, eps_halfwidth: float, J_halfwidth: float, u_eps: np.ndarray,
+                 u_J: np.ndarray, eps_mean: Optional[np.ndarray] = None,
+                 J_mean: Optional[np.ndarray] = None, round_to_f32: bool = True, stream=None):
+        lib = load()
+        self.m = int(m)
+        self.statistics = int(statistics)
+        self.sizes = np.ascontiguousarray(np.asarray(sizes, dtype=np.int32))
+        self.R = len(self.sizes)
+        self._u_eps = np.ascontiguousarray(u_eps, dtype=np.float64)
+        self._u_J = np.ascontiguousarray(u_J, dtype=np.float64)
+        self._em = None if eps_mean is None else np.ascontiguousarray(eps_mean, dtype=np.float64)
+        self._jm = None if J_mean is None else np.ascontiguousarray(J_mean, dtype=np.float64)
+        d = LatticeDesc()
+        d.n_particles = self.m
+        d.statistics = self.statistics
+        d.periodic = 1 if periodic else 0
+        d.n_realizations = self.R
+        d.n_sites = self.sizes.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.n_sites_uniform = 0
+        d.round_to_f32 = 1 if round_to_f32 else 0
+        d.J0, d.U = float(J0), float(U)
+        d.eps_halfwidth, d.J_halfwidth = float(eps_halfwidth), float(J_halfwidth)
+        d.eps_mean = _dptr(self._em)
+        d.J_mean = _dptr(self._jm)
+        d.u_eps_host = _dptr(self._u_eps)
+        d.u_J_host = _dptr(self._u_J)
+        h = ctypes.c_void_p()
+        _check(lib.ctqw_build_hamiltonian(ctypes.byref(d), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        total = ctypes.c_int64()
+        st_off = np.zeros(self.R + 1, dtype=np.int64)
+        _check(lib.ctqw_state_size(h, ctypes.byref(total),
+                                   st_off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        self.total_amplitudes = int(total.value)
+        self.st_off = st_off
+        pw, ng = ctypes.c_int64(), ctypes.c_int32()
+        _check(lib.ctqw_output_layout(h, ctypes.byref(pw), ctypes.byref(ng), None, None))
+        gs = np.zeros(ng.value, dtype=np.int32)
+        gc = np.zeros(ng.value, dtype=np.int32)
+        _check(lib.ctqw_output_layout(h, None, None, gs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      gc.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        self.p_width = int(pw.value)
+        self.group_sizes = gs
+        self.group_count = gc
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ctqw_destroy_hamiltonian(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        """(eps, J) host float64 arrays [sum_r N_r] (ctqw_get_params)."""
+        n = int(self.sizes.sum())
+        eps = np.zeros(n)
+        J = np.zeros(n)
+        _check(load().ctqw_get_params(self._h, _dptr(eps), _dptr(J)))
+        return eps, J
+
+    def new_state(self, dtype: int, device="cuda") -> torch.Tensor:
+        return torch.zeros(self.total_amplitudes, dtype=torch_dtype(dtype), device=device)
+
+    def workspace(self, dtype: int, method: int = TAYLOR, flags: int = 0, device="cuda"):
+        b = ctypes.c_size_t()
+        _check(load().ctqw_workspace_size(self._h, dtype, method, flags, ctypes.byref(b)))
+        if b.value == 0:
+            return None
+        return torch.empty(b.value, dtype=torch.uint8, device=device)
+
+    def n_obs(self, n_steps: int, obs_every: int) -> int:
+        return n_steps // obs_every + 1 if obs_every > 0 else 0
+
+
+def ctqw_init_state(h: Hamiltonian, psi: torch.Tensor, sites, dtype: int, stream=None) -> None:
+    s = np.ascontiguousarray(np.asarray(sites, dtype=np.int32).reshape(h.R, h.m))
+    _check(load().ctqw_init_state(h.handle, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), dtype,
+                                  _ptr(psi), _stream(stream)))
+
+
+def _outputs(h: Hamiltonian, n_obs: int, want_P: bool, want_norm: bool, want_energy: bool, device):
+    P = torch.empty((n_obs, h.p_width), dtype=torch.float64, device=device) if want_P and n_obs else None
+    nr = torch.empty((n_obs, h.R), dtype=torch.float64, device=device) if want_norm and n_obs else None
+    en = torch.empty((n_obs, h.R), dtype=torch.float64, device=device) if want_energy and n_obs else None
+    return P, nr, en
+
+
+def ctqw_propagate_taylor(h: Hamiltonian, psi: torch.Tensor, dtype: int, dt: float, K: int,
+                          n_steps: int, obs_every: int = 0, P_mean=None, norm=None, energy=None,
+                          flags: int = 0, workspace: Optional[torch.Tensor] = None, stream=None):
+    ws_bytes = 0 if workspace is None else workspace.numel()
+    _check(load().ctqw_propagate_taylor(h.handle, dtype, _ptr(psi), float(dt), int(K), int(n_steps),
+                                        int(obs_every), _ptr(P_mean), _ptr(norm), _ptr(energy),
+                                        int(flags), _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def ctqw_propagate_rk4(h: Hamiltonian, psi: torch.Tensor, dtype: int, dt: float, n_steps: int,
+                       obs_every: int = 0, P_mean=None, norm=None, energy=None, flags: int = 0,
+                       workspace: Optional[torch.Tensor] = None, stream=None):
+    ws_bytes = 0 if workspace is None else workspace.numel()
+    _check(load().ctqw_propagate_rk4(h.handle, dtype, _ptr(psi), float(dt), int(n_steps),
+                                     int(obs_every), _ptr(P_mean), _ptr(norm), _ptr(energy),
+                                     int(flags), _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def ctqw_ensemble_observables(h: Hamiltonian, psi: torch.Tensor, dtype: int, P_mean=None,
+                              P_joint=None, norm=None, energy=None, stream=None):
+    _check(load().ctqw_ensemble_observables(h.handle, dtype, _ptr(psi), _ptr(P_mean), _ptr(P_joint),
+                                            _ptr(norm), _ptr(energy), _stream(stream)))
+
+
+def ctqw_version() -> str:
+    return load().ctqw_version().decode()
+
+
+# ------------------------------------------------------------------ workloads
+def build_for_workload(w, realizations=None, eps_mean=None, J_mean=None, round_to_f32=True,
+                       stream=None) -> Hamiltonian:
+    """Hamiltonian handle of (a subset of) a ctqw_workloads.Workload."""
+    import ctqw_workloads as cw
+
+    u_eps, u_J, sizes, _ = cw.packed_draws(w, realizations)
+    return Hamiltonian(w.m, w.statistics, w.periodic, sizes, w.J0, w.U, w.eps_halfwidth,
+                       w.J_halfwidth, u_eps, u_J, eps_mean, J_mean, round_to_f32, stream)
+
+
+def initial_sites(w, h: Hamiltonian) -> np.ndarray:
+    return np.array([w.initial_sites(int(n)) for n in h.sizes], dtype=np.int32)
+
+
+def run_workload(w, realizations=None, method: int = TAYLOR, dtype: Optional[int] = None,
+                 n_steps: Optional[int] = None, obs_every: Optional[int] = None,
+                 K: Optional[int] = None, flags: int = 0, device="cuda"):
+    """Build, initialise and propagate a workload; returns host results."""
+    dtype = w.dtype if dtype is None else dtype
+    n_steps = w.n_steps if n_steps is None else n_steps
+    obs_every = w.obs_every if obs_every is None else obs_every
+    K = w.K if K is None else K
+    h = build_for_workload(w, realizations)
+    psi = h.new_state(dtype, device)
+    ctqw_init_state(h, psi, initial_sites(w, h), dtype)
+    n_obs = h.n_obs(n_steps, obs_every)
+    P, nr, en = _outputs(h, n_obs, True, True, True, device)
+    ws = h.workspace(dtype, method, flags, device)
+    if method == TAYLOR:
+        ctqw_propagate_taylor(h, psi, dtype, w.dt, K, n_steps, obs_every, P, nr, en, flags, ws)
+    else:
+        ctqw_propagate_rk4(h, psi, dtype, w.dt, n_steps, obs_every, P, nr, en, flags, ws)
+    torch.cuda.synchronize()
+    out = {"psi": psi.cpu().numpy(), "st_off": h.st_off, "sizes": h.sizes,
+           "group_sizes": h.group_sizes, "p_width": h.p_width}
+    out["P_mean"] = P.cpu().numpy() if P is not None else None
+    out["norm"] = nr.cpu().numpy() if nr is not None else None
+    out["energy"] = en.cpu().numpy() if en is not None else None
+    h.close()
+    return out

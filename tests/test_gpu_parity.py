@@ -1,0 +1,252 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Sizes here are small enough for the oracle to finish in seconds while still
+spanning several warp blocks / CTAs and, for the plain kernels, a ragged tail.
+"""
+import numpy as np
+import pytest
+
+import ctqw_workloads as cw
+import oracle
+from gpu_helpers import TOL_FP32, TOL_FP64, TOL_NORM_DRIFT, oracle_params, per_realization_P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctqw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_00746_gb300 import build, ctqw as c
+
+    build.build()
+    c.load()
+    return c
+
+
+def _compare(got, ref, tolP, tol_norm, tol_energy):
+    dP = np.max(np.abs(got["P_mean"] - ref["P_mean"]))
+    dn = np.max(np.abs(got["norm"] - ref["norm"].T))
+    de = np.max(np.abs(got["energy"] - ref["energy"].T))
+    assert dP <= tolP, f"max|dP| = {dP:.3e} > {tolP:.1e}"
+    assert dn <= tol_norm, f"max|dnorm| = {dn:.3e}"
+    assert de <= tol_energy, f"max|dE| = {de:.3e}"
+    return dP, dn, de
+
+
+# ------------------------------------------------------------------ inputs
+@pytest.mark.parametrize("name,kw", [
+    ("bosons_small", {}),
+    ("ring3_small", {}),
+    ("fp64_plain_small", {}),
+    ("ragged_n128_1024", {"ragged_sizes": (6, 10, 64), "R": 7}),
+])
+def test_params_bit_exact(ctqw, name, kw):
+    w = cw.get(name).with_(**kw)
+    h = ctqw.build_for_workload(w)
+    eps, J = h.params()
+    ref = oracle_params(w)
+    off = 0
+    for r, (e_ref, j_ref) in enumerate(ref):
+        N = len(e_ref)
+        assert np.array_equal(eps[off:off + N], e_ref), r
+        assert np.array_equal(J[off:off + N], j_ref), r
+        off += N
+    h.close()
+
+
+def test_params_with_means_bit_exact(ctqw):
+    w = cw.get("adjoint_n512").with_(N=16, R=3)
+    rng = np.random.default_rng(0)
+    em = rng.uniform(-1, 1, 16)
+    jm = 1 + rng.uniform(-0.2, 0.2, 16)
+    h = ctqw.build_for_workload(w, eps_mean=em, J_mean=jm)
+    eps, J = h.params()
+    for r, (e_ref, j_ref) in enumerate(oracle_params(w, eps_mean=em, J_mean=jm[:15])):
+        assert np.array_equal(eps[16 * r:16 * r + 16], e_ref)
+        assert np.array_equal(J[16 * r:16 * r + 16], j_ref)
+    h.close()
+
+
+@pytest.mark.parametrize("m,stats,sites", [(2, 0, (3, 5)), (2, 1, (3, 5)), (2, 1, (4, 4)),
+                                           (2, 2, (1, 6)), (3, 0, (0, 2, 2)), (3, 1, (0, 2, 2)),
+                                           (3, 1, (1, 1, 1)), (3, 2, (0, 3, 5))])
+def test_initial_states(ctqw, m, stats, sites):
+    N = 7
+    w = cw.Workload(name="t", m=m, statistics=stats, periodic=False, N=N, R=2, J0=1, U=0,
+                    eps_halfwidth=0, J_halfwidth=0, sites=sites, dt=0.1, K=4, n_steps=1,
+                    obs_every=1, dtype=cw.C128)
+    h = ctqw.build_for_workload(w)
+    psi = h.new_state(cw.C128)
+    ctqw.ctqw_init_state(h, psi, ctqw.initial_sites(w, h), cw.C128)
+    got = psi.cpu().numpy()
+    ref = oracle.initial_state(N, m, sites, stats)
+    for r in range(2):
+        np.testing.assert_allclose(got[r * N ** m:(r + 1) * N ** m], ref, rtol=0, atol=1e-15)
+    h.close()
+
+
+def test_fermions_on_same_site_rejected(ctqw):
+    w = cw.get("bosons_small").with_(statistics=cw.FERMIONS, R=1)
+    h = ctqw.build_for_workload(w)
+    psi = h.new_state(cw.C128)
+    with pytest.raises(ctqw.CtqwError, match="same site"):
+        ctqw.ctqw_init_state(h, psi, [[3, 3]], cw.C128)
+    with pytest.raises(ctqw.CtqwError, match="outside"):
+        ctqw.ctqw_init_state(h, psi, [[3, 64]], cw.C128)
+    h.close()
+
+
+# ------------------------------------------------------------------ FP64 plain path
+def test_taylor_fp64_plain_two_particles(ctqw):
+    w = cw.get("fp64_plain_small")
+    got = ctqw.run_workload(w)
+    ref = oracle.ensemble_run(w)
+    _compare(got, ref, TOL_FP64, 1e-12, 1e-11)
+
+
+def test_taylor_fp64_three_bosons_ring(ctqw):
+    w = cw.get("ring3_small").with_(dtype=cw.C128)
+    got = ctqw.run_workload(w)
+    ref = oracle.ensemble_run(w)
+    _compare(got, ref, TOL_FP64, 1e-12, 1e-10)
+
+
+def test_taylor_fp64_ragged_sizes_grouped(ctqw):
+    w = cw.get("ragged_n128_1024").with_(ragged_sizes=(6, 10, 17), R=7, n_steps=60, obs_every=20,
+                                         dtype=cw.C128, K=10)
+    got = ctqw.run_workload(w)
+    ref = oracle.ensemble_run(w)
+    assert list(got["group_sizes"]) == ref["groups"]
+    _compare(got, ref, TOL_FP64, 1e-12, 1e-10)
+
+
+def test_rk4_fp64(ctqw):
+    w = cw.get("bosons_small").with_(R=2, n_steps=100, obs_every=25, dtype=cw.C128)
+    got = ctqw.run_workload(w, method=ctqw.RK4)
+    ref = oracle.ensemble_run(w, method="rk4")
+    _compare(got, ref, TOL_FP64, 1e-12, 1e-10)
+
+
+def test_rk4_equals_order4_taylor_on_gpu(ctqw):
+    w = cw.get("bosons_small").with_(R=2, n_steps=50, obs_every=50, dtype=cw.C128)
+    a = ctqw.run_workload(w, method=ctqw.RK4)
+    b = ctqw.run_workload(w, K=4, flags=ctqw.FLAG_PLAIN)
+    assert np.max(np.abs(a["psi"] - b["psi"])) < 1e-13
+
+
+@pytest.mark.parametrize("K", [1, 2, 5, 7])
+def test_fp64_plain_any_order(ctqw, K):
+    w = cw.get("bosons_small").with_(R=2, n_steps=30, obs_every=10, dtype=cw.C128, K=K)
+    got = ctqw.run_workload(w)
+    ref = oracle.ensemble_run(w)
+    _compare(got, ref, TOL_FP64, 1e-12, 1e-10)
+
+
+# ------------------------------------------------------------------ FP32 paths
+def test_fused_c64_bosons(ctqw):
+    w = cw.get("bosons_small")
+    got = ctqw.run_workload(w)
+    ref = oracle.ensemble_run(w)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
+    assert np.max(np.abs(got["norm"] - 1.0)) <= TOL_NORM_DRIFT
+
+
+@pytest.mark.parametrize("N,periodic,K", [(64, True, 16), (128, False, 16), (192, False, 13),
+                                          (256, False, 16), (256, True, 5)])
+def test_fused_c64_shapes(ctqw, N, periodic, K):
+    w = cw.get("bosons_n256_u2").with_(N=N, R=2, periodic=periodic, K=K, n_steps=24, obs_every=8,
+                                       sites=(N // 2 - 1, N // 2))
+    got = ctqw.run_workload(w)
+    ref = oracle.ensemble_run(w)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
+    P = per_realization_P(got["psi"], got["st_off"], got["sizes"], 2)
+    for r in range(2):
+        assert np.max(np.abs(P[r] - ref["P"][r][-1])) <= TOL_FP32
+
+
+def test_fused_c64_distinguishable_open(ctqw):
+    w = cw.get("fp64_plain_small").with_(dtype=cw.C64, n_steps=300, obs_every=30)
+    got = ctqw.run_workload(w)
+    ref = oracle.ensemble_run(w)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
+
+
+def test_plain_c64(ctqw):
+    w = cw.get("bosons_small").with_(n_steps=100, obs_every=25)
+    got = ctqw.run_workload(w, flags=ctqw.FLAG_PLAIN)
+    ref = oracle.ensemble_run(w)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
+
+
+def test_rk4_c64(ctqw):
+    w = cw.get("bosons_small").with_(R=2, n_steps=100, obs_every=25)
+    got = ctqw.run_workload(w, method=ctqw.RK4)
+    ref = oracle.ensemble_run(w, method="rk4")
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("dtype,flags", [(cw.C128, 1), (cw.C64, 0)])
+def test_zero_steps_samples_initial_state(ctqw, dtype, flags):
+    w = cw.get("bosons_small").with_(R=2, n_steps=0, obs_every=5)
+    got = ctqw.run_workload(w, dtype=dtype, flags=flags)
+    ref = oracle.ensemble_run(w)
+    assert got["P_mean"].shape == (1, w.N)
+    _compare(got, ref, 1e-7 if dtype == cw.C64 else 1e-15, 1e-7, 1e-5)
+
+
+def test_no_observables(ctqw):
+    w = cw.get("bosons_small").with_(R=2, n_steps=10, obs_every=0)
+    got = ctqw.run_workload(w)
+    assert got["P_mean"] is None
+    ref = oracle.ensemble_run(w.with_(obs_every=10))
+    P = per_realization_P(got["psi"], got["st_off"], got["sizes"], 2)
+    assert np.max(np.abs(P[0] - ref["P"][0][-1])) < TOL_FP32
+
+
+def test_two_site_lattice_and_single_realization(ctqw):
+    w = cw.Workload(name="tiny", m=2, statistics=cw.BOSONS, periodic=False, N=2, R=1, J0=0.9,
+                    U=2.3, eps_halfwidth=0.0, J_halfwidth=0.0, sites=(0, 0), dt=0.01, K=16,
+                    n_steps=310, obs_every=310, dtype=cw.C128)
+    got = ctqw.run_workload(w)
+    ref = oracle.ensemble_run(w)
+    _compare(got, ref, TOL_FP64, 1e-12, 1e-11)
+
+
+def test_ensemble_observables_pair_distribution(ctqw):
+    w = cw.get("ragged_n128_1024").with_(ragged_sizes=(5, 8), R=5, n_steps=20, obs_every=20,
+                                         dtype=cw.C128, K=10)
+    h = ctqw.build_for_workload(w)
+    psi = h.new_state(cw.C128)
+    ctqw.ctqw_init_state(h, psi, ctqw.initial_sites(w, h), cw.C128)
+    ws = h.workspace(cw.C128)
+    ctqw.ctqw_propagate_taylor(h, psi, cw.C128, w.dt, w.K, w.n_steps, 0, workspace=ws)
+    joint = torch.empty(int(sum(int(g) ** 2 for g in h.group_sizes)), dtype=torch.float64,
+                        device="cuda")
+    P = torch.empty(h.p_width, dtype=torch.float64, device="cuda")
+    ctqw.ctqw_ensemble_observables(h, psi, cw.C128, P_mean=P, P_joint=joint)
+    ref = oracle.ensemble_run(w)
+    off = 0
+    joint = joint.cpu().numpy()
+    for g in ref["groups"]:
+        members = [k for k in range(w.R) if ref["sizes"][k] == g]
+        expect = sum(oracle.pair_correlation(ref["psi"][k], g) for k in members) / len(members)
+        np.testing.assert_allclose(joint[off:off + g * g].reshape(g, g), expect, atol=1e-13)
+        off += g * g
+    np.testing.assert_allclose(P.cpu().numpy(), ref["P_mean"][-1], atol=1e-13)
+    h.close()
+
+
+def test_bad_arguments_rejected(ctqw):
+    w = cw.get("bosons_small").with_(R=1)
+    h = ctqw.build_for_workload(w)
+    psi = h.new_state(cw.C128)
+    with pytest.raises(ctqw.CtqwError, match="workspace"):
+        ctqw.ctqw_propagate_taylor(h, psi, cw.C128, 0.01, 4, 1, 0)
+    with pytest.raises(ctqw.CtqwError, match="K must be"):
+        ctqw.ctqw_propagate_taylor(h, psi, cw.C128, 0.01, 0, 1, 0, workspace=h.workspace(cw.C128))
+    with pytest.raises(ctqw.CtqwError, match="dt"):
+        ctqw.ctqw_propagate_taylor(h, psi, cw.C128, float("nan"), 4, 1, 0, workspace=h.workspace(cw.C128))
+    h.close()

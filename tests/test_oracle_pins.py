@@ -372,3 +372,20 @@ def test_adjoint_gradient_matches_eigenbasis_derivative():
         d1 = np.zeros((N, N)); d1[b, (b + 1) % N] -= 1; d1[(b + 1) % N, b] -= 1
         dH = O.many_particle_hamiltonian(d1, m, 0.0).toarray()
         assert abs(grad(dH) - gJ[0, b]) < 1e-10
+
+
+@pytest.mark.parametrize("m,periodic,stats", [(2, False, 0), (2, True, 1), (3, False, 1), (3, True, 2)])
+def test_noninteracting_evolution_matches_dense_exact_and_taylor(m, periodic, stats):
+    rng = np.random.default_rng(21 + m)
+    N = 5
+    eps, J = _rand_params(rng, N, periodic)
+    psi0 = O.initial_state(N, m, tuple(range(m)), stats)
+    H = O.many_particle_hamiltonian(O.single_particle_hamiltonian(eps, J, periodic), m, 0.0)
+    t = [0.0, 0.7, 3.3]
+    a = O.noninteracting_evolution(eps, J, periodic, m, psi0, t)
+    b = O.exact_evolution(H, psi0, t)
+    assert np.max(np.abs(a - b)) < 1e-13
+    psi = psi0.copy()
+    for _ in range(330):
+        psi = O.taylor_step(H, psi, 0.01, 14)
+    assert np.max(np.abs(a[2] - psi)) < 1e-12
