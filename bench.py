@@ -217,6 +217,10 @@ def run_ours(args):
     ctqw.load()
 
     w = cw.get(args.workload)
+    if args.realizations:
+        w = w.with_(R=args.realizations)
+    if args.n_steps:
+        w = w.with_(n_steps=args.n_steps)
     # cpu baseline first (spawned workers, before heavy GPU use), rank 0 at N=1 only
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -253,7 +257,8 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-        ctqw.ctqw_propagate_taylor(h, psi, dtype, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en, 0, ws)
+        ctqw.ctqw_propagate_taylor(h, psi, dtype, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en,
+                                   args.flags, ws)
         if record:
             e1.record(stream)
             prop_events.append((e0, e1))
@@ -299,21 +304,25 @@ def run_ours(args):
         h2 = ctqw.Hamiltonian(w.m, w.statistics, w.periodic, sizes, w.J0, w.U, w.eps_halfwidth,
                               w.J_halfwidth, ue_p.numpy(), uj_p.numpy())
         ctqw.ctqw_init_state(h2, psi, sites, dtype)
-        ctqw.ctqw_propagate_taylor(h2, psi, dtype, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en, 0, ws)
+        ctqw.ctqw_propagate_taylor(h2, psi, dtype, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en,
+                                   args.flags, ws)
         P_host.copy_(P, non_blocking=True)
         n_host.copy_(nr, non_blocking=True)
         e_host.copy_(en, non_blocking=True)
         torch.cuda.synchronize()
         h2.close()
 
-    e2e_steps = max(1, min(args.steps, 3))
-    e2e_step()
-    torch.cuda.synchronize()
-    te = time.perf_counter()
-    for _ in range(e2e_steps):
+    e2e = None
+    if not args.no_e2e:
+        e2e_steps = max(1, min(args.steps, 3))
         e2e_step()
-    e2e_s = max_over_ranks((time.perf_counter() - te) / e2e_steps, dev)
-    e2e_value = world * units_per_step / e2e_s
+        torch.cuda.synchronize()
+        te = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        e2e_s = max_over_ranks((time.perf_counter() - te) / e2e_steps, dev)
+        e2e = {"value": world * units_per_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
 
     # plain per-term FP64 path on a subset (the comparison path of the metric)
     fp64 = None
@@ -377,8 +386,7 @@ def run_ours(args):
                      "flops_per_site_update": flops_per_unit,
                      "peak_basis": "152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz (derived)",
                      "hbm_gbs_measured": peaks.get("hbm_gbs")},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+        "e2e": e2e,
         "cpu_baseline": cpu,
         "fp64_plain": fp64,
         "norm_drift": norm_drift,
@@ -403,6 +411,10 @@ def main(argv=None):
     ap.add_argument("--ref-steps", type=int, default=60, help="steps per realization per reference step")
     ap.add_argument("--fp64-realizations", type=int, default=16)
     ap.add_argument("--fp64-steps", type=int, default=100)
+    ap.add_argument("--realizations", type=int, default=0, help="override R (small profiling cases)")
+    ap.add_argument("--n-steps", type=int, default=0, help="override the workload's steps")
+    ap.add_argument("--flags", type=int, default=0, help="ctqw propagation flags (e.g. 4 = wide CTA)")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-plain", action="store_true")
     args = ap.parse_args(argv)

@@ -43,6 +43,7 @@ extern "C" {
 #define CTQW_ENOMEM 2          /* a device allocation failed                     */
 #define CTQW_ECUDA 3           /* a CUDA runtime call or kernel launch failed    */
 #define CTQW_EUNSUPPORTED 4    /* valid request the library does not implement  */
+#define CTQW_ETIMEOUT 6        /* a bounded wait inside a kernel gave up (see ctqw_check_status) */
 
 /* Particle statistics (initial-state symmetry). */
 #define CTQW_DISTINGUISHABLE 0
@@ -56,6 +57,14 @@ extern "C" {
 /* Propagation flags. */
 #define CTQW_FLAG_PLAIN 0x1            /* force the per-term path (one launch per Taylor term) */
 #define CTQW_FLAG_NO_COMPENSATION 0x2  /* c64 fused path: plain FP32 state update (no carried error term) */
+#define CTQW_FLAG_TEST_WAIT_TIMEOUT 0x8 /* failure-path test: the fused kernel first waits on an mbarrier that
+                                           nothing completes, gives up after 1 ms and flags the handle */
+/* Fused path tuning: CTQW_FUSED_SHAPE(k) selects the k-th compiled CTA/cluster
+ * shape for the lattice size (0 = default; 1 = more warps per CTA and fewer
+ * CTAs per cluster; 2 = default split with registers uncapped, one CTA per SM).
+ * An index with no compiled shape returns CTQW_EUNSUPPORTED. */
+#define CTQW_FUSED_SHAPE_SHIFT 8
+#define CTQW_FUSED_SHAPE(k) (((uint32_t)(k) & 0xFu) << CTQW_FUSED_SHAPE_SHIFT)
 
 typedef struct ctqw_hamiltonian ctqw_hamiltonian;   /* opaque, owned by the library */
 
@@ -158,7 +167,8 @@ int ctqw_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t method
  * on the fused path, carries the rounding error of every state update in a
  * second FP32 word (compensated summation) kept on chip for the whole call.
  * Path: m = 2 chains with N a multiple of 64 up to 256 in CTQW_C64 run the
- * fused cluster kernel (every Taylor term of every step on chip); everything
+ * fused cluster kernel (every Taylor term of every step on chip; halo rows move between the CTAs
+ * of a cluster point to point, see ctqw_check_status); everything
  * else, or CTQW_FLAG_PLAIN, runs one launch per Taylor term and needs the
  * workspace of ctqw_workspace_size (3 states).  Asynchronous.
  */
@@ -189,6 +199,15 @@ int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, 
 int ctqw_ensemble_observables(const ctqw_hamiltonian *h, int32_t dtype, const void *psi_dev,
                               double *P_mean_dev, double *P_joint_dev, double *norm_dev,
                               double *energy_dev, void *stream);
+
+/*
+ * Synchronize `stream` and report whether a kernel of an earlier call on this
+ * handle gave up a bounded wait (the fused kernel waits for halo rows from
+ * its neighbour CTAs with a 2 s limit; it never spins unbounded).  Returns
+ * CTQW_ETIMEOUT once per such event (the flag is cleared), CTQW_OK otherwise.
+ * The results of a call that timed out are invalid.
+ */
+int ctqw_check_status(const ctqw_hamiltonian *h, void *stream);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char *ctqw_last_error(void);

@@ -20,7 +20,7 @@ int64_t n_samples(int64_t n_steps, int obs_every) {
 
 void free_device(ctqw_hamiltonian *h) {
     void *ptrs[] = {h->eps32, h->J32, h->eps64, h->J64, h->sizes_d, h->group_of_d, h->par_off_d,
-                    h->st_off_d, h->group_off_d, h->joint_off_d, h->inv_count_d};
+                    h->st_off_d, h->group_off_d, h->joint_off_d, h->inv_count_d, h->status_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -177,10 +177,12 @@ int ctqw_build_hamiltonian(const ctqw_lattice_desc *d, void *stream, ctqw_hamilt
     if (cudaMalloc(&h->eps32, sizeof(float) * h->total_par) != cudaSuccess ||
         cudaMalloc(&h->J32, sizeof(float) * h->total_par) != cudaSuccess ||
         cudaMalloc(&h->eps64, pb) != cudaSuccess || cudaMalloc(&h->J64, pb) != cudaSuccess ||
-        cudaMalloc(&u_eps_d, pb) != cudaSuccess || cudaMalloc(&u_J_d, pb) != cudaSuccess) {
+        cudaMalloc(&u_eps_d, pb) != cudaSuccess || cudaMalloc(&u_J_d, pb) != cudaSuccess ||
+        cudaMalloc(&h->status_d, sizeof(int)) != cudaSuccess) {
         ctqw_set_error("cudaMalloc of the parameter arrays failed");
         return fail(CTQW_ENOMEM);
     }
+    if (cudaMemsetAsync(h->status_d, 0, sizeof(int), s) != cudaSuccess) return fail(CTQW_ECUDA);
     if ((st = upload(&h->sizes_d, h->sizes, s)) || (st = upload(&h->par_off_d, h->par_off, s)) ||
         (st = upload(&h->st_off_d, h->st_off, s)) || (st = upload(&h->group_of_d, h->group_of, s)) ||
         (st = upload(&h->group_off_d, h->group_off, s)) ||
@@ -310,7 +312,9 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
     CTQW_TRY(zero_outputs(h, n_obs, P_mean_dev, norm_dev, energy_dev, s));
     if (fused)
         return launch_taylor_fused(h, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
-                                   energy_dev, (flags & CTQW_FLAG_NO_COMPENSATION) ? 0 : 1, 0, s);
+                                   energy_dev, (flags & CTQW_FLAG_NO_COMPENSATION) ? 0 : 1,
+                                   (int)((flags >> CTQW_FUSED_SHAPE_SHIFT) & 0xF),
+                                   (flags & CTQW_FLAG_TEST_WAIT_TIMEOUT) ? 1 : 0, s);
 
     const size_t sb = (size_t)h->total_amp * elem_bytes(dtype);
     char *ws = (char *)workspace_dev;
@@ -373,6 +377,20 @@ int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, 
         std::swap(cur, acc);
     }
     if (cur != psi_dev) CTQW_CUDA_TRY(cudaMemcpyAsync(psi_dev, cur, sb, cudaMemcpyDeviceToDevice, s));
+    return CTQW_OK;
+}
+
+int ctqw_check_status(const ctqw_hamiltonian *h, void *stream) {
+    if (!h) { ctqw_set_error("null handle"); return CTQW_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    CTQW_CUDA_TRY(cudaStreamSynchronize(s));
+    int v = 0;
+    CTQW_CUDA_TRY(cudaMemcpy(&v, h->status_d, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v != 0) {
+        CTQW_CUDA_TRY(cudaMemset(h->status_d, 0, sizeof(int)));
+        ctqw_set_error("a bounded wait inside a propagation kernel gave up; results of that call are invalid");
+        return CTQW_ETIMEOUT;
+    }
     return CTQW_OK;
 }
 

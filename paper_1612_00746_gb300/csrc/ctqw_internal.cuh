@@ -31,6 +31,7 @@ struct ctqw_hamiltonian {
     int64_t *par_off_d = nullptr, *st_off_d = nullptr, *group_off_d = nullptr,
             *joint_off_d = nullptr;
     double *inv_count_d = nullptr;  // [G] 1 / R_g
+    int *status_d = nullptr;        // nonzero after a kernel's bounded wait gave up
 };
 
 // Per-launch view of the realization table (passed by value to kernels).
@@ -101,4 +102,4 @@ int launch_observables(const ctqw_hamiltonian *h, int dtype, const void *psi, do
 bool fused_taylor_supported(const ctqw_hamiltonian *h, int dtype);
 int launch_taylor_fused(const ctqw_hamiltonian *h, void *psi, double dt, int K, int64_t n_steps,
                         int obs_every, double *P_mean, double *norm, double *energy,
-                        int compensated, int cta_threads, cudaStream_t s);
+                        int compensated, int shape, int test_timeout, cudaStream_t s);

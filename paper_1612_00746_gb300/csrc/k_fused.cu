@@ -4,11 +4,13 @@
 // state once per step.  Here one thread-block cluster owns one realization
 // for the whole call: the N x N amplitude tile is split into row slabs, one
 // per CTA, and each warp keeps an 8-row x 64-column block of the current
-// Taylor term in registers.  Per term only the two edge rows of every warp
-// band (and the edge columns of every warp) move, through shared memory or
-// distributed shared memory of the neighbouring CTA, behind one cluster
-// barrier.  psi is read from HBM once and written once per call, so the
-// K * n_steps stencil applications run at on-chip speed.
+// Taylor term in registers.  Per term only edges move: the edge rows of the
+// warp bands and the edge columns of the warps through this CTA's shared
+// memory (behind one __syncthreads), and the slab's first and last rows
+// straight into the neighbouring CTAs' shared memory with st.async, which
+// completes on the receiver's mbarrier (point to point; no cluster-wide
+// barrier or memory fence per term).  psi is read from HBM once and written
+// once per call, so the K * n_steps stencil applications run at on-chip speed.
 //
 // Arithmetic: the same order-K polynomial as Algorithm 3, evaluated in
 // Horner form with A = -i dt H (a real stencil applied to re and im alike):
@@ -20,11 +22,7 @@
 // each term at its own scale.  The final increment A w_2 is added to the
 // state with its rounding error carried in a second FP32 word (lo, in shared
 // memory): hi + lo holds the state to ~2^-48 relative across all steps.
-#include <cooperative_groups.h>
-
 #include "ctqw_internal.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace {
 
@@ -45,6 +43,9 @@ struct FusedArgs {
     long long p_width;
     double *P_mean, *norm, *energy;
     int compensated;
+    int *status;             // set to nonzero when a bounded wait gives up
+    unsigned long long wait_limit_ns;
+    int test_timeout;        // wait once on an mbarrier nothing completes (failure-path test)
     float inv_j[kMaxK + 1];  // 1 / j
 };
 
@@ -54,10 +55,67 @@ __device__ __forceinline__ unsigned cluster_rank() {
     return r;
 }
 
+// Full cluster barrier (used at the start and the end of the kernel only).
 __device__ __forceinline__ void cluster_barrier() {
     __syncwarp();
     asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
                  "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mb, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mb, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes)
+                 : "memory");
+}
+
+// 16-byte store into another CTA's shared memory, counted on its mbarrier.
+__device__ __forceinline__ void st_async16(uint32_t raddr, float4 v, uint32_t rmbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+                 ::"r"(raddr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rmbar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mb, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(mb), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of parity `parity` of mbarrier `mb`, giving up after
+// limit_ns of global time: then the status word is set and false returned.
+__device__ __noinline__ bool mbar_wait_bounded(uint32_t mb, uint32_t parity,
+                                               unsigned long long limit_ns, int *status) {
+    if (mbar_try_wait(mb, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try_wait(mb, parity)) return true;
+        if ((it & 255u) == 0 && global_ns() - t0 > limit_ns) {
+            atomicOr(status, 1);
+            return false;
+        }
+    }
 }
 
 __device__ __forceinline__ float2 ffma2(float a, float2 b, float2 c) {
@@ -77,9 +135,11 @@ enum { kHorner = 0, kFinal = 1, kEnergyOnly = 2 };
 //   kFinal:      P <- -i y              (the increment A w_2)
 //   kEnergyOnly: P unchanged
 // ENERGY adds sum Re(conj(P) y) (= dt <psi|H|psi> when P = psi) into e.
-template <int MODE, bool ENERGY>
+// V: this warp's first row of the diagonal dt*(eps_x1 + eps_x2 + U delta) in
+// shared memory, at the lane's two columns (row stride N).
+template <int MODE, bool ENERGY, int N>
 __device__ __forceinline__ void stencil_term(float2 (&P)[RL][2], const float2 (&Q)[RL][2],
-                                             const float (&V)[RL][2], const float (&nJr)[RL + 1],
+                                             const float *__restrict__ V, const float (&nJr)[RL + 1],
                                              const float (&nJc)[3], float2 up0, float2 up1,
                                              float2 dn0, float2 dn1, const float2 *__restrict__ seam,
                                              int lane, float inv_j, float &e) {
@@ -93,12 +153,13 @@ __device__ __forceinline__ void stencil_term(float2 (&P)[RL][2], const float2 (&
         const float2 sv = seam[i];
         const float2 lft = shfl2(lane == 31 ? sv : c1, from_left);
         const float2 rgt = shfl2(lane == 0 ? sv : c0, from_right);
-        float2 y0 = make_float2(V[i][0] * c0.x, V[i][0] * c0.y);
+        const float2 v = *reinterpret_cast<const float2 *>(V + i * N);
+        float2 y0 = make_float2(v.x * c0.x, v.x * c0.y);
         y0 = ffma2(nJr[i], prev0, y0);
         y0 = ffma2(nJr[i + 1], n0, y0);
         y0 = ffma2(nJc[0], lft, y0);
         y0 = ffma2(nJc[1], c1, y0);
-        float2 y1 = make_float2(V[i][1] * c1.x, V[i][1] * c1.y);
+        float2 y1 = make_float2(v.y * c1.x, v.y * c1.y);
         y1 = ffma2(nJr[i], prev1, y1);
         y1 = ffma2(nJr[i + 1], n1, y1);
         y1 = ffma2(nJc[1], c0, y1);
@@ -146,11 +207,14 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
     static_assert(N % 64 == 0 && N % SR == 0 && C <= 16, "unsupported fused shape");
     float2 *hi = reinterpret_cast<float2 *>(smem_raw);
     float2 *lo = hi + SR * N;
-    float2 *edge = lo + SR * N;                  // [2][BPC][2][N]
-    float2 *seamb = edge + 2 * BPC * 2 * N;      // [2][W][2][RL]
-    float *pacc = reinterpret_cast<float *>(seamb + 2 * W * 2 * RL);   // [N]
+    float2 *halo = lo + SR * N;                  // [2 parity][2: row above, row below][N], filled by neighbours
+    float2 *edge = halo + 2 * 2 * N;             // [2][BPC][2][N] band edges inside this CTA
+    float2 *seamb = edge + 2 * BPC * 2 * N;      // [2][W][2][RL] warp edge columns
+    float *Vs = reinterpret_cast<float *>(seamb + 2 * W * 2 * RL);     // [SR][N] diagonal of dt H
+    float *pacc = Vs + SR * N;                                           // [N]
+    __shared__ __align__(8) unsigned long long mbar[2][2];   // [parity][side] halo arrivals
+    __shared__ __align__(8) unsigned long long mbar_never;    // failure-path test only
 
-    cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster_rank();
     const int r = blockIdx.x / C;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -164,14 +228,15 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
     const double *eps = a.eps + po;
     const double *J = a.J + po;
     const double dt = a.dt, U = a.tab.U;
-    float V[RL][2], nJr[RL + 1], nJc[3];
+    float nJr[RL + 1], nJc[3];
+    float *V = Vs + lrow0 * N + x2_0;
 #pragma unroll
     for (int i = 0; i < RL; ++i) {
         const int x1 = x1_0 + i;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             const int x2 = x2_0 + c;
-            V[i][c] = (float)(dt * (eps[x1] + eps[x2] + (x1 == x2 ? U : 0.0)));
+            V[i * N + c] = (float)(dt * (eps[x1] + eps[x2] + (x1 == x2 ? U : 0.0)));
         }
     }
 #pragma unroll
@@ -194,17 +259,30 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
     for (int x = threadIdx.x; x < N; x += blockDim.x) pacc[x] = 0.f;
 
     const int rank_up = (rank + C - 1) % C, rank_dn = (rank + 1) % C;
-    float2 *edge_up = cluster.map_shared_rank(edge, rank_up);
-    float2 *edge_dn = cluster.map_shared_rank(edge, rank_dn);
+    // band 0 sends its first row into rank_up's "row below" slot, band BPC-1
+    // its last row into rank_dn's "row above" slot
+    const uint32_t send_up = map_rank(smem_u32(halo + N + x2_0), rank_up);
+    const uint32_t send_up_mb = map_rank(smem_u32(&mbar[0][1]), rank_up);
+    const uint32_t send_dn = map_rank(smem_u32(halo + x2_0), rank_dn);
+    const uint32_t send_dn_mb = map_rank(smem_u32(&mbar[0][0]), rank_dn);
     const int w_left = band * WB + (wc + WB - 1) % WB;
     const int w_right = band * WB + (wc + 1) % WB;
     const int g = a.tab.group_of[r];
     const double pscale = a.tab.inv_count[g] * 0.5;
     double *Pg = a.P_mean ? a.P_mean + a.tab.group_off[g] : nullptr;
+    bool dead = false;   // a bounded wait gave up: stop waiting, finish, report
 
-    cluster_barrier();   // every CTA of the cluster is running and initialised
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 2; ++q)
+            for (int sd = 0; sd < 2; ++sd) mbar_init(smem_u32(&mbar[q][sd]), 1);
+        mbar_init(smem_u32(&mbar_never), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cluster_barrier();   // every CTA of the cluster is running, its mbarriers initialised
+    if (a.test_timeout && threadIdx.x == 0 && blockIdx.x == 0)   // exercises the give-up path; the halo protocol is untouched
+        (void)mbar_wait_bounded(smem_u32(&mbar_never), 0, 1000000ull /* 1 ms */, a.status);
 
-    int parity = 0;
+    unsigned tc = 0;     // terms done: slot parity tc & 1, mbarrier phase (tc >> 1) & 1
     long long obs = 0;
     const long long n_steps = a.n_steps;
     for (long long step = 0; step <= n_steps; ++step) {
@@ -242,11 +320,19 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
         const int K = a.K;
         const int j_end = last ? K : 1;   // the energy-only pass is one stencil
         for (int j = K; j >= j_end; --j) {
-            // publish this warp's edge rows and edge columns
+            const int parity = tc & 1;
+            const uint32_t phase = (tc >> 1) & 1;
+            // publish: slab edge rows to the neighbour CTAs, band edges and
+            // warp edge columns to this CTA's shared memory
+            const float4 top = make_float4(P[0][0].x, P[0][0].y, P[0][1].x, P[0][1].y);
+            const float4 bot = make_float4(P[RL - 1][0].x, P[RL - 1][0].y, P[RL - 1][1].x, P[RL - 1][1].y);
+            if (band == 0)
+                st_async16(send_up + parity * (2 * N * 8), top, send_up_mb + parity * 16);
+            if (band == BPC - 1)
+                st_async16(send_dn + parity * (2 * N * 8), bot, send_dn_mb + parity * 16);
             float2 *eb = edge + parity * (BPC * 2 * N) + band * (2 * N);
-            *reinterpret_cast<float4 *>(eb + x2_0) = make_float4(P[0][0].x, P[0][0].y, P[0][1].x, P[0][1].y);
-            *reinterpret_cast<float4 *>(eb + N + x2_0) =
-                make_float4(P[RL - 1][0].x, P[RL - 1][0].y, P[RL - 1][1].x, P[RL - 1][1].y);
+            *reinterpret_cast<float4 *>(eb + x2_0) = top;
+            *reinterpret_cast<float4 *>(eb + N + x2_0) = bot;
             float2 *sb = seamb + parity * (W * 2 * RL) + warp * (2 * RL);
             if (lane == 0) {
 #pragma unroll
@@ -255,16 +341,25 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
 #pragma unroll
                 for (int i = 0; i < RL; ++i) sb[RL + i] = P[i][1];
             }
-            cluster_barrier();
+            __syncthreads();
+            if (threadIdx.x == 0) {   // this term's arrival + expected bytes on both halo slots
+                mbar_expect_tx(smem_u32(&mbar[parity][0]), N * 8);
+                mbar_expect_tx(smem_u32(&mbar[parity][1]), N * 8);
+            }
             // gather halos
-            const float2 *up_src = (band > 0)
-                ? edge + parity * (BPC * 2 * N) + (band - 1) * (2 * N) + N
-                : edge_up + parity * (BPC * 2 * N) + (BPC - 1) * (2 * N) + N;
-            const float2 *dn_src = (band < BPC - 1)
-                ? edge + parity * (BPC * 2 * N) + (band + 1) * (2 * N)
-                : edge_dn + parity * (BPC * 2 * N);
-            const float4 u4 = *reinterpret_cast<const float4 *>(up_src + x2_0);
-            const float4 d4 = *reinterpret_cast<const float4 *>(dn_src + x2_0);
+            float4 u4, d4;
+            if (band > 0) {
+                u4 = *reinterpret_cast<const float4 *>(edge + parity * (BPC * 2 * N) + (band - 1) * (2 * N) + N + x2_0);
+            } else {
+                if (!dead) dead = !mbar_wait_bounded(smem_u32(&mbar[parity][0]), phase, a.wait_limit_ns, a.status);
+                u4 = *reinterpret_cast<const float4 *>(halo + parity * (2 * N) + x2_0);
+            }
+            if (band < BPC - 1) {
+                d4 = *reinterpret_cast<const float4 *>(edge + parity * (BPC * 2 * N) + (band + 1) * (2 * N) + x2_0);
+            } else {
+                if (!dead) dead = !mbar_wait_bounded(smem_u32(&mbar[parity][1]), phase, a.wait_limit_ns, a.status);
+                d4 = *reinterpret_cast<const float4 *>(halo + parity * (2 * N) + N + x2_0);
+            }
             // lane 0 reads the right neighbour warp's first column, the others
             // the left neighbour warp's last column (only lane 31 uses it)
             const float2 *seam = seamb + parity * (W * 2 * RL) +
@@ -276,22 +371,22 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
             const bool en = first && sample && a.energy;
             float e = 0.f;
             if (last) {
-                stencil_term<kEnergyOnly, true>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
+                stencil_term<kEnergyOnly, true, N>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
             } else if (j == 1) {
                 if (en)
-                    stencil_term<kFinal, true>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
+                    stencil_term<kFinal, true, N>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
                 else
-                    stencil_term<kFinal, false>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
+                    stencil_term<kFinal, false, N>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
             } else if (en) {
-                stencil_term<kHorner, true>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
+                stencil_term<kHorner, true, N>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
             } else {
-                stencil_term<kHorner, false>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
+                stencil_term<kHorner, false, N>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
             }
             if (en || last) {
                 const float es = warp_sum(e);
                 if (lane == 0) atomicAdd(a.energy + obs * a.tab.R + r, (double)es * (double)a.inv_dt);
             }
-            parity ^= 1;
+            ++tc;
         }
         if (sample) ++obs;
         if (last) break;
@@ -326,7 +421,7 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
         const float4 h4 = *reinterpret_cast<const float4 *>(hi + (lrow0 + i) * N + x2_0);
         *reinterpret_cast<float4 *>(gpsi + (size_t)(x1_0 + i) * N + x2_0) = h4;
     }
-    cluster_barrier();   // no CTA leaves while a neighbour may still read its shared memory
+    cluster_barrier();   // no CTA leaves while a neighbour may still write its shared memory
 }
 
 using FusedKernel = void (*)(FusedArgs);
@@ -344,27 +439,29 @@ FusedShape make_shape() {
     f.BPC = BPC;
     f.C = N / SR;
     f.threads = 32 * W;
-    f.smem = sizeof(float2) * ((size_t)2 * SR * N + (size_t)2 * BPC * 2 * N + (size_t)2 * W * 2 * RL) +
-             sizeof(float) * (size_t)N;
+    f.smem = sizeof(float2) * ((size_t)2 * SR * N + (size_t)2 * 2 * N + (size_t)2 * BPC * 2 * N +
+                               (size_t)2 * W * 2 * RL) +
+             sizeof(float) * ((size_t)SR * N + (size_t)N);
     f.kern = taylor_fused_kernel<N, BPC, MINB>;
     return f;
 }
 
-// Shapes compiled in: (N, warp bands per CTA).  cta_threads picks among the
-// shapes of one N (0 = the default, listed first).
-bool fused_shape(int N, int cta_threads, FusedShape &f) {
-    FusedShape opts[2];
-    int n = 0;
+// Shapes compiled in per N: (warp bands per CTA, CTAs per SM the registers are
+// capped for).  Index 0 is the default; the others are selected with
+// CTQW_FUSED_SHAPE(k) for tuning.
+constexpr int kShapes = 3;
+
+bool fused_shape(int N, int idx, FusedShape &f) {
+    FusedShape opts[kShapes];
     switch (N) {
-        case 64: opts[n++] = make_shape<64, 8, 2>(); opts[n++] = make_shape<64, 4, 2>(); break;
-        case 128: opts[n++] = make_shape<128, 4, 2>(); opts[n++] = make_shape<128, 2, 2>(); break;
-        case 192: opts[n++] = make_shape<192, 2, 2>(); opts[n++] = make_shape<192, 4, 1>(); break;
-        case 256: opts[n++] = make_shape<256, 2, 2>(); opts[n++] = make_shape<256, 4, 1>(); break;
+        case 64: opts[0] = make_shape<64, 8, 2>(); opts[1] = make_shape<64, 4, 2>(); opts[2] = make_shape<64, 8, 1>(); break;
+        case 128: opts[0] = make_shape<128, 4, 2>(); opts[1] = make_shape<128, 2, 2>(); opts[2] = make_shape<128, 4, 1>(); break;
+        case 192: opts[0] = make_shape<192, 2, 2>(); opts[1] = make_shape<192, 4, 1>(); opts[2] = make_shape<192, 2, 1>(); break;
+        case 256: opts[0] = make_shape<256, 2, 2>(); opts[1] = make_shape<256, 4, 1>(); opts[2] = make_shape<256, 2, 1>(); break;
         default: return false;
     }
-    f = opts[0];
-    for (int i = 0; i < n; ++i)
-        if (opts[i].threads == cta_threads) f = opts[i];
+    if (idx < 0 || idx >= kShapes) return false;
+    f = opts[idx];
     return true;
 }
 
@@ -377,10 +474,10 @@ bool fused_taylor_supported(const ctqw_hamiltonian *h, int dtype) {
 
 int launch_taylor_fused(const ctqw_hamiltonian *h, void *psi, double dt, int K, int64_t n_steps,
                         int obs_every, double *P_mean, double *norm, double *energy,
-                        int compensated, int cta_threads, cudaStream_t s) {
+                        int compensated, int shape, int test_timeout, cudaStream_t s) {
     FusedShape f;
-    if (!fused_shape(h->Nmax, cta_threads, f)) {
-        ctqw_set_error("fused path: unsupported size N=%d", h->Nmax);
+    if (!fused_shape(h->Nmax, shape, f)) {
+        ctqw_set_error("fused path: unsupported size N=%d or shape %d", h->Nmax, shape);
         return CTQW_EUNSUPPORTED;
     }
     if (K > kMaxK) {
@@ -403,6 +500,9 @@ int launch_taylor_fused(const ctqw_hamiltonian *h, void *psi, double dt, int K, 
     a.norm = norm;
     a.energy = energy;
     a.compensated = compensated;
+    a.status = h->status_d;
+    a.test_timeout = test_timeout;
+    a.wait_limit_ns = 2000000000ull;   // 2 s: halo rows normally arrive within microseconds
     a.inv_j[0] = 0.f;
     for (int j = 1; j <= kMaxK; ++j) a.inv_j[j] = (float)(1.0 / j);
     FusedKernel kern = f.kern;

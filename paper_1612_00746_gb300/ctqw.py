@@ -18,16 +18,24 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libctqw.so")
 
 CTQW_OK, CTQW_EINVAL, CTQW_ENOMEM, CTQW_ECUDA, CTQW_EUNSUPPORTED = 0, 1, 2, 3, 4
+CTQW_ETIMEOUT = 6
 DISTINGUISHABLE, BOSONS, FERMIONS = 0, 1, 2
 C64, C128 = 0, 1
 FLAG_PLAIN = 0x1
 FLAG_NO_COMPENSATION = 0x2
+FLAG_TEST_WAIT_TIMEOUT = 0x8
+
+
+def FUSED_SHAPE(k: int) -> int:
+    return (int(k) & 0xF) << 8
+
 TAYLOR, RK4 = 0, 1
 
 EXPORTED = (
     "ctqw_build_hamiltonian", "ctqw_destroy_hamiltonian", "ctqw_get_params", "ctqw_state_size",
     "ctqw_output_layout", "ctqw_init_state", "ctqw_workspace_size", "ctqw_propagate_taylor",
-    "ctqw_propagate_rk4", "ctqw_ensemble_observables", "ctqw_last_error", "ctqw_version",
+    "ctqw_propagate_rk4", "ctqw_ensemble_observables", "ctqw_check_status", "ctqw_last_error",
+    "ctqw_version",
 )
 
 
@@ -77,6 +85,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "ctqw_propagate_taylor": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, u32, vp, sz, vp],
         "ctqw_propagate_rk4": [vp, i32, vp, dbl, i64, i32, vp, vp, vp, u32, vp, sz, vp],
         "ctqw_ensemble_observables": [vp, i32, vp, vp, vp, vp, vp, vp],
+        "ctqw_check_status": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -238,6 +247,10 @@ def ctqw_ensemble_observables(h: Hamiltonian, psi: torch.Tensor, dtype: int, P_m
                                             _ptr(norm), _ptr(energy), _stream(stream)))
 
 
+def ctqw_check_status(h: Hamiltonian, stream=None) -> None:
+    _check(load().ctqw_check_status(h.handle, _stream(stream)))
+
+
 def ctqw_version() -> str:
     return load().ctqw_version().decode()
 
@@ -275,7 +288,7 @@ def run_workload(w, realizations=None, method: int = TAYLOR, dtype: Optional[int
         ctqw_propagate_taylor(h, psi, dtype, w.dt, K, n_steps, obs_every, P, nr, en, flags, ws)
     else:
         ctqw_propagate_rk4(h, psi, dtype, w.dt, n_steps, obs_every, P, nr, en, flags, ws)
-    torch.cuda.synchronize()
+    ctqw_check_status(h)
     out = {"psi": psi.cpu().numpy(), "st_off": h.st_off, "sizes": h.sizes,
            "group_sizes": h.group_sizes, "p_width": h.p_width}
     out["P_mean"] = P.cpu().numpy() if P is not None else None

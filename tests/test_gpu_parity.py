@@ -250,3 +250,40 @@ def test_bad_arguments_rejected(ctqw):
     with pytest.raises(ctqw.CtqwError, match="dt"):
         ctqw.ctqw_propagate_taylor(h, psi, cw.C128, float("nan"), 4, 1, 0, workspace=h.workspace(cw.C128))
     h.close()
+
+
+# ------------------------------------------------------------------ fused shapes and failure path
+@pytest.mark.parametrize("N,shape", [(64, 1), (64, 2), (128, 1), (128, 2), (192, 1), (192, 2),
+                                     (256, 1), (256, 2)])
+def test_fused_c64_alternative_shapes(ctqw, N, shape):
+    w = cw.get("bosons_n256_u2").with_(N=N, R=3, K=9, n_steps=12, obs_every=4,
+                                       sites=(N // 2 - 1, N // 2))
+    got = ctqw.run_workload(w, flags=ctqw.FUSED_SHAPE(shape))
+    ref = oracle.ensemble_run(w)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
+
+
+def test_fused_unknown_shape_rejected(ctqw):
+    w = cw.get("bosons_small").with_(R=1, n_steps=2)
+    with pytest.raises(ctqw.CtqwError, match="shape"):
+        ctqw.run_workload(w, flags=ctqw.FUSED_SHAPE(7))
+
+
+def test_fused_bounded_wait_gives_up_and_reports(ctqw):
+    """The failure path of the fused kernel's bounded waits: with the test flag
+    one thread waits on an mbarrier that nothing completes; it must give up
+    (1 ms), flag the handle, and leave the GPU and the results usable."""
+    w = cw.get("bosons_small").with_(R=2, n_steps=20, obs_every=10)
+    h = ctqw.build_for_workload(w)
+    psi = h.new_state(cw.C64)
+    ctqw.ctqw_init_state(h, psi, ctqw.initial_sites(w, h), cw.C64)
+    ctqw.ctqw_propagate_taylor(h, psi, cw.C64, w.dt, w.K, w.n_steps, 0,
+                               flags=ctqw.FLAG_TEST_WAIT_TIMEOUT)
+    with pytest.raises(ctqw.CtqwError) as ei:
+        ctqw.ctqw_check_status(h)
+    assert ei.value.status == ctqw.CTQW_ETIMEOUT
+    ctqw.ctqw_check_status(h)          # the flag is cleared once reported
+    got = ctqw.run_workload(w)         # and the device keeps working
+    ref = oracle.ensemble_run(w)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
+    h.close()
