@@ -22,6 +22,8 @@
 // each term at its own scale.  The final increment A w_2 is added to the
 // state with its rounding error carried in a second FP32 word (lo, in shared
 // memory): hi + lo holds the state to ~2^-48 relative across all steps.
+#include <type_traits>
+
 #include "ctqw_internal.cuh"
 
 namespace {
@@ -82,6 +84,14 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mb, uint32_t bytes) {
                  : "memory");
 }
 
+// Arrival + expected bytes on two mbarriers, from the threads with flag != 0 only (no branch).
+__device__ __forceinline__ void mbar_expect_tx2_if(uint32_t mb0, uint32_t mb1, uint32_t bytes, int flag) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %3, 0;\n\t"
+                 "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %2;\n\t"
+                 "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n\t}"
+                 ::"r"(mb0), "r"(mb1), "r"(bytes), "r"(flag) : "memory");
+}
+
 // 16-byte store into another CTA's shared memory, counted on its mbarrier.
 __device__ __forceinline__ void st_async16(uint32_t raddr, float4 v, uint32_t rmbar) {
     asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
@@ -131,43 +141,61 @@ enum { kHorner = 0, kFinal = 1, kEnergyOnly = 2 };
 
 // up/dn: the rows above and below the block; seam: the column beyond the
 // block's left edge (used by lane 31) or right edge (used by lane 0).
-//   kHorner:     P <- Q + (-i/j) y      (Q = psi of this step)
+//   kHorner:     P <- Q + (-i/j) y      (Q = psi of this step, read from shared memory)
 //   kFinal:      P <- -i y              (the increment A w_2)
 //   kEnergyOnly: P unchanged
 // ENERGY adds sum Re(conj(P) y) (= dt <psi|H|psi> when P = psi) into e.
-// V: this warp's first row of the diagonal dt*(eps_x1 + eps_x2 + U delta) in
-// shared memory, at the lane's two columns (row stride N).
-template <int MODE, bool ENERGY, int N>
-__device__ __forceinline__ void stencil_term(float2 (&P)[RL][2], const float2 (&Q)[RL][2],
-                                             const float *__restrict__ V, const float (&nJr)[RL + 1],
-                                             const float (&nJc)[3], float2 up0, float2 up1,
-                                             float2 dn0, float2 dn1, const float2 *__restrict__ seam,
-                                             int lane, float inv_j, float &e) {
-    float2 prev0 = up0, prev1 = up1;
+// V4: this warp's diagonal dt*(eps_x1 + eps_x2 + U delta) in shared memory as
+// float4 per row pair and lane, (row 2k col 0, row 2k col 1, row 2k+1 col 0,
+// row 2k+1 col 1), row-pair stride N/2 float4.  Coefficient pairs (c, c) are
+// kept duplicated so every tap is one FFMA2 on the (re, im) pair.
+// Rows are visited top-down (REV = false) or bottom-up (REV = true); both
+// orders compute the same values (each new row only replaces a row whose old
+// value is no longer needed).
+template <int MODE, bool ENERGY, int N, bool REV>
+__device__ __forceinline__ void stencil_term(float2 (&P)[RL][2], const float2 *__restrict__ Q,
+                                             const float4 *__restrict__ V4,
+                                             const float2 (&nJr)[RL + 1], const float2 (&nJc)[3],
+                                             float2 up0, float2 up1, float2 dn0, float2 dn1,
+                                             const float4 *__restrict__ seam4, int lane,
+                                             float inv_j, float &e) {
+    // "prev" is the old row already passed (above when top-down, below when bottom-up)
+    float2 prev0 = REV ? dn0 : up0, prev1 = REV ? dn1 : up1;
     const int from_left = (lane + 31) & 31, from_right = (lane + 1) & 31;
+    const bool l31 = lane == 31, l0 = lane == 0;
+    float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f), s4 = v4;
 #pragma unroll
-    for (int i = 0; i < RL; ++i) {
+    for (int ii = 0; ii < RL; ++ii) {
+        const int i = REV ? RL - 1 - ii : ii;
+        if ((ii & 1) == 0) {
+            v4 = V4[(i >> 1) * (N / 2)];
+            s4 = seam4[i >> 1];
+        }
         const float2 c0 = P[i][0], c1 = P[i][1];
-        const float2 n0 = (i < RL - 1) ? P[i + 1][0] : dn0;
-        const float2 n1 = (i < RL - 1) ? P[i + 1][1] : dn1;
-        const float2 sv = seam[i];
-        const float2 lft = shfl2(lane == 31 ? sv : c1, from_left);
-        const float2 rgt = shfl2(lane == 0 ? sv : c0, from_right);
-        const float2 v = *reinterpret_cast<const float2 *>(V + i * N);
-        float2 y0 = make_float2(v.x * c0.x, v.x * c0.y);
-        y0 = ffma2(nJr[i], prev0, y0);
-        y0 = ffma2(nJr[i + 1], n0, y0);
-        y0 = ffma2(nJc[0], lft, y0);
-        y0 = ffma2(nJc[1], c1, y0);
-        float2 y1 = make_float2(v.y * c1.x, v.y * c1.y);
-        y1 = ffma2(nJr[i], prev1, y1);
-        y1 = ffma2(nJr[i + 1], n1, y1);
-        y1 = ffma2(nJc[1], c0, y1);
-        y1 = ffma2(nJc[2], rgt, y1);
+        // old neighbour rows: "nxt" is the one not yet visited
+        const float2 nx0 = REV ? ((i > 0) ? P[i - 1][0] : up0) : ((i < RL - 1) ? P[i + 1][0] : dn0);
+        const float2 nx1 = REV ? ((i > 0) ? P[i - 1][1] : up1) : ((i < RL - 1) ? P[i + 1][1] : dn1);
+        const float2 a0 = REV ? nx0 : prev0, a1 = REV ? nx1 : prev1;   // row above (old)
+        const float2 b0 = REV ? prev0 : nx0, b1 = REV ? prev1 : nx1;   // row below (old)
+        const float2 sv = (i & 1) ? make_float2(s4.z, s4.w) : make_float2(s4.x, s4.y);
+        const float vx = (i & 1) ? v4.z : v4.x, vy = (i & 1) ? v4.w : v4.y;
+        const float2 lft = shfl2(l31 ? sv : c1, from_left);
+        const float2 rgt = shfl2(l0 ? sv : c0, from_right);
+        float2 y0 = make_float2(vx * c0.x, vx * c0.y);
+        y0 = __ffma2_rn(nJr[i], a0, y0);
+        y0 = __ffma2_rn(nJr[i + 1], b0, y0);
+        y0 = __ffma2_rn(nJc[0], lft, y0);
+        y0 = __ffma2_rn(nJc[1], c1, y0);
+        float2 y1 = make_float2(vy * c1.x, vy * c1.y);
+        y1 = __ffma2_rn(nJr[i], a1, y1);
+        y1 = __ffma2_rn(nJr[i + 1], b1, y1);
+        y1 = __ffma2_rn(nJc[1], c0, y1);
+        y1 = __ffma2_rn(nJc[2], rgt, y1);
         if (ENERGY) e += c0.x * y0.x + c0.y * y0.y + c1.x * y1.x + c1.y * y1.y;
         if (MODE == kHorner) {
-            P[i][0] = make_float2(fmaf(inv_j, y0.y, Q[i][0].x), fmaf(-inv_j, y0.x, Q[i][0].y));
-            P[i][1] = make_float2(fmaf(inv_j, y1.y, Q[i][1].x), fmaf(-inv_j, y1.x, Q[i][1].y));
+            const float4 q = *reinterpret_cast<const float4 *>(Q + i * N);
+            P[i][0] = make_float2(fmaf(inv_j, y0.y, q.x), fmaf(-inv_j, y0.x, q.y));
+            P[i][1] = make_float2(fmaf(inv_j, y1.y, q.z), fmaf(-inv_j, y1.x, q.w));
         } else if (MODE == kFinal) {
             P[i][0] = make_float2(y0.y, -y0.x);
             P[i][1] = make_float2(y1.y, -y1.x);
@@ -175,6 +203,20 @@ __device__ __forceinline__ void stencil_term(float2 (&P)[RL][2], const float2 (&
         prev0 = c0;
         prev1 = c1;
     }
+}
+
+// Store 8 float2 (one per row) to shared memory from the lanes where flag != 0
+// only, as four predicated 16-byte stores (no branch).
+__device__ __forceinline__ void st_shared_col8_if(uint32_t addr, int flag, const float2 (&v)[RL]) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %1, 0;\n\t"
+                 "@p st.shared.v4.f32 [%0], {%2, %3, %4, %5};\n\t"
+                 "@p st.shared.v4.f32 [%0+16], {%6, %7, %8, %9};\n\t"
+                 "@p st.shared.v4.f32 [%0+32], {%10, %11, %12, %13};\n\t"
+                 "@p st.shared.v4.f32 [%0+48], {%14, %15, %16, %17};\n\t}"
+                 ::"r"(addr), "r"(flag), "f"(v[0].x), "f"(v[0].y), "f"(v[1].x), "f"(v[1].y),
+                   "f"(v[2].x), "f"(v[2].y), "f"(v[3].x), "f"(v[3].y), "f"(v[4].x), "f"(v[4].y),
+                   "f"(v[5].x), "f"(v[5].y), "f"(v[6].x), "f"(v[6].y), "f"(v[7].x), "f"(v[7].y)
+                 : "memory");
 }
 
 // hi + lo + s rounded back into (hi, lo): TwoSum then FastTwoSum.
@@ -210,8 +252,8 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
     float2 *halo = lo + SR * N;                  // [2 parity][2: row above, row below][N], filled by neighbours
     float2 *edge = halo + 2 * 2 * N;             // [2][BPC][2][N] band edges inside this CTA
     float2 *seamb = edge + 2 * BPC * 2 * N;      // [2][W][2][RL] warp edge columns
-    float *Vs = reinterpret_cast<float *>(seamb + 2 * W * 2 * RL);     // [SR][N] diagonal of dt H
-    float *pacc = Vs + SR * N;                                           // [N]
+    float4 *Vs = reinterpret_cast<float4 *>(seamb + 2 * W * 2 * RL);   // [SR/2][N/2] diagonal of dt H
+    float *pacc = reinterpret_cast<float *>(Vs + (SR / 2) * (N / 2));   // [N]
     __shared__ __align__(8) unsigned long long mbar[2][2];   // [parity][side] halo arrivals
     __shared__ __align__(8) unsigned long long mbar_never;    // failure-path test only
 
@@ -228,31 +270,38 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
     const double *eps = a.eps + po;
     const double *J = a.J + po;
     const double dt = a.dt, U = a.tab.U;
-    float nJr[RL + 1], nJc[3];
-    float *V = Vs + lrow0 * N + x2_0;
+    float2 nJr[RL + 1], nJc[3];   // (c, c) pairs of -dt J
+    const float4 *V4 = Vs + (lrow0 / 2) * (N / 2) + x2_0 / 2;
 #pragma unroll
-    for (int i = 0; i < RL; ++i) {
-        const int x1 = x1_0 + i;
+    for (int k = 0; k < RL / 2; ++k) {
+        float vv[4];
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int x2 = x2_0 + c;
-            V[i * N + c] = (float)(dt * (eps[x1] + eps[x2] + (x1 == x2 ? U : 0.0)));
+        for (int q = 0; q < 4; ++q) {
+            const int x1 = x1_0 + 2 * k + (q >> 1), x2 = x2_0 + (q & 1);
+            vv[q] = (float)(dt * (eps[x1] + eps[x2] + (x1 == x2 ? U : 0.0)));
         }
+        Vs[(lrow0 / 2 + k) * (N / 2) + x2_0 / 2] = make_float4(vv[0], vv[1], vv[2], vv[3]);
     }
 #pragma unroll
-    for (int i = 0; i <= RL; ++i) nJr[i] = (float)(-dt * J[(x1_0 + i - 1 + N) % N]);
-    nJc[0] = (float)(-dt * J[(x2_0 - 1 + N) % N]);
-    nJc[1] = (float)(-dt * J[x2_0]);
-    nJc[2] = (float)(-dt * J[x2_0 + 1]);
+    for (int i = 0; i <= RL; ++i) {
+        const float c = (float)(-dt * J[(x1_0 + i - 1 + N) % N]);
+        nJr[i] = make_float2(c, c);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float c = (float)(-dt * J[(x2_0 - 1 + q + N) % N]);
+        nJc[q] = make_float2(c, c);
+    }
 
     // ---- load the state (one HBM read per call)
     float2 *gpsi = a.psi + a.tab.st_off[r];
-    float2 P[RL][2], Q[RL][2];   // current Horner iterate, psi of this step
+    float2 P[RL][2];             // current Horner iterate (psi of this step is hi in shared memory)
+    const float2 *Q = hi + lrow0 * N + x2_0;
 #pragma unroll
     for (int i = 0; i < RL; ++i) {
         const float4 v = *reinterpret_cast<const float4 *>(gpsi + (size_t)(x1_0 + i) * N + x2_0);
-        P[i][0] = Q[i][0] = make_float2(v.x, v.y);
-        P[i][1] = Q[i][1] = make_float2(v.z, v.w);
+        P[i][0] = make_float2(v.x, v.y);
+        P[i][1] = make_float2(v.z, v.w);
         *reinterpret_cast<float4 *>(hi + (lrow0 + i) * N + x2_0) = v;
         *reinterpret_cast<float4 *>(lo + (lrow0 + i) * N + x2_0) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -318,8 +367,9 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
         if (last && !(sample && a.energy)) break;
 
         const int K = a.K;
-        const int j_end = last ? K : 1;   // the energy-only pass is one stencil
-        for (int j = K; j >= j_end; --j) {
+        // One Horner stage (or the energy-only stencil of the last sample).
+        auto term = [&](auto rev_tag, const int j) {
+            constexpr bool REV = decltype(rev_tag)::value;
             const int parity = tc & 1;
             const uint32_t phase = (tc >> 1) & 1;
             // publish: slab edge rows to the neighbour CTAs, band edges and
@@ -333,19 +383,21 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
             float2 *eb = edge + parity * (BPC * 2 * N) + band * (2 * N);
             *reinterpret_cast<float4 *>(eb + x2_0) = top;
             *reinterpret_cast<float4 *>(eb + N + x2_0) = bot;
-            float2 *sb = seamb + parity * (W * 2 * RL) + warp * (2 * RL);
-            if (lane == 0) {
+            {
+                float2 c0v[RL], c1v[RL];
 #pragma unroll
-                for (int i = 0; i < RL; ++i) sb[i] = P[i][0];
-            } else if (lane == 31) {
-#pragma unroll
-                for (int i = 0; i < RL; ++i) sb[RL + i] = P[i][1];
+                for (int i = 0; i < RL; ++i) {
+                    c0v[i] = P[i][0];
+                    c1v[i] = P[i][1];
+                }
+                const uint32_t sb = smem_u32(seamb + parity * (W * 2 * RL) + warp * (2 * RL));
+                st_shared_col8_if(sb, lane == 0, c0v);
+                st_shared_col8_if(sb + RL * 8, lane == 31, c1v);
             }
             __syncthreads();
-            if (threadIdx.x == 0) {   // this term's arrival + expected bytes on both halo slots
-                mbar_expect_tx(smem_u32(&mbar[parity][0]), N * 8);
-                mbar_expect_tx(smem_u32(&mbar[parity][1]), N * 8);
-            }
+            // this term's arrival + expected bytes on both halo slots (thread 0)
+            mbar_expect_tx2_if(smem_u32(&mbar[parity][0]), smem_u32(&mbar[parity][1]), N * 8,
+                               threadIdx.x == 0);
             // gather halos
             float4 u4, d4;
             if (band > 0) {
@@ -362,8 +414,8 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
             }
             // lane 0 reads the right neighbour warp's first column, the others
             // the left neighbour warp's last column (only lane 31 uses it)
-            const float2 *seam = seamb + parity * (W * 2 * RL) +
-                                 (lane == 0 ? w_right * (2 * RL) : w_left * (2 * RL) + RL);
+            const float4 *seam4 = reinterpret_cast<const float4 *>(
+                seamb + parity * (W * 2 * RL) + (lane == 0 ? w_right * (2 * RL) : w_left * (2 * RL) + RL));
             const float2 up0 = make_float2(u4.x, u4.y), up1 = make_float2(u4.z, u4.w);
             const float2 dn0 = make_float2(d4.x, d4.y), dn1 = make_float2(d4.z, d4.w);
             const float inv_j = a.inv_j[j];
@@ -371,22 +423,27 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
             const bool en = first && sample && a.energy;
             float e = 0.f;
             if (last) {
-                stencil_term<kEnergyOnly, true, N>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
+                stencil_term<kEnergyOnly, true, N, REV>(P, Q, V4, nJr, nJc, up0, up1, dn0, dn1, seam4, lane, inv_j, e);
             } else if (j == 1) {
                 if (en)
-                    stencil_term<kFinal, true, N>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
+                    stencil_term<kFinal, true, N, REV>(P, Q, V4, nJr, nJc, up0, up1, dn0, dn1, seam4, lane, inv_j, e);
                 else
-                    stencil_term<kFinal, false, N>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
+                    stencil_term<kFinal, false, N, REV>(P, Q, V4, nJr, nJc, up0, up1, dn0, dn1, seam4, lane, inv_j, e);
             } else if (en) {
-                stencil_term<kHorner, true, N>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
+                stencil_term<kHorner, true, N, REV>(P, Q, V4, nJr, nJc, up0, up1, dn0, dn1, seam4, lane, inv_j, e);
             } else {
-                stencil_term<kHorner, false, N>(P, Q, V, nJr, nJc, up0, up1, dn0, dn1, seam, lane, inv_j, e);
+                stencil_term<kHorner, false, N, REV>(P, Q, V4, nJr, nJc, up0, up1, dn0, dn1, seam4, lane, inv_j, e);
             }
             if (en || last) {
                 const float es = warp_sum(e);
                 if (lane == 0) atomicAdd(a.energy + obs * a.tab.R + r, (double)es * (double)a.inv_dt);
             }
             ++tc;
+        };
+        if (last) {
+            term(std::false_type(), K);
+        } else {
+            for (int j = K; j >= 1; --j) term(std::false_type(), j);
         }
         if (sample) ++obs;
         if (last) break;
@@ -410,8 +467,8 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
                 h4.w += P[i][1].y;
             }
             *hp = h4;
-            P[i][0] = Q[i][0] = make_float2(h4.x, h4.y);
-            P[i][1] = Q[i][1] = make_float2(h4.z, h4.w);
+            P[i][0] = make_float2(h4.x, h4.y);
+            P[i][1] = make_float2(h4.z, h4.w);
         }
     }
 
@@ -441,7 +498,7 @@ FusedShape make_shape() {
     f.threads = 32 * W;
     f.smem = sizeof(float2) * ((size_t)2 * SR * N + (size_t)2 * 2 * N + (size_t)2 * BPC * 2 * N +
                                (size_t)2 * W * 2 * RL) +
-             sizeof(float) * ((size_t)SR * N + (size_t)N);
+             sizeof(float) * ((size_t)SR * N + (size_t)N);   // diagonal (as float4 [SR/2][N/2]) + pacc
     f.kern = taylor_fused_kernel<N, BPC, MINB>;
     return f;
 }
