@@ -201,6 +201,38 @@ int ctqw_ensemble_observables(const ctqw_hamiltonian *h, int32_t dtype, const vo
                               double *energy_dev, void *stream);
 
 /*
+ * Workspace bytes of ctqw_adjoint_grad: (ceil(n_steps / checkpoint_every) +
+ * checkpoint_every + K + 7) states plus 2 p_width doubles.
+ */
+int ctqw_adjoint_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t K,
+                                int64_t n_steps, int32_t checkpoint_every, size_t *bytes);
+
+/*
+ * Loss on the ensemble-averaged occupations at T = n_steps dt and its exact
+ * gradient through the discrete Taylor propagation (Sec. 2.3, Algorithm 3):
+ *   loss = sum_x (Pbar(x, T) - P_target(x))^2   (sum over the size groups)
+ * grad_eps_dev / grad_J_dev ([sum_r N_r] FP64, laid out like ctqw_get_params)
+ * receive dloss/deps_{r,i} and dloss/dJ_{r,b} of every realization; sum them
+ * over realizations for the gradient with respect to shared means (the
+ * rounding of the disorder to float32 is passed straight through).
+ * psi0_dev: initial states (not modified).  P_target_dev: [p_width] FP64.
+ * loss_dev: [1] FP64.  P_final_dev: [p_width] FP64 or NULL.
+ * Method: forward pass storing psi every checkpoint_every steps, then per
+ * segment a replay from its checkpoint and the reverse sweep
+ *   lambda_T = g psi_T,  g(s) = dloss/d|psi(s)|^2,  lambda_n = T^dagger lambda_{n+1},
+ *   grad += 2 Re sum_{a<K} <mu_a, dH phi_a>,  phi_a = H^a psi_n,
+ *   mu_{K-1} = conj(c_K) lambda_{n+1},  mu_a = conj(c_{a+1}) lambda_{n+1} + H mu_{a+1},
+ * with c_k = (-i dt)^k / k!.  States in `dtype` (c64: FP32 states), all
+ * gradient accumulation in FP64.  Needs the workspace of
+ * ctqw_adjoint_workspace_size.  Asynchronous.
+ */
+int ctqw_adjoint_grad(const ctqw_hamiltonian *h, int32_t dtype, const void *psi0_dev, double dt,
+                      int32_t K, int64_t n_steps, int32_t checkpoint_every,
+                      const double *P_target_dev, double *loss_dev, double *grad_eps_dev,
+                      double *grad_J_dev, double *P_final_dev, void *workspace_dev,
+                      size_t workspace_bytes, void *stream);
+
+/*
  * Synchronize `stream` and report whether a kernel of an earlier call on this
  * handle gave up a bounded wait (the fused kernel waits for halo rows from
  * its neighbour CTAs with a 2 s limit; it never spins unbounded).  Returns

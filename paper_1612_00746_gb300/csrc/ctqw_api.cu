@@ -63,6 +63,42 @@ int check_common(const ctqw_hamiltonian *h, int dtype, const void *psi, double d
         if (_st != CTQW_OK) return _st; \
     } while (0)
 
+// out = T in with T the order-K Taylor polynomial of exp(-i H dt)
+// (Algorithm 3 with one launch per term); phiA, phiB scratch states.
+int taylor_step_plain(const ctqw_hamiltonian *h, int dtype, const void *in, void *out, void *phiA,
+                      void *phiB, double dt, int K, cudaStream_t s) {
+    const void *src = in;
+    void *dst = phiA;
+    for (int j = 1; j <= K; ++j) {
+        int st = launch_taylor_term(h, dtype, src, dst, in, out, dt / j, j == 1, s);
+        if (st != CTQW_OK) return st;
+        src = dst;
+        dst = (dst == phiA) ? phiB : phiA;
+    }
+    return CTQW_OK;
+}
+
+struct AdjointLayout {
+    int64_t n_ck = 0;
+    size_t state = 0, total = 0;
+    size_t off_ck = 0, off_seg = 0, off_phi = 0, off_misc = 0, off_dbl = 0;
+};
+
+// Workspace: checkpoints every M steps, one segment of M replayed states,
+// phi_1..phi_{K-1}, 8 scratch states, then Pbar and diff (FP64).
+AdjointLayout adjoint_layout(const ctqw_hamiltonian *h, int dtype, int K, int64_t n_steps, int M) {
+    AdjointLayout L;
+    L.state = (size_t)h->total_amp * elem_bytes(dtype);
+    L.n_ck = n_steps > 0 ? (n_steps - 1) / M + 1 : 1;
+    L.off_ck = 0;
+    L.off_seg = L.off_ck + (size_t)L.n_ck * L.state;
+    L.off_phi = L.off_seg + (size_t)M * L.state;
+    L.off_misc = L.off_phi + (size_t)(K > 1 ? K - 1 : 0) * L.state;
+    L.off_dbl = L.off_misc + 8 * L.state;
+    L.total = L.off_dbl + 2 * sizeof(double) * (size_t)h->p_width;
+    return L;
+}
+
 }  // namespace
 
 void ctqw_set_error(const char *fmt, ...) {
@@ -390,6 +426,102 @@ int ctqw_check_status(const ctqw_hamiltonian *h, void *stream) {
         CTQW_CUDA_TRY(cudaMemset(h->status_d, 0, sizeof(int)));
         ctqw_set_error("a bounded wait inside a propagation kernel gave up; results of that call are invalid");
         return CTQW_ETIMEOUT;
+    }
+    return CTQW_OK;
+}
+
+int ctqw_adjoint_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t K,
+                                int64_t n_steps, int32_t checkpoint_every, size_t *bytes) {
+    if (!h || !bytes) { ctqw_set_error("null argument"); return CTQW_EINVAL; }
+    if (dtype != CTQW_C64 && dtype != CTQW_C128) { ctqw_set_error("dtype %d", dtype); return CTQW_EINVAL; }
+    if (K < 1 || K > 30 || n_steps < 0 || checkpoint_every < 1) {
+        ctqw_set_error("bad K / n_steps / checkpoint_every");
+        return CTQW_EINVAL;
+    }
+    *bytes = adjoint_layout(h, dtype, K, n_steps, checkpoint_every).total;
+    return CTQW_OK;
+}
+
+int ctqw_adjoint_grad(const ctqw_hamiltonian *h, int32_t dtype, const void *psi0_dev, double dt,
+                      int32_t K, int64_t n_steps, int32_t checkpoint_every,
+                      const double *P_target_dev, double *loss_dev, double *grad_eps_dev,
+                      double *grad_J_dev, double *P_final_dev, void *workspace_dev,
+                      size_t workspace_bytes, void *stream) {
+    CTQW_TRY(check_common(h, dtype, psi0_dev, dt, n_steps, 0));
+    if (K < 1 || K > 30) { ctqw_set_error("K must be in 1..30 (got %d)", K); return CTQW_EINVAL; }
+    if (checkpoint_every < 1) { ctqw_set_error("checkpoint_every must be >= 1"); return CTQW_EINVAL; }
+    if (!P_target_dev || !loss_dev || !grad_eps_dev || !grad_J_dev) {
+        ctqw_set_error("null target / loss / gradient pointer");
+        return CTQW_EINVAL;
+    }
+    const int M = checkpoint_every;
+    const AdjointLayout L = adjoint_layout(h, dtype, K, n_steps, M);
+    if (!workspace_dev || workspace_bytes < L.total) {
+        ctqw_set_error("adjoint needs a workspace of %zu bytes (got %zu)", L.total, workspace_bytes);
+        return CTQW_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    char *ws = (char *)workspace_dev;
+    auto ck = [&](int64_t c) { return (void *)(ws + L.off_ck + (size_t)c * L.state); };
+    auto seg = [&](int64_t k) { return (void *)(ws + L.off_seg + (size_t)k * L.state); };
+    auto phi = [&](int a) { return (void *)(ws + L.off_phi + (size_t)(a - 1) * L.state); };
+    void *misc[8];
+    for (int q = 0; q < 8; ++q) misc[q] = ws + L.off_misc + (size_t)q * L.state;
+    void *X = misc[0], *Y = misc[1], *tA = misc[2], *tB = misc[3];
+    void *lam = misc[4], *lam2 = misc[5], *muA = misc[6], *muB = misc[7];
+    double *Pbar = (double *)(ws + L.off_dbl);
+    double *diff = Pbar + h->p_width;
+
+    CTQW_CUDA_TRY(cudaMemsetAsync(grad_eps_dev, 0, sizeof(double) * h->total_par, s));
+    CTQW_CUDA_TRY(cudaMemsetAsync(grad_J_dev, 0, sizeof(double) * h->total_par, s));
+    CTQW_CUDA_TRY(cudaMemsetAsync(Pbar, 0, sizeof(double) * h->p_width, s));
+
+    // forward pass with checkpoints psi_{cM}
+    CTQW_CUDA_TRY(cudaMemcpyAsync(X, psi0_dev, L.state, cudaMemcpyDeviceToDevice, s));
+    void *cur = X, *nxt = Y;
+    for (int64_t n = 0; n < n_steps; ++n) {
+        if (n % M == 0) CTQW_CUDA_TRY(cudaMemcpyAsync(ck(n / M), cur, L.state, cudaMemcpyDeviceToDevice, s));
+        CTQW_TRY(taylor_step_plain(h, dtype, cur, nxt, tA, tB, dt, K, s));
+        std::swap(cur, nxt);
+    }
+    // loss at T and the terminal adjoint state
+    CTQW_TRY(launch_observables(h, dtype, cur, Pbar, nullptr, nullptr, nullptr, s));
+    CTQW_TRY(launch_loss(Pbar, P_target_dev, h->p_width, diff, loss_dev, s));
+    if (P_final_dev)
+        CTQW_CUDA_TRY(cudaMemcpyAsync(P_final_dev, Pbar, sizeof(double) * h->p_width,
+                                      cudaMemcpyDeviceToDevice, s));
+    CTQW_TRY(launch_lambda_init(h, dtype, cur, diff, lam, s));
+
+    // conj(c_k) = (i dt)^k / k!
+    double cre[31], cim[31];
+    {
+        double mag = 1.0;
+        for (int k = 0; k <= K; ++k) {
+            if (k > 0) mag *= dt / k;
+            const int q = k & 3;   // i^k = 1, i, -1, -i
+            cre[k] = (q == 0) ? mag : (q == 2 ? -mag : 0.0);
+            cim[k] = (q == 1) ? mag : (q == 3 ? -mag : 0.0);
+        }
+    }
+    // backward over the segments, replaying each from its checkpoint
+    for (int64_t c = L.n_ck - 1; c >= 0 && n_steps > 0; --c) {
+        const int64_t n0 = c * M, n1 = std::min<int64_t>(n0 + M, n_steps);
+        for (int64_t k = 1; k < n1 - n0; ++k)
+            CTQW_TRY(taylor_step_plain(h, dtype, k == 1 ? ck(c) : seg(k - 1), seg(k), tA, tB, dt, K, s));
+        for (int64_t n = n1 - 1; n >= n0; --n) {
+            const void *psi_n = (n == n0) ? ck(c) : seg(n - n0);
+            for (int a = 1; a < K; ++a) CTQW_TRY(launch_apply_h(h, dtype, a == 1 ? psi_n : phi(a - 1), phi(a), s));
+            // mu_{K-1} = conj(c_K) lambda;  mu_a = conj(c_{a+1}) lambda + H mu_{a+1}
+            void *mu = muA, *mu_prev = muB;
+            for (int a = K - 1; a >= 0; --a) {
+                CTQW_TRY(launch_mu(h, dtype, mu_prev, lam, mu, cre[a + 1], cim[a + 1], a == K - 1, s));
+                CTQW_TRY(launch_grad(h, dtype, mu, a == 0 ? psi_n : phi(a), grad_eps_dev, grad_J_dev, s));
+                std::swap(mu, mu_prev);
+            }
+            // lambda_n = T^dagger lambda_{n+1} (the Taylor polynomial of exp(+i H dt))
+            CTQW_TRY(taylor_step_plain(h, dtype, lam, lam2, tA, tB, -dt, K, s));
+            std::swap(lam, lam2);
+        }
     }
     return CTQW_OK;
 }

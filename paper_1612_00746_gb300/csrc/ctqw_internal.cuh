@@ -98,6 +98,18 @@ int launch_rk4_stage(const ctqw_hamiltonian *h, int dtype, const void *in, void 
 int launch_observables(const ctqw_hamiltonian *h, int dtype, const void *psi, double *P_mean,
                        double *P_joint, double *norm, double *energy, cudaStream_t s);
 
+// Adjoint pieces: out = H in; out = H in + c lam (first: c lam);
+// 2 Re <mu, dH phi> into per-realization gradients; loss and lambda_T.
+int launch_apply_h(const ctqw_hamiltonian *h, int dtype, const void *in, void *out, cudaStream_t s);
+int launch_mu(const ctqw_hamiltonian *h, int dtype, const void *in, const void *lam, void *out,
+              double cre, double cim, int first, cudaStream_t s);
+int launch_grad(const ctqw_hamiltonian *h, int dtype, const void *mu, const void *phi,
+                double *grad_eps, double *grad_J, cudaStream_t s);
+int launch_loss(const double *Pbar, const double *target, int64_t n, double *diff, double *loss,
+                cudaStream_t s);
+int launch_lambda_init(const ctqw_hamiltonian *h, int dtype, const void *psi, const double *diff,
+                       void *lam, cudaStream_t s);
+
 // Fused cluster-resident Taylor propagation (m = 2, c64).
 bool fused_taylor_supported(const ctqw_hamiltonian *h, int dtype);
 int launch_taylor_fused(const ctqw_hamiltonian *h, void *psi, double dt, int K, int64_t n_steps,

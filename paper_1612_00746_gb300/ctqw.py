@@ -35,7 +35,7 @@ EXPORTED = (
     "ctqw_build_hamiltonian", "ctqw_destroy_hamiltonian", "ctqw_get_params", "ctqw_state_size",
     "ctqw_output_layout", "ctqw_init_state", "ctqw_workspace_size", "ctqw_propagate_taylor",
     "ctqw_propagate_rk4", "ctqw_ensemble_observables", "ctqw_check_status", "ctqw_last_error",
-    "ctqw_version",
+    "ctqw_version", "ctqw_adjoint_workspace_size", "ctqw_adjoint_grad",
 )
 
 
@@ -86,6 +86,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "ctqw_propagate_rk4": [vp, i32, vp, dbl, i64, i32, vp, vp, vp, u32, vp, sz, vp],
         "ctqw_ensemble_observables": [vp, i32, vp, vp, vp, vp, vp, vp],
         "ctqw_check_status": [vp, vp],
+        "ctqw_adjoint_workspace_size": [vp, i32, i32, i64, i32, ctypes.POINTER(sz)],
+        "ctqw_adjoint_grad": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, vp, vp, vp, sz, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -249,6 +251,60 @@ def ctqw_ensemble_observables(h: Hamiltonian, psi: torch.Tensor, dtype: int, P_m
 
 def ctqw_check_status(h: Hamiltonian, stream=None) -> None:
     _check(load().ctqw_check_status(h.handle, _stream(stream)))
+
+
+def ctqw_adjoint_grad(h: Hamiltonian, psi0: torch.Tensor, dtype: int, dt: float, K: int,
+                      n_steps: int, checkpoint_every: int, P_target: torch.Tensor, stream=None):
+    """Loss on Pbar(x, T) and its gradient w.r.t. every realization's eps and J.
+
+    Returns (loss [1], grad_eps [sum N], grad_J [sum N], P_final [p_width]) as
+    FP64 device tensors (ctqw_adjoint_grad).
+    """
+    dev = psi0.device
+    b = ctypes.c_size_t()
+    _check(load().ctqw_adjoint_workspace_size(h.handle, dtype, int(K), int(n_steps),
+                                              int(checkpoint_every), ctypes.byref(b)))
+    ws = torch.empty(b.value, dtype=torch.uint8, device=dev)
+    n = int(h.sizes.sum())
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+    ge = torch.empty(n, dtype=torch.float64, device=dev)
+    gJ = torch.empty(n, dtype=torch.float64, device=dev)
+    Pf = torch.empty(h.p_width, dtype=torch.float64, device=dev)
+    tgt = P_target.to(device=dev, dtype=torch.float64).contiguous()
+    _check(load().ctqw_adjoint_grad(h.handle, dtype, _ptr(psi0), float(dt), int(K), int(n_steps),
+                                    int(checkpoint_every), _ptr(tgt), _ptr(loss), _ptr(ge), _ptr(gJ),
+                                    _ptr(Pf), _ptr(ws), ws.numel(), _stream(stream)))
+    return loss, ge, gJ, Pf
+
+
+class EnsembleOccupationLoss(torch.autograd.Function):
+    """loss = sum_x (Pbar(x, T) - P_target(x))^2 as a function of the mean on-site
+    energies and hoppings shared by all realizations (each realization adds its
+    own disorder drawn from the uniform draws of the workload).
+
+    forward(eps_mean [N], J_mean [N], w, P_target [N], dtype, checkpoint_every)
+    runs the CUDA adjoint once and keeps the gradients for backward.
+    """
+
+    @staticmethod
+    def forward(ctx, eps_mean, J_mean, w, P_target, dtype=C64, checkpoint_every=50):
+        em = eps_mean.detach().to("cpu", torch.float64).numpy()
+        jm = J_mean.detach().to("cpu", torch.float64).numpy()
+        h = build_for_workload(w, eps_mean=em, J_mean=jm)
+        psi = h.new_state(dtype, P_target.device if P_target.is_cuda else "cuda")
+        ctqw_init_state(h, psi, initial_sites(w, h), dtype)
+        loss, ge, gJ, _ = ctqw_adjoint_grad(h, psi, dtype, w.dt, w.K, w.n_steps, checkpoint_every,
+                                            P_target)
+        N = int(h.sizes[0])
+        ctx.save_for_backward(ge.view(h.R, N).sum(0).to(eps_mean.device, eps_mean.dtype),
+                              gJ.view(h.R, N).sum(0).to(J_mean.device, J_mean.dtype))
+        h.close()
+        return loss[0].to(eps_mean.device, eps_mean.dtype)
+
+    @staticmethod
+    def backward(ctx, g):
+        ge, gJ = ctx.saved_tensors
+        return g * ge, g * gJ, None, None, None, None
 
 
 def ctqw_version() -> str:

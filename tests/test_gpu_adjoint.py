@@ -1,0 +1,124 @@
+"""Adjoint gradient (ctqw_adjoint_grad) against the FP64 oracle's discrete adjoint,
+against central differences of the GPU's own loss, and checkpoint invariance."""
+import numpy as np
+import pytest
+
+import ctqw_workloads as cw
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctqw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_00746_gb300 import build, ctqw as c
+
+    build.build()
+    c.load()
+    return c
+
+
+def _workload(m=2, N=6, R=2, periodic=False, K=8, n_steps=12, dt=0.05, U=1.0, stats=0):
+    sites = (1, 3) if m == 2 else (0, 1, 2)
+    return cw.Workload(name="adj", m=m, statistics=stats, periodic=periodic, N=N, R=R, J0=1.0, U=U,
+                       eps_halfwidth=0.5, J_halfwidth=0.2, sites=sites, dt=dt, K=K,
+                       n_steps=n_steps, obs_every=0, dtype=cw.C128, seed=3)
+
+
+def _gpu(ctqw, w, dtype, target, M=5, eps_mean=None, J_mean=None, round_to_f32=True):
+    h = ctqw.build_for_workload(w, eps_mean=eps_mean, J_mean=J_mean, round_to_f32=round_to_f32)
+    psi = h.new_state(dtype)
+    ctqw.ctqw_init_state(h, psi, ctqw.initial_sites(w, h), dtype)
+    loss, ge, gJ, Pf = ctqw.ctqw_adjoint_grad(h, psi, dtype, w.dt, w.K, w.n_steps, M,
+                                              torch.tensor(target))
+    ctqw.ctqw_check_status(h)
+    eps, J = h.params()
+    h.close()
+    return (float(loss.item()), ge.cpu().numpy().reshape(w.R, w.N), gJ.cpu().numpy().reshape(w.R, w.N),
+            Pf.cpu().numpy(), eps.reshape(w.R, w.N), J.reshape(w.R, w.N))
+
+
+def _oracle(w, eps, J, target):
+    nb = w.N if w.periodic else w.N - 1
+    psi0 = oracle.initial_state(w.N, w.m, w.sites, w.statistics)
+    return oracle.loss_and_adjoint_gradient([e for e in eps], [j[:nb] for j in J], w.N, w.m,
+                                            w.periodic, w.U, psi0, w.dt, w.K, w.n_steps, target)
+
+
+@pytest.mark.parametrize("m,N,periodic,K", [(2, 6, False, 8), (2, 5, True, 7), (3, 4, True, 6)])
+def test_adjoint_fp64_matches_oracle(ctqw, m, N, periodic, K):
+    w = _workload(m=m, N=N, periodic=periodic, K=K)
+    target = np.random.default_rng(1).dirichlet(np.ones(N))
+    loss, ge, gJ, Pf, eps, J = _gpu(ctqw, w, cw.C128, target)
+    lo, ge_o, gJ_o = _oracle(w, eps, J, target)
+    assert abs(loss - lo) <= 1e-13 * max(1.0, abs(lo))
+    scale = max(np.max(np.abs(ge_o)), np.max(np.abs(gJ_o)))
+    nb = N if periodic else N - 1
+    assert np.max(np.abs(ge - ge_o)) <= 1e-11 * scale
+    assert np.max(np.abs(gJ[:, :nb] - gJ_o)) <= 1e-11 * scale
+    if not periodic:
+        assert np.all(gJ[:, N - 1] == 0.0)
+
+
+def test_adjoint_checkpoint_spacing_does_not_change_result(ctqw):
+    w = _workload(n_steps=13)
+    target = np.full(w.N, 1.0 / w.N)
+    ref = _gpu(ctqw, w, cw.C128, target, M=1)
+    for M in (2, 5, 13, 40):
+        got = _gpu(ctqw, w, cw.C128, target, M=M)
+        assert abs(got[0] - ref[0]) < 1e-15
+        assert np.max(np.abs(got[1] - ref[1])) < 1e-13
+        assert np.max(np.abs(got[2] - ref[2])) < 1e-13
+
+
+def test_adjoint_fp32_states_fp64_accumulation(ctqw):
+    w = _workload(N=8, R=3, n_steps=40, K=10)
+    target = np.random.default_rng(2).dirichlet(np.ones(w.N))
+    loss, ge, gJ, Pf, eps, J = _gpu(ctqw, w, cw.C64, target)
+    lo, ge_o, gJ_o = _oracle(w, eps, J, target)
+    scale = max(np.max(np.abs(ge_o)), np.max(np.abs(gJ_o)))
+    assert abs(loss - lo) <= 1e-6 * max(1.0, lo)
+    assert np.max(np.abs(ge - ge_o)) <= 1e-5 * scale
+    assert np.max(np.abs(gJ[:, :w.N - 1] - gJ_o)) <= 1e-5 * scale
+
+
+def test_adjoint_against_central_differences_of_gpu_loss(ctqw):
+    """Gradient w.r.t. shared means (sum over realizations) vs central FD (h = 1e-4)
+    of the GPU's own FP64 loss, without float32 rounding of the parameters."""
+    w = _workload(N=6, R=2, n_steps=10, K=8)
+    rng = np.random.default_rng(4)
+    em = rng.uniform(-0.3, 0.3, w.N)
+    jm = 1.0 + rng.uniform(-0.1, 0.1, w.N)
+    target = rng.dirichlet(np.ones(w.N))
+    _, ge, gJ, *_ = _gpu(ctqw, w, cw.C128, target, eps_mean=em, J_mean=jm, round_to_f32=False)
+    h_fd = 1e-4
+    for i in (0, 2, 5):
+        ep, emn = em.copy(), em.copy()
+        ep[i] += h_fd
+        emn[i] -= h_fd
+        fd = (_gpu(ctqw, w, cw.C128, target, eps_mean=ep, J_mean=jm, round_to_f32=False)[0] -
+              _gpu(ctqw, w, cw.C128, target, eps_mean=emn, J_mean=jm, round_to_f32=False)[0]) / (2 * h_fd)
+        assert abs(fd - ge[:, i].sum()) <= 1e-8 * max(1.0, abs(fd))
+    for b in (0, 3):
+        jp, jmn = jm.copy(), jm.copy()
+        jp[b] += h_fd
+        jmn[b] -= h_fd
+        fd = (_gpu(ctqw, w, cw.C128, target, eps_mean=em, J_mean=jp, round_to_f32=False)[0] -
+              _gpu(ctqw, w, cw.C128, target, eps_mean=em, J_mean=jmn, round_to_f32=False)[0]) / (2 * h_fd)
+        assert abs(fd - gJ[:, b].sum()) <= 1e-8 * max(1.0, abs(fd))
+
+
+def test_autograd_function_returns_summed_gradients(ctqw):
+    w = _workload(N=6, R=3, n_steps=8, K=8)
+    em = torch.zeros(w.N, dtype=torch.float64, requires_grad=True)
+    jm = torch.ones(w.N, dtype=torch.float64, requires_grad=True)
+    target = torch.full((w.N,), 1.0 / w.N, dtype=torch.float64, device="cuda")
+    loss = ctqw.EnsembleOccupationLoss.apply(em, jm, w, target, cw.C128, 4)
+    loss.backward()
+    _, ge, gJ, *_ = _gpu(ctqw, w, cw.C128, target.cpu().numpy(), M=4,
+                         eps_mean=np.zeros(w.N), J_mean=np.ones(w.N))
+    np.testing.assert_allclose(em.grad.numpy(), ge.sum(0), atol=1e-14)
+    np.testing.assert_allclose(jm.grad.numpy(), gJ.sum(0), atol=1e-14)
