@@ -149,6 +149,24 @@ def measured_peaks():
         return {}
 
 
+def fused_traffic(workload: str):
+    """DRAM bytes per launch of the fused kernel from the committed ncu capture,
+    or None when the kernel source changed since the counters were taken."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "taylor_fused_traffic.json")) as f:
+            rec = json.load(f)
+        src = os.path.join(ROOT, "paper_1612_00746_gb300", "csrc", "k_fused.cu")
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(workload)
+    if not ent or ent.get("source_sha256") != digest:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -381,7 +399,8 @@ def run_ours(args):
                    "parallelism": f"realizations sharded, {world} rank(s)"},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": fused_traffic(w.name) if not (args.realizations or args.n_steps) else None,
                      "kernel": "taylor_fused_kernel", "kernel_ms": kernel_ms,
                      "flops_per_site_update": flops_per_unit,
                      "peak_basis": "152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz (derived)",
