@@ -201,6 +201,29 @@ int ctqw_ensemble_observables(const ctqw_hamiltonian *h, int32_t dtype, const vo
                               double *energy_dev, void *stream);
 
 /*
+ * ctqw_propagate_taylor on the per-term path for callers that cannot
+ * allocate device memory (the paper has no counterpart).  Such callers
+ * include code running while a CUDA graph is captured, loops that must not
+ * call cudaMalloc because it can synchronize the device, and plugins whose
+ * host program owns the device-memory budget.  Instead of a caller-provided
+ * workspace, the three scratch states live in one statically sized device
+ * array of 48 MiB inside this library (held on every GPU that loads it until
+ * the process exits): 3 x amplitudes_total x 8 bytes (CTQW_C64) or x 16
+ * bytes (CTQW_C128) must fit, else CTQW_EINVAL with a message and nothing
+ * launched.  The call allocates and frees nothing.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the one array, so calls whose work overlaps on the GPU
+ * (e.g. on two streams) race and give wrong results; serialise them.
+ * Arguments, outputs and results are those of ctqw_propagate_taylor with
+ * CTQW_FLAG_PLAIN.  Asynchronous.
+ */
+int ctqw_propagate_taylor_noalloc(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev,
+                                  double dt, int32_t K, int64_t n_steps, int32_t obs_every,
+                                  double *P_mean_dev, double *norm_dev, double *energy_dev,
+                                  void *stream);
+
+/*
  * Workspace bytes of ctqw_adjoint_grad: (ceil(n_steps / checkpoint_every) +
  * checkpoint_every + K + 7) states plus 2 p_width doubles.
  */
