@@ -59,9 +59,11 @@ extern "C" {
 #define CTQW_FLAG_NO_COMPENSATION 0x2  /* c64 fused path: plain FP32 state update (no carried error term) */
 #define CTQW_FLAG_TEST_WAIT_TIMEOUT 0x8 /* failure-path test: the fused kernel first waits on an mbarrier that
                                            nothing completes, gives up after 1 ms and flags the handle */
-/* Fused path tuning: CTQW_FUSED_SHAPE(k) selects the k-th compiled CTA/cluster
- * shape for the lattice size (0 = default; 1 = more warps per CTA and fewer
- * CTAs per cluster; 2 = default split with registers uncapped, one CTA per SM).
+/* Fused path tuning: CTQW_FUSED_SHAPE(k) selects a compiled CTA/cluster shape
+ * for the lattice size.  k = 0..2: full-row kernel (each warp owns whole rows;
+ * 0 = default, 1 = twice the warps per CTA and half the CTAs per cluster,
+ * 2 = the default split with registers capped for two CTAs per SM instead of
+ * three); k = 4..6: the banded kernel (warps share rows), its shapes 0..2.
  * An index with no compiled shape returns CTQW_EUNSUPPORTED. */
 #define CTQW_FUSED_SHAPE_SHIFT 8
 #define CTQW_FUSED_SHAPE(k) (((uint32_t)(k) & 0xFu) << CTQW_FUSED_SHAPE_SHIFT)

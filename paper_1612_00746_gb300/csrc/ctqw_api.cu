@@ -324,7 +324,7 @@ int ctqw_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t method
                         size_t *bytes) {
     if (!h || !bytes) { ctqw_set_error("null argument"); return CTQW_EINVAL; }
     if (dtype != CTQW_C64 && dtype != CTQW_C128) { ctqw_set_error("dtype %d", dtype); return CTQW_EINVAL; }
-    const bool fused = method == 0 && !(flags & CTQW_FLAG_PLAIN) && fused_taylor_supported(h, dtype);
+    const bool fused = method == 0 && !(flags & CTQW_FLAG_PLAIN) && fused_rows_supported(h, dtype);
     *bytes = fused ? 0 : 3 * (size_t)h->total_amp * elem_bytes(dtype);
     return CTQW_OK;
 }
@@ -337,7 +337,7 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
     if (K < 1 || K > 30) { ctqw_set_error("K must be in 1..30 (got %d)", K); return CTQW_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n_obs = n_samples(n_steps, obs_every);
-    const bool fused = !(flags & CTQW_FLAG_PLAIN) && fused_taylor_supported(h, dtype);
+    const bool fused = !(flags & CTQW_FLAG_PLAIN) && fused_rows_supported(h, dtype);
     if (!fused) {
         const size_t need = 3 * (size_t)h->total_amp * elem_bytes(dtype);
         if (!workspace_dev || workspace_bytes < need) {
@@ -346,11 +346,17 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
         }
     }
     CTQW_TRY(zero_outputs(h, n_obs, P_mean_dev, norm_dev, energy_dev, s));
-    if (fused)
+    if (fused) {
+        // shape index 0..3: full-row kernel; 4..7: the banded kernel (shape - 4)
+        const int shape = (int)((flags >> CTQW_FUSED_SHAPE_SHIFT) & 0xF);
+        const int comp = (flags & CTQW_FLAG_NO_COMPENSATION) ? 0 : 1;
+        const int test = (flags & CTQW_FLAG_TEST_WAIT_TIMEOUT) ? 1 : 0;
+        if (shape < 4)
+            return launch_taylor_fused_rows(h, psi_dev, dt, K, n_steps, obs_every, P_mean_dev,
+                                            norm_dev, energy_dev, comp, shape, test, s);
         return launch_taylor_fused(h, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
-                                   energy_dev, (flags & CTQW_FLAG_NO_COMPENSATION) ? 0 : 1,
-                                   (int)((flags >> CTQW_FUSED_SHAPE_SHIFT) & 0xF),
-                                   (flags & CTQW_FLAG_TEST_WAIT_TIMEOUT) ? 1 : 0, s);
+                                   energy_dev, comp, shape - 4, test, s);
+    }
 
     const size_t sb = (size_t)h->total_amp * elem_bytes(dtype);
     char *ws = (char *)workspace_dev;

@@ -110,7 +110,14 @@ int launch_loss(const double *Pbar, const double *target, int64_t n, double *dif
 int launch_lambda_init(const ctqw_hamiltonian *h, int dtype, const void *psi, const double *diff,
                        void *lam, cudaStream_t s);
 
-// Fused cluster-resident Taylor propagation (m = 2, c64).
+// Fused cluster-resident Taylor propagation (m = 2, c64), full-row layout.
+bool fused_rows_supported(const ctqw_hamiltonian *h, int dtype);
+int launch_taylor_fused_rows(const ctqw_hamiltonian *h, void *psi, double dt, int K,
+                             int64_t n_steps, int obs_every, double *P_mean, double *norm,
+                             double *energy, int compensated, int shape, int test_timeout,
+                             cudaStream_t s);
+
+// Fused cluster-resident Taylor propagation (m = 2, c64), multi-warp bands.
 bool fused_taylor_supported(const ctqw_hamiltonian *h, int dtype);
 int launch_taylor_fused(const ctqw_hamiltonian *h, void *psi, double dt, int K, int64_t n_steps,
                         int obs_every, double *P_mean, double *norm, double *energy,

@@ -1,0 +1,124 @@
+// Device helpers shared by the fused propagation kernels: cluster rank and
+// barrier, shared-memory addressing across the cluster, mbarrier arrivals and
+// bounded waits, st.async pushes into a neighbour CTA, and the compensated
+// (TwoSum / FastTwoSum) state update.
+#pragma once
+
+#include <cstdint>
+
+#include "ctqw_internal.cuh"
+
+namespace fused {
+
+// (static: each translation unit keeps its own copy)
+
+static __device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Full cluster barrier (used at the start and the end of the kernel only).
+static __device__ __forceinline__ void cluster_barrier() {
+    __syncwarp();
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+static __device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+static __device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+static __device__ __forceinline__ void mbar_init(uint32_t mb, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count) : "memory");
+}
+
+static __device__ __forceinline__ void mbar_expect_tx(uint32_t mb, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes)
+                 : "memory");
+}
+
+// Arrival + expected bytes on two mbarriers, from the threads with flag != 0 only (no branch).
+static __device__ __forceinline__ void mbar_expect_tx2_if(uint32_t mb0, uint32_t mb1, uint32_t bytes, int flag) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %3, 0;\n\t"
+                 "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %2;\n\t"
+                 "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n\t}"
+                 ::"r"(mb0), "r"(mb1), "r"(bytes), "r"(flag) : "memory");
+}
+
+// 16-byte store into another CTA's shared memory, counted on its mbarrier.
+static __device__ __forceinline__ void st_async16(uint32_t raddr, float4 v, uint32_t rmbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+                 ::"r"(raddr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rmbar) : "memory");
+}
+
+static __device__ __forceinline__ bool mbar_try_wait(uint32_t mb, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(mb), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+static __device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of parity `parity` of mbarrier `mb`, giving up after
+// limit_ns of global time: then the status word is set and false returned.
+static __device__ __noinline__ bool mbar_wait_slow(uint32_t mb, uint32_t parity,
+                                            unsigned long long limit_ns, int *status) {
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try_wait(mb, parity)) return true;
+        if ((it & 255u) == 0 && global_ns() - t0 > limit_ns) {
+            atomicOr(status, 1);
+            return false;
+        }
+    }
+}
+
+static __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mb, uint32_t parity,
+                                                  unsigned long long limit_ns, int *status) {
+    return mbar_try_wait(mb, parity) || mbar_wait_slow(mb, parity, limit_ns, status);
+}
+
+static __device__ __forceinline__ float2 ffma2(float a, float2 b, float2 c) {
+    return __ffma2_rn(make_float2(a, a), b, c);
+}
+
+// (re, im) pair moved between lanes as one 64-bit value.
+static __device__ __forceinline__ float2 shfl2(float2 v, int src) {
+    const unsigned long long u = __shfl_sync(0xffffffffu, *reinterpret_cast<unsigned long long *>(&v), src);
+    return *reinterpret_cast<const float2 *>(&u);
+}
+
+// hi + lo + s rounded back into (hi, lo): TwoSum then FastTwoSum.
+static __device__ __forceinline__ void compensated_add(float &hi, float &lo, float s) {
+    const float t = __fadd_rn(hi, s);
+    const float bb = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(s, bb));
+    const float l = __fadd_rn(err, lo);
+    const float h2 = __fadd_rn(t, l);
+    lo = __fsub_rn(l, __fsub_rn(h2, t));
+    hi = h2;
+}
+
+static __device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+
+}  // namespace fused

@@ -25,8 +25,11 @@
 #include <type_traits>
 
 #include "ctqw_internal.cuh"
+#include "fused_common.cuh"
 
 namespace {
+
+using namespace fused;
 
 constexpr int RL = 8;        // rows per warp band
 constexpr int kMaxK = 30;
@@ -50,91 +53,6 @@ struct FusedArgs {
     int test_timeout;        // wait once on an mbarrier nothing completes (failure-path test)
     float inv_j[kMaxK + 1];  // 1 / j
 };
-
-__device__ __forceinline__ unsigned cluster_rank() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-// Full cluster barrier (used at the start and the end of the kernel only).
-__device__ __forceinline__ void cluster_barrier() {
-    __syncwarp();
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
-                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Address of the same shared-memory location in CTA `rank` of the cluster.
-__device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
-    return r;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t mb, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mb, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes)
-                 : "memory");
-}
-
-// Arrival + expected bytes on two mbarriers, from the threads with flag != 0 only (no branch).
-__device__ __forceinline__ void mbar_expect_tx2_if(uint32_t mb0, uint32_t mb1, uint32_t bytes, int flag) {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %3, 0;\n\t"
-                 "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %2;\n\t"
-                 "@p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%1], %2;\n\t}"
-                 ::"r"(mb0), "r"(mb1), "r"(bytes), "r"(flag) : "memory");
-}
-
-// 16-byte store into another CTA's shared memory, counted on its mbarrier.
-__device__ __forceinline__ void st_async16(uint32_t raddr, float4 v, uint32_t rmbar) {
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
-                 ::"r"(raddr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rmbar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t mb, uint32_t parity) {
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\t"
-                 "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(ok) : "r"(mb), "r"(parity) : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for the phase of parity `parity` of mbarrier `mb`, giving up after
-// limit_ns of global time: then the status word is set and false returned.
-__device__ __noinline__ bool mbar_wait_bounded(uint32_t mb, uint32_t parity,
-                                               unsigned long long limit_ns, int *status) {
-    if (mbar_try_wait(mb, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (unsigned it = 1;; ++it) {
-        if (mbar_try_wait(mb, parity)) return true;
-        if ((it & 255u) == 0 && global_ns() - t0 > limit_ns) {
-            atomicOr(status, 1);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ float2 ffma2(float a, float2 b, float2 c) {
-    return __ffma2_rn(make_float2(a, a), b, c);
-}
-
-__device__ __forceinline__ float2 shfl2(float2 v, int src) {
-    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
-}
 
 // Modes of one stencil application y = (dt H) P on the warp's 8 x 64 block.
 enum { kHorner = 0, kFinal = 1, kEnergyOnly = 2 };
@@ -217,23 +135,6 @@ __device__ __forceinline__ void st_shared_col8_if(uint32_t addr, int flag, const
                    "f"(v[2].x), "f"(v[2].y), "f"(v[3].x), "f"(v[3].y), "f"(v[4].x), "f"(v[4].y),
                    "f"(v[5].x), "f"(v[5].y), "f"(v[6].x), "f"(v[6].y), "f"(v[7].x), "f"(v[7].y)
                  : "memory");
-}
-
-// hi + lo + s rounded back into (hi, lo): TwoSum then FastTwoSum.
-__device__ __forceinline__ void compensated_add(float &hi, float &lo, float s) {
-    const float t = __fadd_rn(hi, s);
-    const float bb = __fsub_rn(t, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(s, bb));
-    const float l = __fadd_rn(err, lo);
-    const float h2 = __fadd_rn(t, l);
-    lo = __fsub_rn(l, __fsub_rn(h2, t));
-    hi = h2;
-}
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 // N sites, BPC warp bands per CTA (compile-time so that every offset is an

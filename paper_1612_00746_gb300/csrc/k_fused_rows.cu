@@ -1,0 +1,497 @@
+// Fused, cluster-resident Taylor propagation for two particles in complex FP32,
+// full-row layout.
+//
+// One thread-block cluster owns one realization for the whole call (the
+// order-K Taylor polynomial of Algorithm 3, Sec. 2.3, applied n_steps times).
+// The N x N tile is split into row slabs, one per CTA; every warp owns RL
+// whole rows and each lane CL = N/32 adjacent columns of them, so a warp
+// covers full rows: neighbours along x2 are in the lane's registers or one
+// 64-bit rotate-shuffle away (the rotation wraps from column N-1 to 0, which
+// is the ring's bond and is multiplied by J[N-1] = 0 on an open chain).
+// Neighbours along x1 are in registers except for the warp's first and last
+// rows, which come from the adjacent warps through shared memory (one
+// __syncthreads per stage) or, at the slab's edges, are pushed by the
+// neighbour CTAs straight into this CTA's shared memory with st.async on an
+// mbarrier (bounded waits).
+//
+// Arithmetic: the same polynomial in Horner form with A = -i dt H applied to
+// (re, im) pairs with FFMA2:
+//   w_K = psi + (A/K) psi,  w_j = psi + (A/j) w_{j+1},  psi(t+dt) = psi + A w_2,
+// (forward FP32 summation would drop every term below half an ulp of the
+// running sum).  The diagonal dt*(eps_x1 + eps_x2) enters as two FFMA2 with
+// a per-row and a per-column pair; dt*U on x1 = x2 is added for the one lane
+// of a row that owns the diagonal.  The increment A w_2 is added to the state
+// with its rounding error carried in a second FP32 word, kept in the
+// caller's psi buffer during the call (psi is only read at the start and
+// written at the end), so hi + lo holds the state to ~2^-48 relative.
+//
+// Row layout in shared memory (and of the carried error in global memory):
+// lane-major, the k-th column pair of lane l at float4 slot (k/2)*32 + l of
+// the row, so that every 16-byte access of a warp touches 32 consecutive
+// slots (a plain row-major layout puts lanes CL*8 bytes apart, a 4-way bank
+// conflict for CL = 8).  Every reader uses the writer's lane mapping.
+#include <type_traits>
+
+#include "ctqw_internal.cuh"
+#include "fused_common.cuh"
+
+namespace {
+
+using namespace fused;
+
+constexpr int kMaxK = 30;
+
+struct RowsArgs {
+    const double *eps;
+    const double *J;
+    RealTable tab;
+    float2 *psi;
+    double dt;
+    float inv_dt;
+    float dtU;
+    int K;
+    long long n_steps;
+    int obs_every;
+    long long p_width;
+    double *P_mean, *norm, *energy;
+    int compensated;
+    int *status;
+    unsigned long long wait_limit_ns;
+    int test_timeout;
+    float inv_j[kMaxK + 1];
+};
+
+enum { kHorner = 0, kFinal = 1, kEnergyOnly = 2 };
+
+// Register state of one lane: RL rows x CL columns of the Horner iterate and
+// the coefficient pairs (c, c) of dt H that touch them.
+template <int CL, int RL>
+struct Lane {
+    float2 P[RL][CL];
+    float2 er[RL];        // dt eps_x1 per row
+    float2 ec[CL];        // dt eps_x2 per column
+    float2 nJr[RL + 1];   // -dt J of the bond above row i (i = RL: below the last row)
+    float2 nJc[CL + 1];   // -dt J of the bond left of column k (k = CL: right of the last)
+};
+
+// One stencil application y = (dt H) P on the lane's block, then
+//   kHorner: P <- Q + (-i/j) y;  kFinal: P <- -i y;  kEnergyOnly: P unchanged.
+// usrc/dsrc: the rows above the first and below the last row in shared memory
+// (this lane's first column), read when needed so they do not hold registers.
+// Q: psi of the step in shared memory (this lane's first element, row stride N).
+// OFF = (first row) mod CL, which fixes where the diagonal x1 = x2 falls.
+template <int MODE, int CL, int RL, int N, int OFF>
+__device__ __forceinline__ void stage(Lane<CL, RL> &L, const float2 *__restrict__ usrc,
+                                      const float2 *__restrict__ dsrc, const float2 *__restrict__ Q,
+                                      int lane, int x1_0, float dtU, float inv_j, bool energy,
+                                      float &e) {
+    const int from_left = (lane + 31) & 31, from_right = (lane + 1) & 31;
+    const float2 dU = make_float2(dtU, dtU);
+    float2 prev[CL];   // old row above the current one
+#pragma unroll
+    for (int k = 0; k < CL; k += 2) {
+        const float4 u4 = *reinterpret_cast<const float4 *>(usrc + k * 32);
+        prev[k] = make_float2(u4.x, u4.y);
+        prev[k + 1] = make_float2(u4.z, u4.w);
+    }
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+        float2 c[CL];
+#pragma unroll
+        for (int k = 0; k < CL; ++k) c[k] = L.P[i][k];
+        const float2 lft = shfl2(c[CL - 1], from_left);
+        const float2 rgt = shfl2(c[0], from_right);
+        float2 dn[CL];   // old row below (read from shared memory for the last row)
+        if (i == RL - 1) {
+#pragma unroll
+            for (int k = 0; k < CL; k += 2) {
+                const float4 d4 = *reinterpret_cast<const float4 *>(dsrc + k * 32);
+                dn[k] = make_float2(d4.x, d4.y);
+                dn[k + 1] = make_float2(d4.z, d4.w);
+            }
+        }
+        float2 y[CL];
+#pragma unroll
+        for (int k = 0; k < CL; ++k) {
+            const float2 nb = (i < RL - 1) ? L.P[i + 1][k] : dn[k];   // old row below
+            const float2 l = (k == 0) ? lft : c[k - 1];
+            const float2 r = (k == CL - 1) ? rgt : c[k + 1];
+            float2 t = __fmul2_rn(L.ec[k], c[k]);
+            t = __ffma2_rn(L.er[i], c[k], t);
+            t = __ffma2_rn(L.nJr[i], prev[k], t);
+            t = __ffma2_rn(L.nJr[i + 1], nb, t);
+            t = __ffma2_rn(L.nJc[k], l, t);
+            t = __ffma2_rn(L.nJc[k + 1], r, t);
+            y[k] = t;
+        }
+        // dt U on the diagonal x2 = x1: column (OFF + i) % CL of the lane (x1_0 + i) / CL
+        {
+            const int kd = (OFF + i) % CL;   // a constant once the row loop is unrolled
+            if (lane == (x1_0 + i) / CL) y[kd] = __ffma2_rn(dU, c[kd], y[kd]);
+        }
+        if (energy) {
+#pragma unroll
+            for (int k = 0; k < CL; ++k) e += c[k].x * y[k].x + c[k].y * y[k].y;
+        }
+        if (MODE == kHorner) {
+#pragma unroll
+            for (int k = 0; k < CL; k += 2) {
+                const float4 q = *reinterpret_cast<const float4 *>(Q + i * N + k * 32);
+                L.P[i][k] = make_float2(fmaf(inv_j, y[k].y, q.x), fmaf(-inv_j, y[k].x, q.y));
+                L.P[i][k + 1] = make_float2(fmaf(inv_j, y[k + 1].y, q.z), fmaf(-inv_j, y[k + 1].x, q.w));
+            }
+        } else if (MODE == kFinal) {
+#pragma unroll
+            for (int k = 0; k < CL; ++k) L.P[i][k] = make_float2(y[k].y, -y[k].x);
+        }
+#pragma unroll
+        for (int k = 0; k < CL; ++k) prev[k] = c[k];
+    }
+}
+
+// CL columns per lane (N = 32 CL), RL rows per warp, W warps per CTA.
+template <int CL, int RL, int W, int MINB>
+__global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const __grid_constant__ RowsArgs a) {
+    constexpr int N = 32 * CL;
+    constexpr int SR = RL * W;     // slab rows
+    constexpr int C = N / SR;      // CTAs per cluster
+    static_assert(N % SR == 0 && C >= 1 && C <= 16 && CL % 2 == 0, "unsupported shape");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *hi = reinterpret_cast<float2 *>(smem_raw);      // [SR][N] psi of the step
+    float2 *halo = hi + SR * N;                             // [2 parity][2: above, below][N]
+    float2 *edge = halo + 2 * 2 * N;                        // [2 parity][W][2: first, last][N]
+    float *pacc = reinterpret_cast<float *>(edge + 2 * W * 2 * N);   // [N]
+    __shared__ __align__(8) unsigned long long mbar[2][2];
+    __shared__ __align__(8) unsigned long long mbar_never;
+
+    const int rank = (int)cluster_rank();
+    const int r = blockIdx.x / C;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lrow0 = warp * RL;
+    const int x1_0 = rank * SR + lrow0;
+    const int x2_0 = lane * CL;
+
+    Lane<CL, RL> L;
+    {
+        const int64_t po = a.tab.par_off[r];
+        const double *eps = a.eps + po, *J = a.J + po;
+        const double dt = a.dt;
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            const float v = (float)(dt * eps[x1_0 + i]);
+            L.er[i] = make_float2(v, v);
+        }
+#pragma unroll
+        for (int k = 0; k < CL; ++k) {
+            const float v = (float)(dt * eps[x2_0 + k]);
+            L.ec[k] = make_float2(v, v);
+        }
+#pragma unroll
+        for (int i = 0; i <= RL; ++i) {
+            const float v = (float)(-dt * J[(x1_0 + i - 1 + N) % N]);
+            L.nJr[i] = make_float2(v, v);
+        }
+#pragma unroll
+        for (int k = 0; k <= CL; ++k) {
+            const float v = (float)(-dt * J[(x2_0 + k - 1 + N) % N]);
+            L.nJc[k] = make_float2(v, v);
+        }
+    }
+
+    // state in: hi = psi (shared), P = psi (registers), lo = 0 (kept in psi's own buffer)
+    float2 *gpsi = a.psi + a.tab.st_off[r];
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+#pragma unroll
+        for (int k = 0; k < CL; k += 2) {
+            const float4 v = *reinterpret_cast<const float4 *>(gpsi + (size_t)(x1_0 + i) * N + x2_0 + k);
+            L.P[i][k] = make_float2(v.x, v.y);
+            L.P[i][k + 1] = make_float2(v.z, v.w);
+            *reinterpret_cast<float4 *>(hi + (lrow0 + i) * N + lane * 2 + k * 32) = v;
+        }
+    }
+    // the carried error starts at zero; it lives in this CTA's rows of psi's
+    // buffer (lane-major), which nobody reads until the final write-back
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+#pragma unroll
+        for (int k = 0; k < CL; k += 2)
+            *reinterpret_cast<float4 *>(gpsi + (size_t)(x1_0 + i) * N + lane * 2 + k * 32) =
+                make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int x = threadIdx.x; x < N; x += blockDim.x) pacc[x] = 0.f;
+
+    const int rank_up = (rank + C - 1) % C, rank_dn = (rank + 1) % C;
+    const uint32_t send_up = map_rank(smem_u32(halo + N + lane * 2), rank_up);    // their "row below" slot
+    const uint32_t send_up_mb = map_rank(smem_u32(&mbar[0][1]), rank_up);
+    const uint32_t send_dn = map_rank(smem_u32(halo + lane * 2), rank_dn);        // their "row above" slot
+    const uint32_t send_dn_mb = map_rank(smem_u32(&mbar[0][0]), rank_dn);
+    const int g = a.tab.group_of[r];
+    const double pscale = a.tab.inv_count[g] * 0.5;
+    double *Pg = a.P_mean ? a.P_mean + a.tab.group_off[g] : nullptr;
+    bool dead = false;
+    const float2 *Q = hi + lrow0 * N + lane * 2;
+    const int off = x1_0 % CL;
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 2; ++q)
+            for (int sd = 0; sd < 2; ++sd) mbar_init(smem_u32(&mbar[q][sd]), 1);
+        mbar_init(smem_u32(&mbar_never), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cluster_barrier();
+    if (a.test_timeout && threadIdx.x == 0 && blockIdx.x == 0)
+        (void)mbar_wait_bounded(smem_u32(&mbar_never), 0, 1000000ull, a.status);
+
+    unsigned tc = 0;
+    long long obs = 0;
+    const long long n_steps = a.n_steps;
+    for (long long step = 0; step <= n_steps; ++step) {
+        const bool sample = a.obs_every > 0 && (step % a.obs_every) == 0;
+        if (sample) {
+            // P(x) = (row sums + column sums) / 2, norm = sum |psi|^2 (state = hi = P)
+            float colp[CL], nrm = 0.f;
+#pragma unroll
+            for (int k = 0; k < CL; ++k) colp[k] = 0.f;
+#pragma unroll
+            for (int i = 0; i < RL; ++i) {
+                float rs = 0.f;
+#pragma unroll
+                for (int k = 0; k < CL; ++k) {
+                    const float p = L.P[i][k].x * L.P[i][k].x + L.P[i][k].y * L.P[i][k].y;
+                    colp[k] += p;
+                    rs += p;
+                }
+                rs = warp_sum(rs);
+                nrm += rs;
+                if (lane == 0 && Pg) atomicAdd(pacc + x1_0 + i, rs);
+            }
+            if (Pg) {
+#pragma unroll
+                for (int k = 0; k < CL; ++k) atomicAdd(pacc + x2_0 + k, colp[k]);
+            }
+            if (lane == 0 && a.norm) atomicAdd(a.norm + obs * a.tab.R + r, (double)nrm);
+            __syncthreads();
+            if (Pg) {
+                for (int x = threadIdx.x; x < N; x += blockDim.x) {
+                    const float v = pacc[x];
+                    if (v != 0.f) atomicAdd(Pg + obs * a.p_width + x, (double)v * pscale);
+                    pacc[x] = 0.f;
+                }
+            }
+        }
+        const bool last = step == n_steps;
+        if (last && !(sample && a.energy)) break;
+
+        const int K = a.K;
+        auto run_stage = [&](const int j) {
+            const int parity = tc & 1;
+            const uint32_t phase = (tc >> 1) & 1;
+            // publish: this warp's first and last rows (shared memory; the slab
+            // edge rows also into the neighbour CTAs)
+            float2 *eb = edge + parity * (W * 2 * N) + warp * (2 * N) + lane * 2;
+#pragma unroll
+            for (int k = 0; k < CL; k += 2) {
+                const float4 t = make_float4(L.P[0][k].x, L.P[0][k].y, L.P[0][k + 1].x, L.P[0][k + 1].y);
+                const float4 b = make_float4(L.P[RL - 1][k].x, L.P[RL - 1][k].y, L.P[RL - 1][k + 1].x,
+                                             L.P[RL - 1][k + 1].y);
+                *reinterpret_cast<float4 *>(eb + k * 32) = t;
+                *reinterpret_cast<float4 *>(eb + N + k * 32) = b;
+                if (warp == 0) st_async16(send_up + parity * (2 * N * 8) + k * 256, t, send_up_mb + parity * 16);
+                if (warp == W - 1) st_async16(send_dn + parity * (2 * N * 8) + k * 256, b, send_dn_mb + parity * 16);
+            }
+            __syncthreads();
+            mbar_expect_tx2_if(smem_u32(&mbar[parity][0]), smem_u32(&mbar[parity][1]), N * 8,
+                               threadIdx.x == 0);
+            // locate the rows above and below this warp's block
+            const float2 *usrc, *dsrc;
+            if (warp > 0) {
+                usrc = edge + parity * (W * 2 * N) + (warp - 1) * (2 * N) + N + lane * 2;
+            } else {
+                if (!dead) dead = !mbar_wait_bounded(smem_u32(&mbar[parity][0]), phase, a.wait_limit_ns, a.status);
+                usrc = halo + parity * (2 * N) + lane * 2;
+            }
+            if (warp < W - 1) {
+                dsrc = edge + parity * (W * 2 * N) + (warp + 1) * (2 * N) + lane * 2;
+            } else {
+                if (!dead) dead = !mbar_wait_bounded(smem_u32(&mbar[parity][1]), phase, a.wait_limit_ns, a.status);
+                dsrc = halo + parity * (2 * N) + N + lane * 2;
+            }
+            const float inv_j = a.inv_j[j];
+            const bool en = (j == K && sample && a.energy) || last;
+            float e = 0.f;
+            auto go = [&](auto off_tag) {
+                constexpr int OFF = decltype(off_tag)::value;
+                if (last)
+                    stage<kEnergyOnly, CL, RL, N, OFF>(L, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j, true, e);
+                else if (j == 1)
+                    stage<kFinal, CL, RL, N, OFF>(L, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j, en, e);
+                else
+                    stage<kHorner, CL, RL, N, OFF>(L, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j, en, e);
+            };
+            // the first row's offset modulo CL is a multiple of gcd(RL, CL)
+            static_assert(CL == 2 || CL == 4 || CL == 6 || CL == 8, "diagonal offsets enumerated for CL <= 8");
+            switch (off) {
+                case 0: go(std::integral_constant<int, 0>()); break;
+                case 2: if constexpr (CL > 2) go(std::integral_constant<int, 2 % CL>()); break;
+                case 4: if constexpr (CL > 4) go(std::integral_constant<int, 4 % CL>()); break;
+                case 6: if constexpr (CL > 6) go(std::integral_constant<int, 6 % CL>()); break;
+                default: if constexpr (CL % 2 == 1) go(std::integral_constant<int, 1>()); break;
+            }
+            if (en) {
+                const float es = warp_sum(e);
+                if (lane == 0) atomicAdd(a.energy + obs * a.tab.R + r, (double)es * (double)a.inv_dt);
+            }
+            ++tc;
+        };
+        if (last) {
+            run_stage(K);
+        } else {
+            for (int j = K; j >= 1; --j) run_stage(j);
+        }
+        if (sample) ++obs;
+        if (last) break;
+
+        // psi(t+dt) = psi + A w_2 (in P); rounding error carried in lo (psi's buffer)
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+#pragma unroll
+            for (int k = 0; k < CL; k += 2) {
+                float4 *hp = reinterpret_cast<float4 *>(hi + (lrow0 + i) * N + lane * 2 + k * 32);
+                float4 *lp = reinterpret_cast<float4 *>(gpsi + (size_t)(x1_0 + i) * N + lane * 2 + k * 32);
+                float4 h4 = *hp;
+                if (a.compensated) {
+                    float4 l4 = *lp;
+                    compensated_add(h4.x, l4.x, L.P[i][k].x);
+                    compensated_add(h4.y, l4.y, L.P[i][k].y);
+                    compensated_add(h4.z, l4.z, L.P[i][k + 1].x);
+                    compensated_add(h4.w, l4.w, L.P[i][k + 1].y);
+                    *lp = l4;
+                } else {
+                    h4.x += L.P[i][k].x;
+                    h4.y += L.P[i][k].y;
+                    h4.z += L.P[i][k + 1].x;
+                    h4.w += L.P[i][k + 1].y;
+                }
+                *hp = h4;
+                L.P[i][k] = make_float2(h4.x, h4.y);
+                L.P[i][k + 1] = make_float2(h4.z, h4.w);
+            }
+        }
+    }
+
+    // state out (hi; the carried error is below half an ulp of it)
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+#pragma unroll
+        for (int k = 0; k < CL; k += 2)
+            *reinterpret_cast<float4 *>(gpsi + (size_t)(x1_0 + i) * N + x2_0 + k) =
+                *reinterpret_cast<const float4 *>(hi + (lrow0 + i) * N + lane * 2 + k * 32);
+    }
+    cluster_barrier();
+}
+
+using RowsKernel = void (*)(RowsArgs);
+
+struct RowsShape {
+    int C, threads;
+    size_t smem;
+    RowsKernel kern;
+};
+
+template <int CL, int RL, int W, int MINB>
+RowsShape rows_shape() {
+    constexpr int N = 32 * CL, SR = RL * W;
+    RowsShape f;
+    f.C = N / SR;
+    f.threads = 32 * W;
+    f.smem = sizeof(float2) * ((size_t)SR * N + (size_t)2 * 2 * N + (size_t)2 * W * 2 * N) +
+             sizeof(float) * (size_t)N;
+    f.kern = taylor_fused_rows_kernel<CL, RL, W, MINB>;
+    return f;
+}
+
+constexpr int kRowsShapes = 3;
+
+bool rows_shape_for(int N, int idx, RowsShape &f) {
+    RowsShape opts[kRowsShapes];
+    switch (N) {
+        case 64: opts[0] = rows_shape<2, 8, 8, 2>(); opts[1] = rows_shape<2, 4, 8, 2>(); opts[2] = rows_shape<2, 8, 4, 3>(); break;
+        case 128: opts[0] = rows_shape<4, 4, 4, 3>(); opts[1] = rows_shape<4, 4, 8, 2>(); opts[2] = rows_shape<4, 8, 4, 2>(); break;
+        case 192: opts[0] = rows_shape<6, 4, 4, 3>(); opts[1] = rows_shape<6, 4, 8, 1>(); opts[2] = rows_shape<6, 4, 4, 2>(); break;
+        case 256: opts[0] = rows_shape<8, 4, 4, 3>(); opts[1] = rows_shape<8, 4, 8, 1>(); opts[2] = rows_shape<8, 4, 4, 2>(); break;
+        default: return false;
+    }
+    if (idx < 0 || idx >= kRowsShapes) return false;
+    f = opts[idx];
+    return true;
+}
+
+}  // namespace
+
+bool fused_rows_supported(const ctqw_hamiltonian *h, int dtype) {
+    RowsShape f;
+    return dtype == CTQW_C64 && h->m == 2 && h->uniform && rows_shape_for(h->Nmax, 0, f);
+}
+
+int launch_taylor_fused_rows(const ctqw_hamiltonian *h, void *psi, double dt, int K,
+                             int64_t n_steps, int obs_every, double *P_mean, double *norm,
+                             double *energy, int compensated, int shape, int test_timeout,
+                             cudaStream_t s) {
+    RowsShape f;
+    if (!rows_shape_for(h->Nmax, shape, f)) {
+        ctqw_set_error("fused path: unsupported size N=%d or shape %d", h->Nmax, shape);
+        return CTQW_EUNSUPPORTED;
+    }
+    if (K > kMaxK) {
+        ctqw_set_error("fused path: K=%d above %d", K, kMaxK);
+        return CTQW_EUNSUPPORTED;
+    }
+    RowsArgs a;
+    a.eps = h->eps64;
+    a.J = h->J64;
+    a.tab = real_table(h);
+    a.psi = (float2 *)psi;
+    a.dt = dt;
+    a.inv_dt = (float)(1.0 / dt);
+    a.dtU = (float)(dt * h->U);
+    a.K = K;
+    a.n_steps = n_steps;
+    a.obs_every = obs_every;
+    a.p_width = h->p_width;
+    a.P_mean = P_mean;
+    a.norm = norm;
+    a.energy = energy;
+    a.compensated = compensated;
+    a.status = h->status_d;
+    a.test_timeout = test_timeout;
+    a.wait_limit_ns = 2000000000ull;
+    a.inv_j[0] = 0.f;
+    for (int j = 1; j <= kMaxK; ++j) a.inv_j[j] = (float)(1.0 / j);
+    CTQW_CUDA_TRY(cudaFuncSetAttribute((const void *)f.kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)f.smem));
+    if (f.C > 8)
+        CTQW_CUDA_TRY(cudaFuncSetAttribute((const void *)f.kern,
+                                           cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(h->R * f.C));
+    cfg.blockDim = dim3((unsigned)f.threads);
+    cfg.dynamicSmemBytes = f.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)f.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    CTQW_CUDA_TRY(cudaOccupancyMaxActiveClusters(&clusters, (const void *)f.kern, &cfg));
+    if (clusters < 1) {
+        ctqw_set_error("fused path: no cluster of %d CTAs x %d threads fits", f.C, f.threads);
+        return CTQW_EUNSUPPORTED;
+    }
+    CTQW_CUDA_TRY(cudaLaunchKernelEx(&cfg, f.kern, a));
+    return CTQW_OK;
+}

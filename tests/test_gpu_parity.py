@@ -253,8 +253,7 @@ def test_bad_arguments_rejected(ctqw):
 
 
 # ------------------------------------------------------------------ fused shapes and failure path
-@pytest.mark.parametrize("N,shape", [(64, 1), (64, 2), (128, 1), (128, 2), (192, 1), (192, 2),
-                                     (256, 1), (256, 2)])
+@pytest.mark.parametrize("N,shape", [(N, k) for N in (64, 128, 192, 256) for k in (1, 2, 4, 5, 6)])
 def test_fused_c64_alternative_shapes(ctqw, N, shape):
     w = cw.get("bosons_n256_u2").with_(N=N, R=3, K=9, n_steps=12, obs_every=4,
                                        sites=(N // 2 - 1, N // 2))
@@ -266,7 +265,7 @@ def test_fused_c64_alternative_shapes(ctqw, N, shape):
 def test_fused_unknown_shape_rejected(ctqw):
     w = cw.get("bosons_small").with_(R=1, n_steps=2)
     with pytest.raises(ctqw.CtqwError, match="shape"):
-        ctqw.run_workload(w, flags=ctqw.FUSED_SHAPE(7))
+        ctqw.run_workload(w, flags=ctqw.FUSED_SHAPE(9))
 
 
 def test_fused_bounded_wait_gives_up_and_reports(ctqw):
