@@ -157,7 +157,7 @@ def fused_traffic(workload: str):
     try:
         with open(os.path.join(ROOT, "profiles", "taylor_fused_traffic.json")) as f:
             rec = json.load(f)
-        src = os.path.join(ROOT, "paper_1612_00746_gb300", "csrc", "k_fused.cu")
+        src = os.path.join(ROOT, "paper_1612_00746_gb300", "csrc", "k_fused_rows.cu")
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except (OSError, ValueError):
         return None
@@ -401,7 +401,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": fused_traffic(w.name) if not (args.realizations or args.n_steps) else None,
-                     "kernel": "taylor_fused_kernel", "kernel_ms": kernel_ms,
+                     "kernel": "taylor_fused_rows_kernel", "kernel_ms": kernel_ms,
                      "flops_per_site_update": flops_per_unit,
                      "peak_basis": "152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz (derived)",
                      "hbm_gbs_measured": peaks.get("hbm_gbs")},

@@ -61,9 +61,9 @@ extern "C" {
                                            nothing completes, gives up after 1 ms and flags the handle */
 /* Fused path tuning: CTQW_FUSED_SHAPE(k) selects a compiled CTA/cluster shape
  * for the lattice size.  k = 0..2: full-row kernel (each warp owns whole rows;
- * 0 = default, 1 = twice the warps per CTA and half the CTAs per cluster,
- * 2 = the default split with registers capped for two CTAs per SM instead of
- * three); k = 4..6: the banded kernel (warps share rows), its shapes 0..2.
+ * 0 = default, the fastest measured for the size; 1 and 2 = other splits of
+ * rows over warps, CTAs and clusters); k = 4..6: the banded kernel (warps
+ * share rows), its shapes 0..2.
  * An index with no compiled shape returns CTQW_EUNSUPPORTED. */
 #define CTQW_FUSED_SHAPE_SHIFT 8
 #define CTQW_FUSED_SHAPE(k) (((uint32_t)(k) & 0xFu) << CTQW_FUSED_SHAPE_SHIFT)

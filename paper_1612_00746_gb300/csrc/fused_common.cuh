@@ -114,6 +114,20 @@ static __device__ __forceinline__ void compensated_add(float &hi, float &lo, flo
     hi = h2;
 }
 
+// The same on an (re, im) pair with FP32x2 operations (x - y as fma(y, -1, x),
+// which rounds exactly like the subtraction).
+static __device__ __forceinline__ void compensated_add2(float2 &hi, float2 &lo, float2 s) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 t = __fadd2_rn(hi, s);
+    const float2 bb = __ffma2_rn(hi, m1, t);
+    const float2 tb = __ffma2_rn(bb, m1, t);
+    const float2 err = __fadd2_rn(__ffma2_rn(tb, m1, hi), __ffma2_rn(bb, m1, s));
+    const float2 l = __fadd2_rn(err, lo);
+    const float2 h2 = __fadd2_rn(t, l);
+    lo = __ffma2_rn(__ffma2_rn(t, m1, h2), m1, l);
+    hi = h2;
+}
+
 static __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

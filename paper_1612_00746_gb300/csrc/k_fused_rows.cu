@@ -64,13 +64,12 @@ struct RowsArgs {
 enum { kHorner = 0, kFinal = 1, kEnergyOnly = 2 };
 
 // Register state of one lane: RL rows x CL columns of the Horner iterate and
-// the coefficient pairs (c, c) of dt H that touch them.
+// the per-column coefficient pairs (c, c) of dt H.  The per-row pairs are the
+// same for the whole warp and are read from shared memory (rowc) instead.
 template <int CL, int RL>
 struct Lane {
     float2 P[RL][CL];
-    float2 er[RL];        // dt eps_x1 per row
     float2 ec[CL];        // dt eps_x2 per column
-    float2 nJr[RL + 1];   // -dt J of the bond above row i (i = RL: below the last row)
     float2 nJc[CL + 1];   // -dt J of the bond left of column k (k = CL: right of the last)
 };
 
@@ -80,13 +79,17 @@ struct Lane {
 // (this lane's first column), read when needed so they do not hold registers.
 // Q: psi of the step in shared memory (this lane's first element, row stride N).
 // OFF = (first row) mod CL, which fixes where the diagonal x1 = x2 falls.
+// rowc: per slab row (dt eps_x1, dt eps_x1, -dt J above, -dt J above) for this
+// warp's rows and the one below them (broadcast loads).
 template <int MODE, int CL, int RL, int N, int OFF>
-__device__ __forceinline__ void stage(Lane<CL, RL> &L, const float2 *__restrict__ usrc,
+__device__ __forceinline__ void stage(Lane<CL, RL> &L, const float4 *__restrict__ rowc,
+                                      const float2 *__restrict__ usrc,
                                       const float2 *__restrict__ dsrc, const float2 *__restrict__ Q,
                                       int lane, int x1_0, float dtU, float inv_j, bool energy,
                                       float &e) {
     const int from_left = (lane + 31) & 31, from_right = (lane + 1) & 31;
     const float2 dU = make_float2(dtU, dtU);
+    float4 rc = rowc[0];
     float2 prev[CL];   // old row above the current one
 #pragma unroll
     for (int k = 0; k < CL; k += 2) {
@@ -110,6 +113,10 @@ __device__ __forceinline__ void stage(Lane<CL, RL> &L, const float2 *__restrict_
                 dn[k + 1] = make_float2(d4.z, d4.w);
             }
         }
+        const float4 rn = rowc[i + 1];
+        const float2 er = make_float2(rc.x, rc.y), jup = make_float2(rc.z, rc.w);
+        const float2 jdn = make_float2(rn.z, rn.w);
+        rc = rn;
         float2 y[CL];
 #pragma unroll
         for (int k = 0; k < CL; ++k) {
@@ -117,9 +124,9 @@ __device__ __forceinline__ void stage(Lane<CL, RL> &L, const float2 *__restrict_
             const float2 l = (k == 0) ? lft : c[k - 1];
             const float2 r = (k == CL - 1) ? rgt : c[k + 1];
             float2 t = __fmul2_rn(L.ec[k], c[k]);
-            t = __ffma2_rn(L.er[i], c[k], t);
-            t = __ffma2_rn(L.nJr[i], prev[k], t);
-            t = __ffma2_rn(L.nJr[i + 1], nb, t);
+            t = __ffma2_rn(er, c[k], t);
+            t = __ffma2_rn(jup, prev[k], t);
+            t = __ffma2_rn(jdn, nb, t);
             t = __ffma2_rn(L.nJc[k], l, t);
             t = __ffma2_rn(L.nJc[k + 1], r, t);
             y[k] = t;
@@ -160,7 +167,8 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
     float2 *hi = reinterpret_cast<float2 *>(smem_raw);      // [SR][N] psi of the step
     float2 *halo = hi + SR * N;                             // [2 parity][2: above, below][N]
     float2 *edge = halo + 2 * 2 * N;                        // [2 parity][W][2: first, last][N]
-    float *pacc = reinterpret_cast<float *>(edge + 2 * W * 2 * N);   // [N]
+    float4 *rowc = reinterpret_cast<float4 *>(edge + 2 * W * 2 * N);  // [SR + 1] row coefficient pairs
+    float *pacc = reinterpret_cast<float *>(rowc + SR + 1);           // [N]
     __shared__ __align__(8) unsigned long long mbar[2][2];
     __shared__ __align__(8) unsigned long long mbar_never;
 
@@ -176,20 +184,16 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
         const int64_t po = a.tab.par_off[r];
         const double *eps = a.eps + po, *J = a.J + po;
         const double dt = a.dt;
-#pragma unroll
-        for (int i = 0; i < RL; ++i) {
-            const float v = (float)(dt * eps[x1_0 + i]);
-            L.er[i] = make_float2(v, v);
+        for (int q = threadIdx.x; q <= SR; q += blockDim.x) {
+            const int x1 = rank * SR + q;   // q = SR: only the bond below the slab is used
+            const float e = q < SR ? (float)(dt * eps[x1]) : 0.f;
+            const float j = (float)(-dt * J[(x1 - 1 + N) % N]);
+            rowc[q] = make_float4(e, e, j, j);
         }
 #pragma unroll
         for (int k = 0; k < CL; ++k) {
             const float v = (float)(dt * eps[x2_0 + k]);
             L.ec[k] = make_float2(v, v);
-        }
-#pragma unroll
-        for (int i = 0; i <= RL; ++i) {
-            const float v = (float)(-dt * J[(x1_0 + i - 1 + N) % N]);
-            L.nJr[i] = make_float2(v, v);
         }
 #pragma unroll
         for (int k = 0; k <= CL; ++k) {
@@ -324,11 +328,11 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
             auto go = [&](auto off_tag) {
                 constexpr int OFF = decltype(off_tag)::value;
                 if (last)
-                    stage<kEnergyOnly, CL, RL, N, OFF>(L, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j, true, e);
+                    stage<kEnergyOnly, CL, RL, N, OFF>(L, rowc + lrow0, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j, true, e);
                 else if (j == 1)
-                    stage<kFinal, CL, RL, N, OFF>(L, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j, en, e);
+                    stage<kFinal, CL, RL, N, OFF>(L, rowc + lrow0, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j, en, e);
                 else
-                    stage<kHorner, CL, RL, N, OFF>(L, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j, en, e);
+                    stage<kHorner, CL, RL, N, OFF>(L, rowc + lrow0, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j, en, e);
             };
             // the first row's offset modulo CL is a multiple of gcd(RL, CL)
             static_assert(CL == 2 || CL == 4 || CL == 6 || CL == 8, "diagonal offsets enumerated for CL <= 8");
@@ -363,11 +367,12 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
                 float4 h4 = *hp;
                 if (a.compensated) {
                     float4 l4 = *lp;
-                    compensated_add(h4.x, l4.x, L.P[i][k].x);
-                    compensated_add(h4.y, l4.y, L.P[i][k].y);
-                    compensated_add(h4.z, l4.z, L.P[i][k + 1].x);
-                    compensated_add(h4.w, l4.w, L.P[i][k + 1].y);
-                    *lp = l4;
+                    float2 h0 = make_float2(h4.x, h4.y), h1 = make_float2(h4.z, h4.w);
+                    float2 l0 = make_float2(l4.x, l4.y), l1 = make_float2(l4.z, l4.w);
+                    compensated_add2(h0, l0, L.P[i][k]);
+                    compensated_add2(h1, l1, L.P[i][k + 1]);
+                    h4 = make_float4(h0.x, h0.y, h1.x, h1.y);
+                    *lp = make_float4(l0.x, l0.y, l1.x, l1.y);
                 } else {
                     h4.x += L.P[i][k].x;
                     h4.y += L.P[i][k].y;
@@ -407,7 +412,7 @@ RowsShape rows_shape() {
     f.C = N / SR;
     f.threads = 32 * W;
     f.smem = sizeof(float2) * ((size_t)SR * N + (size_t)2 * 2 * N + (size_t)2 * W * 2 * N) +
-             sizeof(float) * (size_t)N;
+             sizeof(float4) * (size_t)(SR + 1) + sizeof(float) * (size_t)N;
     f.kern = taylor_fused_rows_kernel<CL, RL, W, MINB>;
     return f;
 }
@@ -418,7 +423,7 @@ bool rows_shape_for(int N, int idx, RowsShape &f) {
     RowsShape opts[kRowsShapes];
     switch (N) {
         case 64: opts[0] = rows_shape<2, 8, 8, 2>(); opts[1] = rows_shape<2, 4, 8, 2>(); opts[2] = rows_shape<2, 8, 4, 3>(); break;
-        case 128: opts[0] = rows_shape<4, 4, 4, 3>(); opts[1] = rows_shape<4, 4, 8, 2>(); opts[2] = rows_shape<4, 8, 4, 2>(); break;
+        case 128: opts[0] = rows_shape<4, 8, 4, 2>(); opts[1] = rows_shape<4, 4, 8, 2>(); opts[2] = rows_shape<4, 4, 4, 3>(); break;
         case 192: opts[0] = rows_shape<6, 4, 4, 3>(); opts[1] = rows_shape<6, 4, 8, 1>(); opts[2] = rows_shape<6, 4, 4, 2>(); break;
         case 256: opts[0] = rows_shape<8, 4, 4, 3>(); opts[1] = rows_shape<8, 4, 8, 1>(); opts[2] = rows_shape<8, 4, 4, 2>(); break;
         default: return false;

@@ -286,3 +286,44 @@ def test_fused_bounded_wait_gives_up_and_reports(ctqw):
     ref = oracle.ensemble_run(w)
     _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
     h.close()
+
+
+def test_fused_propagation_replays_from_a_cuda_graph(ctqw):
+    """init + fused propagation captured once in a CUDA graph and replayed:
+    identical results to eager calls (no host synchronisation or allocation
+    inside the fused path)."""
+    w = cw.get("bosons_n256_u2").with_(N=128, R=4, n_steps=30, obs_every=10, sites=(63, 64))
+    h = ctqw.build_for_workload(w)
+    sites = ctqw.initial_sites(w, h)
+    n_obs = h.n_obs(w.n_steps, w.obs_every)
+
+    def buffers():
+        return (h.new_state(cw.C64),
+                torch.empty((n_obs, h.p_width), dtype=torch.float64, device="cuda"),
+                torch.empty((n_obs, h.R), dtype=torch.float64, device="cuda"),
+                torch.empty((n_obs, h.R), dtype=torch.float64, device="cuda"))
+
+    psi, P, nr, en = buffers()
+    ctqw.ctqw_init_state(h, psi, sites, cw.C64)
+    ctqw.ctqw_propagate_taylor(h, psi, cw.C64, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en)
+    torch.cuda.synchronize()
+    ref = [t.clone() for t in (psi, P, nr, en)]
+
+    gpsi, gP, gnr, gen = buffers()
+    ctqw.ctqw_init_state(h, gpsi, sites, cw.C64)   # first call outside capture (sites upload)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ctqw.ctqw_propagate_taylor(h, gpsi, cw.C64, w.dt, w.K, w.n_steps, w.obs_every, gP, gnr, gen,
+                                   stream=s)
+    for _ in range(2):
+        ctqw.ctqw_init_state(h, gpsi, sites, cw.C64)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(gpsi, ref[0])   # the state involves no atomics: bit-identical
+        for a, b in zip((gP, gnr, gen), ref[1:]):   # FP64 atomics: summation order may differ
+            assert torch.allclose(a, b, rtol=0, atol=1e-13)
+    ctqw.ctqw_check_status(h)
+    h.close()
