@@ -344,6 +344,8 @@ def run_ours(args):
 
     # plain per-term FP64 path on a subset (the comparison path of the metric)
     fp64 = None
+    plain32 = None
+    peaks = measured_peaks()
     if not args.no_fp64_plain and rank == 0:
         sub = list(range(args.fp64_realizations))
         ue_s, uj_s, sz_s, _ = cw.packed_draws(w, sub)
@@ -377,6 +379,27 @@ def run_ours(args):
                                    None, None, 0, None)
         torch.cuda.synchronize()
         dP = float((P32 - P64).abs().max().item())
+        # the plain per-term path in FP32 on the same subset: HBM-bound, 32 bytes
+        # per site-update (read Phi, write Phi, read + write the running sum)
+        psi32p = hs.new_state(ctqw.C64, dev)
+        ws32 = hs.workspace(ctqw.C64, ctqw.TAYLOR, ctqw.FLAG_PLAIN, dev)
+        ctqw.ctqw_init_state(hs, psi32p, sites_s, ctqw.C64)
+        ctqw.ctqw_propagate_taylor(hs, psi32p, ctqw.C64, w.dt, w.K, 2, 0, None, None, None,
+                                   ctqw.FLAG_PLAIN, ws32)
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        ctqw.ctqw_propagate_taylor(hs, psi32p, ctqw.C64, w.dt, w.K, steps64, 0, None, None, None,
+                                   ctqw.FLAG_PLAIN, ws32)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        ms32p = b0.elapsed_time(b1)
+        gbs = units64 * 32.0 / (ms32p / 1000.0) / 1e9
+        plain32 = {"value": units64 / (ms32p / 1000.0), "unit": UNIT, "bound": "hbm",
+                   "achieved_gbs": gbs, "peak_gbs": peaks.get("hbm_gbs"),
+                   "frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+                   "bytes_per_site_update": 32,
+                   "sample": f"{len(sub)} realizations x {steps64} steps, taylor_term_kernel<float, 2>"}
         fp64 = {"value": units64 / (ms64 / 1000.0), "unit": UNIT,
                 "sample": f"{len(sub)} realizations x {steps64} steps, plain per-term FP64 kernels",
                 "fp32_speedup": value / world / (units64 / (ms64 / 1000.0)),
@@ -408,6 +431,7 @@ def run_ours(args):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "fp64_plain": fp64,
+        "plain_fp32_hbm": plain32,
         "norm_drift": norm_drift,
         "clocks": clk,
     }

@@ -184,7 +184,12 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
  * step of Sec. 2.2 (Algorithm 2): K^(1) = -iH Psi, K^(2) = -iH(Psi + dt/2 K^(1)),
  * K^(3) = -iH(Psi + dt/2 K^(2)), K^(4) = -iH(Psi + dt K^(3)),
  * Psi(t+dt) = Psi + dt/6 (K^(1) + 2K^(2) + 2K^(3) + K^(4)).  The norm is not
- * corrected.  Needs the workspace of ctqw_workspace_size(method = 1).
+ * corrected.  This update map is the order-4 Taylor polynomial of
+ * exp(-i H dt) (Sec. 2.3: order-n RK and order-n Taylor coincide for the
+ * exponential); where the fused kernel applies (see ctqw_propagate_taylor)
+ * it evaluates that polynomial on chip, otherwise, or with CTQW_FLAG_PLAIN,
+ * one launch per stage runs the four stages above and needs the workspace
+ * of ctqw_workspace_size(method = 1).
  */
 int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
                        int64_t n_steps, int32_t obs_every, double *P_mean_dev, double *norm_dev,

@@ -324,7 +324,8 @@ int ctqw_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t method
                         size_t *bytes) {
     if (!h || !bytes) { ctqw_set_error("null argument"); return CTQW_EINVAL; }
     if (dtype != CTQW_C64 && dtype != CTQW_C128) { ctqw_set_error("dtype %d", dtype); return CTQW_EINVAL; }
-    const bool fused = method == 0 && !(flags & CTQW_FLAG_PLAIN) && fused_rows_supported(h, dtype);
+    const bool fused = (method == 0 || method == 1) && !(flags & CTQW_FLAG_PLAIN) &&
+                       fused_rows_supported(h, dtype);
     *bytes = fused ? 0 : 3 * (size_t)h->total_amp * elem_bytes(dtype);
     return CTQW_OK;
 }
@@ -387,14 +388,15 @@ int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, 
                        int64_t n_steps, int32_t obs_every, double *P_mean_dev, double *norm_dev,
                        double *energy_dev, uint32_t flags, void *workspace_dev,
                        size_t workspace_bytes, void *stream) {
-    (void)flags;
     CTQW_TRY(check_common(h, dtype, psi_dev, dt, n_steps, obs_every));
     cudaStream_t s = (cudaStream_t)stream;
+    // RK4's update map is the order-4 Taylor polynomial of exp(-i H dt)
+    // (Sec. 2.3): the fused kernel evaluates it directly
+    if (!(flags & CTQW_FLAG_PLAIN) && fused_rows_supported(h, dtype))
+        return ctqw_propagate_taylor(h, dtype, psi_dev, dt, 4, n_steps, obs_every, P_mean_dev,
+                                     norm_dev, energy_dev, flags, workspace_dev, workspace_bytes,
+                                     stream);
     const size_t sb = (size_t)h->total_amp * elem_bytes(dtype);
-    if (!workspace_dev || workspace_bytes < 3 * sb) {
-        ctqw_set_error("RK4 needs a workspace of %zu bytes (got %zu)", 3 * sb, workspace_bytes);
-        return CTQW_EINVAL;
-    }
     const int64_t n_obs = n_samples(n_steps, obs_every);
     CTQW_TRY(zero_outputs(h, n_obs, P_mean_dev, norm_dev, energy_dev, s));
     char *ws = (char *)workspace_dev;

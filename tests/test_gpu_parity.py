@@ -180,9 +180,10 @@ def test_plain_c64(ctqw):
     _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
 
 
-def test_rk4_c64(ctqw):
+@pytest.mark.parametrize("flags", [0, 1])   # fused (order-4 polynomial on chip), plain stages
+def test_rk4_c64(ctqw, flags):
     w = cw.get("bosons_small").with_(R=2, n_steps=100, obs_every=25)
-    got = ctqw.run_workload(w, method=ctqw.RK4)
+    got = ctqw.run_workload(w, method=ctqw.RK4, flags=flags)
     ref = oracle.ensemble_run(w, method="rk4")
     _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
 
