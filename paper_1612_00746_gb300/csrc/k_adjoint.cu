@@ -70,7 +70,16 @@ __global__ void __launch_bounds__(256) apply_h_kernel(RealTable tab, const T *__
 // grad_eps[r][i] += 2 Re <mu, n_i phi>,  grad_J[r][b] += 2 Re <mu, dH/dJ_b phi>.
 // Per-block accumulation in shared memory (FP64) when N <= kSmemN, then one
 // FP64 atomic per touched entry; otherwise FP64 atomics straight to global.
+// For a particle whose site is the same on every lane of a warp (the slow
+// indices x_1..x_{M-1} when N is a multiple of 32) the warp sums first, so
+// that a block does not serialize on one address.
 constexpr int kSmemN = 1024;
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 template <typename T, int M>
 __global__ void __launch_bounds__(256) grad_kernel(RealTable tab, const cplx_t<T> *__restrict__ mu,
@@ -90,28 +99,53 @@ __global__ void __launch_bounds__(256) grad_kernel(RealTable tab, const cplx_t<T
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t base = tab.st_off[r];
     const int64_t po = tab.par_off[r];
-    if (s < D) {
-        int x[M];
+    const bool live = s < D;
+    int x[M];
+    double d = 0.0;
+    cplx_t<T> u, p;
+    if (live) {
         unflatten<M>(s, N, x);
-        const cplx_t<T> u = mu[base + s], p = phi[base + s];
+        u = mu[base + s];
+        p = phi[base + s];
         // Re(conj(u) p)
-        const double d = (double)u.x * (double)p.x + (double)u.y * (double)p.y;
-        int64_t stride = 1;
+        d = (double)u.x * (double)p.x + (double)u.y * (double)p.y;
+    } else {
 #pragma unroll
-        for (int j = M - 1; j >= 0; --j) {
-            const int b = x[j];
+        for (int j = 0; j < M; ++j) x[j] = -1;
+    }
+    int64_t stride = 1;
+#pragma unroll
+    for (int j = M - 1; j >= 0; --j) {
+        const int b = x[j];
+        const bool bond = live && (tab.periodic || b < N - 1);
+        double h = 0.0;
+        if (bond) {
+            const int64_t s2 = s + (int64_t)((b == N - 1) ? (1 - N) : 1) * stride;   // particle j on b+1
+            const cplx_t<T> u2 = mu[base + s2], p2 = phi[base + s2];
+            h = (double)u.x * (double)p2.x + (double)u.y * (double)p2.y + (double)u2.x * (double)p.x +
+                (double)u2.y * (double)p.y;
+        }
+        const int b0 = __shfl_sync(0xffffffffu, b, 0);
+        if (__all_sync(0xffffffffu, b == b0)) {
+            // the whole warp on one site (b0 >= 0: every lane is live)
+            const double de = warp_sum_d(2.0 * d), dh = warp_sum_d(-2.0 * h);
+            if ((threadIdx.x & 31) == 0 && b0 >= 0) {
+                if (use_smem) atomicAdd(ge + b0, de);
+                else atomicAdd(grad_eps + po + b0, de);
+                if (tab.periodic || b0 < N - 1) {
+                    if (use_smem) atomicAdd(gj + b0, dh);
+                    else atomicAdd(grad_J + po + b0, dh);
+                }
+            }
+        } else if (live) {
             if (use_smem) atomicAdd(ge + b, 2.0 * d);
             else atomicAdd(grad_eps + po + b, 2.0 * d);
-            if (tab.periodic || b < N - 1) {
-                const int64_t s2 = s + (int64_t)((b == N - 1) ? (1 - N) : 1) * stride;   // particle j on b+1
-                const cplx_t<T> u2 = mu[base + s2], p2 = phi[base + s2];
-                const double h = (double)u.x * (double)p2.x + (double)u.y * (double)p2.y +
-                                 (double)u2.x * (double)p.x + (double)u2.y * (double)p.y;
+            if (bond) {
                 if (use_smem) atomicAdd(gj + b, -2.0 * h);
                 else atomicAdd(grad_J + po + b, -2.0 * h);
             }
-            stride *= N;
         }
+        stride *= N;
     }
     if (use_smem) {
         __syncthreads();
