@@ -261,11 +261,17 @@ def run_ours(args):
     P = torch.empty((n_obs, h.p_width), dtype=torch.float64, device=dev)
     nr = torch.empty((n_obs, h.R), dtype=torch.float64, device=dev)
     en = torch.empty((n_obs, h.R), dtype=torch.float64, device=dev)
-    ws = h.workspace(dtype, ctqw.TAYLOR, 0, dev)
+    ws = h.workspace(dtype, ctqw.TAYLOR, args.flags, dev)
     counts = torch.tensor(np.repeat(h.group_count, h.group_sizes), dtype=torch.float64, device=dev)
     D = float(np.sum(sizes.astype(np.float64) ** w.m))
     units_per_step = D * w.K * w.n_steps
-    launches_per_step = 2   # init_state kernel + fused propagation kernel
+    if (args.flags >> 8) & 0xF == ctqw.SHAPE_WAVEFRONT:
+        # init_state + one observables kernel per sample + one wavefront launch
+        # per segment between samples and size group
+        n_seg = -(-w.n_steps // w.obs_every) if w.obs_every else 1
+        launches_per_step = 1 + n_obs + n_seg * len(h.group_sizes)
+    else:
+        launches_per_step = 2   # init_state kernel + fused propagation kernel
 
     prop_events = []
 
@@ -379,8 +385,10 @@ def run_ours(args):
                                    None, None, 0, None)
         torch.cuda.synchronize()
         dP = float((P32 - P64).abs().max().item())
-        # the plain per-term path in FP32 on the same subset: HBM-bound, 32 bytes
-        # per site-update (read Phi, write Phi, read + write the running sum)
+        # the plain per-term path in FP32 on the same subset: HBM-bound.  Its
+        # K-1 Horner stages read w and psi and write w (24 bytes per amplitude);
+        # the last reads w, psi and the rounding word and writes psi and the
+        # rounding word (40 bytes).
         psi32p = hs.new_state(ctqw.C64, dev)
         ws32 = hs.workspace(ctqw.C64, ctqw.TAYLOR, ctqw.FLAG_PLAIN, dev)
         ctqw.ctqw_init_state(hs, psi32p, sites_s, ctqw.C64)
@@ -394,12 +402,14 @@ def run_ours(args):
         b1.record(stream)
         torch.cuda.synchronize()
         ms32p = b0.elapsed_time(b1)
-        gbs = units64 * 32.0 / (ms32p / 1000.0) / 1e9
+        bpu = ((w.K - 1) * 24.0 + 40.0) / w.K
+        gbs = units64 * bpu / (ms32p / 1000.0) / 1e9
         plain32 = {"value": units64 / (ms32p / 1000.0), "unit": UNIT, "bound": "hbm",
                    "achieved_gbs": gbs, "peak_gbs": peaks.get("hbm_gbs"),
                    "frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
-                   "bytes_per_site_update": 32,
-                   "sample": f"{len(sub)} realizations x {steps64} steps, taylor_term_kernel<float, 2>"}
+                   "bytes_per_site_update": bpu,
+                   "sample": f"{len(sub)} realizations x {steps64} steps, "
+                             "horner_stage_kernel<2> + horner_final_kernel<2>"}
         fp64 = {"value": units64 / (ms64 / 1000.0), "unit": UNIT,
                 "sample": f"{len(sub)} realizations x {steps64} steps, plain per-term FP64 kernels",
                 "fp32_speedup": value / world / (units64 / (ms64 / 1000.0)),

@@ -63,10 +63,15 @@ extern "C" {
  * for the lattice size.  k = 0..2: full-row kernel (each warp owns whole rows;
  * 0 = default, the fastest measured for the size; 1 and 2 = other splits of
  * rows over warps, CTAs and clusters); k = 4..6: the banded kernel (warps
- * share rows), its shapes 0..2.
+ * share rows), its shapes 0..2; k = CTQW_SHAPE_WAVEFRONT: the row-wavefront
+ * kernel (one CTA per realization, one warp per Taylor term, rows streamed
+ * through a pipeline; open chains, N in {64, 128, 192, 256}, also ragged,
+ * K <= 16 with N + 1 > 2K + 8; needs ctqw_workspace_size bytes of workspace,
+ * one c64 state, or allocates it stream-ordered when workspace_dev is NULL).
  * An index with no compiled shape returns CTQW_EUNSUPPORTED. */
 #define CTQW_FUSED_SHAPE_SHIFT 8
 #define CTQW_FUSED_SHAPE(k) (((uint32_t)(k) & 0xFu) << CTQW_FUSED_SHAPE_SHIFT)
+#define CTQW_SHAPE_WAVEFRONT 8
 
 typedef struct ctqw_hamiltonian ctqw_hamiltonian;   /* opaque, owned by the library */
 
@@ -172,7 +177,12 @@ int ctqw_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t method
  * fused cluster kernel (every Taylor term of every step on chip; halo rows move between the CTAs
  * of a cluster point to point, see ctqw_check_status); everything
  * else, or CTQW_FLAG_PLAIN, runs one launch per Taylor term and needs the
- * workspace of ctqw_workspace_size (3 states).  Asynchronous.
+ * workspace of ctqw_workspace_size (3 states): in CTQW_C128 in the order of
+ * Algorithm 3 (Phi^(j) from Phi^(j-1), summed forward); in CTQW_C64 as the
+ * same polynomial in Horner form (w_j = Psi + (-i dt / j) H w_{j+1}, j = K..2,
+ * Psi(t+dt) = Psi - i dt H w_2) with the state update compensated, because a
+ * forward FP32 sum drops every term below half an ulp of the running sum.
+ * Asynchronous.
  */
 int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
                           int32_t K, int64_t n_steps, int32_t obs_every, double *P_mean_dev,

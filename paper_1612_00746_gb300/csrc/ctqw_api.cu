@@ -20,7 +20,8 @@ int64_t n_samples(int64_t n_steps, int obs_every) {
 
 void free_device(ctqw_hamiltonian *h) {
     void *ptrs[] = {h->eps32, h->J32, h->eps64, h->J64, h->sizes_d, h->group_of_d, h->par_off_d,
-                    h->st_off_d, h->group_off_d, h->joint_off_d, h->inv_count_d, h->status_d};
+                    h->st_off_d, h->group_off_d, h->joint_off_d, h->inv_count_d, h->status_d,
+                    h->by_group_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -224,6 +225,14 @@ int ctqw_build_hamiltonian(const ctqw_lattice_desc *d, void *stream, ctqw_hamilt
         (st = upload(&h->group_off_d, h->group_off, s)) ||
         (st = upload(&h->joint_off_d, h->joint_off, s)) || (st = upload(&h->inv_count_d, inv, s)))
         return fail(st);
+    {
+        std::vector<int32_t> by_group;
+        by_group.reserve(h->R);
+        for (int g = 0; g < G; ++g)
+            for (int r = 0; r < h->R; ++r)
+                if (h->group_of[r] == g) by_group.push_back(r);
+        if ((st = upload(&h->by_group_d, by_group, s))) return fail(st);
+    }
     if (cudaMemcpyAsync(u_eps_d, d->u_eps_host, pb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(u_J_d, d->u_J_host, pb, cudaMemcpyHostToDevice, s) != cudaSuccess) {
         ctqw_set_error("copy of the uniform draws failed");
@@ -324,10 +333,60 @@ int ctqw_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t method
                         size_t *bytes) {
     if (!h || !bytes) { ctqw_set_error("null argument"); return CTQW_EINVAL; }
     if (dtype != CTQW_C64 && dtype != CTQW_C128) { ctqw_set_error("dtype %d", dtype); return CTQW_EINVAL; }
+    const int shape = (int)((flags >> CTQW_FUSED_SHAPE_SHIFT) & 0xF);
+    if ((method == 0 || method == 1) && !(flags & CTQW_FLAG_PLAIN) && shape == CTQW_SHAPE_WAVEFRONT &&
+        dtype == CTQW_C64) {
+        *bytes = wavefront_workspace_bytes(h);
+        return CTQW_OK;
+    }
     const bool fused = (method == 0 || method == 1) && !(flags & CTQW_FLAG_PLAIN) &&
                        fused_rows_supported(h, dtype);
     *bytes = fused ? 0 : 3 * (size_t)h->total_amp * elem_bytes(dtype);
     return CTQW_OK;
+}
+
+// The row-wavefront kernel between observation points; the observables of
+// each sample from the state in psi.  The carried rounding error lives in
+// the workspace (allocated stream-ordered when none is given).
+static int propagate_wavefront(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
+                               int32_t K, int64_t n_steps, int32_t obs_every, double *P_mean_dev,
+                               double *norm_dev, double *energy_dev, uint32_t flags,
+                               void *workspace_dev, size_t workspace_bytes, cudaStream_t s) {
+    if (!wavefront_supported(h, dtype, K)) {
+        ctqw_set_error("wavefront path: needs c64, m = 2, an open chain, every N in {64, 128, 192, "
+                       "256} with N + 1 > 2K + 8, and K <= 16");
+        return CTQW_EUNSUPPORTED;
+    }
+    const size_t need = wavefront_workspace_bytes(h);
+    void *lo = workspace_dev;
+    bool own = false;
+    if (workspace_dev && workspace_bytes < need) {
+        ctqw_set_error("wavefront path needs a workspace of %zu bytes (got %zu)", need, workspace_bytes);
+        return CTQW_EINVAL;
+    }
+    if (!lo) {
+        CTQW_CUDA_TRY(cudaMallocAsync(&lo, need, s));
+        own = true;
+    }
+    const int64_t n_obs = n_samples(n_steps, obs_every);
+    int st = zero_outputs(h, n_obs, P_mean_dev, norm_dev, energy_dev, s);
+    if (st == CTQW_OK && cudaMemsetAsync(lo, 0, need, s) != cudaSuccess) st = ctqw_cuda_fail(cudaGetLastError(), "memset");
+    const int comp = (flags & CTQW_FLAG_NO_COMPENSATION) ? 0 : 1;
+    int64_t obs = 0;
+    for (int64_t step = 0; st == CTQW_OK && step <= n_steps;) {
+        if (obs_every > 0 && step % obs_every == 0) {
+            st = launch_observables(h, dtype, psi_dev, P_mean_dev ? P_mean_dev + obs * h->p_width : nullptr,
+                                    nullptr, norm_dev ? norm_dev + obs * h->R : nullptr,
+                                    energy_dev ? energy_dev + obs * h->R : nullptr, s);
+            ++obs;
+        }
+        if (st != CTQW_OK || step == n_steps) break;
+        const int64_t next = obs_every > 0 ? std::min<int64_t>(n_steps, (step / obs_every + 1) * obs_every) : n_steps;
+        st = launch_taylor_wavefront(h, psi_dev, lo, dt, K, next - step, comp, s);
+        step = next;
+    }
+    if (own) cudaFreeAsync(lo, s);
+    return st;
 }
 
 int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
@@ -338,6 +397,10 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
     if (K < 1 || K > 30) { ctqw_set_error("K must be in 1..30 (got %d)", K); return CTQW_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n_obs = n_samples(n_steps, obs_every);
+    const int shape = (int)((flags >> CTQW_FUSED_SHAPE_SHIFT) & 0xF);
+    if (!(flags & CTQW_FLAG_PLAIN) && shape == CTQW_SHAPE_WAVEFRONT)
+        return propagate_wavefront(h, dtype, psi_dev, dt, K, n_steps, obs_every, P_mean_dev,
+                                   norm_dev, energy_dev, flags, workspace_dev, workspace_bytes, s);
     const bool fused = !(flags & CTQW_FLAG_PLAIN) && fused_rows_supported(h, dtype);
     if (!fused) {
         const size_t need = 3 * (size_t)h->total_amp * elem_bytes(dtype);
@@ -349,7 +412,6 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
     CTQW_TRY(zero_outputs(h, n_obs, P_mean_dev, norm_dev, energy_dev, s));
     if (fused) {
         // shape index 0..3: full-row kernel; 4..7: the banded kernel (shape - 4)
-        const int shape = (int)((flags >> CTQW_FUSED_SHAPE_SHIFT) & 0xF);
         const int comp = (flags & CTQW_FLAG_NO_COMPENSATION) ? 0 : 1;
         const int test = (flags & CTQW_FLAG_TEST_WAIT_TIMEOUT) ? 1 : 0;
         if (shape < 4)
@@ -361,6 +423,34 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
 
     const size_t sb = (size_t)h->total_amp * elem_bytes(dtype);
     char *ws = (char *)workspace_dev;
+    if (dtype == CTQW_C64) {
+        // FP32: Horner stages and a compensated state update (see k_plain.cu)
+        void *wa = ws, *wb = ws + sb, *lo = ws + 2 * sb;
+        CTQW_CUDA_TRY(cudaMemsetAsync(lo, 0, sb, s));
+        int64_t obs = 0;
+        for (int64_t step = 0; step <= n_steps; ++step) {
+            if (obs_every > 0 && step % obs_every == 0) {
+                CTQW_TRY(launch_observables(h, dtype, psi_dev, P_mean_dev ? P_mean_dev + obs * h->p_width : nullptr,
+                                            nullptr, norm_dev ? norm_dev + obs * h->R : nullptr,
+                                            energy_dev ? energy_dev + obs * h->R : nullptr, s));
+                ++obs;
+            }
+            if (step == n_steps) break;
+            const void *in = psi_dev;
+            void *out = wa;
+            if (K == 1) {
+                CTQW_CUDA_TRY(cudaMemcpyAsync(wa, psi_dev, sb, cudaMemcpyDeviceToDevice, s));
+                in = wa;
+            }
+            for (int j = K; j >= 2; --j) {
+                CTQW_TRY(launch_horner_stage(h, in, psi_dev, out, dt / j, s));
+                in = out;
+                out = (out == wa) ? wb : wa;
+            }
+            CTQW_TRY(launch_horner_final(h, in, psi_dev, lo, dt, s));
+        }
+        return CTQW_OK;
+    }
     void *cur = psi_dev, *acc = ws, *phi1 = ws + sb, *phi2 = ws + 2 * sb;
     int64_t obs = 0;
     for (int64_t step = 0; step <= n_steps; ++step) {

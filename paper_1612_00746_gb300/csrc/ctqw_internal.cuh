@@ -31,6 +31,7 @@ struct ctqw_hamiltonian {
     int64_t *par_off_d = nullptr, *st_off_d = nullptr, *group_off_d = nullptr,
             *joint_off_d = nullptr;
     double *inv_count_d = nullptr;  // [G] 1 / R_g
+    int32_t *by_group_d = nullptr;  // [R] realization indices ordered by size group
     int *status_d = nullptr;        // nonzero after a kernel's bounded wait gave up
 };
 
@@ -89,6 +90,13 @@ int launch_init_state(const ctqw_hamiltonian *h, const int32_t *sites_d, int dty
 int launch_taylor_term(const ctqw_hamiltonian *h, int dtype, const void *in, void *out,
                        const void *psi, void *acc, double coef, int first, cudaStream_t s);
 
+// FP32 per-term path in Horner form: out = psi + coef (-i) H in;
+// final: psi (+lo, carried rounding error) += -i dt H w2.
+int launch_horner_stage(const ctqw_hamiltonian *h, const void *in, const void *psi, void *out,
+                        double coef, cudaStream_t s);
+int launch_horner_final(const ctqw_hamiltonian *h, const void *w2, void *psi, void *lo, double dt,
+                        cudaStream_t s);
+
 // RK4 stage (a4): k = -i H in; next = psi + a k (if next); acc (= psi if first) += b k.
 int launch_rk4_stage(const ctqw_hamiltonian *h, int dtype, const void *in, void *next,
                      const void *psi, void *acc, double a, double b, int first, cudaStream_t s);
@@ -116,6 +124,14 @@ int launch_taylor_fused_rows(const ctqw_hamiltonian *h, void *psi, double dt, in
                              int64_t n_steps, int obs_every, double *P_mean, double *norm,
                              double *energy, int compensated, int shape, int test_timeout,
                              cudaStream_t s);
+
+// Fused row-wavefront Taylor propagation (m = 2, c64, open chains): every
+// Taylor term of a step on chip, psi streamed once per step; lo: the carried
+// rounding error (one c64 state, lane-major rows, zero before the first step).
+bool wavefront_supported(const ctqw_hamiltonian *h, int dtype, int K);
+size_t wavefront_workspace_bytes(const ctqw_hamiltonian *h);
+int launch_taylor_wavefront(const ctqw_hamiltonian *h, void *psi, void *lo, double dt, int K,
+                            int64_t n_steps, int compensated, cudaStream_t s);
 
 // Fused cluster-resident Taylor propagation (m = 2, c64), multi-warp bands.
 bool fused_taylor_supported(const ctqw_hamiltonian *h, int dtype);

@@ -103,3 +103,96 @@ int launch_rk4_stage(const ctqw_hamiltonian *h, int dtype, const void *in, void 
     CTQW_CUDA_TRY(cudaGetLastError());
     return CTQW_OK;
 }
+
+// ---------------------------------------------------------------- FP32 per-term path
+// Horner form of the same order-K polynomial (Sec. 2.3), one launch per stage:
+//   w_K = psi + (A/K) psi,  w_j = psi + (A/j) w_{j+1},  psi(t+dt) = psi + A w_2,
+// A = -i dt H.  In FP32 the forward sum drops every term below half an ulp
+// of the running sum, which truncates the series; Horner keeps each term at
+// its own scale.  The final stage adds A w_2 to the state with its rounding
+// error carried in a second FP32 word (lo).
+namespace {
+
+template <int M>
+__global__ void __launch_bounds__(256) horner_stage_kernel(RealTable tab, const float *__restrict__ eps,
+                                                           const float *__restrict__ J,
+                                                           const float2 *__restrict__ in,
+                                                           const float2 *__restrict__ psi,
+                                                           float2 *__restrict__ out, float coef) {
+    const int r = blockIdx.y;
+    const int N = tab.N[r];
+    int64_t D = N;
+#pragma unroll
+    for (int j = 1; j < M; ++j) D *= N;
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= D) return;
+    const int64_t base = tab.st_off[r];
+    const int64_t po = tab.par_off[r];
+    int x[M];
+    unflatten<M>(s, N, x);
+    const float2 y = apply_h<float, M>(in + base, s, x, N, eps + po, J + po, (float)tab.U);
+    const float2 q = psi[base + s];
+    out[base + s] = make_float2(fmaf(coef, y.y, q.x), fmaf(-coef, y.x, q.y));   // q + coef (-i) y
+}
+
+template <int M>
+__global__ void __launch_bounds__(256) horner_final_kernel(RealTable tab, const float *__restrict__ eps,
+                                                           const float *__restrict__ J,
+                                                           const float2 *__restrict__ w2,
+                                                           float2 *__restrict__ psi,
+                                                           float2 *__restrict__ lo, float dt) {
+    const int r = blockIdx.y;
+    const int N = tab.N[r];
+    int64_t D = N;
+#pragma unroll
+    for (int j = 1; j < M; ++j) D *= N;
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= D) return;
+    const int64_t base = tab.st_off[r];
+    const int64_t po = tab.par_off[r];
+    int x[M];
+    unflatten<M>(s, N, x);
+    const float2 y = apply_h<float, M>(w2 + base, s, x, N, eps + po, J + po, (float)tab.U);
+    const float sx = dt * y.y, sy = -dt * y.x;   // -i dt H w2
+    float2 h = psi[base + s], l = lo[base + s];
+    // TwoSum then FastTwoSum per component
+    auto add = [](float &hi, float &lw, float v) {
+        const float t = __fadd_rn(hi, v);
+        const float bb = __fsub_rn(t, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(v, bb));
+        const float e = __fadd_rn(err, lw);
+        const float h2 = __fadd_rn(t, e);
+        lw = __fsub_rn(e, __fsub_rn(h2, t));
+        hi = h2;
+    };
+    add(h.x, l.x, sx);
+    add(h.y, l.y, sy);
+    psi[base + s] = h;
+    lo[base + s] = l;
+}
+
+dim3 grid_all(const ctqw_hamiltonian *h) {
+    int64_t D = 1;
+    for (int j = 0; j < h->m; ++j) D *= h->Nmax;
+    return dim3((unsigned)((D + 255) / 256), (unsigned)h->R);
+}
+
+}  // namespace
+
+int launch_horner_stage(const ctqw_hamiltonian *h, const void *in, const void *psi, void *out,
+                        double coef, cudaStream_t s) {
+    auto k = h->m == 2 ? horner_stage_kernel<2> : horner_stage_kernel<3>;
+    k<<<grid_all(h), 256, 0, s>>>(real_table(h), h->eps32, h->J32, (const float2 *)in,
+                                  (const float2 *)psi, (float2 *)out, (float)coef);
+    CTQW_CUDA_TRY(cudaGetLastError());
+    return CTQW_OK;
+}
+
+int launch_horner_final(const ctqw_hamiltonian *h, const void *w2, void *psi, void *lo, double dt,
+                        cudaStream_t s) {
+    auto k = h->m == 2 ? horner_final_kernel<2> : horner_final_kernel<3>;
+    k<<<grid_all(h), 256, 0, s>>>(real_table(h), h->eps32, h->J32, (const float2 *)w2,
+                                  (float2 *)psi, (float2 *)lo, (float)dt);
+    CTQW_CUDA_TRY(cudaGetLastError());
+    return CTQW_OK;
+}

@@ -29,6 +29,10 @@ FLAG_TEST_WAIT_TIMEOUT = 0x8
 def FUSED_SHAPE(k: int) -> int:
     return (int(k) & 0xF) << 8
 
+
+SHAPE_WAVEFRONT = 8
+FLAG_WAVEFRONT = FUSED_SHAPE(SHAPE_WAVEFRONT)   # the row-wavefront kernel
+
 TAYLOR, RK4 = 0, 1
 
 EXPORTED = (
