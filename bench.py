@@ -37,6 +37,7 @@ import ctqw_workloads as cw  # noqa: E402
 METRIC = "site-updates/s (dim x K x steps x realizations)"
 UNIT = "site-updates/s"
 FP32_FMA_LANES_PER_SM = 128      # FP32 FMA lanes per SM
+FP64_FMA_PER_SM = 2              # FP64 FMA per SM per cycle
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
@@ -167,6 +168,70 @@ def fused_traffic(workload: str):
     return ent.get("dram_bytes_per_launch")
 
 
+def propagation_path(w, dtype, flags):
+    """Which kernels ctqw_propagate_taylor runs for this workload (mirrors the library)."""
+    from paper_1612_00746_gb300 import ctqw
+
+    shape = (flags >> 8) & 0xF
+    if flags & ctqw.FLAG_PLAIN:
+        return "plain"
+    if shape == ctqw.SHAPE_WAVEFRONT:
+        return "wavefront"
+    uniform = w.ragged_sizes is None
+    if dtype == ctqw.C64 and w.m == 2 and uniform and w.N in (64, 128, 192, 256):
+        return "rows" if shape < 4 else "banded"
+    return "plain"
+
+
+def roofline_of(w, dtype, flags, units, kernel_ms, peaks, traffic):
+    """Roofline entry of the kernel that dominates the propagate call.
+
+    Fused kernels (every Taylor term on chip) are bound by the FP32 FMA pipe:
+    8m+4 algorithmic flops per site-update against 152 SMs x 128 lanes x 2
+    flop x 2070 MHz.  The FP32 per-term kernels stream the state through HBM:
+    per site-update ((K-1) 24 + 40)/K bytes (Horner stages and the
+    compensated final stage), against the measured copy bandwidth.  The FP64
+    per-term kernels move 64 bytes per site-update but are bound by the FP64
+    pipe (2 DFMA per SM per cycle).
+    """
+    from paper_1612_00746_gb300 import ctqw
+
+    path = propagation_path(w, dtype, flags)
+    sec = kernel_ms / 1000.0
+    if path in ("rows", "banded", "wavefront"):
+        flops_per_unit = 8 * w.m + 4
+        achieved = units * flops_per_unit / sec / 1e12
+        peak = SM_COUNT * FP32_FMA_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        kernel = {"rows": "taylor_fused_rows_kernel", "banded": "taylor_fused_kernel",
+                  "wavefront": "taylor_wavefront_kernel"}[path]
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic if path == "rows" else None,
+                "kernel": kernel, "kernel_ms": kernel_ms, "flops_per_site_update": flops_per_unit,
+                "peak_basis": "152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz (derived)",
+                "hbm_gbs_measured": peaks.get("hbm_gbs")}
+    if dtype == ctqw.C128:
+        # FP64 on GB300 runs 2 DFMA per SM per cycle: the per-term FP64
+        # kernels are bound by that pipe, not by HBM (64 B per site-update)
+        flops_per_unit = 8 * w.m + 4
+        achieved = units * flops_per_unit / sec / 1e12
+        peak = SM_COUNT * FP64_FMA_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "taylor_term_kernel<double>",
+                "kernel_ms": kernel_ms, "flops_per_site_update": flops_per_unit,
+                "hbm_gbs_achieved": units * 64.0 / sec / 1e9, "bytes_per_site_update": 64.0,
+                "peak_basis": "152 SMs x 2 DFMA x 2 flop x 2070 MHz (FP64, derived)",
+                "timing": "the whole propagate call (observables kernels included)"}
+    bpu = ((w.K - 1) * 24.0 + 40.0) / w.K
+    kernel = "horner_stage_kernel + horner_final_kernel"
+    gbs = units * bpu / sec / 1e9
+    peak = peaks.get("hbm_gbs")
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+            "frac": gbs / peak if peak else None, "traffic": None, "kernel": kernel,
+            "kernel_ms": kernel_ms, "bytes_per_site_update": bpu,
+            "peak_basis": "measured copy bandwidth" if peak else None,
+            "timing": "the whole propagate call (observables kernels included)"}
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -251,7 +316,7 @@ def run_ours(args):
     # realizations of this rank: its own block of the (weakly scaled) ensemble
     realizations = list(range(rank * w.R, (rank + 1) * w.R))
     u_eps, u_J, sizes, _ = cw.packed_draws(w, realizations)
-    dtype = w.dtype
+    dtype = w.dtype if not args.dtype else {"c64": ctqw.C64, "c128": ctqw.C128}[args.dtype]
     stream = torch.cuda.current_stream()
     h = ctqw.Hamiltonian(w.m, w.statistics, w.periodic, sizes, w.J0, w.U, w.eps_halfwidth,
                          w.J_halfwidth, u_eps, u_J)
@@ -265,11 +330,15 @@ def run_ours(args):
     counts = torch.tensor(np.repeat(h.group_count, h.group_sizes), dtype=torch.float64, device=dev)
     D = float(np.sum(sizes.astype(np.float64) ** w.m))
     units_per_step = D * w.K * w.n_steps
-    if (args.flags >> 8) & 0xF == ctqw.SHAPE_WAVEFRONT:
+    path = propagation_path(w, dtype, args.flags)
+    if path == "wavefront":
         # init_state + one observables kernel per sample + one wavefront launch
         # per segment between samples and size group
         n_seg = -(-w.n_steps // w.obs_every) if w.obs_every else 1
         launches_per_step = 1 + n_obs + n_seg * len(h.group_sizes)
+    elif path == "plain":
+        # init_state + K stage launches per step + one observables kernel per sample
+        launches_per_step = 1 + w.n_steps * w.K + n_obs
     else:
         launches_per_step = 2   # init_state kernel + fused propagation kernel
 
@@ -417,27 +486,22 @@ def run_ours(args):
         hs.close()
 
     peaks = measured_peaks()
-    flops_per_unit = 8 * w.m + 4
-    achieved = units_per_step * flops_per_unit / (kernel_ms / 1000.0) / 1e12
-    peak = SM_COUNT * FP32_FMA_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roofline = roofline_of(w, dtype, args.flags, units_per_step, kernel_ms, peaks,
+                           fused_traffic(w.name) if not (args.realizations or args.n_steps) else None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if dtype == ctqw.C64 else "f64",
+        "data": "synthetic",
         "config": {"workload": w.name, "m": w.m, "N": w.N, "R_per_gpu": w.R, "K": w.K,
                    "dt": w.dt, "n_steps": w.n_steps, "obs_every": w.obs_every,
                    "statistics": "bosons" if w.statistics == cw.BOSONS else "distinguishable",
-                   "precision": "complex FP32, compensated state update, FP64 reductions",
-                   "l2": "inputs larger than L2 (states %.0f MB per GPU)" % (D * 8 / 1e6),
+                   "precision": ("complex FP32, compensated state update, FP64 reductions"
+                                 if dtype == ctqw.C64 else "complex FP64"),
+                   "l2": "inputs larger than L2 (states %.0f MB per GPU)" % (D * (8 if dtype == ctqw.C64 else 16) / 1e6),
                    "parallelism": f"realizations sharded, {world} rank(s)"},
         "gpu_launches": launches_per_step * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak,
-                     "traffic": fused_traffic(w.name) if not (args.realizations or args.n_steps) else None,
-                     "kernel": "taylor_fused_rows_kernel", "kernel_ms": kernel_ms,
-                     "flops_per_site_update": flops_per_unit,
-                     "peak_basis": "152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz (derived)",
-                     "hbm_gbs_measured": peaks.get("hbm_gbs")},
+        "roofline": roofline,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "fp64_plain": fp64,
@@ -467,6 +531,7 @@ def main(argv=None):
     ap.add_argument("--realizations", type=int, default=0, help="override R (small profiling cases)")
     ap.add_argument("--n-steps", type=int, default=0, help="override the workload's steps")
     ap.add_argument("--flags", type=int, default=0, help="ctqw propagation flags (e.g. 4 = wide CTA)")
+    ap.add_argument("--dtype", choices=["c64", "c128"], default=None, help="override the workload's type")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-plain", action="store_true")

@@ -7,27 +7,54 @@
 
 namespace {
 
+// Grid of the per-term kernels: x = block of rows (x_1..x_{M-1} flattened;
+// blockDim.y rows a block, for rows shorter than 256), y = chunk of the last
+// coordinate x_M, z = realization within one size group (list: that group's
+// realizations).  One launch per size group (and per 65535 realizations of
+// it), so a ragged batch launches no empty blocks and no thread divides a
+// 64-bit index.
+template <int M>
+struct Site {
+    int r, N;
+    int64_t s;   // flat index within the realization's state
+    int x[M];
+};
+
+template <int M>
+__device__ __forceinline__ bool site_of(const RealTable &tab, const int32_t *__restrict__ list, Site<M> &p) {
+    p.r = list[blockIdx.z];
+    p.N = tab.N[p.r];
+    const int xm = blockIdx.y * blockDim.x + threadIdx.x;
+    if (xm >= p.N) return false;
+    const int q = blockIdx.x * blockDim.y + threadIdx.y;
+    if (q >= (M == 2 ? p.N : p.N * p.N)) return false;
+    if (M == 2) {
+        p.x[0] = q;
+    } else {
+        p.x[0] = q / p.N;
+        p.x[1] = q - p.x[0] * p.N;
+    }
+    p.x[M - 1] = xm;
+    p.s = (int64_t)q * p.N + xm;
+    return true;
+}
+
 // Phi^(j) = -(i dt/j) H Phi^(j-1);  acc = (first ? psi : acc) + Phi^(j).
 template <typename T, int M>
-__global__ void __launch_bounds__(256) taylor_term_kernel(RealTable tab, const T *__restrict__ eps,
+__global__ void __launch_bounds__(256) taylor_term_kernel(RealTable tab, const int32_t *__restrict__ list,
+                                                          const T *__restrict__ eps,
                                                           const T *__restrict__ J,
                                                           const cplx_t<T> *__restrict__ in,
                                                           cplx_t<T> *__restrict__ out,
                                                           const cplx_t<T> *__restrict__ psi,
                                                           cplx_t<T> *__restrict__ acc, T coef,
                                                           int first) {
-    const int r = blockIdx.y;
-    const int N = tab.N[r];
-    int64_t D = N;
-#pragma unroll
-    for (int j = 1; j < M; ++j) D *= N;
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= D) return;
-    const int64_t base = tab.st_off[r];
-    const int64_t po = tab.par_off[r];
-    int x[M];
-    unflatten<M>(s, N, x);
-    cplx_t<T> y = apply_h<T, M>(in + base, s, x, N, eps + po, J + po, (T)tab.U);
+    Site<M> p;
+    if (!site_of<M>(tab, list, p)) return;
+    const int64_t s = p.s;
+    const int64_t base = tab.st_off[p.r];
+    const int64_t po = tab.par_off[p.r];
+    cplx_t<T> y = apply_h<T, M>(in + base, s, p.x, p.N, eps + po, J + po, (T)tab.U);
     cplx_t<T> phi = mk<T>(coef * y.y, -coef * y.x);   // -(i coef) y
     out[base + s] = phi;
     cplx_t<T> a = first ? psi[base + s] : acc[base + s];
@@ -36,72 +63,85 @@ __global__ void __launch_bounds__(256) taylor_term_kernel(RealTable tab, const T
 
 // k = -i H in;  next = psi + a k (when next != null);  acc = (first ? psi : acc) + b k.
 template <typename T, int M>
-__global__ void __launch_bounds__(256) rk4_stage_kernel(RealTable tab, const T *__restrict__ eps,
+__global__ void __launch_bounds__(256) rk4_stage_kernel(RealTable tab, const int32_t *__restrict__ list,
+                                                        const T *__restrict__ eps,
                                                         const T *__restrict__ J,
                                                         const cplx_t<T> *__restrict__ in,
                                                         cplx_t<T> *__restrict__ next,
                                                         const cplx_t<T> *__restrict__ psi,
                                                         cplx_t<T> *__restrict__ acc, T a, T b,
                                                         int first) {
-    const int r = blockIdx.y;
-    const int N = tab.N[r];
-    int64_t D = N;
-#pragma unroll
-    for (int j = 1; j < M; ++j) D *= N;
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= D) return;
-    const int64_t base = tab.st_off[r];
-    const int64_t po = tab.par_off[r];
-    int x[M];
-    unflatten<M>(s, N, x);
-    cplx_t<T> y = apply_h<T, M>(in + base, s, x, N, eps + po, J + po, (T)tab.U);
+    Site<M> p;
+    if (!site_of<M>(tab, list, p)) return;
+    const int64_t s = p.s;
+    const int64_t base = tab.st_off[p.r];
+    const int64_t po = tab.par_off[p.r];
+    cplx_t<T> y = apply_h<T, M>(in + base, s, p.x, p.N, eps + po, J + po, (T)tab.U);
     cplx_t<T> k = mk<T>(y.y, -y.x);   // -i H in
-    cplx_t<T> p = psi[base + s];
-    if (next) next[base + s] = mk<T>(p.x + a * k.x, p.y + a * k.y);
-    cplx_t<T> c = first ? p : acc[base + s];
+    cplx_t<T> q = psi[base + s];
+    if (next) next[base + s] = mk<T>(q.x + a * k.x, q.y + a * k.y);
+    cplx_t<T> c = first ? q : acc[base + s];
     acc[base + s] = mk<T>(c.x + b * k.x, c.y + b * k.y);
 }
 
-dim3 grid_for(const ctqw_hamiltonian *h) {
-    int64_t D = 1;
-    for (int j = 0; j < h->m; ++j) D *= h->Nmax;
-    return dim3((unsigned)((D + 255) / 256), (unsigned)h->R);
+// One launch per size group (per 65535 of its realizations): grid (rows,
+// chunks of x_M, realizations).
+template <typename F>
+int for_each_group(const ctqw_hamiltonian *h, F &&launch) {
+    int off = 0;
+    for (size_t g = 0; g < h->group_N.size(); ++g) {
+        const int N = h->group_N[g], cnt = h->group_count[g];
+        int64_t rows = 1;
+        for (int j = 1; j < h->m; ++j) rows *= N;
+        if (rows > 0x7fffffff) {
+            ctqw_set_error("per-term path: N^(m-1) = %lld rows above the grid limit", (long long)rows);
+            return CTQW_EUNSUPPORTED;
+        }
+        const int tx = N >= 256 ? 256 : ((N + 31) / 32) * 32;
+        const int ty = 256 / tx;   // rows a block
+        for (int done = 0; done < cnt; done += 65535) {
+            const int part = cnt - done < 65535 ? cnt - done : 65535;
+            const dim3 grid((unsigned)((rows + ty - 1) / ty), (unsigned)((N + tx - 1) / tx), (unsigned)part);
+            launch(grid, dim3((unsigned)tx, (unsigned)ty), h->by_group_d + off + done);
+            CTQW_CUDA_TRY(cudaGetLastError());
+        }
+        off += cnt;
+    }
+    return CTQW_OK;
 }
 
 }  // namespace
 
 int launch_taylor_term(const ctqw_hamiltonian *h, int dtype, const void *in, void *out,
                        const void *psi, void *acc, double coef, int first, cudaStream_t s) {
-    dim3 grid = grid_for(h), block(256);
     RealTable t = real_table(h);
-    if (dtype == CTQW_C64) {
-        auto k = h->m == 2 ? taylor_term_kernel<float, 2> : taylor_term_kernel<float, 3>;
-        k<<<grid, block, 0, s>>>(t, h->eps32, h->J32, (const float2 *)in, (float2 *)out,
-                                 (const float2 *)psi, (float2 *)acc, (float)coef, first);
-    } else {
-        auto k = h->m == 2 ? taylor_term_kernel<double, 2> : taylor_term_kernel<double, 3>;
-        k<<<grid, block, 0, s>>>(t, h->eps64, h->J64, (const double2 *)in, (double2 *)out,
-                                 (const double2 *)psi, (double2 *)acc, coef, first);
-    }
-    CTQW_CUDA_TRY(cudaGetLastError());
-    return CTQW_OK;
+    return for_each_group(h, [&](dim3 grid, dim3 block, const int32_t *list) {
+        if (dtype == CTQW_C64) {
+            auto k = h->m == 2 ? taylor_term_kernel<float, 2> : taylor_term_kernel<float, 3>;
+            k<<<grid, block, 0, s>>>(t, list, h->eps32, h->J32, (const float2 *)in, (float2 *)out,
+                                     (const float2 *)psi, (float2 *)acc, (float)coef, first);
+        } else {
+            auto k = h->m == 2 ? taylor_term_kernel<double, 2> : taylor_term_kernel<double, 3>;
+            k<<<grid, block, 0, s>>>(t, list, h->eps64, h->J64, (const double2 *)in, (double2 *)out,
+                                     (const double2 *)psi, (double2 *)acc, coef, first);
+        }
+    });
 }
 
 int launch_rk4_stage(const ctqw_hamiltonian *h, int dtype, const void *in, void *next,
                      const void *psi, void *acc, double a, double b, int first, cudaStream_t s) {
-    dim3 grid = grid_for(h), block(256);
     RealTable t = real_table(h);
-    if (dtype == CTQW_C64) {
-        auto k = h->m == 2 ? rk4_stage_kernel<float, 2> : rk4_stage_kernel<float, 3>;
-        k<<<grid, block, 0, s>>>(t, h->eps32, h->J32, (const float2 *)in, (float2 *)next,
-                                 (const float2 *)psi, (float2 *)acc, (float)a, (float)b, first);
-    } else {
-        auto k = h->m == 2 ? rk4_stage_kernel<double, 2> : rk4_stage_kernel<double, 3>;
-        k<<<grid, block, 0, s>>>(t, h->eps64, h->J64, (const double2 *)in, (double2 *)next,
-                                 (const double2 *)psi, (double2 *)acc, a, b, first);
-    }
-    CTQW_CUDA_TRY(cudaGetLastError());
-    return CTQW_OK;
+    return for_each_group(h, [&](dim3 grid, dim3 block, const int32_t *list) {
+        if (dtype == CTQW_C64) {
+            auto k = h->m == 2 ? rk4_stage_kernel<float, 2> : rk4_stage_kernel<float, 3>;
+            k<<<grid, block, 0, s>>>(t, list, h->eps32, h->J32, (const float2 *)in, (float2 *)next,
+                                     (const float2 *)psi, (float2 *)acc, (float)a, (float)b, first);
+        } else {
+            auto k = h->m == 2 ? rk4_stage_kernel<double, 2> : rk4_stage_kernel<double, 3>;
+            k<<<grid, block, 0, s>>>(t, list, h->eps64, h->J64, (const double2 *)in, (double2 *)next,
+                                     (const double2 *)psi, (double2 *)acc, a, b, first);
+        }
+    });
 }
 
 // ---------------------------------------------------------------- FP32 per-term path
@@ -114,45 +154,35 @@ int launch_rk4_stage(const ctqw_hamiltonian *h, int dtype, const void *in, void 
 namespace {
 
 template <int M>
-__global__ void __launch_bounds__(256) horner_stage_kernel(RealTable tab, const float *__restrict__ eps,
+__global__ void __launch_bounds__(256) horner_stage_kernel(RealTable tab, const int32_t *__restrict__ list,
+                                                           const float *__restrict__ eps,
                                                            const float *__restrict__ J,
                                                            const float2 *__restrict__ in,
                                                            const float2 *__restrict__ psi,
                                                            float2 *__restrict__ out, float coef) {
-    const int r = blockIdx.y;
-    const int N = tab.N[r];
-    int64_t D = N;
-#pragma unroll
-    for (int j = 1; j < M; ++j) D *= N;
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= D) return;
-    const int64_t base = tab.st_off[r];
-    const int64_t po = tab.par_off[r];
-    int x[M];
-    unflatten<M>(s, N, x);
-    const float2 y = apply_h<float, M>(in + base, s, x, N, eps + po, J + po, (float)tab.U);
+    Site<M> p;
+    if (!site_of<M>(tab, list, p)) return;
+    const int64_t s = p.s;
+    const int64_t base = tab.st_off[p.r];
+    const int64_t po = tab.par_off[p.r];
+    const float2 y = apply_h<float, M>(in + base, s, p.x, p.N, eps + po, J + po, (float)tab.U);
     const float2 q = psi[base + s];
     out[base + s] = make_float2(fmaf(coef, y.y, q.x), fmaf(-coef, y.x, q.y));   // q + coef (-i) y
 }
 
 template <int M>
-__global__ void __launch_bounds__(256) horner_final_kernel(RealTable tab, const float *__restrict__ eps,
+__global__ void __launch_bounds__(256) horner_final_kernel(RealTable tab, const int32_t *__restrict__ list,
+                                                           const float *__restrict__ eps,
                                                            const float *__restrict__ J,
                                                            const float2 *__restrict__ w2,
                                                            float2 *__restrict__ psi,
                                                            float2 *__restrict__ lo, float dt) {
-    const int r = blockIdx.y;
-    const int N = tab.N[r];
-    int64_t D = N;
-#pragma unroll
-    for (int j = 1; j < M; ++j) D *= N;
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= D) return;
-    const int64_t base = tab.st_off[r];
-    const int64_t po = tab.par_off[r];
-    int x[M];
-    unflatten<M>(s, N, x);
-    const float2 y = apply_h<float, M>(w2 + base, s, x, N, eps + po, J + po, (float)tab.U);
+    Site<M> p;
+    if (!site_of<M>(tab, list, p)) return;
+    const int64_t s = p.s;
+    const int64_t base = tab.st_off[p.r];
+    const int64_t po = tab.par_off[p.r];
+    const float2 y = apply_h<float, M>(w2 + base, s, p.x, p.N, eps + po, J + po, (float)tab.U);
     const float sx = dt * y.y, sy = -dt * y.x;   // -i dt H w2
     float2 h = psi[base + s], l = lo[base + s];
     // TwoSum then FastTwoSum per component
@@ -171,28 +201,24 @@ __global__ void __launch_bounds__(256) horner_final_kernel(RealTable tab, const 
     lo[base + s] = l;
 }
 
-dim3 grid_all(const ctqw_hamiltonian *h) {
-    int64_t D = 1;
-    for (int j = 0; j < h->m; ++j) D *= h->Nmax;
-    return dim3((unsigned)((D + 255) / 256), (unsigned)h->R);
-}
-
 }  // namespace
 
 int launch_horner_stage(const ctqw_hamiltonian *h, const void *in, const void *psi, void *out,
                         double coef, cudaStream_t s) {
-    auto k = h->m == 2 ? horner_stage_kernel<2> : horner_stage_kernel<3>;
-    k<<<grid_all(h), 256, 0, s>>>(real_table(h), h->eps32, h->J32, (const float2 *)in,
-                                  (const float2 *)psi, (float2 *)out, (float)coef);
-    CTQW_CUDA_TRY(cudaGetLastError());
-    return CTQW_OK;
+    RealTable t = real_table(h);
+    return for_each_group(h, [&](dim3 grid, dim3 block, const int32_t *list) {
+        auto k = h->m == 2 ? horner_stage_kernel<2> : horner_stage_kernel<3>;
+        k<<<grid, block, 0, s>>>(t, list, h->eps32, h->J32, (const float2 *)in, (const float2 *)psi,
+                                 (float2 *)out, (float)coef);
+    });
 }
 
 int launch_horner_final(const ctqw_hamiltonian *h, const void *w2, void *psi, void *lo, double dt,
                         cudaStream_t s) {
-    auto k = h->m == 2 ? horner_final_kernel<2> : horner_final_kernel<3>;
-    k<<<grid_all(h), 256, 0, s>>>(real_table(h), h->eps32, h->J32, (const float2 *)w2,
-                                  (float2 *)psi, (float2 *)lo, (float)dt);
-    CTQW_CUDA_TRY(cudaGetLastError());
-    return CTQW_OK;
+    RealTable t = real_table(h);
+    return for_each_group(h, [&](dim3 grid, dim3 block, const int32_t *list) {
+        auto k = h->m == 2 ? horner_final_kernel<2> : horner_final_kernel<3>;
+        k<<<grid, block, 0, s>>>(t, list, h->eps32, h->J32, (const float2 *)w2, (float2 *)psi,
+                                 (float2 *)lo, (float)dt);
+    });
 }
