@@ -343,6 +343,19 @@ def run_ours(args):
         launches_per_step = 2   # init_state kernel + fused propagation kernel
 
     prop_events = []
+    graph = None
+    if args.graph:
+        # the propagate call (all its launches) captured once, replayed every step
+        ctqw.ctqw_init_state(h, psi, sites, dtype)
+        torch.cuda.synchronize()
+        gs = torch.cuda.Stream()
+        gs.wait_stream(stream)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gs):
+            ctqw.ctqw_propagate_taylor(h, psi, dtype, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en,
+                                       args.flags, ws, stream=gs)
+        stream.wait_stream(gs)
+        torch.cuda.synchronize()
 
     def step(record=False):
         ctqw.ctqw_init_state(h, psi, sites, dtype)
@@ -350,8 +363,11 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-        ctqw.ctqw_propagate_taylor(h, psi, dtype, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en,
-                                   args.flags, ws)
+        if graph is not None:
+            graph.replay()
+        else:
+            ctqw.ctqw_propagate_taylor(h, psi, dtype, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en,
+                                       args.flags, ws)
         if record:
             e1.record(stream)
             prop_events.append((e0, e1))
@@ -499,7 +515,8 @@ def run_ours(args):
                    "precision": ("complex FP32, compensated state update, FP64 reductions"
                                  if dtype == ctqw.C64 else "complex FP64"),
                    "l2": "inputs larger than L2 (states %.0f MB per GPU)" % (D * (8 if dtype == ctqw.C64 else 16) / 1e6),
-                   "parallelism": f"realizations sharded, {world} rank(s)"},
+                   "parallelism": f"realizations sharded, {world} rank(s)",
+                   "launch": "cuda graph replay" if args.graph else "eager"},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline,
         "e2e": e2e,
@@ -514,6 +531,71 @@ def run_ours(args):
     h.close()
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def run_adjoint(args):
+    """Time ctqw_adjoint_grad (loss on Pbar(x, T) and its gradient) on one GPU.
+
+    Reported as forward-equivalent site-updates/s (N^m K steps R of the
+    forward map per call), next to the forward pass alone on the same inputs.
+    """
+    import numpy as np
+    import torch
+
+    from paper_1612_00746_gb300 import ctqw
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ctqw.load()
+    w = cw.get(args.workload)
+    if args.realizations:
+        w = w.with_(R=args.realizations)
+    if args.n_steps:
+        w = w.with_(n_steps=args.n_steps)
+    M = 50
+    u_eps, u_J, sizes, _ = cw.packed_draws(w, list(range(w.R)))
+    em, jm = np.zeros(w.N), np.full(w.N, w.J0)
+    h = ctqw.Hamiltonian(w.m, w.statistics, w.periodic, sizes, w.J0, w.U, w.eps_halfwidth,
+                         w.J_halfwidth, u_eps, u_J, eps_mean=em, J_mean=jm)
+    psi = h.new_state(ctqw.C64, dev)
+    ctqw.ctqw_init_state(h, psi, ctqw.initial_sites(w, h), ctqw.C64)
+    target = torch.full((h.p_width,), 1.0 / w.N, dtype=torch.float64, device=dev)
+    ws = ctqw.adjoint_workspace(h, ctqw.C64, w.K, w.n_steps, M, dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ctqw.ctqw_adjoint_grad(h, psi, ctqw.C64, w.dt, w.K, w.n_steps, M, target, workspace=ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        loss, ge, gJ, _ = ctqw.ctqw_adjoint_grad(h, psi, ctqw.C64, w.dt, w.K, w.n_steps, M, target,
+                                                 workspace=ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the forward pass alone (same path the adjoint's forward sweep takes)
+    fws = h.workspace(ctqw.C64, ctqw.TAYLOR, ctqw.FLAG_PLAIN, dev)
+    scratch = psi.clone()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    ctqw.ctqw_propagate_taylor(h, scratch, ctqw.C64, w.dt, w.K, w.n_steps, 0, None, None, None,
+                               ctqw.FLAG_PLAIN, fws)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = f0.elapsed_time(f1)
+    units = float(np.sum(sizes.astype(np.float64) ** w.m)) * w.K * w.n_steps
+    line = {
+        "metric": METRIC + ", forward-equivalent, adjoint gradient", "value": units / (ms / 1000.0),
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "m": w.m, "N": w.N, "R": w.R, "K": w.K, "n_steps": w.n_steps,
+                   "checkpoint_every": M, "precision": "c64 states, FP64 gradient accumulation"},
+        "forward_ms": fwd_ms, "adjoint_over_forward": ms / fwd_ms,
+        "loss": float(loss.item()), "grad_abs_max": float(max(ge.abs().max().item(), gJ.abs().max().item())),
+    }
+    print(json.dumps(line), flush=True)
+    h.close()
     return 0
 
 
@@ -532,12 +614,17 @@ def main(argv=None):
     ap.add_argument("--n-steps", type=int, default=0, help="override the workload's steps")
     ap.add_argument("--flags", type=int, default=0, help="ctqw propagation flags (e.g. 4 = wide CTA)")
     ap.add_argument("--dtype", choices=["c64", "c128"], default=None, help="override the workload's type")
+    ap.add_argument("--graph", action="store_true", help="replay the propagate call from a CUDA graph")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time ctqw_adjoint_grad on the workload (use --workload adjoint_n512)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-plain", action="store_true")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.adjoint:
+        return run_adjoint(args)
     return run_ours(args)
 
 

@@ -160,6 +160,29 @@ int ctqw_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t method
                         size_t *bytes);
 
 /*
+ * Order of the truncated Taylor series (Sec. 2.3) from its remainder bound:
+ * the smallest K in K_min..K_max (1 <= K_min <= K_max <= 30) with
+ *   n_steps * h_dt^(K+1) / (K+1)! * exp(h_dt) <= tol / 10,
+ * h_dt an upper bound of ||H dt||_2 (Lagrange remainder of exp, summed over
+ * the steps; the propagator is a contraction up to that remainder).
+ * *K_out gets that order and *bound_out (may be NULL) the bound it reaches.
+ * When no order in range meets it: *K_out = K_max, the bound of K_max, and
+ * CTQW_EUNSUPPORTED.  Pure host function: no device, no handle.
+ */
+int ctqw_taylor_order(double h_dt, int64_t n_steps, double tol, int32_t K_min, int32_t K_max,
+                      int32_t *K_out, double *bound_out);
+
+/*
+ * ctqw_taylor_order for the handle's Hamiltonians: h_dt = |dt| times
+ * m (max|eps| + 2 max|J|) + |U| m(m-1)/2, with the maxima bounded from the
+ * lattice descriptor (|mean| + half width, so no device read), and tol the
+ * stated tolerance of the type (2e-6 for CTQW_C64, 1e-11 for CTQW_C128).
+ * Errors as ctqw_taylor_order, EINVAL for a null handle or a bad dtype.
+ */
+int ctqw_autotune_order(const ctqw_hamiltonian *h, int32_t dtype, double dt, int64_t n_steps,
+                        int32_t K_min, int32_t K_max, int32_t *K_out);
+
+/*
  * Advance every realization by n_steps steps of the order-K truncated Taylor
  * series of exp(-i H dt) (Sec. 2.3, Algorithm 3):
  *   Phi^(0) = Psi, Phi^(j) = -(i dt / j) H Phi^(j-1), Psi(t+dt) = sum_{j<=K} Phi^(j).
@@ -169,7 +192,8 @@ int ctqw_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t method
  *   P_mean_dev [n_obs][p_width] FP64: per size group, (1/R_g) sum_r P_r(x)
  *   norm_dev   [n_obs][R] FP64:  <Psi_r|Psi_r>
  *   energy_dev [n_obs][R] FP64:  <Psi_r|H_r|Psi_r>
- * The outputs are overwritten (zeroed on the stream first).  K in 1..30.
+ * The outputs are overwritten (zeroed on the stream first).  K in 1..30, or
+ * 0: the order ctqw_autotune_order picks over 1..30 (host arithmetic only).
  * Precision: CTQW_C128 propagates in FP64; CTQW_C64 propagates in FP32 and,
  * on the fused path, carries the rounding error of every state update in a
  * second FP32 word (compensated summation) kept on chip for the whole call.

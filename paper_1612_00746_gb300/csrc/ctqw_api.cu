@@ -158,6 +158,22 @@ int ctqw_build_hamiltonian(const ctqw_lattice_desc *d, void *stream, ctqw_hamilt
         h->sizes[r] = n;
     }
     h->Nmax = *std::max_element(h->sizes.begin(), h->sizes.end());
+    {
+        // ||H||_2 <= m (max|eps| + 2 max|J|) + |U| m(m-1)/2 (Gershgorin on the
+        // Kronecker sum); |eps| <= |mean| + half width, the same for J, with a
+        // relative margin for the rounding of the parameters to float32
+        double em = 0.0, jm = std::fabs(d->J0);
+        if (d->eps_mean) {
+            for (int i = 0; i < h->Nmax; ++i) em = std::max(em, std::fabs(d->eps_mean[i]));
+        }
+        if (d->J_mean) {
+            jm = 0.0;
+            for (int i = 0; i < h->Nmax; ++i) jm = std::max(jm, std::fabs(d->J_mean[i]));
+        }
+        const double eb = (em + std::fabs(d->eps_halfwidth)) * (1.0 + 1e-6);
+        const double jb = (jm + std::fabs(d->J_halfwidth)) * (1.0 + 1e-6);
+        h->h_norm_bound = h->m * (eb + 2.0 * jb) + std::fabs(h->U) * h->m * (h->m - 1) / 2.0;
+    }
     h->uniform = std::all_of(h->sizes.begin(), h->sizes.end(), [&](int n) { return n == h->Nmax; });
     h->par_off.assign(h->R + 1, 0);
     h->st_off.assign(h->R + 1, 0);
@@ -329,6 +345,43 @@ int ctqw_init_state(const ctqw_hamiltonian *h, const int32_t *sites_host, int32_
     return st;
 }
 
+int ctqw_taylor_order(double h_dt, int64_t n_steps, double tol, int32_t K_min, int32_t K_max,
+                      int32_t *K_out, double *bound_out) {
+    if (!K_out) { ctqw_set_error("null K_out"); return CTQW_EINVAL; }
+    if (!(h_dt >= 0.0) || !std::isfinite(h_dt) || n_steps < 0 || !(tol > 0.0) || K_min < 1 ||
+        K_max > 30 || K_min > K_max) {
+        ctqw_set_error("taylor_order: need h_dt >= 0, n_steps >= 0, tol > 0, 1 <= K_min <= K_max <= 30");
+        return CTQW_EINVAL;
+    }
+    // remainder of the order-K series per step: h^(K+1)/(K+1)! e^h; over the
+    // run n_steps times that (the propagator is a contraction up to it)
+    const double steps = n_steps > 0 ? (double)n_steps : 1.0;
+    double term = 1.0;   // h^k / k!
+    for (int k = 1; k <= K_min; ++k) term *= h_dt / k;
+    for (int K = K_min; K <= K_max; ++K) {
+        const double rem = term * h_dt / (K + 1) * std::exp(h_dt) * steps;
+        if (rem <= tol / 10.0) {
+            *K_out = K;
+            if (bound_out) *bound_out = rem;
+            return CTQW_OK;
+        }
+        term *= h_dt / (K + 1);
+    }
+    *K_out = K_max;
+    if (bound_out) *bound_out = term * std::exp(h_dt) * steps;
+    ctqw_set_error("taylor_order: no K in %d..%d keeps the truncation within tol/10 (h dt = %g)",
+                   K_min, K_max, h_dt);
+    return CTQW_EUNSUPPORTED;
+}
+
+int ctqw_autotune_order(const ctqw_hamiltonian *h, int32_t dtype, double dt, int64_t n_steps,
+                        int32_t K_min, int32_t K_max, int32_t *K_out) {
+    if (!h) { ctqw_set_error("null handle"); return CTQW_EINVAL; }
+    if (dtype != CTQW_C64 && dtype != CTQW_C128) { ctqw_set_error("dtype %d", dtype); return CTQW_EINVAL; }
+    const double tol = dtype == CTQW_C64 ? 2e-6 : 1e-11;
+    return ctqw_taylor_order(h->h_norm_bound * std::fabs(dt), n_steps, tol, K_min, K_max, K_out, nullptr);
+}
+
 int ctqw_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t method, uint32_t flags,
                         size_t *bytes) {
     if (!h || !bytes) { ctqw_set_error("null argument"); return CTQW_EINVAL; }
@@ -394,7 +447,8 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
                           double *norm_dev, double *energy_dev, uint32_t flags,
                           void *workspace_dev, size_t workspace_bytes, void *stream) {
     CTQW_TRY(check_common(h, dtype, psi_dev, dt, n_steps, obs_every));
-    if (K < 1 || K > 30) { ctqw_set_error("K must be in 1..30 (got %d)", K); return CTQW_EINVAL; }
+    if (K == 0) CTQW_TRY(ctqw_autotune_order(h, dtype, dt, n_steps, 1, 30, &K));
+    if (K < 1 || K > 30) { ctqw_set_error("K must be in 1..30, or 0 (got %d)", K); return CTQW_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n_obs = n_samples(n_steps, obs_every);
     const int shape = (int)((flags >> CTQW_FUSED_SHAPE_SHIFT) & 0xF);

@@ -15,6 +15,7 @@ struct ctqw_hamiltonian {
     double J0 = 1.0, U = 0.0;
     int Nmax = 0;
     bool uniform = true;
+    double h_norm_bound = 0.0;   // upper bound of ||H_r||_2 over all realizations (from the descriptor)
     int device = 0;
     std::vector<int32_t> sizes;                 // N_r
     std::vector<int64_t> par_off;               // [R+1] offsets of eps/J (sum N)

@@ -39,7 +39,8 @@ EXPORTED = (
     "ctqw_build_hamiltonian", "ctqw_destroy_hamiltonian", "ctqw_get_params", "ctqw_state_size",
     "ctqw_output_layout", "ctqw_init_state", "ctqw_workspace_size", "ctqw_propagate_taylor",
     "ctqw_propagate_rk4", "ctqw_ensemble_observables", "ctqw_check_status", "ctqw_last_error",
-    "ctqw_version", "ctqw_adjoint_workspace_size", "ctqw_adjoint_grad",
+    "ctqw_version", "ctqw_adjoint_workspace_size", "ctqw_adjoint_grad", "ctqw_taylor_order",
+    "ctqw_autotune_order",
 )
 
 
@@ -92,6 +93,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "ctqw_check_status": [vp, vp],
         "ctqw_adjoint_workspace_size": [vp, i32, i32, i64, i32, ctypes.POINTER(sz)],
         "ctqw_adjoint_grad": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, vp, vp, vp, sz, vp],
+        "ctqw_taylor_order": [dbl, i64, dbl, i32, i32, ctypes.POINTER(i32), pd],
+        "ctqw_autotune_order": [vp, i32, dbl, i64, i32, i32, ctypes.POINTER(i32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -140,6 +143,7 @@ class Hamiltonian:
         lib = load()
         self.m = int(m)
         self.statistics = int(statistics)
+        self.periodic = bool(periodic)
         self.sizes = np.ascontiguousarray(np.asarray(sizes, dtype=np.int32))
         self.R = len(self.sizes)
         self._u_eps = np.ascontiguousarray(u_eps, dtype=np.float64)
@@ -253,22 +257,48 @@ def ctqw_ensemble_observables(h: Hamiltonian, psi: torch.Tensor, dtype: int, P_m
                                             _ptr(norm), _ptr(energy), _stream(stream)))
 
 
+def ctqw_taylor_order(h_dt: float, n_steps: int, tol: float, K_min: int = 1, K_max: int = 30):
+    """(K, bound): smallest order whose summed truncation bound is within tol/10."""
+    K = ctypes.c_int32()
+    b = ctypes.c_double()
+    _check(load().ctqw_taylor_order(float(h_dt), int(n_steps), float(tol), int(K_min), int(K_max),
+                                    ctypes.byref(K), ctypes.byref(b)))
+    return K.value, b.value
+
+
+def ctqw_autotune_order(h: Hamiltonian, dtype: int, dt: float, n_steps: int, K_min: int = 1,
+                        K_max: int = 30) -> int:
+    """Order the library picks for this handle (as K = 0 in ctqw_propagate_taylor)."""
+    K = ctypes.c_int32()
+    _check(load().ctqw_autotune_order(h.handle, dtype, float(dt), int(n_steps), int(K_min),
+                                      int(K_max), ctypes.byref(K)))
+    return K.value
+
+
 def ctqw_check_status(h: Hamiltonian, stream=None) -> None:
     _check(load().ctqw_check_status(h.handle, _stream(stream)))
 
 
-def ctqw_adjoint_grad(h: Hamiltonian, psi0: torch.Tensor, dtype: int, dt: float, K: int,
-                      n_steps: int, checkpoint_every: int, P_target: torch.Tensor, stream=None):
-    """Loss on Pbar(x, T) and its gradient w.r.t. every realization's eps and J.
-
-    Returns (loss [1], grad_eps [sum N], grad_J [sum N], P_final [p_width]) as
-    FP64 device tensors (ctqw_adjoint_grad).
-    """
-    dev = psi0.device
+def adjoint_workspace(h: Hamiltonian, dtype: int, K: int, n_steps: int, checkpoint_every: int,
+                      device="cuda") -> torch.Tensor:
     b = ctypes.c_size_t()
     _check(load().ctqw_adjoint_workspace_size(h.handle, dtype, int(K), int(n_steps),
                                               int(checkpoint_every), ctypes.byref(b)))
-    ws = torch.empty(b.value, dtype=torch.uint8, device=dev)
+    return torch.empty(b.value, dtype=torch.uint8, device=device)
+
+
+def ctqw_adjoint_grad(h: Hamiltonian, psi0: torch.Tensor, dtype: int, dt: float, K: int,
+                      n_steps: int, checkpoint_every: int, P_target: torch.Tensor, stream=None,
+                      workspace: Optional[torch.Tensor] = None):
+    """Loss on Pbar(x, T) and its gradient w.r.t. every realization's eps and J.
+
+    Returns (loss [1], grad_eps [sum N], grad_J [sum N], P_final [p_width]) as
+    FP64 device tensors (ctqw_adjoint_grad).  workspace: from adjoint_workspace
+    (allocated here when None).
+    """
+    dev = psi0.device
+    ws = workspace if workspace is not None else adjoint_workspace(h, dtype, K, n_steps,
+                                                                   checkpoint_every, dev)
     n = int(h.sizes.sum())
     loss = torch.empty(1, dtype=torch.float64, device=dev)
     ge = torch.empty(n, dtype=torch.float64, device=dev)

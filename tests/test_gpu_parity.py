@@ -246,8 +246,9 @@ def test_bad_arguments_rejected(ctqw):
     psi = h.new_state(cw.C128)
     with pytest.raises(ctqw.CtqwError, match="workspace"):
         ctqw.ctqw_propagate_taylor(h, psi, cw.C128, 0.01, 4, 1, 0)
-    with pytest.raises(ctqw.CtqwError, match="K must be"):
-        ctqw.ctqw_propagate_taylor(h, psi, cw.C128, 0.01, 0, 1, 0, workspace=h.workspace(cw.C128))
+    for K in (-1, 31):   # K = 0 asks for the autotuned order
+        with pytest.raises(ctqw.CtqwError, match="K must be"):
+            ctqw.ctqw_propagate_taylor(h, psi, cw.C128, 0.01, K, 1, 0, workspace=h.workspace(cw.C128))
     with pytest.raises(ctqw.CtqwError, match="dt"):
         ctqw.ctqw_propagate_taylor(h, psi, cw.C128, float("nan"), 4, 1, 0, workspace=h.workspace(cw.C128))
     h.close()
