@@ -77,6 +77,32 @@ int ctqw_cuda_fail(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return ctqw_cuda_fail(_e, #call); \
     } while (0)
 
+// One launch per size group (per 65535 of its realizations): grid (rows,
+// chunks of x_M, realizations).
+template <typename F>
+inline int for_each_group(const ctqw_hamiltonian *h, F &&launch) {
+    int off = 0;
+    for (size_t g = 0; g < h->group_N.size(); ++g) {
+        const int N = h->group_N[g], cnt = h->group_count[g];
+        int64_t rows = 1;
+        for (int j = 1; j < h->m; ++j) rows *= N;
+        if (rows > 0x7fffffff) {
+            ctqw_set_error("per-term path: N^(m-1) = %lld rows above the grid limit", (long long)rows);
+            return CTQW_EUNSUPPORTED;
+        }
+        const int tx = N >= 256 ? 256 : ((N + 31) / 32) * 32;
+        const int ty = 256 / tx;   // rows a block
+        for (int done = 0; done < cnt; done += 65535) {
+            const int part = cnt - done < 65535 ? cnt - done : 65535;
+            const dim3 grid((unsigned)((rows + ty - 1) / ty), (unsigned)((N + tx - 1) / tx), (unsigned)part);
+            launch(grid, dim3((unsigned)tx, (unsigned)ty), h->by_group_d + off + done);
+            CTQW_CUDA_TRY(cudaGetLastError());
+        }
+        off += cnt;
+    }
+    return CTQW_OK;
+}
+
 // ---------------------------------------------------------------- launchers
 // Parameter build (a1): eps/J of every realization from the uniform draws.
 int launch_build_params(const ctqw_hamiltonian *h, const double *u_eps_d, const double *u_J_d,

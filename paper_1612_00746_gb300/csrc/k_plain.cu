@@ -7,38 +7,6 @@
 
 namespace {
 
-// Grid of the per-term kernels: x = block of rows (x_1..x_{M-1} flattened;
-// blockDim.y rows a block, for rows shorter than 256), y = chunk of the last
-// coordinate x_M, z = realization within one size group (list: that group's
-// realizations).  One launch per size group (and per 65535 realizations of
-// it), so a ragged batch launches no empty blocks and no thread divides a
-// 64-bit index.
-template <int M>
-struct Site {
-    int r, N;
-    int64_t s;   // flat index within the realization's state
-    int x[M];
-};
-
-template <int M>
-__device__ __forceinline__ bool site_of(const RealTable &tab, const int32_t *__restrict__ list, Site<M> &p) {
-    p.r = list[blockIdx.z];
-    p.N = tab.N[p.r];
-    const int xm = blockIdx.y * blockDim.x + threadIdx.x;
-    if (xm >= p.N) return false;
-    const int q = blockIdx.x * blockDim.y + threadIdx.y;
-    if (q >= (M == 2 ? p.N : p.N * p.N)) return false;
-    if (M == 2) {
-        p.x[0] = q;
-    } else {
-        p.x[0] = q / p.N;
-        p.x[1] = q - p.x[0] * p.N;
-    }
-    p.x[M - 1] = xm;
-    p.s = (int64_t)q * p.N + xm;
-    return true;
-}
-
 // Phi^(j) = -(i dt/j) H Phi^(j-1);  acc = (first ? psi : acc) + Phi^(j).
 template <typename T, int M>
 __global__ void __launch_bounds__(256) taylor_term_kernel(RealTable tab, const int32_t *__restrict__ list,
@@ -82,32 +50,6 @@ __global__ void __launch_bounds__(256) rk4_stage_kernel(RealTable tab, const int
     if (next) next[base + s] = mk<T>(q.x + a * k.x, q.y + a * k.y);
     cplx_t<T> c = first ? q : acc[base + s];
     acc[base + s] = mk<T>(c.x + b * k.x, c.y + b * k.y);
-}
-
-// One launch per size group (per 65535 of its realizations): grid (rows,
-// chunks of x_M, realizations).
-template <typename F>
-int for_each_group(const ctqw_hamiltonian *h, F &&launch) {
-    int off = 0;
-    for (size_t g = 0; g < h->group_N.size(); ++g) {
-        const int N = h->group_N[g], cnt = h->group_count[g];
-        int64_t rows = 1;
-        for (int j = 1; j < h->m; ++j) rows *= N;
-        if (rows > 0x7fffffff) {
-            ctqw_set_error("per-term path: N^(m-1) = %lld rows above the grid limit", (long long)rows);
-            return CTQW_EUNSUPPORTED;
-        }
-        const int tx = N >= 256 ? 256 : ((N + 31) / 32) * 32;
-        const int ty = 256 / tx;   // rows a block
-        for (int done = 0; done < cnt; done += 65535) {
-            const int part = cnt - done < 65535 ? cnt - done : 65535;
-            const dim3 grid((unsigned)((rows + ty - 1) / ty), (unsigned)((N + tx - 1) / tx), (unsigned)part);
-            launch(grid, dim3((unsigned)tx, (unsigned)ty), h->by_group_d + off + done);
-            CTQW_CUDA_TRY(cudaGetLastError());
-        }
-        off += cnt;
-    }
-    return CTQW_OK;
 }
 
 }  // namespace

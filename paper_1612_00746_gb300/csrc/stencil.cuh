@@ -10,6 +10,8 @@
 
 #include <cstdint>
 
+#include "ctqw_internal.cuh"
+
 template <typename T> struct cplx;
 template <> struct cplx<float> { using type = float2; };
 template <> struct cplx<double> { using type = double2; };
@@ -64,4 +66,36 @@ __device__ __forceinline__ cplx_t<T> apply_h(const cplx_t<T> *__restrict__ a, in
         stride *= N;
     }
     return mk<T>(yr, yi);
+}
+
+// Grid of the per-term kernels: x = block of rows (x_1..x_{M-1} flattened;
+// blockDim.y rows a block, for rows shorter than 256), y = chunk of the last
+// coordinate x_M, z = realization within one size group (list: that group's
+// realizations).  One launch per size group (and per 65535 realizations of
+// it), so a ragged batch launches no empty blocks and no thread divides a
+// 64-bit index.
+template <int M>
+struct Site {
+    int r, N;
+    int64_t s;   // flat index within the realization's state
+    int x[M];
+};
+
+template <int M>
+__device__ __forceinline__ bool site_of(const RealTable &tab, const int32_t *__restrict__ list, Site<M> &p) {
+    p.r = list[blockIdx.z];
+    p.N = tab.N[p.r];
+    const int xm = blockIdx.y * blockDim.x + threadIdx.x;
+    if (xm >= p.N) return false;
+    const int q = blockIdx.x * blockDim.y + threadIdx.y;
+    if (q >= (M == 2 ? p.N : p.N * p.N)) return false;
+    if (M == 2) {
+        p.x[0] = q;
+    } else {
+        p.x[0] = q / p.N;
+        p.x[1] = q - p.x[0] * p.N;
+    }
+    p.x[M - 1] = xm;
+    p.s = (int64_t)q * p.N + xm;
+    return true;
 }
