@@ -177,9 +177,13 @@ def propagation_path(w, dtype, flags):
         return "plain"
     if shape == ctqw.SHAPE_WAVEFRONT:
         return "wavefront"
+    if shape >= 9:
+        return "tiled"
     uniform = w.ragged_sizes is None
     if dtype == ctqw.C64 and w.m == 2 and uniform and w.N in (64, 128, 192, 256):
         return "rows" if shape < 4 else "banded"
+    if dtype == ctqw.C64 and w.m == 2 and shape == 0:
+        return "tiled"   # the library's default for the other two-particle FP32 handles
     return "plain"
 
 
@@ -198,12 +202,12 @@ def roofline_of(w, dtype, flags, units, kernel_ms, peaks, traffic):
 
     path = propagation_path(w, dtype, flags)
     sec = kernel_ms / 1000.0
-    if path in ("rows", "banded", "wavefront"):
+    if path in ("rows", "banded", "wavefront", "tiled"):
         flops_per_unit = 8 * w.m + 4
         achieved = units * flops_per_unit / sec / 1e12
         peak = SM_COUNT * FP32_FMA_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
         kernel = {"rows": "taylor_fused_rows_kernel", "banded": "taylor_fused_kernel",
-                  "wavefront": "taylor_wavefront_kernel"}[path]
+                  "wavefront": "taylor_wavefront_kernel", "tiled": "taylor_tiled_kernel"}[path]
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic if path == "rows" else None,
                 "kernel": kernel, "kernel_ms": kernel_ms, "flops_per_site_update": flops_per_unit,
@@ -339,6 +343,10 @@ def run_ours(args):
     elif path == "plain":
         # init_state + K stage launches per step + one observables kernel per sample
         launches_per_step = 1 + w.n_steps * w.K + n_obs
+    elif path == "tiled":
+        # ceil(K / D) launches per step and size group, observables, init
+        depth = {0: 8, 9: 4, 10: 2, 11: 8, 12: 4, 13: 8, 14: 2}[(args.flags >> 8) & 0xF]
+        launches_per_step = 1 + w.n_steps * (-(-w.K // depth)) * len(h.group_sizes) + n_obs
     else:
         launches_per_step = 2   # init_state kernel + fused propagation kernel
 

@@ -72,6 +72,13 @@ extern "C" {
 #define CTQW_FUSED_SHAPE_SHIFT 8
 #define CTQW_FUSED_SHAPE(k) (((uint32_t)(k) & 0xFu) << CTQW_FUSED_SHAPE_SHIFT)
 #define CTQW_SHAPE_WAVEFRONT 8
+/* k = CTQW_SHAPE_TILED(i), i = 0..5: the temporally blocked tiled kernel
+ * (m = 2, CTQW_C64, any N, open or ring, ragged): ceil(K/D) launches per step,
+ * each applying up to D Horner stages on tiles with halos.  i = 0..2 keep the
+ * iterate in shared memory: (tile <= 56, D = 4), (tile <= 60, D = 2),
+ * (tile <= 48, D = 8); i = 3..5 keep it in registers on a 64 x 64 region:
+ * D = 4, 8, 2 (tile 64 - 2D).  Needs the per-term workspace (3 states). */
+#define CTQW_SHAPE_TILED(i) (9 + (i))
 
 typedef struct ctqw_hamiltonian ctqw_hamiltonian;   /* opaque, owned by the library */
 
@@ -199,9 +206,12 @@ int ctqw_autotune_order(const ctqw_hamiltonian *h, int32_t dtype, double dt, int
  * second FP32 word (compensated summation) kept on chip for the whole call.
  * Path: m = 2 chains with N a multiple of 64 up to 256 in CTQW_C64 run the
  * fused cluster kernel (every Taylor term of every step on chip; halo rows move between the CTAs
- * of a cluster point to point, see ctqw_check_status); everything
- * else, or CTQW_FLAG_PLAIN, runs one launch per Taylor term and needs the
- * workspace of ctqw_workspace_size (3 states): in CTQW_C128 in the order of
+ * of a cluster point to point, see ctqw_check_status); other m = 2 handles
+ * in CTQW_C64 (N > 256, ragged sizes) run the temporally blocked tiled
+ * kernel (CTQW_SHAPE_TILED(4), 8 Horner stages per launch); everything
+ * else, or CTQW_FLAG_PLAIN, runs one launch per Taylor term.  All but the
+ * fused kernel need the workspace of ctqw_workspace_size (3 states).  The
+ * per-term path runs in CTQW_C128 in the order of
  * Algorithm 3 (Phi^(j) from Phi^(j-1), summed forward); in CTQW_C64 as the
  * same polynomial in Horner form (w_j = Psi + (-i dt / j) H w_{j+1}, j = K..2,
  * Psi(t+dt) = Psi - i dt H w_2) with the state update compensated, because a

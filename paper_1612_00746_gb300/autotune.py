@@ -1,7 +1,8 @@
 """Kernel-shape autotuner for ctqw_propagate_taylor.
 
 The library compiles several CTA / cluster shapes of its fused kernels and,
-besides them, the row-wavefront kernel and the per-term path.  Which one is
+besides them, the row-wavefront kernel, the tiled kernel at several
+temporal-blocking depths and the per-term path.  Which one is
 fastest depends on N, K, the number of realizations and the GPU.  The tuner
 times every candidate the handle supports on a scratch copy of the state for
 a few steps (CUDA events on the caller's stream, after one untimed warm-up),
@@ -22,11 +23,12 @@ import torch
 from . import ctqw
 
 # candidate flag words: full-row shapes 0..2, banded shapes 4..6, the row
-# wavefront, and the per-term path
+# wavefront, the tiled kernel at depths 4, 2, 8, and the per-term path
 CANDIDATES: Tuple[int, ...] = (
     ctqw.FUSED_SHAPE(0), ctqw.FUSED_SHAPE(1), ctqw.FUSED_SHAPE(2),
     ctqw.FUSED_SHAPE(4), ctqw.FUSED_SHAPE(5), ctqw.FUSED_SHAPE(6),
-    ctqw.FLAG_WAVEFRONT, ctqw.FLAG_PLAIN,
+    ctqw.FLAG_WAVEFRONT, ctqw.FLAG_TILED(0), ctqw.FLAG_TILED(1), ctqw.FLAG_TILED(2),
+    ctqw.FLAG_TILED(3), ctqw.FLAG_TILED(4), ctqw.FLAG_TILED(5), ctqw.FLAG_PLAIN,
 )
 
 DEFAULT_CACHE = os.environ.get(

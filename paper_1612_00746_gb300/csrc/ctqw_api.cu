@@ -65,9 +65,24 @@ int check_common(const ctqw_hamiltonian *h, int dtype, const void *psi, double d
     } while (0)
 
 // out = T in with T the order-K Taylor polynomial of exp(-i H dt)
-// (Algorithm 3 with one launch per term); phiA, phiB scratch states.
+// (Algorithm 3 with one launch per term); phiA, phiB scratch states.  In
+// FP32 the same polynomial in Horner form (one launch per stage, the last
+// one out = in - i dt H w_2), which moves a quarter less and does not drop
+// the terms a forward FP32 sum would.
 int taylor_step_plain(const ctqw_hamiltonian *h, int dtype, const void *in, void *out, void *phiA,
                       void *phiB, double dt, int K, cudaStream_t s) {
+    if (dtype == CTQW_C64) {
+        const void *w = in;
+        void *dst = phiA;
+        for (int j = K; j >= 1; --j) {
+            void *o = (j == 1) ? out : dst;
+            int st = launch_horner_stage(h, w, in, o, dt / j, s);
+            if (st != CTQW_OK) return st;
+            w = o;
+            dst = (dst == phiA) ? phiB : phiA;
+        }
+        return CTQW_OK;
+    }
     const void *src = in;
     void *dst = phiA;
     for (int j = 1; j <= K; ++j) {
@@ -393,7 +408,7 @@ int ctqw_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t method
         return CTQW_OK;
     }
     const bool fused = (method == 0 || method == 1) && !(flags & CTQW_FLAG_PLAIN) &&
-                       fused_rows_supported(h, dtype);
+                       shape < CTQW_SHAPE_TILED(0) && fused_rows_supported(h, dtype);
     *bytes = fused ? 0 : 3 * (size_t)h->total_amp * elem_bytes(dtype);
     return CTQW_OK;
 }
@@ -442,6 +457,60 @@ static int propagate_wavefront(const ctqw_hamiltonian *h, int32_t dtype, void *p
     return st;
 }
 
+constexpr int kTiledDefault = 4;   // CTQW_SHAPE_TILED(4): the iterate in registers, depth 8
+
+// The temporally blocked tiled kernels: ceil(K / D) launches per step.  The
+// state rotates through psi and the two iterate buffers of the workspace
+// (the new state cannot overwrite the one other tiles read as halo); the
+// carried rounding error stays in the third workspace state.
+static int propagate_tiled(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
+                           int32_t K, int64_t n_steps, int32_t obs_every, double *P_mean_dev,
+                           double *norm_dev, double *energy_dev, uint32_t flags, int shape,
+                           void *workspace_dev, size_t workspace_bytes, cudaStream_t s) {
+    if (!tiled_supported(h, dtype, shape)) {
+        ctqw_set_error("tiled path: needs c64 and m = 2 (shape %d)", shape);
+        return CTQW_EUNSUPPORTED;
+    }
+    const size_t sb = (size_t)h->total_amp * elem_bytes(dtype);
+    if (!workspace_dev || workspace_bytes < 3 * sb) {
+        ctqw_set_error("tiled path needs a workspace of %zu bytes (got %zu)", 3 * sb, workspace_bytes);
+        return CTQW_EINVAL;
+    }
+    const int64_t n_obs = n_samples(n_steps, obs_every);
+    CTQW_TRY(zero_outputs(h, n_obs, P_mean_dev, norm_dev, energy_dev, s));
+    char *ws = (char *)workspace_dev;
+    void *bufs[3] = {psi_dev, ws, ws + sb};
+    void *lo = ws + 2 * sb;
+    CTQW_CUDA_TRY(cudaMemsetAsync(lo, 0, sb, s));
+    const int comp = (flags & CTQW_FLAG_NO_COMPENSATION) ? 0 : 1;
+    const int D = tiled_depth(shape);
+    int cur = 0;
+    int64_t obs = 0;
+    for (int64_t step = 0; step <= n_steps; ++step) {
+        if (obs_every > 0 && step % obs_every == 0) {
+            CTQW_TRY(launch_observables(h, dtype, bufs[cur], P_mean_dev ? P_mean_dev + obs * h->p_width : nullptr,
+                                        nullptr, norm_dev ? norm_dev + obs * h->R : nullptr,
+                                        energy_dev ? energy_dev + obs * h->R : nullptr, s));
+            ++obs;
+        }
+        if (step == n_steps) break;
+        const int o1 = (cur + 1) % 3, o2 = (cur + 2) % 3;
+        int win = cur;
+        for (int j0 = K; j0 >= 1;) {
+            const int nst = j0 < D ? j0 : D;
+            const int final = (j0 - nst + 1 == 1) ? 1 : 0;
+            const int wout = (win == o1) ? o2 : o1;   // neither the state nor the input iterate
+            CTQW_TRY(launch_taylor_tiled(h, shape, bufs[win], bufs[cur], bufs[wout], lo, dt, j0, nst,
+                                         final, comp, s));
+            win = wout;
+            j0 -= nst;
+            if (final) cur = wout;
+        }
+    }
+    if (cur != 0) CTQW_CUDA_TRY(cudaMemcpyAsync(psi_dev, bufs[cur], sb, cudaMemcpyDeviceToDevice, s));
+    return CTQW_OK;
+}
+
 int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
                           int32_t K, int64_t n_steps, int32_t obs_every, double *P_mean_dev,
                           double *norm_dev, double *energy_dev, uint32_t flags,
@@ -455,7 +524,18 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
     if (!(flags & CTQW_FLAG_PLAIN) && shape == CTQW_SHAPE_WAVEFRONT)
         return propagate_wavefront(h, dtype, psi_dev, dt, K, n_steps, obs_every, P_mean_dev,
                                    norm_dev, energy_dev, flags, workspace_dev, workspace_bytes, s);
+    if (!(flags & CTQW_FLAG_PLAIN) && shape >= CTQW_SHAPE_TILED(0))
+        return propagate_tiled(h, dtype, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
+                               energy_dev, flags, shape - CTQW_SHAPE_TILED(0), workspace_dev,
+                               workspace_bytes, s);
     const bool fused = !(flags & CTQW_FLAG_PLAIN) && fused_rows_supported(h, dtype);
+    // two particles in FP32 that the cluster-resident kernel cannot hold
+    // (N > 256, ragged sizes, other N): the temporally blocked tiled kernel,
+    // iterate in registers, depth 8 (the fastest measured on N = 512 and on the
+    // ragged batch)
+    if (!fused && !(flags & CTQW_FLAG_PLAIN) && shape == 0 && tiled_supported(h, dtype, kTiledDefault))
+        return propagate_tiled(h, dtype, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
+                               energy_dev, flags, kTiledDefault, workspace_dev, workspace_bytes, s);
     if (!fused) {
         const size_t need = 3 * (size_t)h->total_amp * elem_bytes(dtype);
         if (!workspace_dev || workspace_bytes < need) {

@@ -160,6 +160,16 @@ size_t wavefront_workspace_bytes(const ctqw_hamiltonian *h);
 int launch_taylor_wavefront(const ctqw_hamiltonian *h, void *psi, void *lo, double dt, int K,
                             int64_t n_steps, int compensated, cudaStream_t s);
 
+// Temporally blocked Taylor stages (m = 2, c64): up to D Horner stages per
+// launch on shared-memory tiles with halos; final launches add A w_2 to psi
+// (compensated, lo in place) and write the new state to w_out.
+int tiled_shape_count();
+bool tiled_supported(const ctqw_hamiltonian *h, int dtype, int shape);
+int tiled_depth(int shape);
+int launch_taylor_tiled(const ctqw_hamiltonian *h, int shape, const void *w_in, const void *psi,
+                        void *w_out, void *lo, double dt, int j0, int n_stages, int final,
+                        int compensated, cudaStream_t s);
+
 // Fused cluster-resident Taylor propagation (m = 2, c64), multi-warp bands.
 bool fused_taylor_supported(const ctqw_hamiltonian *h, int dtype);
 int launch_taylor_fused(const ctqw_hamiltonian *h, void *psi, double dt, int K, int64_t n_steps,

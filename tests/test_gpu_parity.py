@@ -264,10 +264,11 @@ def test_fused_c64_alternative_shapes(ctqw, N, shape):
     _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
 
 
-def test_fused_unknown_shape_rejected(ctqw):
+@pytest.mark.parametrize("k", [3, 7, 15])   # no compiled shape at these indices
+def test_fused_unknown_shape_rejected(ctqw, k):
     w = cw.get("bosons_small").with_(R=1, n_steps=2)
     with pytest.raises(ctqw.CtqwError, match="shape"):
-        ctqw.run_workload(w, flags=ctqw.FUSED_SHAPE(9))
+        ctqw.run_workload(w, flags=ctqw.FUSED_SHAPE(k))
 
 
 def test_fused_bounded_wait_gives_up_and_reports(ctqw):
