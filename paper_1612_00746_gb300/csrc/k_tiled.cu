@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(256) taylor_tiled_kernel(const __grid_constant
 // wrap from column 63 to 0 and the outermost warps read zero rows: both
 // only touch the halo's outer ring, which stage 1 already leaves inexact.
 template <int D>
-__global__ void __launch_bounds__(256) taylor_tiled_reg_kernel(const __grid_constant__ TiledArgs a) {
+__global__ void __launch_bounds__(256, 3) taylor_tiled_reg_kernel(const __grid_constant__ TiledArgs a) {
     constexpr int RS = 64, T = RS - 2 * D, RL = 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *Q = reinterpret_cast<float4 *>(smem_raw);            // [RS][32] psi, (row, lane) -> 2 columns
