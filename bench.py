@@ -582,13 +582,12 @@ def run_adjoint(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    # the forward pass alone (same path the adjoint's forward sweep takes)
-    fws = h.workspace(ctqw.C64, ctqw.TAYLOR, ctqw.FLAG_PLAIN, dev)
+    # the forward pass alone on the library's default path for this handle
+    fws = h.workspace(ctqw.C64, ctqw.TAYLOR, 0, dev)
     scratch = psi.clone()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
-    ctqw.ctqw_propagate_taylor(h, scratch, ctqw.C64, w.dt, w.K, w.n_steps, 0, None, None, None,
-                               ctqw.FLAG_PLAIN, fws)
+    ctqw.ctqw_propagate_taylor(h, scratch, ctqw.C64, w.dt, w.K, w.n_steps, 0, None, None, None, 0, fws)
     f1.record(stream)
     torch.cuda.synchronize()
     fwd_ms = f0.elapsed_time(f1)

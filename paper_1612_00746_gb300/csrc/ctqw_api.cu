@@ -64,13 +64,32 @@ int check_common(const ctqw_hamiltonian *h, int dtype, const void *psi, double d
         if (_st != CTQW_OK) return _st; \
     } while (0)
 
+constexpr int kTiledDefault = 4;   // CTQW_SHAPE_TILED(4): the iterate in registers, depth 8
+
 // out = T in with T the order-K Taylor polynomial of exp(-i H dt)
 // (Algorithm 3 with one launch per term); phiA, phiB scratch states.  In
-// FP32 the same polynomial in Horner form (one launch per stage, the last
-// one out = in - i dt H w_2), which moves a quarter less and does not drop
-// the terms a forward FP32 sum would.
+// FP32 the same polynomial in Horner form, which does not drop the terms a
+// forward FP32 sum would: for two particles on the temporally blocked tiles
+// (D stages per launch, the last out = in - i dt H w_2, uncompensated),
+// otherwise one launch per stage.
 int taylor_step_plain(const ctqw_hamiltonian *h, int dtype, const void *in, void *out, void *phiA,
                       void *phiB, double dt, int K, cudaStream_t s) {
+    if (dtype == CTQW_C64 && tiled_supported(h, dtype, kTiledDefault)) {
+        const int D = tiled_depth(kTiledDefault);
+        const void *w = in;
+        void *dst = phiA;
+        for (int j0 = K; j0 >= 1;) {
+            const int nst = j0 < D ? j0 : D;
+            const int final = (j0 - nst + 1 == 1) ? 1 : 0;
+            void *o = final ? out : dst;
+            int st = launch_taylor_tiled(h, kTiledDefault, w, in, o, nullptr, dt, j0, nst, final, 0, s);
+            if (st != CTQW_OK) return st;
+            w = o;
+            dst = (dst == phiA) ? phiB : phiA;
+            j0 -= nst;
+        }
+        return CTQW_OK;
+    }
     if (dtype == CTQW_C64) {
         const void *w = in;
         void *dst = phiA;
@@ -456,8 +475,6 @@ static int propagate_wavefront(const ctqw_hamiltonian *h, int32_t dtype, void *p
     if (own) cudaFreeAsync(lo, s);
     return st;
 }
-
-constexpr int kTiledDefault = 4;   // CTQW_SHAPE_TILED(4): the iterate in registers, depth 8
 
 // The temporally blocked tiled kernels: ceil(K / D) launches per step.  The
 // state rotates through psi and the two iterate buffers of the workspace

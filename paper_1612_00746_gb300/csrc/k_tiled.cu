@@ -35,7 +35,7 @@ struct TiledArgs {
     const float2 *w_in;      // input iterate (w_{j0+1}; psi itself when j0 = K)
     const float2 *psi;       // state of the step
     float2 *w_out;           // output iterate w_{j0-D+1}, or the new state when final
-    float2 *lo;              // carried rounding error (final launches)
+    float2 *lo;              // carried rounding error (final launches when compensated)
     float dt, dtU;
     int T;                   // tile side for this size group (<= the compiled maximum)
     int j0;                  // first stage of the launch (stage j maps w_{j+1} -> w_j)
@@ -162,16 +162,16 @@ __global__ void __launch_bounds__(256) taylor_tiled_kernel(const __grid_constant
                     // psi(t+dt) = psi + (-i) y, rounding error carried in lo
                     const int64_t g = base + (int64_t)x_row[i] * N + X2w;
                     float2 h = q;
-                    float2 l = a.lo[g];
                     const float2 inc = make_float2(yy, -yx);
                     if (a.compensated) {
+                        float2 l = a.lo[g];
                         compensated_add(h.x, l.x, inc.x);
                         compensated_add(h.y, l.y, inc.y);
+                        a.lo[g] = l;
                     } else {
                         h.x += inc.x;
                         h.y += inc.y;
                     }
-                    a.lo[g] = l;
                     a.w_out[g] = h;
                 }
                 wu = wc;
@@ -326,16 +326,16 @@ __global__ void __launch_bounds__(256, 3) taylor_tiled_reg_kernel(const __grid_c
                         const int64_t g = base + (int64_t)X1w * N + X2[k];
                         const float2 yk = k ? y1 : y0;
                         float2 h = k ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
-                        float2 l = a.lo[g];
                         const float2 inc = make_float2(yk.y, -yk.x);
                         if (a.compensated) {
+                            float2 l = a.lo[g];
                             compensated_add(h.x, l.x, inc.x);
                             compensated_add(h.y, l.y, inc.y);
+                            a.lo[g] = l;
                         } else {
                             h.x += inc.x;
                             h.y += inc.y;
                         }
-                        a.lo[g] = l;
                         a.w_out[g] = h;
                     }
                 }
