@@ -76,8 +76,8 @@ extern "C" {
  * (m = 2, CTQW_C64, any N, open or ring, ragged): ceil(K/D) launches per step,
  * each applying up to D Horner stages on tiles with halos.  i = 0..2 keep the
  * iterate in shared memory: (tile <= 56, D = 4), (tile <= 60, D = 2),
- * (tile <= 48, D = 8); i = 3..5 keep it in registers on a 64 x 64 region:
- * D = 4, 8, 2 (tile 64 - 2D).  Needs the per-term workspace (3 states). */
+ * (tile <= 48, D = 8); i = 3..6 keep it in registers on a 64 x 64 region:
+ * D = 4, 8, 2, 7 (tile 64 - 2D).  Needs the per-term workspace (3 states). */
 #define CTQW_SHAPE_TILED(i) (9 + (i))
 
 typedef struct ctqw_hamiltonian ctqw_hamiltonian;   /* opaque, owned by the library */
@@ -208,7 +208,8 @@ int ctqw_autotune_order(const ctqw_hamiltonian *h, int32_t dtype, double dt, int
  * fused cluster kernel (every Taylor term of every step on chip; halo rows move between the CTAs
  * of a cluster point to point, see ctqw_check_status); other m = 2 handles
  * in CTQW_C64 (N > 256, ragged sizes) run the temporally blocked tiled
- * kernel (CTQW_SHAPE_TILED(4), 8 Horner stages per launch); everything
+ * kernel with the iterate in registers, ceil(K / 8) launches a step with the
+ * stages split evenly between them; everything
  * else, or CTQW_FLAG_PLAIN, runs one launch per Taylor term.  All but the
  * fused kernel need the workspace of ctqw_workspace_size (3 states).  The
  * per-term path runs in CTQW_C128 in the order of

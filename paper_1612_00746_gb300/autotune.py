@@ -28,7 +28,8 @@ CANDIDATES: Tuple[int, ...] = (
     ctqw.FUSED_SHAPE(0), ctqw.FUSED_SHAPE(1), ctqw.FUSED_SHAPE(2),
     ctqw.FUSED_SHAPE(4), ctqw.FUSED_SHAPE(5), ctqw.FUSED_SHAPE(6),
     ctqw.FLAG_WAVEFRONT, ctqw.FLAG_TILED(0), ctqw.FLAG_TILED(1), ctqw.FLAG_TILED(2),
-    ctqw.FLAG_TILED(3), ctqw.FLAG_TILED(4), ctqw.FLAG_TILED(5), ctqw.FLAG_PLAIN,
+    ctqw.FLAG_TILED(3), ctqw.FLAG_TILED(4), ctqw.FLAG_TILED(5), ctqw.FLAG_TILED(6),
+    ctqw.FLAG_PLAIN,
 )
 
 DEFAULT_CACHE = os.environ.get(

@@ -64,8 +64,6 @@ int check_common(const ctqw_hamiltonian *h, int dtype, const void *psi, double d
         if (_st != CTQW_OK) return _st; \
     } while (0)
 
-constexpr int kTiledDefault = 4;   // CTQW_SHAPE_TILED(4): the iterate in registers, depth 8
-
 // out = T in with T the order-K Taylor polynomial of exp(-i H dt)
 // (Algorithm 3 with one launch per term); phiA, phiB scratch states.  In
 // FP32 the same polynomial in Horner form, which does not drop the terms a
@@ -74,15 +72,16 @@ constexpr int kTiledDefault = 4;   // CTQW_SHAPE_TILED(4): the iterate in regist
 // otherwise one launch per stage.
 int taylor_step_plain(const ctqw_hamiltonian *h, int dtype, const void *in, void *out, void *phiA,
                       void *phiB, double dt, int K, cudaStream_t s) {
-    if (dtype == CTQW_C64 && tiled_supported(h, dtype, kTiledDefault)) {
-        const int D = tiled_depth(kTiledDefault);
+    const int tshape = tiled_default_shape(K);
+    if (dtype == CTQW_C64 && tiled_supported(h, dtype, tshape)) {
+        const int D = tiled_depth(tshape);
         const void *w = in;
         void *dst = phiA;
         for (int j0 = K; j0 >= 1;) {
             const int nst = j0 < D ? j0 : D;
             const int final = (j0 - nst + 1 == 1) ? 1 : 0;
             void *o = final ? out : dst;
-            int st = launch_taylor_tiled(h, kTiledDefault, w, in, o, nullptr, dt, j0, nst, final, 0, s);
+            int st = launch_taylor_tiled(h, tshape, w, in, o, nullptr, dt, j0, nst, final, 0, s);
             if (st != CTQW_OK) return st;
             w = o;
             dst = (dst == phiA) ? phiB : phiA;
@@ -547,12 +546,13 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
                                workspace_bytes, s);
     const bool fused = !(flags & CTQW_FLAG_PLAIN) && fused_rows_supported(h, dtype);
     // two particles in FP32 that the cluster-resident kernel cannot hold
-    // (N > 256, ragged sizes, other N): the temporally blocked tiled kernel,
-    // iterate in registers, depth 8 (the fastest measured on N = 512 and on the
-    // ragged batch)
-    if (!fused && !(flags & CTQW_FLAG_PLAIN) && shape == 0 && tiled_supported(h, dtype, kTiledDefault))
+    // (N > 256, ragged sizes, other N): the temporally blocked tiled kernel
+    // with the iterate in registers, at the depth that needs the fewest
+    // launches a step (depth 8 was the fastest measured of 2, 4, 8)
+    if (!fused && !(flags & CTQW_FLAG_PLAIN) && shape == 0 && tiled_supported(h, dtype, tiled_default_shape(K)))
         return propagate_tiled(h, dtype, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
-                               energy_dev, flags, kTiledDefault, workspace_dev, workspace_bytes, s);
+                               energy_dev, flags, tiled_default_shape(K), workspace_dev,
+                               workspace_bytes, s);
     if (!fused) {
         const size_t need = 3 * (size_t)h->total_amp * elem_bytes(dtype);
         if (!workspace_dev || workspace_bytes < need) {

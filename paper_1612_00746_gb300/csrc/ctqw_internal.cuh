@@ -166,6 +166,7 @@ int launch_taylor_wavefront(const ctqw_hamiltonian *h, void *psi, void *lo, doub
 int tiled_shape_count();
 bool tiled_supported(const ctqw_hamiltonian *h, int dtype, int shape);
 int tiled_depth(int shape);
+int tiled_default_shape(int K);   // register tiles at the depth that needs the fewest launches
 int launch_taylor_tiled(const ctqw_hamiltonian *h, int shape, const void *w_in, const void *psi,
                         void *w_out, void *lo, double dt, int j0, int n_stages, int final,
                         int compensated, cudaStream_t s);

@@ -392,8 +392,8 @@ TiledShape tiled_reg_shape() {
 }
 
 // regions of at most 64 x 64 (two 32-lane column passes per row); shapes
-// 3..5: the iterate in registers
-constexpr int kTiledShapes = 6;
+// 3..10: the iterate in registers at depths 4, 8, 2, 7, 6, 5, 3 and 1
+constexpr int kTiledShapes = 11;
 
 bool tiled_shape_for(int idx, TiledShape &s) {
     switch (idx) {
@@ -403,6 +403,11 @@ bool tiled_shape_for(int idx, TiledShape &s) {
         case 3: s = tiled_reg_shape<4>(); return true;
         case 4: s = tiled_reg_shape<8>(); return true;
         case 5: s = tiled_reg_shape<2>(); return true;
+        case 6: s = tiled_reg_shape<7>(); return true;
+        case 7: s = tiled_reg_shape<6>(); return true;
+        case 8: s = tiled_reg_shape<5>(); return true;
+        case 9: s = tiled_reg_shape<3>(); return true;
+        case 10: s = tiled_reg_shape<1>(); return true;
         default: return false;
     }
 }
@@ -419,6 +424,15 @@ bool tiled_supported(const ctqw_hamiltonian *h, int dtype, int shape) {
 int tiled_depth(int shape) {
     TiledShape s;
     return tiled_shape_for(shape, s) ? s.D : 0;
+}
+
+int tiled_default_shape(int K) {
+    // the fewest launches a step at depth <= 8, with the stages split evenly
+    // between them (a larger tile for the same launch count)
+    const int launches = (K + 7) / 8;
+    const int D = (K + launches - 1) / launches;
+    static const int by_depth[9] = {4, 10, 5, 9, 3, 8, 7, 6, 4};
+    return by_depth[D < 1 ? 1 : (D > 8 ? 8 : D)];
 }
 
 int launch_taylor_tiled(const ctqw_hamiltonian *h, int shape, const void *w_in, const void *psi,

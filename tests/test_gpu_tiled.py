@@ -1,6 +1,7 @@
 """Parity of the temporally blocked tiled kernels (D Horner stages per launch
 on tiles with halos; the iterate in shared memory, shapes 0..2, or in
-registers, shapes 3..5) with the FP64 oracle, through the C ABI.
+registers, shapes 3..6; the library's default picks its depth from K) with
+the FP64 oracle, through the C ABI.
 
 Cases: every compiled depth, lattice sides that are not multiples of the
 tile and smaller than one region, open chains and rings, K not a multiple
@@ -37,7 +38,7 @@ def _check(got, ref, tol_energy=2e-5):
     assert de <= tol_energy, f"max|dE| = {de:.3e}"
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("N,periodic,K", [(40, False, 16), (100, True, 9), (130, False, 3),
                                           (256, False, 16), (17, True, 5)])
 def test_tiled_bosons_against_oracle(ctqw, shape, N, periodic, K):
@@ -81,7 +82,7 @@ def test_tiled_rejects_unknown_shape_and_short_workspace(ctqw):
     ctqw.ctqw_init_state(h, psi, ctqw.initial_sites(w, h), cw.C64)
     with pytest.raises(ctqw.CtqwError, match="shape"):
         ctqw.ctqw_propagate_taylor(h, psi, cw.C64, w.dt, w.K, 2, 0, None, None, None,
-                                   ctqw.FUSED_SHAPE(15), h.workspace(cw.C64, ctqw.TAYLOR, ctqw.FLAG_PLAIN))
+                                   ctqw.FUSED_SHAPE(7), None)
     with pytest.raises(ctqw.CtqwError, match="workspace"):
         ctqw.ctqw_propagate_taylor(h, psi, cw.C64, w.dt, w.K, 2, 0, None, None, None,
                                    ctqw.FLAG_TILED(0), torch.empty(8, dtype=torch.uint8, device="cuda"))
@@ -89,3 +90,13 @@ def test_tiled_rejects_unknown_shape_and_short_workspace(ctqw):
         ctqw.ctqw_propagate_taylor(h, psi, cw.C128, w.dt, w.K, 2, 0, None, None, None,
                                    ctqw.FLAG_TILED(0), h.workspace(cw.C128, ctqw.TAYLOR, ctqw.FLAG_PLAIN))
     h.close()
+
+
+@pytest.mark.parametrize("K", [1, 3, 5, 6, 7, 9, 12])
+def test_tiled_default_depths(ctqw, K):
+    """Every register depth the default path picks (ceil(K / ceil(K / 8)))."""
+    w = cw.get("bosons_n256_u2").with_(N=300, R=2, K=K, dt=0.01, n_steps=10, obs_every=5,
+                                       sites=(149, 150))
+    got = ctqw.run_workload(w)
+    ref = oracle.ensemble_run(w)
+    _check(got, ref)
