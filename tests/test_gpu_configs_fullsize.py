@@ -156,3 +156,23 @@ def test_adjoint_full_size_against_central_differences(ctqw):
         fd = (loss64(a, b, target) - loss64(a2, b2, target)) / (2 * hfd)
         got = ge[i] if kind == "eps" else gJ[i]
         assert abs(got - fd) <= 1e-3 * max(abs(fd), 1e-6), (kind, i, got, fd)
+
+
+def test_large_two_particle_states_on_the_tiled_path_against_oracle(ctqw):
+    """The default path for two particles in FP32 beyond N = 256 (temporally
+    blocked register tiles), at full batch size, first steps: N = 512
+    (256 realizations) and the ragged batch's largest members (N = 1024)."""
+    w = cw.get("adjoint_n512").with_(n_steps=12, obs_every=12)
+    got = ctqw.run_workload(w)
+    P = per_realization_P(got["psi"], got["st_off"], got["sizes"], 2)
+    for r in (0, w.R - 1):
+        ref = _oracle_one(w, r)
+        assert np.max(np.abs(P[r] - ref["P"][-1])) <= TOL_FP32
+        assert abs(got["norm"][-1, r] - ref["norm"][-1]) <= TOL_NORM_DRIFT
+    wr = cw.get("ragged_n128_1024").with_(n_steps=6, obs_every=6)
+    got = ctqw.run_workload(wr)
+    sizes = got["sizes"]
+    P = per_realization_P(got["psi"], got["st_off"], sizes, 2)
+    for r in [int(i) for i in np.nonzero(sizes == sizes.max())[0][:2]]:
+        ref = _oracle_one(wr, r)
+        assert np.max(np.abs(P[r] - ref["P"][-1])) <= TOL_FP32
