@@ -72,12 +72,13 @@ extern "C" {
 #define CTQW_FUSED_SHAPE_SHIFT 8
 #define CTQW_FUSED_SHAPE(k) (((uint32_t)(k) & 0xFu) << CTQW_FUSED_SHAPE_SHIFT)
 #define CTQW_SHAPE_WAVEFRONT 8
-/* k = CTQW_SHAPE_TILED(i), i = 0..5: the temporally blocked tiled kernel
+/* k = CTQW_SHAPE_TILED(i), i = 0..6: the temporally blocked tiled kernel
  * (m = 2, CTQW_C64, any N, open or ring, ragged): ceil(K/D) launches per step,
- * each applying up to D Horner stages on tiles with halos.  i = 0..2 keep the
- * iterate in shared memory: (tile <= 56, D = 4), (tile <= 60, D = 2),
- * (tile <= 48, D = 8); i = 3..6 keep it in registers on a 64 x 64 region:
- * D = 4, 8, 2, 7 (tile 64 - 2D).  Needs the per-term workspace (3 states). */
+ * each applying up to D Horner stages on tiles with halos.  i = 0 keeps the
+ * iterate in shared memory (tile <= 56, D = 4); i = 1, 2 keep it in registers
+ * on 64 x 128 regions (4 columns a lane), D = 8, 4; i = 3..6 in registers on
+ * 64 x 64 regions (2 columns a lane), D = 4, 8, 2, 7 (tile 64 - 2D).  Needs
+ * the per-term workspace (3 states). */
 #define CTQW_SHAPE_TILED(i) (9 + (i))
 
 typedef struct ctqw_hamiltonian ctqw_hamiltonian;   /* opaque, owned by the library */

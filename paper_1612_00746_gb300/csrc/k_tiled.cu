@@ -358,13 +358,195 @@ __global__ void __launch_bounds__(256, 3) taylor_tiled_reg_kernel(const __grid_c
     }
 }
 
+// The register tiles on a wider region: 64 rows x 32 CL columns (tile
+// (64 - 2D) x (32 CL - 2D)), every lane owning CL adjacent columns, so a
+// smaller share of the region is halo and neighbours along x2 are mostly in
+// the lane.  psi rows in shared memory are lane-major (column pair k/2 of
+// lane l at float4 slot (k/2)*32 + l), as in the full-row kernel.
+template <int D, int CL>
+__global__ void __launch_bounds__(256, 2) taylor_tiled_wide_kernel(const __grid_constant__ TiledArgs a) {
+    constexpr int RR = 64, RC = 32 * CL, T1 = RR - 2 * D, T2 = RC - 2 * D, RL = 8;
+    static_assert(CL % 2 == 0, "column pairs");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *Q = reinterpret_cast<float4 *>(smem_raw);            // [RR][RC / 2] lane-major pairs
+    float4 *edge = Q + RR * (RC / 2);                             // [2 parity][8 warps][2][RC / 2]
+    float4 *zero = edge + 2 * 8 * 2 * (RC / 2);                   // [RC / 2]
+    float4 *rowc = zero + RC / 2;                                 // [RR + 1]
+    int *x_row = reinterpret_cast<int *>(rowc + RR + 1);          // [RR]
+
+    const int r = a.list[blockIdx.z];
+    const int N = a.tab.N[r];
+    const int x1_0 = blockIdx.y * T1 - D, x2_0 = blockIdx.x * T2 - D;
+    const int64_t base = a.tab.st_off[r];
+    const int64_t po = a.tab.par_off[r];
+    const float dt = a.dt;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = warp * RL;
+
+    for (int i = threadIdx.x; i <= RR; i += blockDim.x) {
+        const int X1 = ((x1_0 + i) % N + N) % N;
+        if (i < RR) x_row[i] = X1;
+        const float e = i < RR ? dt * a.eps[po + X1] : 0.f;
+        const float j = -dt * a.J[po + (X1 + N - 1) % N];
+        rowc[i] = make_float4(e, e, j, j);
+    }
+    for (int q = threadIdx.x; q < RC / 2; q += blockDim.x) zero[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int X2[CL];
+    float2 ec[CL], nJc[CL + 1];
+#pragma unroll
+    for (int k = 0; k < CL; ++k) {
+        X2[k] = ((x2_0 + CL * lane + k) % N + N) % N;
+        const float v = dt * a.eps[po + X2[k]];
+        ec[k] = make_float2(v, v);
+    }
+#pragma unroll
+    for (int k = 0; k <= CL; ++k) {
+        const int X = ((x2_0 + CL * lane + k - 1) % N + N) % N;   // bond left of column CL lane + k
+        const float v = -dt * a.J[po + X];
+        nJc[k] = make_float2(v, v);
+    }
+    __syncthreads();
+    const float2 *win = a.w_in + base, *gpsi = a.psi + base;
+    const uint32_t sQ = smem_u32(Q);
+    for (int i = warp; i < RR; i += 8) {
+        const int64_t grow = (int64_t)x_row[i] * N;
+#pragma unroll
+        for (int k = 0; k < CL; ++k) {
+            const uint32_t slot = (uint32_t)(i * (RC / 2) + (k / 2) * 32 + lane);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sQ + slot * 16u + 8u * (k & 1)),
+                         "l"(gpsi + grow + X2[k])
+                         : "memory");
+        }
+    }
+    float2 P[RL][CL];
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+        const int64_t grow = (int64_t)x_row[r0 + i] * N;
+#pragma unroll
+        for (int k = 0; k < CL; ++k) P[i][k] = win[grow + X2[k]];
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+
+    const float2 dU = make_float2(a.dtU, a.dtU);
+    const int from_left = (lane + 31) & 31, from_right = (lane + 1) & 31;
+#pragma unroll 1
+    for (int d = 1; d <= a.n_stages; ++d) {
+        const int par = d & 1;
+        const int j = a.j0 - d + 1;
+        const bool last_final = a.final && d == a.n_stages;   // j == 1
+        const float inv_j = 1.0f / (float)j;
+        float4 *eb = edge + (par * 8 + warp) * 2 * (RC / 2);
+#pragma unroll
+        for (int k = 0; k < CL; k += 2) {
+            eb[(k / 2) * 32 + lane] = make_float4(P[0][k].x, P[0][k].y, P[0][k + 1].x, P[0][k + 1].y);
+            eb[RC / 2 + (k / 2) * 32 + lane] =
+                make_float4(P[RL - 1][k].x, P[RL - 1][k].y, P[RL - 1][k + 1].x, P[RL - 1][k + 1].y);
+        }
+        __syncthreads();
+        const float4 *us = warp > 0 ? edge + (par * 8 + warp - 1) * 2 * (RC / 2) + RC / 2 : zero;
+        const float4 *ds = warp < 7 ? edge + (par * 8 + warp + 1) * 2 * (RC / 2) : zero;
+        float2 prev[CL];
+#pragma unroll
+        for (int k = 0; k < CL; k += 2) {
+            const float4 u4 = us[(k / 2) * 32 + lane];
+            prev[k] = make_float2(u4.x, u4.y);
+            prev[k + 1] = make_float2(u4.z, u4.w);
+        }
+        float4 rc = rowc[r0];
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            float2 c[CL];
+#pragma unroll
+            for (int k = 0; k < CL; ++k) c[k] = P[i][k];
+            const float2 lft = shfl2(c[CL - 1], from_left), rgt = shfl2(c[0], from_right);
+            float2 nb[CL];
+            if (i < RL - 1) {
+#pragma unroll
+                for (int k = 0; k < CL; ++k) nb[k] = P[i + 1][k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < CL; k += 2) {
+                    const float4 d4 = ds[(k / 2) * 32 + lane];
+                    nb[k] = make_float2(d4.x, d4.y);
+                    nb[k + 1] = make_float2(d4.z, d4.w);
+                }
+            }
+            const float4 rn = rowc[r0 + i + 1];
+            const float2 er = make_float2(rc.x, rc.y), jup = make_float2(rc.z, rc.w), jdn = make_float2(rn.z, rn.w);
+            rc = rn;
+            const int X1w = x_row[r0 + i];
+            float2 y[CL];
+#pragma unroll
+            for (int k = 0; k < CL; ++k) {
+                const float2 l = (k == 0) ? lft : c[k - 1];
+                const float2 rr = (k == CL - 1) ? rgt : c[k + 1];
+                float2 t = __fmul2_rn(ec[k], c[k]);
+                t = __ffma2_rn(er, c[k], t);
+                t = __ffma2_rn(jup, prev[k], t);
+                t = __ffma2_rn(jdn, nb[k], t);
+                t = __ffma2_rn(nJc[k], l, t);
+                t = __ffma2_rn(nJc[k + 1], rr, t);
+                if (X1w == X2[k]) t = __ffma2_rn(dU, c[k], t);   // dt U on x1 = x2
+                y[k] = t;
+            }
+#pragma unroll
+            for (int k = 0; k < CL; ++k) prev[k] = c[k];
+            const int ri = r0 + i;
+#pragma unroll
+            for (int k = 0; k < CL; k += 2) {
+                const float4 q = Q[ri * (RC / 2) + (k / 2) * 32 + lane];
+                if (!last_final) {
+                    P[i][k] = make_float2(fmaf(inv_j, y[k].y, q.x), fmaf(-inv_j, y[k].x, q.y));
+                    P[i][k + 1] = make_float2(fmaf(inv_j, y[k + 1].y, q.z), fmaf(-inv_j, y[k + 1].x, q.w));
+                } else if (ri >= D && ri < D + T1 && x1_0 + ri < N) {
+                    // psi(t+dt) = psi + (-i) y on the tile, rounding error carried in lo
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int ck = CL * lane + k + h2;
+                        if (ck < D || ck >= D + T2 || x2_0 + ck >= N) continue;
+                        const int64_t g = base + (int64_t)X1w * N + X2[k + h2];
+                        const float2 yk = y[k + h2];
+                        float2 hv = h2 ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+                        const float2 inc = make_float2(yk.y, -yk.x);
+                        if (a.compensated) {
+                            float2 l = a.lo[g];
+                            compensated_add(hv.x, l.x, inc.x);
+                            compensated_add(hv.y, l.y, inc.y);
+                            a.lo[g] = l;
+                        } else {
+                            hv.x += inc.x;
+                            hv.y += inc.y;
+                        }
+                        a.w_out[g] = hv;
+                    }
+                }
+            }
+        }
+    }
+    if (!a.final) {
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            const int ri = r0 + i;
+            if (ri < D || ri >= D + T1 || x1_0 + ri >= N) continue;
+            const int64_t grow = base + (int64_t)x_row[ri] * N;
+#pragma unroll
+            for (int k = 0; k < CL; ++k) {
+                const int ck = CL * lane + k;
+                if (ck >= D && ck < D + T2 && x2_0 + ck < N) a.w_out[grow + X2[k]] = P[i][k];
+            }
+        }
+    }
+}
+
 using TiledKernel = void (*)(TiledArgs);
 
 struct TiledShape {
     int TMAX, D;
     TiledKernel kern;
     size_t smem;
-    bool fixed_tile;   // the register kernel: tile T = TMAX exactly
+    bool fixed_tile;   // the register kernels: tile TMAX (rows) x TMAX2 (columns) exactly
+    int TMAX2;
 };
 
 template <int TMAX, int D>
@@ -377,6 +559,7 @@ TiledShape tiled_shape() {
     s.smem = sizeof(float2) * 3 * (size_t)RS * RS + sizeof(float) * (4 * (size_t)RS + 2) +
              sizeof(int) * 2 * (size_t)RS;
     s.fixed_tile = false;
+    s.TMAX2 = TMAX;
     return s;
 }
 
@@ -388,12 +571,27 @@ TiledShape tiled_reg_shape() {
     s.kern = taylor_tiled_reg_kernel<D>;
     s.smem = sizeof(float4) * (64 * 32 + 2 * 8 * 2 * 32 + 32 + 65) + sizeof(int) * 64;
     s.fixed_tile = true;
+    s.TMAX2 = s.TMAX;
+    return s;
+}
+
+template <int D, int CL>
+TiledShape tiled_wide_shape() {
+    constexpr int RC = 32 * CL;
+    TiledShape s;
+    s.TMAX = 64 - 2 * D;
+    s.TMAX2 = RC - 2 * D;
+    s.D = D;
+    s.kern = taylor_tiled_wide_kernel<D, CL>;
+    s.smem = sizeof(float4) * (64 * (RC / 2) + 2 * 8 * 2 * (RC / 2) + RC / 2 + 65) + sizeof(int) * 64;
+    s.fixed_tile = true;
     return s;
 }
 
 // regions of at most 64 x 64 (two 32-lane column passes per row); shapes
-// 3..10: the iterate in registers at depths 4, 8, 2, 7, 6, 5, 3 and 1
-constexpr int kTiledShapes = 11;
+// 3..10: the iterate in registers at depths 4, 8, 2, 7, 6, 5, 3 and 1;
+// 11, 12: registers on 64 x 128 regions at depths 8 and 4
+constexpr int kTiledShapes = 13;
 
 bool tiled_shape_for(int idx, TiledShape &s) {
     switch (idx) {
@@ -408,6 +606,8 @@ bool tiled_shape_for(int idx, TiledShape &s) {
         case 8: s = tiled_reg_shape<5>(); return true;
         case 9: s = tiled_reg_shape<3>(); return true;
         case 10: s = tiled_reg_shape<1>(); return true;
+        case 11: s = tiled_wide_shape<8, 4>(); return true;
+        case 12: s = tiled_wide_shape<4, 4>(); return true;
         default: return false;
     }
 }
@@ -467,10 +667,11 @@ int launch_taylor_tiled(const ctqw_hamiltonian *h, int shape, const void *w_in, 
     for (size_t g = 0; g < h->group_N.size(); ++g) {
         const int N = h->group_N[g], cnt = h->group_count[g];
         // as few tiles per side as the compiled maximum allows, of equal size
-        const int tiles = (N + f.TMAX - 1) / f.TMAX;
+        const int tiles = (N + f.TMAX - 1) / f.TMAX;             // along x1 (and x2 if square)
+        const int tiles2 = (N + f.TMAX2 - 1) / f.TMAX2;          // along x2
         a.T = f.fixed_tile ? f.TMAX : (N + tiles - 1) / tiles;
         a.list = h->by_group_d + off;
-        f.kern<<<dim3((unsigned)tiles, (unsigned)tiles, (unsigned)cnt), 256, f.smem, s>>>(a);
+        f.kern<<<dim3((unsigned)tiles2, (unsigned)tiles, (unsigned)cnt), 256, f.smem, s>>>(a);
         CTQW_CUDA_TRY(cudaGetLastError());
         off += cnt;
     }

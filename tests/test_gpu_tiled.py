@@ -1,7 +1,7 @@
 """Parity of the temporally blocked tiled kernels (D Horner stages per launch
-on tiles with halos; the iterate in shared memory, shapes 0..2, or in
-registers, shapes 3..6; the library's default picks its depth from K) with
-the FP64 oracle, through the C ABI.
+on tiles with halos; the iterate in shared memory, shape 0, or in registers,
+shapes 1..6; the library's default picks its depth from K) with the FP64
+oracle, through the C ABI.
 
 Cases: every compiled depth, lattice sides that are not multiples of the
 tile and smaller than one region, open chains and rings, K not a multiple
