@@ -346,7 +346,7 @@ def run_ours(args):
     elif path == "tiled":
         # ceil(K / D) launches per step and size group, observables, init
         launches8 = -(-w.K // 8)
-        depth = {0: -(-w.K // launches8), 9: 4, 10: 8, 11: 4, 12: 4, 13: 8, 14: 2, 15: 7}[(args.flags >> 8) & 0xF]
+        depth = {0: -(-w.K // launches8), 9: 4, 10: 8, 11: 8, 12: 4, 13: 8, 14: 2, 15: 7}[(args.flags >> 8) & 0xF]
         launches_per_step = 1 + w.n_steps * (-(-w.K // depth)) * len(h.group_sizes) + n_obs
     else:
         launches_per_step = 2   # init_state kernel + fused propagation kernel

@@ -75,10 +75,10 @@ extern "C" {
 /* k = CTQW_SHAPE_TILED(i), i = 0..6: the temporally blocked tiled kernel
  * (m = 2, CTQW_C64, any N, open or ring, ragged): ceil(K/D) launches per step,
  * each applying up to D Horner stages on tiles with halos.  i = 0 keeps the
- * iterate in shared memory (tile <= 56, D = 4); i = 1, 2 keep it in registers
- * on 64 x 128 regions (4 columns a lane), D = 8, 4; i = 3..6 in registers on
- * 64 x 64 regions (2 columns a lane), D = 4, 8, 2, 7 (tile 64 - 2D).  Needs
- * the per-term workspace (3 states). */
+ * iterate in shared memory (tile <= 56, D = 4); i = 1 keeps it in registers
+ * on 64 x 128 regions (4 columns a lane), D = 8; i = 2 on 96 x 64 regions
+ * (12 warps), D = 8; i = 3..6 on 64 x 64 regions (2 columns a lane),
+ * D = 4, 8, 2, 7 (tile 64 - 2D).  Needs the per-term workspace (3 states). */
 #define CTQW_SHAPE_TILED(i) (9 + (i))
 
 typedef struct ctqw_hamiltonian ctqw_hamiltonian;   /* opaque, owned by the library */

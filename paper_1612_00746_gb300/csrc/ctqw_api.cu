@@ -542,7 +542,7 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
                                    norm_dev, energy_dev, flags, workspace_dev, workspace_bytes, s);
     if (!(flags & CTQW_FLAG_PLAIN) && shape >= CTQW_SHAPE_TILED(0)) {
         // public tiled shapes 0..6 -> compiled tile kernels (see include/ctqw.h)
-        static const int tiled_public[7] = {0, 11, 12, 3, 4, 5, 6};
+        static const int tiled_public[7] = {0, 11, 13, 3, 4, 5, 6};
         return propagate_tiled(h, dtype, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
                                energy_dev, flags, tiled_public[shape - CTQW_SHAPE_TILED(0)],
                                workspace_dev, workspace_bytes, s);

@@ -197,27 +197,27 @@ __global__ void __launch_bounds__(256) taylor_tiled_kernel(const __grid_constant
     }
 }
 
-// The same D stages with the iterate in registers: the region is 64 x 64
-// (tile T = 64 - 2D), every warp holds 8 region rows and every lane the two
-// adjacent columns 2l, 2l+1 of them.  Neighbours along x2 are in the lane or
+// The same D stages with the iterate in registers: the region is 8W rows x
+// 64 columns (tile (8W - 2D) x (64 - 2D)), every warp holds 8 region rows
+// and every lane the two adjacent columns 2l, 2l+1 of them.  Neighbours along x2 are in the lane or
 // one 64-bit shuffle away; along x1 in registers except the warp's first
 // and last rows, which pass through shared memory once per stage (one
 // __syncthreads).  psi of the region stays in shared memory.  The shuffles
 // wrap from column 63 to 0 and the outermost warps read zero rows: both
 // only touch the halo's outer ring, which stage 1 already leaves inexact.
-template <int D>
-__global__ void __launch_bounds__(256, 3) taylor_tiled_reg_kernel(const __grid_constant__ TiledArgs a) {
-    constexpr int RS = 64, T = RS - 2 * D, RL = 8;
+template <int D, int W>
+__global__ void __launch_bounds__(32 * W, W == 8 ? 3 : 2) taylor_tiled_reg_kernel(const __grid_constant__ TiledArgs a) {
+    constexpr int RS = 8 * W, T = RS - 2 * D, T2 = 64 - 2 * D, RL = 8;   // rows x 64 columns
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *Q = reinterpret_cast<float4 *>(smem_raw);            // [RS][32] psi, (row, lane) -> 2 columns
-    float4 *edge = Q + RS * 32;                                   // [2 parity][8 warps][2][32]
-    float4 *zero = edge + 2 * 8 * 2 * 32;                         // [32] a row of zeros
+    float4 *edge = Q + RS * 32;                                   // [2 parity][W warps][2][32]
+    float4 *zero = edge + 2 * W * 2 * 32;                         // [32] a row of zeros
     float4 *rowc = zero + 32;                                     // [RS + 1] (dt eps, dt eps, -dt J_up, -dt J_up)
     int *x_row = reinterpret_cast<int *>(rowc + RS + 1);          // [RS]
 
     const int r = a.list[blockIdx.z];
     const int N = a.tab.N[r];
-    const int x1_0 = blockIdx.y * T - D, x2_0 = blockIdx.x * T - D;
+    const int x1_0 = blockIdx.y * T - D, x2_0 = blockIdx.x * T2 - D;
     const int64_t base = a.tab.st_off[r];
     const int64_t po = a.tab.par_off[r];
     const float dt = a.dt;
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(256, 3) taylor_tiled_reg_kernel(const __grid_c
     // psi of the region (asynchronous) and the input iterate into registers
     const float2 *win = a.w_in + base, *gpsi = a.psi + base;
     const uint32_t sQ = smem_u32(Q);
-    for (int i = warp; i < RS; i += 8) {
+    for (int i = warp; i < RS; i += W) {
         const int64_t grow = (int64_t)x_row[i] * N;
 #pragma unroll
         for (int k = 0; k < 2; ++k)
@@ -278,12 +278,12 @@ __global__ void __launch_bounds__(256, 3) taylor_tiled_reg_kernel(const __grid_c
         const bool last_final = a.final && d == a.n_stages;   // j == 1
         const float inv_j = 1.0f / (float)j;
         // publish this warp's first and last rows
-        float4 *eb = edge + (par * 8 + warp) * 2 * 32;
+        float4 *eb = edge + (par * W + warp) * 2 * 32;
         eb[lane] = make_float4(P[0][0].x, P[0][0].y, P[0][1].x, P[0][1].y);
         eb[32 + lane] = make_float4(P[RL - 1][0].x, P[RL - 1][0].y, P[RL - 1][1].x, P[RL - 1][1].y);
         __syncthreads();
-        const float4 u4 = warp > 0 ? edge[(par * 8 + warp - 1) * 2 * 32 + 32 + lane] : zero[lane];
-        const float4 d4 = warp < 7 ? edge[(par * 8 + warp + 1) * 2 * 32 + lane] : zero[lane];
+        const float4 u4 = warp > 0 ? edge[(par * W + warp - 1) * 2 * 32 + 32 + lane] : zero[lane];
+        const float4 d4 = warp < W - 1 ? edge[(par * W + warp + 1) * 2 * 32 + lane] : zero[lane];
         float2 prev[2] = {make_float2(u4.x, u4.y), make_float2(u4.z, u4.w)};
         float4 rc = rowc[r0];
 #pragma unroll
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(256, 3) taylor_tiled_reg_kernel(const __grid_c
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
                         const int ck = 2 * lane + k;
-                        if (ck < D || ck >= D + T || x2_0 + ck >= N) continue;
+                        if (ck < D || ck >= D + T2 || x2_0 + ck >= N) continue;
                         const int64_t g = base + (int64_t)X1w * N + X2[k];
                         const float2 yk = k ? y1 : y0;
                         float2 h = k ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(256, 3) taylor_tiled_reg_kernel(const __grid_c
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const int ck = 2 * lane + k;
-                if (ck >= D && ck < D + T && x2_0 + ck < N) a.w_out[grow + X2[k]] = P[i][k];
+                if (ck >= D && ck < D + T2 && x2_0 + ck < N) a.w_out[grow + X2[k]] = P[i][k];
             }
         }
     }
@@ -547,6 +547,7 @@ struct TiledShape {
     size_t smem;
     bool fixed_tile;   // the register kernels: tile TMAX (rows) x TMAX2 (columns) exactly
     int TMAX2;
+    int threads = 256;
 };
 
 template <int TMAX, int D>
@@ -563,15 +564,17 @@ TiledShape tiled_shape() {
     return s;
 }
 
-template <int D>
+template <int D, int W = 8>
 TiledShape tiled_reg_shape() {
+    constexpr int RS = 8 * W;
     TiledShape s;
-    s.TMAX = 64 - 2 * D;
+    s.TMAX = RS - 2 * D;
+    s.TMAX2 = 64 - 2 * D;
     s.D = D;
-    s.kern = taylor_tiled_reg_kernel<D>;
-    s.smem = sizeof(float4) * (64 * 32 + 2 * 8 * 2 * 32 + 32 + 65) + sizeof(int) * 64;
+    s.kern = taylor_tiled_reg_kernel<D, W>;
+    s.smem = sizeof(float4) * (RS * 32 + 2 * W * 2 * 32 + 32 + RS + 1) + sizeof(int) * RS;
     s.fixed_tile = true;
-    s.TMAX2 = s.TMAX;
+    s.threads = 32 * W;
     return s;
 }
 
@@ -590,8 +593,9 @@ TiledShape tiled_wide_shape() {
 
 // regions of at most 64 x 64 (two 32-lane column passes per row); shapes
 // 3..10: the iterate in registers at depths 4, 8, 2, 7, 6, 5, 3 and 1;
-// 11, 12: registers on 64 x 128 regions at depths 8 and 4
-constexpr int kTiledShapes = 13;
+// 11, 12: registers on 64 x 128 regions at depths 8 and 4; 13, 14:
+// registers on 96 x 64 regions (12 warps) at depths 8 and 7
+constexpr int kTiledShapes = 15;
 
 bool tiled_shape_for(int idx, TiledShape &s) {
     switch (idx) {
@@ -608,6 +612,8 @@ bool tiled_shape_for(int idx, TiledShape &s) {
         case 10: s = tiled_reg_shape<1>(); return true;
         case 11: s = tiled_wide_shape<8, 4>(); return true;
         case 12: s = tiled_wide_shape<4, 4>(); return true;
+        case 13: s = tiled_reg_shape<8, 12>(); return true;
+        case 14: s = tiled_reg_shape<7, 12>(); return true;
         default: return false;
     }
 }
@@ -671,7 +677,7 @@ int launch_taylor_tiled(const ctqw_hamiltonian *h, int shape, const void *w_in, 
         const int tiles2 = (N + f.TMAX2 - 1) / f.TMAX2;          // along x2
         a.T = f.fixed_tile ? f.TMAX : (N + tiles - 1) / tiles;
         a.list = h->by_group_d + off;
-        f.kern<<<dim3((unsigned)tiles2, (unsigned)tiles, (unsigned)cnt), 256, f.smem, s>>>(a);
+        f.kern<<<dim3((unsigned)tiles2, (unsigned)tiles, (unsigned)cnt), f.threads, f.smem, s>>>(a);
         CTQW_CUDA_TRY(cudaGetLastError());
         off += cnt;
     }

@@ -36,8 +36,9 @@ FLAG_WAVEFRONT = FUSED_SHAPE(SHAPE_WAVEFRONT)   # the row-wavefront kernel
 
 def FLAG_TILED(i: int) -> int:
     """The temporally blocked tiled kernel, shape i: iterate in shared memory
-    (0: D = 4), in registers on 64 x 128 regions (1: D = 8, 2: D = 4) or on
-    64 x 64 regions (3: D = 4, 4: D = 8, 5: D = 2, 6: D = 7)."""
+    (0: D = 4), in registers on 64 x 128 regions (1: D = 8), on 96 x 64
+    regions (2: D = 8) or on 64 x 64 regions (3: D = 4, 4: D = 8, 5: D = 2,
+    6: D = 7)."""
     return FUSED_SHAPE(9 + int(i))
 
 TAYLOR, RK4 = 0, 1
