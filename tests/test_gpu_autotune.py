@@ -124,3 +124,40 @@ def test_per_term_ragged_propagation_replays_from_a_cuda_graph(ctqw):
     torch.cuda.synchronize()
     assert np.max(np.abs(P.cpu().numpy() - P1)) <= 1e-14   # FP64 atomics: order of additions
     h.close()
+
+
+def test_tiled_default_propagation_replays_from_a_cuda_graph(ctqw):
+    """The default path for a ragged batch beyond the fused sizes (register
+    tiles, one launch per size group and stage group) captured and replayed."""
+    w = cw.get("ragged_n128_1024").with_(R=4, ragged_sizes=(300, 420), n_steps=6, obs_every=3)
+    h = ctqw.build_for_workload(w)
+    sites = ctqw.initial_sites(w, h)
+    psi = h.new_state(cw.C64)
+    n_obs = h.n_obs(w.n_steps, w.obs_every)
+    P = torch.empty((n_obs, h.p_width), dtype=torch.float64, device="cuda")
+    nr = torch.empty((n_obs, h.R), dtype=torch.float64, device="cuda")
+    en = torch.empty((n_obs, h.R), dtype=torch.float64, device="cuda")
+    ws = h.workspace(cw.C64)
+    ctqw.ctqw_init_state(h, psi, sites, cw.C64)
+    psi0 = psi.clone()
+    # eager run first (also the first use of every kernel)
+    ctqw.ctqw_propagate_taylor(h, psi, cw.C64, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en, 0, ws)
+    torch.cuda.synchronize()
+    P_eager, psi_eager = P.cpu().numpy(), psi.cpu().numpy()
+    psi.copy_(psi0)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            ctqw.ctqw_propagate_taylor(h, psi, cw.C64, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en,
+                                       0, ws, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    psi.copy_(psi0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(psi.cpu().numpy(), psi_eager)
+    assert np.max(np.abs(P.cpu().numpy() - P_eager)) <= 1e-14
+    ref = oracle.ensemble_run(w)
+    assert np.max(np.abs(P.cpu().numpy() - ref["P_mean"])) <= TOL_FP32
+    h.close()
