@@ -14,8 +14,9 @@ Written from the paper's Sec. 2 (arXiv:1612.00746), in its order and notation:
 * Algorithm 2: fourth-order Runge-Kutta step.
 * Sec. 2.3 / Algorithm 3: truncated Taylor series of the evolution operator,
   Phi^(0) = Psi, Phi^(j) = -(i dt / j) H Phi^(j-1), Psi(t+dt) = sum_j Phi^(j).
-* Sec. 2, density matrix <rho> = (1/R) sum_i |Psi_i><Psi_i|: only its diagonal
-  is needed for the site occupations P(x) averaged over realizations.
+* Sec. 2, density matrix <rho> = (1/R) sum_i |Psi_i><Psi_i|: its diagonal
+  gives the site occupations P(x) averaged over realizations; its one-body
+  reduction (partial trace over all particles but one) is one_body_density.
 
 Everything is numpy / scipy in float64 / complex128, one realization at a time,
 with no blocking, fusion or reordering beyond the algorithms themselves.
@@ -35,7 +36,7 @@ __all__ = [
     "exact_evolution", "site_occupation", "pair_correlation", "norm", "energy",
     "propagate", "ensemble_run", "workload_parameters", "n_samples",
     "taylor_truncation_bound", "hamiltonian_norm_bound", "loss_and_adjoint_gradient",
-    "occupation_weights", "noninteracting_evolution",
+    "occupation_weights", "noninteracting_evolution", "one_body_density",
 ]
 
 
@@ -215,15 +216,31 @@ def noninteracting_evolution(eps, J, periodic, m, psi0, times):
 def site_occupation(psi, N, m):
     """P(x) = (1/m) sum_j sum_{basis states with x_j = x} |psi|^2.
 
-    Reading: the paper post-processes <rho> into "any desired observable"
-    without naming one; the one-body site occupation normalised to the norm
-    (its diagonal marginals) is the observable here.
+    Reading: the paper post-processes <rho> into observables without naming
+    one; the one-body site occupation normalised to the norm (its diagonal
+    marginals) is the observable here.
     """
     p = (np.abs(psi) ** 2).reshape((N,) * m)
     out = np.zeros(N, dtype=np.float64)
     for j in range(m):
         axes = tuple(a for a in range(m) if a != j)
         out += p.sum(axis=axes)
+    return out / m
+
+
+def one_body_density(psi, N, m):
+    """One-body reduced density matrix, rho1(x, x') = (1/m) sum_j
+    sum_{other coordinates} psi(.., x_j = x, ..) conj(psi(.., x_j = x', ..)).
+
+    The partial trace of |Psi><Psi| (Sec. 2) over all particles but one,
+    averaged over which particle is kept, so that trace(rho1) = <Psi|Psi>
+    and diag(rho1) = site_occupation.  A matrix product per particle.
+    """
+    t = np.asarray(psi, dtype=np.complex128).reshape((N,) * m)
+    out = np.zeros((N, N), dtype=np.complex128)
+    for j in range(m):
+        a = np.moveaxis(t, j, 0).reshape(N, -1)
+        out += a @ a.conj().T
     return out / m
 
 

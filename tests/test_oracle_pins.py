@@ -389,3 +389,49 @@ def test_noninteracting_evolution_matches_dense_exact_and_taylor(m, periodic, st
     for _ in range(330):
         psi = O.taylor_step(H, psi, 0.01, 14)
     assert np.max(np.abs(a[2] - psi)) < 1e-12
+
+
+# ---------------------------------------------------------------- one-body density matrix
+def _random_unit(N, rng):
+    v = rng.normal(size=N) + 1j * rng.normal(size=N)
+    return v / np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("m,N", [(2, 7), (3, 5)])
+def test_one_body_density_diagonal_trace_hermitian(m, N):
+    rng = np.random.default_rng(11)
+    psi = rng.normal(size=N ** m) + 1j * rng.normal(size=N ** m)
+    rho = O.one_body_density(psi, N, m)
+    assert np.allclose(np.diag(rho).real, O.site_occupation(psi, N, m), rtol=0, atol=1e-12)
+    assert np.allclose(np.diag(rho).imag, 0.0, atol=1e-13)
+    assert abs(np.trace(rho).real - O.norm(psi)) <= 1e-11
+    assert np.allclose(rho, rho.conj().T, atol=1e-13)
+    assert np.min(np.linalg.eigvalsh(rho)) >= -1e-12
+
+
+def test_one_body_density_of_product_states_closed_form():
+    """|phi> x |chi> (x |eta>): rho1 = the mean of the one-particle projectors;
+    the same for the symmetrised state of two orthogonal modes."""
+    rng = np.random.default_rng(12)
+    N = 6
+    phi, chi, eta = (_random_unit(N, rng) for _ in range(3))
+    proj = lambda v: np.outer(v, v.conj())
+    rho2 = O.one_body_density(np.kron(phi, chi), N, 2)
+    assert np.allclose(rho2, (proj(phi) + proj(chi)) / 2, atol=1e-14)
+    rho3 = O.one_body_density(np.kron(np.kron(phi, chi), eta), N, 3)
+    assert np.allclose(rho3, (proj(phi) + proj(chi) + proj(eta)) / 3, atol=1e-14)
+    # two orthogonal modes, bosonic symmetrisation
+    chi_o = chi - phi * np.vdot(phi, chi)
+    chi_o /= np.linalg.norm(chi_o)
+    sym = (np.kron(phi, chi_o) + np.kron(chi_o, phi)) / np.sqrt(2)
+    assert np.allclose(O.one_body_density(sym, N, 2), (proj(phi) + proj(chi_o)) / 2, atol=1e-14)
+
+
+def test_one_body_density_of_localized_state():
+    """|a, b> (distinguishable): rho1 = (|a><a| + |b><b|) / 2 exactly."""
+    N = 9
+    psi = O.initial_state(N, 2, (2, 6), 0)
+    rho = O.one_body_density(psi, N, 2)
+    want = np.zeros((N, N))
+    want[2, 2] = want[6, 6] = 0.5
+    assert np.array_equal(rho, want)
