@@ -614,6 +614,62 @@ def run_adjoint(args):
     return 0
 
 
+def run_rho1(args):
+    """Time ctqw_one_body_density (ensemble-averaged one-body density matrix)
+    on the workload's states after a short propagation.
+
+    Algorithmic flops per call: m N^(m+1) R complex multiply-adds, 8 real
+    flops each, against the FP32 FMA peak (c64 states).
+    """
+    import numpy as np
+    import torch
+
+    from paper_1612_00746_gb300 import ctqw
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ctqw.load()
+    w = cw.get(args.workload)
+    if args.realizations:
+        w = w.with_(R=args.realizations)
+    u_eps, u_J, sizes, _ = cw.packed_draws(w, list(range(w.R)))
+    h = ctqw.Hamiltonian(w.m, w.statistics, w.periodic, sizes, w.J0, w.U, w.eps_halfwidth,
+                         w.J_halfwidth, u_eps, u_J)
+    psi = h.new_state(ctqw.C64, dev)
+    ctqw.ctqw_init_state(h, psi, ctqw.initial_sites(w, h), ctqw.C64)
+    ws = h.workspace(ctqw.C64, ctqw.TAYLOR, 0, dev)
+    ctqw.ctqw_propagate_taylor(h, psi, ctqw.C64, w.dt, w.K, 100, 0, None, None, None, 0, ws)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ctqw.ctqw_one_body_density(h, psi, ctqw.C64)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        rho = ctqw.ctqw_one_body_density(h, psi, ctqw.C64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    flops = float(np.sum(w.m * sizes.astype(np.float64) ** (w.m + 1))) * 8.0
+    peak = SM_COUNT * FP32_FMA_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops / (ms / 1000.0) / 1e12
+    trace = float(sum(torch.diagonal(r).real.sum().item() for r in rho))
+    line = {
+        "metric": "one-body density matrix of the ensemble, TFLOP/s", "value": achieved,
+        "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "m": w.m, "N": w.N, "R": w.R, "states_after_steps": 100},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "kernel": "rho1_term_kernel<float>",
+                     "flops_per_call": flops,
+                     "peak_basis": "152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz (derived)"},
+        "trace_sum_over_groups": trace,
+    }
+    print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -632,6 +688,8 @@ def main(argv=None):
     ap.add_argument("--flags", type=int, default=0, help="ctqw propagation flags (e.g. 4 = wide CTA)")
     ap.add_argument("--dtype", choices=["c64", "c128"], default=None, help="override the workload's type")
     ap.add_argument("--graph", action="store_true", help="replay the propagate call from a CUDA graph")
+    ap.add_argument("--rho1", action="store_true",
+                    help="time ctqw_one_body_density on the workload's states")
     ap.add_argument("--adjoint", action="store_true",
                     help="time ctqw_adjoint_grad on the workload (use --workload adjoint_n512)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -642,6 +700,8 @@ def main(argv=None):
         return run_reference(args)
     if args.adjoint:
         return run_adjoint(args)
+    if args.rho1:
+        return run_rho1(args)
     return run_ours(args)
 
 

@@ -243,6 +243,24 @@ int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, 
                        size_t workspace_bytes, void *stream);
 
 /*
+ * One-body reduced density matrix of every size group, averaged over its
+ * realizations: the partial trace of Sec. 2's ensemble density matrix
+ * <rho> = (1/R) sum_i |Psi_i><Psi_i| over all particles but one, averaged
+ * over which particle is kept,
+ *   rho1_g(x, x') = (1/R_g) (1/m) sum_r sum_j sum_{other coordinates}
+ *                   psi_r(.., x_j = x, ..) conj(psi_r(.., x_j = x', ..)).
+ * Hermitian, trace = the group's mean norm, diagonal = P_mean.  rho_dev:
+ * device, complex128 (interleaved re, im), group g's N_g x N_g block
+ * row-major starting at element sum_{g' < g} N_g'^2 (the order of
+ * ctqw_output_layout's groups); overwritten (zeroed on the stream first).
+ * Products in the state's type (FP32 for CTQW_C64) over chunks of 32
+ * (16 in FP64), accumulated in FP64.  m = 2 or 3.  Asynchronous.
+ * Errors: EINVAL for null pointers or a bad dtype, ECUDA.
+ */
+int ctqw_one_body_density(const ctqw_hamiltonian *h, int32_t dtype, const void *psi_dev,
+                          double *rho_dev, void *stream);
+
+/*
  * One sample of the observables of the current states (the diagonal of
  * <rho>, Sec. 2): P_mean_dev [p_width], norm_dev [R], energy_dev [R] as in
  * ctqw_propagate_taylor, and for m = 2 optionally P_joint_dev: per size group,

@@ -778,6 +778,15 @@ int ctqw_adjoint_grad(const ctqw_hamiltonian *h, int32_t dtype, const void *psi0
     return CTQW_OK;
 }
 
+int ctqw_one_body_density(const ctqw_hamiltonian *h, int32_t dtype, const void *psi_dev,
+                          double *rho_dev, void *stream) {
+    if (!h || !psi_dev || !rho_dev) { ctqw_set_error("null argument"); return CTQW_EINVAL; }
+    if (dtype != CTQW_C64 && dtype != CTQW_C128) { ctqw_set_error("dtype %d", dtype); return CTQW_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    CTQW_CUDA_TRY(cudaMemsetAsync(rho_dev, 0, 2 * sizeof(double) * (size_t)h->joint_width, s));
+    return launch_one_body_density(h, dtype, psi_dev, rho_dev, s);
+}
+
 int ctqw_ensemble_observables(const ctqw_hamiltonian *h, int32_t dtype, const void *psi_dev,
                               double *P_mean_dev, double *P_joint_dev, double *norm_dev,
                               double *energy_dev, void *stream) {

@@ -133,6 +133,11 @@ int launch_rk4_stage(const ctqw_hamiltonian *h, int dtype, const void *in, void 
 int launch_observables(const ctqw_hamiltonian *h, int dtype, const void *psi, double *P_mean,
                        double *P_joint, double *norm, double *energy, cudaStream_t s);
 
+// One-body reduced density matrix per size group (adds into rho, zeroed by
+// the caller): [joint_width] complex128 at the pair-distribution offsets.
+int launch_one_body_density(const ctqw_hamiltonian *h, int dtype, const void *psi, double *rho,
+                            cudaStream_t s);
+
 // Adjoint pieces: out = H in; out = H in + c lam (first: c lam);
 // 2 Re <mu, dH phi> into per-realization gradients; loss and lambda_T.
 int launch_apply_h(const ctqw_hamiltonian *h, int dtype, const void *in, void *out, cudaStream_t s);

@@ -48,7 +48,7 @@ EXPORTED = (
     "ctqw_output_layout", "ctqw_init_state", "ctqw_workspace_size", "ctqw_propagate_taylor",
     "ctqw_propagate_rk4", "ctqw_ensemble_observables", "ctqw_check_status", "ctqw_last_error",
     "ctqw_version", "ctqw_adjoint_workspace_size", "ctqw_adjoint_grad", "ctqw_taylor_order",
-    "ctqw_autotune_order",
+    "ctqw_autotune_order", "ctqw_one_body_density",
 )
 
 
@@ -102,6 +102,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "ctqw_adjoint_workspace_size": [vp, i32, i32, i64, i32, ctypes.POINTER(sz)],
         "ctqw_adjoint_grad": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, vp, vp, vp, sz, vp],
         "ctqw_taylor_order": [dbl, i64, dbl, i32, i32, ctypes.POINTER(i32), pd],
+        "ctqw_one_body_density": [vp, i32, vp, vp, vp],
         "ctqw_autotune_order": [vp, i32, dbl, i64, i32, i32, ctypes.POINTER(i32)],
     }
     for name, args in sig.items():
@@ -281,6 +282,21 @@ def ctqw_autotune_order(h: Hamiltonian, dtype: int, dt: float, n_steps: int, K_m
     _check(load().ctqw_autotune_order(h.handle, dtype, float(dt), int(n_steps), int(K_min),
                                       int(K_max), ctypes.byref(K)))
     return K.value
+
+
+def ctqw_one_body_density(h: Hamiltonian, psi: torch.Tensor, dtype: int, stream=None):
+    """Per size group, the ensemble-averaged one-body density matrix: a list of
+    complex128 device tensors [N_g, N_g] (ctqw_one_body_density)."""
+    sizes = [int(n) for n in h.group_sizes]
+    total = sum(n * n for n in sizes)
+    rho = torch.empty(2 * total, dtype=torch.float64, device=psi.device)
+    _check(load().ctqw_one_body_density(h.handle, dtype, _ptr(psi), _ptr(rho), _stream(stream)))
+    out, off = [], 0
+    c = torch.view_as_complex(rho.view(total, 2))
+    for n in sizes:
+        out.append(c[off:off + n * n].view(n, n))
+        off += n * n
+    return out
 
 
 def ctqw_check_status(h: Hamiltonian, stream=None) -> None:
