@@ -37,6 +37,7 @@ __all__ = [
     "propagate", "ensemble_run", "workload_parameters", "n_samples",
     "taylor_truncation_bound", "hamiltonian_norm_bound", "loss_and_adjoint_gradient",
     "occupation_weights", "noninteracting_evolution", "one_body_density",
+    "philox4x64", "unit_double", "switch_parameters", "propagate_switching",
 ]
 
 
@@ -345,6 +346,93 @@ def ensemble_run(w, realizations=None, method="taylor", K=None, n_steps=None,
         off += g
     return {"P": per_P, "norm": np.array(per_norm), "energy": np.array(per_energy),
             "sizes": sizes, "groups": groups, "P_mean": mean, "psi": finals}
+
+
+# ---------------------------------------------------------------- switching noise
+# Sec. 2: the stochastic parts of the Hamiltonian switch between values at
+# random times, and Algorithms 1-3 update the switching times and H after
+# every step.  Reading (the paper gives no law): after each step every
+# stochastic parameter of every realization is redrawn, independently, with
+# probability p from its own Uniform[-w, w] around its mean (discrete
+# telegraph noise; waiting times geometric with mean 1/p steps).  The draws
+# come from the counter-based generator Philox4x64-10 (Salmon et al., SC'11),
+# written out here from its definition: key (seed, 0), counter
+# (step, realization, site, 0); words 0, 1 decide and redraw eps of the
+# site, words 2, 3 the hopping of the bond to its right.
+
+_PHILOX_M = (0xD2E7470EE14C6C93, 0xCA5A826395121157)
+_PHILOX_W = (0x9E3779B97F4A7C15, 0xBB67AE8584CAA73B)
+_U64 = (1 << 64) - 1
+
+
+def philox4x64(counter, key):
+    """Philox4x64-10: ten rounds of two 64x64 -> 128-bit products and a key
+    schedule bumped by the Weyl constants; four 64-bit output words."""
+    c = [int(x) & _U64 for x in counter]
+    k = [int(x) & _U64 for x in key]
+    for _ in range(10):
+        p0 = _PHILOX_M[0] * c[0]
+        p1 = _PHILOX_M[1] * c[2]
+        hi0, lo0 = p0 >> 64, p0 & _U64
+        hi1, lo1 = p1 >> 64, p1 & _U64
+        c = [hi1 ^ c[1] ^ k[0], lo1, hi0 ^ c[3] ^ k[1], lo0]
+        k = [(k[0] + _PHILOX_W[0]) & _U64, (k[1] + _PHILOX_W[1]) & _U64]
+    return c
+
+
+def unit_double(word):
+    """A 64-bit word to a double in [0, 1) from its top 53 bits."""
+    return (int(word) >> 11) * 2.0 ** -53
+
+
+def switch_parameters(eps, J, r, step, seed, p, N, periodic, eps_mean, eps_halfwidth,
+                      J_mean, J_halfwidth, round_to_f32=True):
+    """The Hamiltonian update after step ``step`` of realization ``r``.
+
+    eps and J as lattice_parameters returns them (J: N - 1 bonds on an open
+    chain, N on a ring); returns updated copies.
+    """
+    eps = np.array(eps, dtype=np.float64)
+    J = np.array(J, dtype=np.float64)
+    em = np.broadcast_to(np.asarray(eps_mean, dtype=np.float64), (N,))
+    jm = np.broadcast_to(np.asarray(J_mean, dtype=np.float64), (N,))
+    for i in range(N):
+        w = philox4x64((step, r, i, 0), (seed, 0))
+        if unit_double(w[0]) < p:
+            v = em[i] + eps_halfwidth * (2.0 * unit_double(w[1]) - 1.0)
+            eps[i] = round_f32(v) if round_to_f32 else v
+        if i < len(J) and unit_double(w[2]) < p:
+            v = jm[i] + J_halfwidth * (2.0 * unit_double(w[3]) - 1.0)
+            J[i] = round_f32(v) if round_to_f32 else v
+    return eps, J
+
+
+def propagate_switching(w, r, seed, p, n_steps=None, obs_every=None, K=None):
+    """One realization with switching noise: a Taylor step (Algorithm 3) with
+    the current H, then the Hamiltonian update, n_steps times."""
+    import ctqw_workloads as cw
+
+    n_steps = w.n_steps if n_steps is None else n_steps
+    obs_every = w.obs_every if obs_every is None else obs_every
+    K = w.K if K is None else K
+    N = int(w.sizes()[r])
+    ue, uj = cw.uniform_draws(w.seed, [r], [N])
+    eps, J = workload_parameters(w, ue[0], uj[0], N)
+    psi = initial_state(N, w.m, w.initial_sites(N), w.statistics)
+    P, nr, en = [], [], []
+    for n in range(n_steps + 1):
+        H = many_particle_hamiltonian(single_particle_hamiltonian(eps, J, w.periodic), w.m, w.U)
+        if obs_every > 0 and n % obs_every == 0:
+            P.append(site_occupation(psi, N, w.m))
+            nr.append(norm(psi))
+            en.append(energy(H, psi))
+        if n == n_steps:
+            break
+        psi = taylor_step(H, psi, w.dt, K)
+        eps, J = switch_parameters(eps, J, r, n, seed, p, N, w.periodic, 0.0, w.eps_halfwidth,
+                                   w.J0, w.J_halfwidth)
+    return {"P": np.array(P), "norm": np.array(nr), "energy": np.array(en), "psi": psi,
+            "eps": eps, "J": J}
 
 
 # ---------------------------------------------------------------- error bounds

@@ -435,3 +435,53 @@ def test_one_body_density_of_localized_state():
     want = np.zeros((N, N))
     want[2, 2] = want[6, 6] = 0.5
     assert np.array_equal(rho, want)
+
+
+# ---------------------------------------------------------------- switching noise
+@pytest.mark.parametrize("ctr,key", [((7, 3, 2, 0), (0x1234, 0x5678)), ((0, 0, 0, 0), (0, 0)),
+                                     ((2 ** 64 - 5, 11, 0, 9), (2 ** 63, 17))])
+def test_philox_matches_numpy_bit_generator(ctr, key):
+    """numpy's Philox (4x64-10) emits the block of counter + 1 first."""
+    # the 256-bit counter minus one (word 0 least significant)
+    v = sum(int(c) << (64 * i) for i, c in enumerate(ctr))
+    v = (v - 1) % 2 ** 256
+    prev = [(v >> (64 * i)) & (2 ** 64 - 1) for i in range(4)]
+    bg = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=np.array(prev, dtype=np.uint64))
+    assert [int(x) for x in bg.random_raw(4)] == O.philox4x64(ctr, key)
+
+
+def test_switching_probability_and_range():
+    N, p = 400, 0.2
+    eps0 = np.zeros(N)
+    J0 = np.ones(N - 1)
+    switched_e, switched_j = 0, 0
+    for step in range(10):
+        e, j = O.switch_parameters(eps0, J0, 3, step, 99, p, N, False, 0.0, 1.0, 1.0, 0.25,
+                                   round_to_f32=False)
+        switched_e += np.count_nonzero(e != eps0)
+        switched_j += np.count_nonzero(j != J0)
+        assert np.all(np.abs(e) <= 1.0) and np.all(np.abs(j - 1.0) <= 0.25)
+    n = 10 * N
+    for k in (switched_e, switched_j * N / (N - 1)):
+        assert abs(k / n - p) <= 5 * math.sqrt(p * (1 - p) / n)   # binomial, 5 sigma
+
+
+def test_switching_with_zero_probability_is_static():
+    w = cw.get("bosons_small").with_(N=10, R=1, sites=(4, 5), n_steps=20, obs_every=5, K=10)
+    a = O.propagate_switching(w, 0, seed=5, p=0.0)
+    b = O.ensemble_run(w)
+    assert np.max(np.abs(a["P"] - b["P"][0])) <= 1e-15
+    assert np.max(np.abs(a["psi"] - b["psi"][0])) <= 1e-15
+
+
+def test_switching_conserves_norm_and_keeps_bosonic_symmetry():
+    w = cw.get("bosons_small").with_(N=8, R=1, sites=(3, 4), n_steps=60, obs_every=10, K=14,
+                                     dt=0.02)
+    res = O.propagate_switching(w, 0, seed=7, p=0.3)
+    assert np.max(np.abs(res["norm"] - 1.0)) <= 1e-12
+    psi = res["psi"].reshape(8, 8)
+    assert np.max(np.abs(psi - psi.T)) <= 1e-13
+    # the parameters did switch, within their ranges
+    static = O.ensemble_run(w)
+    assert np.max(np.abs(res["P"][-1] - static["P"][0][-1])) > 1e-6
+    assert np.all(np.abs(res["eps"]) <= w.eps_halfwidth)
