@@ -168,13 +168,15 @@ def fused_traffic(workload: str):
     return ent.get("dram_bytes_per_launch")
 
 
-def propagation_path(w, dtype, flags):
+def propagation_path(w, dtype, flags, switching=False):
     """Which kernels ctqw_propagate_taylor runs for this workload (mirrors the library)."""
     from paper_1612_00746_gb300 import ctqw
 
     shape = (flags >> 8) & 0xF
     if flags & ctqw.FLAG_PLAIN:
         return "plain"
+    if switching:
+        return "tiled" if dtype == ctqw.C64 and w.m == 2 else "plain"
     if shape == ctqw.SHAPE_WAVEFRONT:
         return "wavefront"
     if shape >= 9:
@@ -187,7 +189,7 @@ def propagation_path(w, dtype, flags):
     return "plain"
 
 
-def roofline_of(w, dtype, flags, units, kernel_ms, peaks, traffic):
+def roofline_of(w, dtype, flags, units, kernel_ms, peaks, traffic, switching=False):
     """Roofline entry of the kernel that dominates the propagate call.
 
     Fused kernels (every Taylor term on chip) are bound by the FP32 FMA pipe:
@@ -200,7 +202,7 @@ def roofline_of(w, dtype, flags, units, kernel_ms, peaks, traffic):
     """
     from paper_1612_00746_gb300 import ctqw
 
-    path = propagation_path(w, dtype, flags)
+    path = propagation_path(w, dtype, flags, switching)
     sec = kernel_ms / 1000.0
     if path in ("rows", "banded", "wavefront", "tiled"):
         flops_per_unit = 8 * w.m + 4
@@ -330,11 +332,11 @@ def run_ours(args):
     P = torch.empty((n_obs, h.p_width), dtype=torch.float64, device=dev)
     nr = torch.empty((n_obs, h.R), dtype=torch.float64, device=dev)
     en = torch.empty((n_obs, h.R), dtype=torch.float64, device=dev)
-    ws = h.workspace(dtype, ctqw.TAYLOR, args.flags, dev)
+    ws = h.workspace(dtype, ctqw.TAYLOR, args.flags | (ctqw.FLAG_PLAIN if args.switch is not None else 0), dev)
     counts = torch.tensor(np.repeat(h.group_count, h.group_sizes), dtype=torch.float64, device=dev)
     D = float(np.sum(sizes.astype(np.float64) ** w.m))
     units_per_step = D * w.K * w.n_steps
-    path = propagation_path(w, dtype, args.flags)
+    path = propagation_path(w, dtype, args.flags, args.switch is not None)
     if path == "wavefront":
         # init_state + one observables kernel per sample + one wavefront launch
         # per segment between samples and size group
@@ -350,6 +352,8 @@ def run_ours(args):
         launches_per_step = 1 + w.n_steps * (-(-w.K // depth)) * len(h.group_sizes) + n_obs
     else:
         launches_per_step = 2   # init_state kernel + fused propagation kernel
+    if args.switch is not None:
+        launches_per_step += 1 + w.n_steps   # parameter restore + one update per step
 
     prop_events = []
     graph = None
@@ -374,6 +378,9 @@ def run_ours(args):
             e0.record(stream)
         if graph is not None:
             graph.replay()
+        elif args.switch is not None:
+            ctqw.ctqw_propagate_taylor_switching(h, psi, dtype, w.dt, w.K, w.n_steps, w.obs_every, P, nr,
+                                                 en, 0x5EED, args.switch, args.flags, ws)
         else:
             ctqw.ctqw_propagate_taylor(h, psi, dtype, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en,
                                        args.flags, ws)
@@ -519,7 +526,8 @@ def run_ours(args):
 
     peaks = measured_peaks()
     roofline = roofline_of(w, dtype, args.flags, units_per_step, kernel_ms, peaks,
-                           fused_traffic(w.name) if not (args.realizations or args.n_steps) else None)
+                           fused_traffic(w.name) if not (args.realizations or args.n_steps or args.switch) else None,
+                           switching=args.switch is not None)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
@@ -532,7 +540,8 @@ def run_ours(args):
                                  if dtype == ctqw.C64 else "complex FP64"),
                    "l2": "inputs larger than L2 (states %.0f MB per GPU)" % (D * (8 if dtype == ctqw.C64 else 16) / 1e6),
                    "parallelism": f"realizations sharded, {world} rank(s)",
-                   "launch": "cuda graph replay" if args.graph else "eager"},
+                   "launch": "cuda graph replay" if args.graph else "eager",
+                   "switching_noise_p": args.switch},
         "gpu_launches": launches_per_step * args.steps,
         "roofline": roofline,
         "e2e": e2e,
@@ -688,6 +697,8 @@ def main(argv=None):
     ap.add_argument("--flags", type=int, default=0, help="ctqw propagation flags (e.g. 4 = wide CTA)")
     ap.add_argument("--dtype", choices=["c64", "c128"], default=None, help="override the workload's type")
     ap.add_argument("--graph", action="store_true", help="replay the propagate call from a CUDA graph")
+    ap.add_argument("--switch", type=float, default=None,
+                    help="propagate with switching noise: redraw probability per parameter and step")
     ap.add_argument("--rho1", action="store_true",
                     help="time ctqw_one_body_density on the workload's states")
     ap.add_argument("--adjoint", action="store_true",

@@ -226,6 +226,33 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
                           void *workspace_dev, size_t workspace_bytes, void *stream);
 
 /*
+ * ctqw_propagate_taylor with switching noise (Sec. 2: the stochastic terms
+ * of Eq. (Hij) switch between values at random times; Algorithms 1-3 update
+ * the switching times and H after every step).  Reading: after each step
+ * every on-site energy and every hopping of every realization is redrawn,
+ * independently with probability p_switch, from its own uniform range
+ * (mean + half width * (2u - 1), rounded to float32 as at the build), and
+ * otherwise keeps its value; waiting times are geometric with mean
+ * 1/p_switch steps.  The draws are Philox4x64-10 (Salmon et al., SC'11)
+ * under key (seed, 0), counter (step, realization, site, 0): words 0 and 1
+ * decide and redraw eps of the site, words 2 and 3 the hopping of the bond
+ * to its right (never the absent wrap bond of an open chain).
+ * The call first restores the parameters as built, so equal arguments give
+ * equal results; afterwards the handle holds the parameters after the last
+ * update (ctqw_get_params).  Paths: two particles in CTQW_C64 on the
+ * temporally blocked tiles, everything else (or CTQW_FLAG_PLAIN) one launch
+ * per term; both need 3 states of workspace (ctqw_workspace_size with
+ * CTQW_FLAG_PLAIN).  Outputs as ctqw_propagate_taylor; energies use H of
+ * the sampled step.  Errors: as ctqw_propagate_taylor, EINVAL for p_switch
+ * outside [0, 1] or a short workspace.  Asynchronous.
+ */
+int ctqw_propagate_taylor_switching(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev,
+                                    double dt, int32_t K, int64_t n_steps, int32_t obs_every,
+                                    double *P_mean_dev, double *norm_dev, double *energy_dev,
+                                    uint32_t flags, void *workspace_dev, size_t workspace_bytes,
+                                    uint64_t seed, double p_switch, void *stream);
+
+/*
  * Same as ctqw_propagate_taylor with the classical fourth-order Runge-Kutta
  * step of Sec. 2.2 (Algorithm 2): K^(1) = -iH Psi, K^(2) = -iH(Psi + dt/2 K^(1)),
  * K^(3) = -iH(Psi + dt/2 K^(2)), K^(4) = -iH(Psi + dt K^(3)),

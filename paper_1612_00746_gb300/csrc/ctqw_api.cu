@@ -21,7 +21,7 @@ int64_t n_samples(int64_t n_steps, int obs_every) {
 void free_device(ctqw_hamiltonian *h) {
     void *ptrs[] = {h->eps32, h->J32, h->eps64, h->J64, h->sizes_d, h->group_of_d, h->par_off_d,
                     h->st_off_d, h->group_off_d, h->joint_off_d, h->inv_count_d, h->status_d,
-                    h->by_group_d};
+                    h->by_group_d, h->eps_mean_d, h->J_mean_d, h->eps64_0, h->J64_0};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -300,10 +300,21 @@ int ctqw_build_hamiltonian(const ctqw_lattice_desc *d, void *stream, ctqw_hamilt
     if ((st = launch_build_params(h, u_eps_d, u_J_d, em_d, jm_d, d->eps_halfwidth, d->J_halfwidth,
                                   d->J0, s)))
         return fail(st);
+    // kept for switching noise: the means, the half widths and the parameters as built
+    h->eps_hw = d->eps_halfwidth;
+    h->J_hw = d->J_halfwidth;
+    h->eps_mean_d = em_d;
+    h->J_mean_d = jm_d;
+    em_d = jm_d = nullptr;
+    if (cudaMalloc(&h->eps64_0, pb) != cudaSuccess || cudaMalloc(&h->J64_0, pb) != cudaSuccess)
+        return fail(CTQW_ENOMEM);
+    if (cudaMemcpyAsync(h->eps64_0, h->eps64, pb, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->J64_0, h->J64, pb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return fail(CTQW_ECUDA);
     cudaError_t e = cudaStreamSynchronize(s);
-    for (void *p : {(void *)u_eps_d, (void *)u_J_d, (void *)em_d, (void *)jm_d})
+    for (void *p : {(void *)u_eps_d, (void *)u_J_d})
         if (p) cudaFree(p);
-    u_eps_d = u_J_d = em_d = jm_d = nullptr;
+    u_eps_d = u_J_d = nullptr;
     if (e != cudaSuccess) {
         ctqw_cuda_fail(e, "parameter build");
         free_device(h);
@@ -475,6 +486,75 @@ static int propagate_wavefront(const ctqw_hamiltonian *h, int32_t dtype, void *p
     return st;
 }
 
+// Switching noise: after every step, the Hamiltonian update (launch_switch_params).
+struct SwitchSpec {
+    bool on = false;
+    uint64_t seed = 0;
+    double p = 0.0;
+};
+
+// One launch per Taylor term (c128, forward order of Algorithm 3) or per
+// Horner stage (c64, compensated state update); outputs already zeroed and
+// the workspace (3 states) checked by the caller.
+static int propagate_per_term(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
+                              int32_t K, int64_t n_steps, int32_t obs_every, double *P_mean_dev,
+                              double *norm_dev, double *energy_dev, void *workspace_dev,
+                              cudaStream_t s, const SwitchSpec &sw) {
+    const size_t sb = (size_t)h->total_amp * elem_bytes(dtype);
+    char *ws = (char *)workspace_dev;
+    if (dtype == CTQW_C64) {
+        // FP32: Horner stages and a compensated state update (see k_plain.cu)
+        void *wa = ws, *wb = ws + sb, *lo = ws + 2 * sb;
+        CTQW_CUDA_TRY(cudaMemsetAsync(lo, 0, sb, s));
+        int64_t obs = 0;
+        for (int64_t step = 0; step <= n_steps; ++step) {
+            if (obs_every > 0 && step % obs_every == 0) {
+                CTQW_TRY(launch_observables(h, dtype, psi_dev, P_mean_dev ? P_mean_dev + obs * h->p_width : nullptr,
+                                            nullptr, norm_dev ? norm_dev + obs * h->R : nullptr,
+                                            energy_dev ? energy_dev + obs * h->R : nullptr, s));
+                ++obs;
+            }
+            if (step == n_steps) break;
+            const void *in = psi_dev;
+            void *out = wa;
+            if (K == 1) {
+                CTQW_CUDA_TRY(cudaMemcpyAsync(wa, psi_dev, sb, cudaMemcpyDeviceToDevice, s));
+                in = wa;
+            }
+            for (int j = K; j >= 2; --j) {
+                CTQW_TRY(launch_horner_stage(h, in, psi_dev, out, dt / j, s));
+                in = out;
+                out = (out == wa) ? wb : wa;
+            }
+            CTQW_TRY(launch_horner_final(h, in, psi_dev, lo, dt, s));
+            if (sw.on) CTQW_TRY(launch_switch_params(h, sw.seed, (uint64_t)step, sw.p, s));
+        }
+        return CTQW_OK;
+    }
+    void *cur = psi_dev, *acc = ws, *phi1 = ws + sb, *phi2 = ws + 2 * sb;
+    int64_t obs = 0;
+    for (int64_t step = 0; step <= n_steps; ++step) {
+        if (obs_every > 0 && step % obs_every == 0) {
+            CTQW_TRY(launch_observables(h, dtype, cur, P_mean_dev ? P_mean_dev + obs * h->p_width : nullptr,
+                                        nullptr, norm_dev ? norm_dev + obs * h->R : nullptr,
+                                        energy_dev ? energy_dev + obs * h->R : nullptr, s));
+            ++obs;
+        }
+        if (step == n_steps) break;
+        const void *in = cur;
+        void *out = phi1;
+        for (int j = 1; j <= K; ++j) {
+            CTQW_TRY(launch_taylor_term(h, dtype, in, out, cur, acc, dt / j, j == 1, s));
+            in = out;
+            out = (out == phi1) ? phi2 : phi1;
+        }
+        std::swap(cur, acc);
+        if (sw.on) CTQW_TRY(launch_switch_params(h, sw.seed, (uint64_t)step, sw.p, s));
+    }
+    if (cur != psi_dev) CTQW_CUDA_TRY(cudaMemcpyAsync(psi_dev, cur, sb, cudaMemcpyDeviceToDevice, s));
+    return CTQW_OK;
+}
+
 // The temporally blocked tiled kernels: ceil(K / D) launches per step.  The
 // state rotates through psi and the two iterate buffers of the workspace
 // (the new state cannot overwrite the one other tiles read as halo); the
@@ -482,7 +562,8 @@ static int propagate_wavefront(const ctqw_hamiltonian *h, int32_t dtype, void *p
 static int propagate_tiled(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
                            int32_t K, int64_t n_steps, int32_t obs_every, double *P_mean_dev,
                            double *norm_dev, double *energy_dev, uint32_t flags, int shape,
-                           void *workspace_dev, size_t workspace_bytes, cudaStream_t s) {
+                           void *workspace_dev, size_t workspace_bytes, cudaStream_t s,
+                           const SwitchSpec &sw = SwitchSpec{}) {
     if (!tiled_supported(h, dtype, shape)) {
         ctqw_set_error("tiled path: needs c64 and m = 2 (shape %d)", shape);
         return CTQW_EUNSUPPORTED;
@@ -522,6 +603,7 @@ static int propagate_tiled(const ctqw_hamiltonian *h, int32_t dtype, void *psi_d
             j0 -= nst;
             if (final) cur = wout;
         }
+        if (sw.on) CTQW_TRY(launch_switch_params(h, sw.seed, (uint64_t)step, sw.p, s));
     }
     if (cur != 0) CTQW_CUDA_TRY(cudaMemcpyAsync(psi_dev, bufs[cur], sb, cudaMemcpyDeviceToDevice, s));
     return CTQW_OK;
@@ -575,57 +657,40 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
                                    energy_dev, comp, shape - 4, test, s);
     }
 
-    const size_t sb = (size_t)h->total_amp * elem_bytes(dtype);
-    char *ws = (char *)workspace_dev;
-    if (dtype == CTQW_C64) {
-        // FP32: Horner stages and a compensated state update (see k_plain.cu)
-        void *wa = ws, *wb = ws + sb, *lo = ws + 2 * sb;
-        CTQW_CUDA_TRY(cudaMemsetAsync(lo, 0, sb, s));
-        int64_t obs = 0;
-        for (int64_t step = 0; step <= n_steps; ++step) {
-            if (obs_every > 0 && step % obs_every == 0) {
-                CTQW_TRY(launch_observables(h, dtype, psi_dev, P_mean_dev ? P_mean_dev + obs * h->p_width : nullptr,
-                                            nullptr, norm_dev ? norm_dev + obs * h->R : nullptr,
-                                            energy_dev ? energy_dev + obs * h->R : nullptr, s));
-                ++obs;
-            }
-            if (step == n_steps) break;
-            const void *in = psi_dev;
-            void *out = wa;
-            if (K == 1) {
-                CTQW_CUDA_TRY(cudaMemcpyAsync(wa, psi_dev, sb, cudaMemcpyDeviceToDevice, s));
-                in = wa;
-            }
-            for (int j = K; j >= 2; --j) {
-                CTQW_TRY(launch_horner_stage(h, in, psi_dev, out, dt / j, s));
-                in = out;
-                out = (out == wa) ? wb : wa;
-            }
-            CTQW_TRY(launch_horner_final(h, in, psi_dev, lo, dt, s));
-        }
-        return CTQW_OK;
+    return propagate_per_term(h, dtype, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
+                              energy_dev, workspace_dev, s, SwitchSpec{});
+}
+
+int ctqw_propagate_taylor_switching(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev,
+                                    double dt, int32_t K, int64_t n_steps, int32_t obs_every,
+                                    double *P_mean_dev, double *norm_dev, double *energy_dev,
+                                    uint32_t flags, void *workspace_dev, size_t workspace_bytes,
+                                    uint64_t seed, double p_switch, void *stream) {
+    CTQW_TRY(check_common(h, dtype, psi_dev, dt, n_steps, obs_every));
+    if (!(p_switch >= 0.0 && p_switch <= 1.0)) {
+        ctqw_set_error("p_switch must be in [0, 1] (got %g)", p_switch);
+        return CTQW_EINVAL;
     }
-    void *cur = psi_dev, *acc = ws, *phi1 = ws + sb, *phi2 = ws + 2 * sb;
-    int64_t obs = 0;
-    for (int64_t step = 0; step <= n_steps; ++step) {
-        if (obs_every > 0 && step % obs_every == 0) {
-            CTQW_TRY(launch_observables(h, dtype, cur, P_mean_dev ? P_mean_dev + obs * h->p_width : nullptr,
-                                        nullptr, norm_dev ? norm_dev + obs * h->R : nullptr,
-                                        energy_dev ? energy_dev + obs * h->R : nullptr, s));
-            ++obs;
-        }
-        if (step == n_steps) break;
-        const void *in = cur;
-        void *out = phi1;
-        for (int j = 1; j <= K; ++j) {
-            CTQW_TRY(launch_taylor_term(h, dtype, in, out, cur, acc, dt / j, j == 1, s));
-            in = out;
-            out = (out == phi1) ? phi2 : phi1;
-        }
-        std::swap(cur, acc);
+    if (K == 0) CTQW_TRY(ctqw_autotune_order(h, dtype, dt, n_steps, 1, 30, &K));
+    if (K < 1 || K > 30) { ctqw_set_error("K must be in 1..30, or 0 (got %d)", K); return CTQW_EINVAL; }
+    const size_t need = 3 * (size_t)h->total_amp * elem_bytes(dtype);
+    if (!workspace_dev || workspace_bytes < need) {
+        ctqw_set_error("switching propagation needs a workspace of %zu bytes (got %zu)", need, workspace_bytes);
+        return CTQW_EINVAL;
     }
-    if (cur != psi_dev) CTQW_CUDA_TRY(cudaMemcpyAsync(psi_dev, cur, sb, cudaMemcpyDeviceToDevice, s));
-    return CTQW_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    CTQW_TRY(restore_params(h, s));
+    SwitchSpec sw;
+    sw.on = true;
+    sw.seed = seed;
+    sw.p = p_switch;
+    const int tshape = tiled_default_shape(K);
+    if (!(flags & CTQW_FLAG_PLAIN) && tiled_supported(h, dtype, tshape))
+        return propagate_tiled(h, dtype, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
+                               energy_dev, flags, tshape, workspace_dev, workspace_bytes, s, sw);
+    CTQW_TRY(zero_outputs(h, n_samples(n_steps, obs_every), P_mean_dev, norm_dev, energy_dev, s));
+    return propagate_per_term(h, dtype, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
+                              energy_dev, workspace_dev, s, sw);
 }
 
 int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,

@@ -33,6 +33,10 @@ struct ctqw_hamiltonian {
             *joint_off_d = nullptr;
     double *inv_count_d = nullptr;  // [G] 1 / R_g
     int32_t *by_group_d = nullptr;  // [R] realization indices ordered by size group
+    // switching noise: the lattice description and the parameters as built
+    double eps_hw = 0.0, J_hw = 0.0;
+    double *eps_mean_d = nullptr, *J_mean_d = nullptr;   // [Nmax] or null (0 / J0)
+    double *eps64_0 = nullptr, *J64_0 = nullptr;         // [total_par] as built
     int *status_d = nullptr;        // nonzero after a kernel's bounded wait gave up
 };
 
@@ -108,6 +112,14 @@ inline int for_each_group(const ctqw_hamiltonian *h, F &&launch) {
 int launch_build_params(const ctqw_hamiltonian *h, const double *u_eps_d, const double *u_J_d,
                         const double *eps_mean_d, const double *J_mean_d, double eps_hw,
                         double J_hw, double J0, cudaStream_t s);
+
+// Switching noise (the Hamiltonian update after step `step`): every eps and
+// J of every realization redrawn with probability p (Philox4x64-10, key
+// (seed, 0), counter (step, r, i, 0)); restore_params puts back the
+// parameters as built.
+int launch_switch_params(const ctqw_hamiltonian *h, uint64_t seed, uint64_t step, double p,
+                         cudaStream_t s);
+int restore_params(const ctqw_hamiltonian *h, cudaStream_t s);
 
 // Initial state (a2).  sites_d: [R][m] int32 on the device.
 int launch_init_state(const ctqw_hamiltonian *h, const int32_t *sites_d, int dtype, void *psi,

@@ -48,7 +48,7 @@ EXPORTED = (
     "ctqw_output_layout", "ctqw_init_state", "ctqw_workspace_size", "ctqw_propagate_taylor",
     "ctqw_propagate_rk4", "ctqw_ensemble_observables", "ctqw_check_status", "ctqw_last_error",
     "ctqw_version", "ctqw_adjoint_workspace_size", "ctqw_adjoint_grad", "ctqw_taylor_order",
-    "ctqw_autotune_order", "ctqw_one_body_density",
+    "ctqw_autotune_order", "ctqw_one_body_density", "ctqw_propagate_taylor_switching",
 )
 
 
@@ -103,6 +103,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "ctqw_adjoint_grad": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, vp, vp, vp, sz, vp],
         "ctqw_taylor_order": [dbl, i64, dbl, i32, i32, ctypes.POINTER(i32), pd],
         "ctqw_one_body_density": [vp, i32, vp, vp, vp],
+        "ctqw_propagate_taylor_switching": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, u32, vp, sz,
+                                            ctypes.c_uint64, dbl, vp],
         "ctqw_autotune_order": [vp, i32, dbl, i64, i32, i32, ctypes.POINTER(i32)],
     }
     for name, args in sig.items():
@@ -249,6 +251,18 @@ def ctqw_propagate_taylor(h: Hamiltonian, psi: torch.Tensor, dtype: int, dt: flo
     _check(load().ctqw_propagate_taylor(h.handle, dtype, _ptr(psi), float(dt), int(K), int(n_steps),
                                         int(obs_every), _ptr(P_mean), _ptr(norm), _ptr(energy),
                                         int(flags), _ptr(workspace), ws_bytes, _stream(stream)))
+
+
+def ctqw_propagate_taylor_switching(h: Hamiltonian, psi: torch.Tensor, dtype: int, dt: float, K: int,
+                                    n_steps: int, obs_every: int, P_mean, norm, energy, seed: int,
+                                    p_switch: float, flags: int = 0,
+                                    workspace: Optional[torch.Tensor] = None, stream=None):
+    if workspace is None:
+        workspace = h.workspace(dtype, TAYLOR, FLAG_PLAIN, psi.device)
+    _check(load().ctqw_propagate_taylor_switching(
+        h.handle, dtype, _ptr(psi), float(dt), int(K), int(n_steps), int(obs_every), _ptr(P_mean),
+        _ptr(norm), _ptr(energy), int(flags), _ptr(workspace), workspace.numel(), int(seed),
+        float(p_switch), _stream(stream)))
 
 
 def ctqw_propagate_rk4(h: Hamiltonian, psi: torch.Tensor, dtype: int, dt: float, n_steps: int,
