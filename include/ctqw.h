@@ -253,6 +253,22 @@ int ctqw_propagate_taylor_switching(const ctqw_hamiltonian *h, int32_t dtype, vo
                                     uint64_t seed, double p_switch, void *stream);
 
 /*
+ * Exact propagation by diagonalisation (Algorithm 1, Eq. (evolPsi)), a
+ * validation path for small states: every realization's dense H (D = N^m
+ * <= 64) is diagonalised on the device by the cyclic Jacobi method, and
+ * psi(t) = W exp(-i E t) W^T psi(0) is formed at the sampled steps
+ * (t = step * dt) and at n_steps.  CTQW_C128 only.  psi_dev (in/out): the
+ * initial states in, the states at n_steps * dt out.  Outputs as
+ * ctqw_propagate_taylor.  sweeps_host (may be NULL): [R] Jacobi sweeps each
+ * realization took (at most 40); written when the stream reaches the end of
+ * the call.  Allocates its scratch stream-ordered.  Errors: EUNSUPPORTED
+ * for CTQW_C64 or N^m > 64, EINVAL as ctqw_propagate_taylor.
+ */
+int ctqw_propagate_exact(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
+                         int64_t n_steps, int32_t obs_every, double *P_mean_dev, double *norm_dev,
+                         double *energy_dev, int32_t *sweeps_host, void *stream);
+
+/*
  * Same as ctqw_propagate_taylor with the classical fourth-order Runge-Kutta
  * step of Sec. 2.2 (Algorithm 2): K^(1) = -iH Psi, K^(2) = -iH(Psi + dt/2 K^(1)),
  * K^(3) = -iH(Psi + dt/2 K^(2)), K^(4) = -iH(Psi + dt K^(3)),

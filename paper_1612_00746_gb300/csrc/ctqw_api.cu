@@ -693,6 +693,53 @@ int ctqw_propagate_taylor_switching(const ctqw_hamiltonian *h, int32_t dtype, vo
                               energy_dev, workspace_dev, s, sw);
 }
 
+int ctqw_propagate_exact(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
+                         int64_t n_steps, int32_t obs_every, double *P_mean_dev, double *norm_dev,
+                         double *energy_dev, int32_t *sweeps_host, void *stream) {
+    CTQW_TRY(check_common(h, dtype, psi_dev, dt, n_steps, obs_every));
+    if (dtype != CTQW_C128) { ctqw_set_error("exact propagation is FP64 (CTQW_C128)"); return CTQW_EUNSUPPORTED; }
+    int64_t D = 1;
+    for (int j = 0; j < h->m; ++j) D *= h->Nmax;
+    if (D > exact_max_dim()) {
+        ctqw_set_error("exact propagation: N^m = %lld above %d", (long long)D, exact_max_dim());
+        return CTQW_EUNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t Dp = D + (D & 1);
+    const size_t sb = (size_t)h->total_amp * sizeof(double2);
+    double *evals = nullptr, *evecs = nullptr;
+    void *psi0 = nullptr;
+    int *sweeps = nullptr;
+    CTQW_CUDA_TRY(cudaMallocAsync((void **)&evals, sizeof(double) * (size_t)(h->R * Dp), s));
+    CTQW_CUDA_TRY(cudaMallocAsync((void **)&evecs, sizeof(double) * (size_t)(h->R * Dp * Dp), s));
+    CTQW_CUDA_TRY(cudaMallocAsync(&psi0, sb, s));
+    CTQW_CUDA_TRY(cudaMallocAsync((void **)&sweeps, sizeof(int) * (size_t)h->R, s));
+    int st = zero_outputs(h, n_samples(n_steps, obs_every), P_mean_dev, norm_dev, energy_dev, s);
+    if (st == CTQW_OK && cudaMemcpyAsync(psi0, psi_dev, sb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        st = ctqw_cuda_fail(cudaGetLastError(), "copy of psi0");
+    if (st == CTQW_OK) st = launch_exact_eigen(h, evals, evecs, sweeps, s);
+    int64_t obs = 0;
+    for (int64_t step = 0; st == CTQW_OK && step <= n_steps; ++step) {
+        const bool sample = obs_every > 0 && step % obs_every == 0;
+        if (!sample && step != n_steps) continue;
+        st = launch_exact_propagate(h, evals, evecs, psi0, psi_dev, dt * (double)step, s);
+        if (st == CTQW_OK && sample) {
+            st = launch_observables(h, dtype, psi_dev, P_mean_dev ? P_mean_dev + obs * h->p_width : nullptr,
+                                    nullptr, norm_dev ? norm_dev + obs * h->R : nullptr,
+                                    energy_dev ? energy_dev + obs * h->R : nullptr, s);
+            ++obs;
+        }
+    }
+    if (st == CTQW_OK && sweeps_host &&
+        cudaMemcpyAsync(sweeps_host, sweeps, sizeof(int) * (size_t)h->R, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        st = ctqw_cuda_fail(cudaGetLastError(), "copy of the sweep counts");
+    cudaFreeAsync(evals, s);
+    cudaFreeAsync(evecs, s);
+    cudaFreeAsync(psi0, s);
+    cudaFreeAsync(sweeps, s);
+    return st;
+}
+
 int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
                        int64_t n_steps, int32_t obs_every, double *P_mean_dev, double *norm_dev,
                        double *energy_dev, uint32_t flags, void *workspace_dev,

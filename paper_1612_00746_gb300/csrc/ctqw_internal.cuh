@@ -150,6 +150,16 @@ int launch_observables(const ctqw_hamiltonian *h, int dtype, const void *psi, do
 int launch_one_body_density(const ctqw_hamiltonian *h, int dtype, const void *psi, double *rho,
                             cudaStream_t s);
 
+// Exact propagation by diagonalisation (FP64, D = N^m <= exact_max_dim()):
+// eigenpairs of every realization (evals [R][Dp], evecs [R][Dp][Dp] with Dp
+// = D rounded up to even, sweeps [R] Jacobi sweeps taken), then
+// psi = W exp(-i E t) W^T psi0.
+int exact_max_dim();
+int launch_exact_eigen(const ctqw_hamiltonian *h, double *evals, double *evecs, int *sweeps,
+                       cudaStream_t s);
+int launch_exact_propagate(const ctqw_hamiltonian *h, const double *evals, const double *evecs,
+                           const void *psi0, void *psi, double t, cudaStream_t s);
+
 // Adjoint pieces: out = H in; out = H in + c lam (first: c lam);
 // 2 Re <mu, dH phi> into per-realization gradients; loss and lambda_T.
 int launch_apply_h(const ctqw_hamiltonian *h, int dtype, const void *in, void *out, cudaStream_t s);

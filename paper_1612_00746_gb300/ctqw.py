@@ -49,6 +49,7 @@ EXPORTED = (
     "ctqw_propagate_rk4", "ctqw_ensemble_observables", "ctqw_check_status", "ctqw_last_error",
     "ctqw_version", "ctqw_adjoint_workspace_size", "ctqw_adjoint_grad", "ctqw_taylor_order",
     "ctqw_autotune_order", "ctqw_one_body_density", "ctqw_propagate_taylor_switching",
+    "ctqw_propagate_exact",
 )
 
 
@@ -103,6 +104,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "ctqw_adjoint_grad": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, vp, vp, vp, sz, vp],
         "ctqw_taylor_order": [dbl, i64, dbl, i32, i32, ctypes.POINTER(i32), pd],
         "ctqw_one_body_density": [vp, i32, vp, vp, vp],
+        "ctqw_propagate_exact": [vp, i32, vp, dbl, i64, i32, vp, vp, vp, ctypes.POINTER(i32), vp],
         "ctqw_propagate_taylor_switching": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, u32, vp, sz,
                                             ctypes.c_uint64, dbl, vp],
         "ctqw_autotune_order": [vp, i32, dbl, i64, i32, i32, ctypes.POINTER(i32)],
@@ -263,6 +265,19 @@ def ctqw_propagate_taylor_switching(h: Hamiltonian, psi: torch.Tensor, dtype: in
         h.handle, dtype, _ptr(psi), float(dt), int(K), int(n_steps), int(obs_every), _ptr(P_mean),
         _ptr(norm), _ptr(energy), int(flags), _ptr(workspace), workspace.numel(), int(seed),
         float(p_switch), _stream(stream)))
+
+
+def ctqw_propagate_exact(h: Hamiltonian, psi: torch.Tensor, dt: float, n_steps: int, obs_every: int = 0,
+                         P_mean=None, norm=None, energy=None, stream=None) -> np.ndarray:
+    """Exact propagation by diagonalisation (FP64, N^m <= 64); returns the
+    Jacobi sweeps of every realization (host, after a synchronisation)."""
+    sweeps = np.zeros(h.R, dtype=np.int32)
+    _check(load().ctqw_propagate_exact(h.handle, C128, _ptr(psi), float(dt), int(n_steps), int(obs_every),
+                                       _ptr(P_mean), _ptr(norm), _ptr(energy),
+                                       sweeps.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                       _stream(stream)))
+    torch.cuda.synchronize()
+    return sweeps
 
 
 def ctqw_propagate_rk4(h: Hamiltonian, psi: torch.Tensor, dtype: int, dt: float, n_steps: int,
