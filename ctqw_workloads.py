@@ -174,3 +174,145 @@ def get(name: str) -> Workload:
     if name in WORKLOADS:
         return WORKLOADS[name]
     return WORKLOADS_SMALL[name]
+
+
+# --------------------------------------------------------------------------
+# q-dimensional lattices and general graphs (Sec. 2: a q-dimensional lattice
+# of N = prod_i N_i nodes, or a general graph where each node has its own
+# number of links).  A topology is an undirected link list shared by all
+# realizations; the noise is one draw per node and one per link.
+# --------------------------------------------------------------------------
+
+
+def lattice_edges(shape: Sequence[int], periodic: bool) -> Tuple[np.ndarray, np.ndarray]:
+    """Nearest-neighbour links of a q-dimensional lattice of extents ``shape``.
+
+    Nodes are numbered row-major (the last direction fastest).  Along each
+    direction i, node c is linked to c + e_i; with ``periodic`` the last node
+    of a line is linked back to the first, so a direction of extent 2 gets
+    two links between the same pair of nodes and extent 1 none.  Returns
+    (u, v) int32 arrays; links are ordered by direction, then by node.
+    """
+    shape = tuple(int(n) for n in shape)
+    n_nodes = int(np.prod(shape)) if shape else 0
+    idx = np.arange(n_nodes).reshape(shape)
+    us, vs = [], []
+    for axis, n in enumerate(shape):
+        if n < 2:
+            continue
+        nxt = np.roll(idx, -1, axis=axis)
+        src = idx
+        if not periodic:
+            sl = [slice(None)] * len(shape)
+            sl[axis] = slice(0, n - 1)
+            src, nxt = idx[tuple(sl)], nxt[tuple(sl)]
+        us.append(src.reshape(-1))
+        vs.append(nxt.reshape(-1))
+    if not us:
+        return np.zeros(0, np.int32), np.zeros(0, np.int32)
+    return np.concatenate(us).astype(np.int32), np.concatenate(vs).astype(np.int32)
+
+
+def ring_with_chords(n_nodes: int, n_chords: int, seed: int) -> Tuple[np.ndarray, np.ndarray]:
+    """A general graph: a ring of ``n_nodes`` plus ``n_chords`` random links.
+
+    Chord endpoints are uniform over distinct node pairs; a chord may repeat
+    a link (the two then add), so node degrees vary from 2 upwards.
+    """
+    u = np.arange(n_nodes, dtype=np.int64)
+    v = (u + 1) % n_nodes
+    g = np.random.Generator(np.random.Philox(np.random.SeedSequence([int(seed), 0x6EA])))
+    a = g.integers(0, n_nodes, size=n_chords)
+    b = (a + 1 + g.integers(0, n_nodes - 1, size=n_chords)) % n_nodes
+    return (np.concatenate([u, a]).astype(np.int32), np.concatenate([v, b]).astype(np.int32))
+
+
+@dataclass(frozen=True)
+class GraphWorkload:
+    """Ensemble propagation on a q-dimensional lattice or a general graph."""
+
+    name: str
+    m: int                      # particles (2 or 3)
+    statistics: int
+    shape: Tuple[int, ...]      # lattice extents N_1..N_q; () for the ring-with-chords graph
+    periodic: bool              # lattices: periodic in every direction
+    R: int
+    J0: float
+    U: float
+    eps_halfwidth: float
+    J_halfwidth: float
+    sites: Tuple[int, ...]      # initial occupied nodes (len m)
+    dt: float
+    K: int
+    n_steps: int
+    obs_every: int
+    dtype: int
+    seed: int = 0
+    ring_nodes: int = 0         # general graph: nodes of the ring
+    chords: int = 0             # general graph: random chords on top of it
+
+    def n_nodes(self) -> int:
+        return int(np.prod(self.shape)) if self.shape else self.ring_nodes
+
+    def edges(self) -> Tuple[np.ndarray, np.ndarray]:
+        if self.shape:
+            return lattice_edges(self.shape, self.periodic)
+        return ring_with_chords(self.ring_nodes, self.chords, self.seed)
+
+    def site_updates(self) -> float:
+        """Amplitude-term updates of the whole job: R * N^m * K * steps."""
+        return float(self.R) * float(self.n_nodes()) ** self.m * self.K * self.n_steps
+
+    def with_(self, **kw) -> "GraphWorkload":
+        return replace(self, **kw)
+
+
+def graph_draws(w: GraphWorkload, realizations: Optional[Sequence[int]] = None):
+    """Uniform draws (u_eps [n][N], u_J [n][E]) of the listed realizations.
+
+    Realization r draws from Philox keyed by SeedSequence([seed, r, 0x62]).
+    """
+    if realizations is None:
+        realizations = range(w.R)
+    realizations = list(realizations)
+    n, e = w.n_nodes(), len(w.edges()[0])
+    ue = np.zeros((len(realizations), n))
+    uj = np.zeros((len(realizations), e))
+    for k, r in enumerate(realizations):
+        g = np.random.Generator(np.random.Philox(np.random.SeedSequence([int(w.seed), int(r), 0x62])))
+        ue[k] = g.random(n)
+        uj[k] = g.random(e)
+    return ue, uj
+
+
+GRAPH_WORKLOADS = {
+    # Two bosons on a 15 x 15 periodic square lattice (q = 2, m = 2,
+    # N_1 N_2 = 225: the size Sec. 3 names as the memory limit of its GPUs),
+    # noisy energies and hoppings, 1000 realizations, 1500 steps.
+    "lattice2d_15x15_m2": GraphWorkload(
+        name="lattice2d_15x15_m2", m=2, statistics=BOSONS, shape=(15, 15), periodic=True, R=1000,
+        J0=1.0, U=2.0, eps_halfwidth=1.0, J_halfwidth=0.25, sites=(112, 113), dt=0.02, K=16,
+        n_steps=1500, obs_every=10, dtype=C64, seed=0),
+}
+
+GRAPH_WORKLOADS_SMALL = {
+    "lattice2d_small": GRAPH_WORKLOADS["lattice2d_15x15_m2"].with_(
+        name="lattice2d_small", shape=(5, 4), R=4, sites=(9, 10), n_steps=120),
+    "lattice2d_open_small": GRAPH_WORKLOADS["lattice2d_15x15_m2"].with_(
+        name="lattice2d_open_small", shape=(6, 5), periodic=False, statistics=FERMIONS, R=3,
+        sites=(14, 15), n_steps=100),
+    "lattice3d_small": GRAPH_WORKLOADS["lattice2d_15x15_m2"].with_(
+        name="lattice3d_small", shape=(3, 3, 4), statistics=DISTINGUISHABLE, R=3,
+        sites=(17, 18), n_steps=80),
+    "lattice2d_m3_small": GRAPH_WORKLOADS["lattice2d_15x15_m2"].with_(
+        name="lattice2d_m3_small", m=3, shape=(4, 3), R=2, sites=(4, 5, 6), n_steps=60),
+    "graph_small": GRAPH_WORKLOADS["lattice2d_15x15_m2"].with_(
+        name="graph_small", shape=(), ring_nodes=40, chords=30, R=4, sites=(0, 20),
+        statistics=DISTINGUISHABLE, n_steps=100),
+}
+
+
+def get_graph(name: str) -> GraphWorkload:
+    if name in GRAPH_WORKLOADS:
+        return GRAPH_WORKLOADS[name]
+    return GRAPH_WORKLOADS_SMALL[name]

@@ -14,6 +14,9 @@ Written from the paper's Sec. 2 (arXiv:1612.00746), in its order and notation:
 * Algorithm 2: fourth-order Runge-Kutta step.
 * Sec. 2.3 / Algorithm 3: truncated Taylor series of the evolution operator,
   Phi^(0) = Psi, Phi^(j) = -(i dt / j) H Phi^(j-1), Psi(t+dt) = sum_j Phi^(j).
+* Sec. 2, q-dimensional lattices and general graphs: the one-particle matrix
+  of a link list (graph_single_particle_hamiltonian), the same Kronecker sum
+  over particles, noise per node and per link (graph_parameters).
 * Sec. 2, density matrix <rho> = (1/R) sum_i |Psi_i><Psi_i|: its diagonal
   gives the site occupations P(x) averaged over realizations; its one-body
   reduction (partial trace over all particles but one) is one_body_density.
@@ -38,6 +41,7 @@ __all__ = [
     "taylor_truncation_bound", "hamiltonian_norm_bound", "loss_and_adjoint_gradient",
     "occupation_weights", "noninteracting_evolution", "one_body_density",
     "philox4x64", "unit_double", "switch_parameters", "propagate_switching",
+    "graph_parameters", "graph_single_particle_hamiltonian", "graph_ensemble_run",
 ]
 
 
@@ -82,6 +86,38 @@ def single_particle_hamiltonian(eps, J, periodic):
         i, k = b, (b + 1) % N
         H1[i, k] += -J[b]
         H1[k, i] += -J[b]
+    return H1
+
+
+def graph_parameters(u_eps, u_J, eps_halfwidth, J_mean, J_halfwidth, round_to_f32=True):
+    """On-site energies of the nodes and hoppings of the links of a graph.
+
+    Sec. 2 allows a q-dimensional lattice or a general graph; the disorder
+    law is that of lattice_parameters (Eq. (Hij), c + xi with xi drawn as
+    w(2u - 1)), one draw per node and one per link, zero mean on the nodes.
+    """
+    u_eps = np.asarray(u_eps, dtype=np.float64)
+    u_J = np.asarray(u_J, dtype=np.float64)
+    eps = 0.0 + eps_halfwidth * (2.0 * u_eps - 1.0)
+    J = J_mean + J_halfwidth * (2.0 * u_J - 1.0)
+    if round_to_f32:
+        eps, J = round_f32(eps), round_f32(J)
+    return np.array(eps, dtype=np.float64), np.array(J, dtype=np.float64)
+
+
+def graph_single_particle_hamiltonian(n_nodes, edge_u, edge_v, eps, J):
+    """Dense one-particle matrix of a graph: eps on the diagonal, -J_e on both
+    entries of link e = (edge_u[e], edge_v[e]) (Sec. 2: tunnelling along the
+    links of the topology, the same topology for every realization).  Entries
+    add, so repeated links sum their hoppings.
+    """
+    H1 = np.diag(np.asarray(eps, dtype=np.float64)[:n_nodes]).astype(np.float64)
+    for e in range(len(edge_u)):
+        i, k = int(edge_u[e]), int(edge_v[e])
+        if i == k:
+            raise ValueError("a link must join two different nodes")
+        H1[i, k] += -J[e]
+        H1[k, i] += -J[e]
     return H1
 
 
@@ -533,3 +569,37 @@ def _dH_J(N, m, b):
     d1[i, k] -= 1.0
     d1[k, i] -= 1.0
     return many_particle_hamiltonian(d1, m, 0.0)
+
+
+# ---------------------------------------------------------------- graphs
+def graph_ensemble_run(w, realizations=None, K=None, n_steps=None, obs_every=None):
+    """Algorithm 3 on every listed realization of a graph workload.
+
+    The many-particle matrix is many_particle_hamiltonian of the graph's
+    one-particle matrix (the Kronecker sum over particles of Sec. 2, with
+    the lattice replaced by the graph).  Returns the realization-averaged P
+    [n_obs][N], norms and energies [n_obs][n] and the final states.
+    """
+    if realizations is None:
+        realizations = range(w.R)
+    realizations = list(realizations)
+    K = w.K if K is None else K
+    n_steps = w.n_steps if n_steps is None else n_steps
+    obs_every = w.obs_every if obs_every is None else obs_every
+    from ctqw_workloads import graph_draws
+    ue, uj = graph_draws(w, realizations)
+    eu, ev = w.edges()
+    N = w.n_nodes()
+    P, norms, energies, finals = None, [], [], []
+    for k in range(len(realizations)):
+        eps, J = graph_parameters(ue[k], uj[k], w.eps_halfwidth, w.J0, w.J_halfwidth)
+        H = many_particle_hamiltonian(graph_single_particle_hamiltonian(N, eu, ev, eps, J), w.m, w.U)
+        psi0 = initial_state(N, w.m, w.sites, w.statistics)
+        out = propagate(H, psi0, N, w.m, w.dt, n_steps, obs_every, "taylor", K)
+        P = out["P"] if P is None else P + out["P"]
+        norms.append(out["norm"])
+        energies.append(out["energy"])
+        finals.append(out["psi"])
+    n = max(len(realizations), 1)
+    return {"P": None if P is None else P / n, "norm": np.array(norms).T,
+            "energy": np.array(energies).T, "psi": finals}
