@@ -679,6 +679,100 @@ def run_rho1(args):
     return 0
 
 
+def run_lattice(args):
+    """Time ctqw_graph_propagate_taylor on a q-dimensional lattice / graph
+    workload (default: two bosons on the 15 x 15 torus, 1000 realizations).
+
+    Per-term kernels stream the states through HBM: per site-update
+    ((K-1) 24 + 40) / K bytes in FP32 (Horner stages and the compensated
+    final stage), the neighbour reads served from L1/L2.
+    """
+    import torch
+
+    from paper_1612_00746_gb300 import ctqw
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ctqw.load()
+    w = cw.get_graph(args.lattice)
+    if args.realizations:
+        w = w.with_(R=args.realizations)
+    if args.n_steps:
+        w = w.with_(n_steps=args.n_steps)
+    if args.dtype:
+        w = w.with_(dtype=cw.C64 if args.dtype == "c64" else cw.C128)
+    g = ctqw.Graph.from_workload(w)
+    if args.chunk:
+        ctqw.ctqw_graph_set_chunk(g, args.chunk)
+    psi = g.new_state(w.dtype, dev)
+    ws = g.workspace(w.dtype, dev)
+    n_obs = g.n_obs(w.n_steps, w.obs_every)
+    P = torch.empty((n_obs, g.N), dtype=torch.float64, device=dev)
+    nr = torch.empty((n_obs, g.R), dtype=torch.float64, device=dev)
+    en = torch.empty((n_obs, g.R), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctqw.ctqw_graph_init_state(g, psi, w.sites, w.dtype)
+        ctqw.ctqw_graph_propagate_taylor(g, psi, w.dtype, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en,
+                                         workspace=ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(visible_gpu_id(0))
+    clocks.start()
+    total = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        ctqw.ctqw_graph_init_state(g, psi, w.sites, w.dtype)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctqw.ctqw_graph_propagate_taylor(g, psi, w.dtype, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en,
+                                         workspace=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ms = total / args.steps
+    units = w.site_updates()
+    value = units / (ms / 1000.0)
+    drift = float((nr[-1] - 1.0).abs().max().item()) if n_obs else None
+    peaks = measured_peaks()
+    if w.dtype == cw.C64:
+        bpu = ((w.K - 1) * 24.0 + 40.0) / w.K
+        gbs = units * bpu / (ms / 1000.0) / 1e9
+        peak = peaks.get("hbm_gbs")
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                "frac": gbs / peak if peak else None, "traffic": None,
+                "kernel": "graph_horner_stage_kernel + graph_horner_final_kernel",
+                "kernel_ms": ms, "bytes_per_site_update": bpu,
+                "peak_basis": "measured copy bandwidth" if peak else None,
+                "timing": "the whole propagate call (observables kernels included)"}
+    else:
+        flops = 8 * w.m + 4
+        ach = units * flops / (ms / 1000.0) / 1e12
+        peak = SM_COUNT * FP64_FMA_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": "graph_taylor_term_kernel<double>", "kernel_ms": ms,
+                "peak_basis": "152 SMs x 2 DFMA x 2 flop x 2070 MHz (FP64, derived)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "dtype": "c64" if w.dtype == cw.C64 else "c128", "data": "synthetic",
+        "config": {"workload": w.name, "shape": list(w.shape), "periodic": w.periodic, "m": w.m,
+                   "chunk": args.chunk or "auto (half of L2)",
+                   "N": w.n_nodes(), "links": int(len(w.edges()[0])), "R": w.R, "K": w.K,
+                   "n_steps": w.n_steps, "obs_every": w.obs_every,
+                   "l2": "states larger than L2" if g.total_amplitudes * 8 > 129e6 else "L2-resident"},
+        "roofline": roof, "norm_drift": drift, "clocks": clk,
+        "gpu_launches": int(args.steps * (w.n_steps * w.K + n_obs + 1)),
+    }
+    print(json.dumps(line), flush=True)
+    g.close()
+    return 0
+
+
 def run_exact(args):
     """Time ctqw_propagate_exact (batched Jacobi diagonalisation, FP64) on many
     small realizations: 2 particles, N = 8 (D = 64), 4096 realizations.
@@ -759,6 +853,10 @@ def main(argv=None):
     ap.add_argument("--graph", action="store_true", help="replay the propagate call from a CUDA graph")
     ap.add_argument("--switch", type=float, default=None,
                     help="propagate with switching noise: redraw probability per parameter and step")
+    ap.add_argument("--lattice", default=None,
+                    help="time a q-dimensional lattice / graph workload (e.g. lattice2d_15x15_m2)")
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="--lattice: realizations per pass (0: sized to L2)")
     ap.add_argument("--exact", action="store_true",
                     help="time ctqw_propagate_exact (batched Jacobi, 4096 x N=8 two-particle states)")
     ap.add_argument("--rho1", action="store_true",
@@ -777,6 +875,8 @@ def main(argv=None):
         return run_rho1(args)
     if args.exact:
         return run_exact(args)
+    if args.lattice:
+        return run_lattice(args)
     return run_ours(args)
 
 

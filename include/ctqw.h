@@ -378,6 +378,116 @@ int ctqw_adjoint_grad(const ctqw_hamiltonian *h, int32_t dtype, const void *psi0
  */
 int ctqw_check_status(const ctqw_hamiltonian *h, void *stream);
 
+/* ------------------------------------------------------------------------
+ * q-dimensional lattices and general graphs (Sec. 2: a q-dimensional lattice
+ * of N = prod_i N_i nodes, or a general graph where each node has its own
+ * number of links; the topology is known in advance and holds for every
+ * realization).  Conventions as above with the chain replaced by the graph:
+ *   H1 = sum_i eps_i |i><i| - sum_e J_e (|u_e><v_e| + |v_e><u_e|)
+ * over the links e = (u_e, v_e); repeated links add.  All realizations have
+ * the same N nodes and P rows have N entries.  State layout: realizations
+ * are the fastest index, amplitude s (x_m fastest, as above) of realization
+ * r at s R + r, so that the kernels read every neighbour as one coalesced
+ * row across realizations.  The topology is stored once as the CSR of the
+ * one-particle graph; the N^m x (mk + 1) many-particle topology of Sec. 2
+ * is regenerated inside the kernels.
+ * ------------------------------------------------------------------------ */
+typedef struct ctqw_graph ctqw_graph;   /* opaque, owned by the library */
+
+/*
+ * Graph and disorder description.  Draws u in [0, 1) are supplied per
+ * realization: u_eps_host [R][N] (one per node), u_J_host [R][E] (one per
+ * link), and
+ *   eps_{r,i} = eps_halfwidth * (2 u_eps - 1),   J_{r,e} = J0 + J_halfwidth * (2 u_J - 1),
+ * each rounded to the nearest float32 when round_to_f32 is nonzero.
+ */
+typedef struct {
+    int32_t n_particles;        /* m: 2 or 3                                         */
+    int32_t statistics;         /* CTQW_DISTINGUISHABLE / BOSONS / FERMIONS           */
+    int32_t n_nodes;            /* N >= 2, N^m <= 2^31 - 1                           */
+    int32_t n_edges;            /* E >= 0 links                                      */
+    const int32_t *edge_u;      /* host [E] first node of each link (0..N-1)         */
+    const int32_t *edge_v;      /* host [E] second node, != edge_u                   */
+    int32_t n_realizations;     /* 1 <= R <= 2097120, R N^m < 2^40                   */
+    int32_t round_to_f32;       /* nonzero: round disorder to float32 values          */
+    double J0;                  /* mean hopping                                      */
+    double U;                   /* on-site interaction per coinciding pair            */
+    double eps_halfwidth;       /* on-site disorder half width                        */
+    double J_halfwidth;         /* hopping disorder half width                        */
+    const double *u_eps_host;   /* host [R][N] uniform draws for eps                  */
+    const double *u_J_host;     /* host [R][E] uniform draws for J                    */
+} ctqw_graph_desc;
+
+/*
+ * Build the topology (CSR, on the host, then copied) and the parameters of
+ * every realization (on the device, on `stream`).  Errors: EINVAL for null
+ * pointers, sizes out of range, a link with a node out of range or with
+ * u_e == v_e; ENOMEM; ECUDA.
+ */
+int ctqw_graph_build(const ctqw_graph_desc *desc, void *stream, ctqw_graph **out);
+
+/* Free the handle and its device arrays (waits for the device first).  NULL is a no-op. */
+int ctqw_graph_destroy(ctqw_graph *g);
+
+/*
+ * Copy the built parameters back (synchronizes the device): eps_host [R][N],
+ * J_host [R][E] doubles, either may be NULL.
+ */
+int ctqw_graph_get_params(const ctqw_graph *g, double *eps_host, double *J_host);
+
+/* Amplitudes of all realizations, R N^m. */
+int ctqw_graph_state_size(const ctqw_graph *g, int64_t *amplitudes_total);
+
+/*
+ * Localised initial states as ctqw_init_state (in the graph layout):
+ * sites_host [R][m] nodes (host, int32).  EINVAL for a node out of range or
+ * coinciding fermions.
+ */
+int ctqw_graph_init_state(const ctqw_graph *g, const int32_t *sites_host, int32_t dtype,
+                          void *psi_dev, void *stream);
+
+/* Workspace bytes of ctqw_graph_propagate_taylor / _rk4: 3 states of `dtype`. */
+int ctqw_graph_workspace_size(const ctqw_graph *g, int32_t dtype, size_t *bytes);
+
+/*
+ * Advance every realization by n_steps order-K Taylor steps (Sec. 2.3,
+ * Algorithm 3), one launch per term over all realizations.  CTQW_C128 runs
+ * the terms in the order of Algorithm 3; CTQW_C64 the same polynomial in
+ * Horner form with the state update compensated (the carried rounding
+ * error lives in the third workspace state), as the chain's per-term path.
+ * Outputs as ctqw_propagate_taylor, with P_mean_dev [n_obs][N]:
+ * (1/R) sum_r P_r(x).  K in 1..30.  Errors: EINVAL for bad arguments or a
+ * short workspace, ECUDA.  Asynchronous.
+ */
+int ctqw_graph_propagate_taylor(const ctqw_graph *g, int32_t dtype, void *psi_dev, double dt,
+                                int32_t K, int64_t n_steps, int32_t obs_every, double *P_mean_dev,
+                                double *norm_dev, double *energy_dev, void *workspace_dev,
+                                size_t workspace_bytes, void *stream);
+
+/*
+ * Realizations per pass of ctqw_graph_propagate_taylor / _rk4 through their
+ * steps.  Each pass runs every step of the call over its realizations only,
+ * so that a small pass keeps its working states (psi, two iterates and the
+ * error word) in L2 between launches.  0 (the default) runs all
+ * realizations in one pass, which measured fastest on the 15 x 15 lattice;
+ * results do not depend on it.
+ */
+int ctqw_graph_set_chunk(ctqw_graph *g, int32_t realizations);
+
+/* Fourth-order Runge-Kutta on the graph (Algorithm 2); arguments as above without K. */
+int ctqw_graph_propagate_rk4(const ctqw_graph *g, int32_t dtype, void *psi_dev, double dt,
+                             int64_t n_steps, int32_t obs_every, double *P_mean_dev, double *norm_dev,
+                             double *energy_dev, void *workspace_dev, size_t workspace_bytes,
+                             void *stream);
+
+/*
+ * One sample of the observables of the current states: P_mean_dev [N],
+ * norm_dev [R], energy_dev [R] as in ctqw_graph_propagate_taylor.  Any may
+ * be NULL; outputs are overwritten.  Asynchronous.
+ */
+int ctqw_graph_observables(const ctqw_graph *g, int32_t dtype, const void *psi_dev,
+                           double *P_mean_dev, double *norm_dev, double *energy_dev, void *stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *ctqw_last_error(void);
 

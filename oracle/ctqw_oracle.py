@@ -572,8 +572,9 @@ def _dH_J(N, m, b):
 
 
 # ---------------------------------------------------------------- graphs
-def graph_ensemble_run(w, realizations=None, K=None, n_steps=None, obs_every=None):
-    """Algorithm 3 on every listed realization of a graph workload.
+def graph_ensemble_run(w, realizations=None, K=None, n_steps=None, obs_every=None, method="taylor"):
+    """Algorithm 3 (or Algorithm 2, method="rk4") on every listed realization
+    of a graph workload.
 
     The many-particle matrix is many_particle_hamiltonian of the graph's
     one-particle matrix (the Kronecker sum over particles of Sec. 2, with
@@ -595,7 +596,7 @@ def graph_ensemble_run(w, realizations=None, K=None, n_steps=None, obs_every=Non
         eps, J = graph_parameters(ue[k], uj[k], w.eps_halfwidth, w.J0, w.J_halfwidth)
         H = many_particle_hamiltonian(graph_single_particle_hamiltonian(N, eu, ev, eps, J), w.m, w.U)
         psi0 = initial_state(N, w.m, w.sites, w.statistics)
-        out = propagate(H, psi0, N, w.m, w.dt, n_steps, obs_every, "taylor", K)
+        out = propagate(H, psi0, N, w.m, w.dt, n_steps, obs_every, method, K)
         P = out["P"] if P is None else P + out["P"]
         norms.append(out["norm"])
         energies.append(out["energy"])

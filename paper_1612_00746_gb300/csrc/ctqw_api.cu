@@ -58,12 +58,6 @@ int check_common(const ctqw_hamiltonian *h, int dtype, const void *psi, double d
     return CTQW_OK;
 }
 
-#define CTQW_TRY(expr)              \
-    do {                            \
-        int _st = (expr);           \
-        if (_st != CTQW_OK) return _st; \
-    } while (0)
-
 // out = T in with T the order-K Taylor polynomial of exp(-i H dt)
 // (Algorithm 3 with one launch per term); phiA, phiB scratch states.  In
 // FP32 the same polynomial in Horner form, which does not drop the terms a

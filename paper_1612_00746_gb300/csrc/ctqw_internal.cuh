@@ -81,6 +81,13 @@ int ctqw_cuda_fail(cudaError_t e, const char *what);
         if (_e != cudaSuccess) return ctqw_cuda_fail(_e, #call); \
     } while (0)
 
+// Propagate a nonzero status of a library call.
+#define CTQW_TRY(expr)                  \
+    do {                                \
+        int _st = (expr);               \
+        if (_st != CTQW_OK) return _st; \
+    } while (0)
+
 // One launch per size group (per 65535 of its realizations): grid (rows,
 // chunks of x_M, realizations).
 template <typename F>

@@ -1,0 +1,463 @@
+// Kernels of the graph path (Sec. 2: a q-dimensional lattice of N nodes, or
+// a general graph where each node has its own number of links; Algorithms 2
+// and 3 then read the neighbours of every row from a topology shared by all
+// realizations).
+//
+// H = sum_j H1 acting on particle j + U * #coinciding pairs, with
+// H1 = diag(eps) - sum_links J_e (|u_e><v_e| + h.c.).  The amplitude at flat
+// index s (coordinates x_1..x_m, x_m fastest, strides S_j = N^(m-1-j)) gets
+//   (H a)(s) = (sum_j eps[x_j] + U pairs) a(s) - sum_j sum_{k in row x_j} w_k a(s + (col_k - x_j) S_j),
+// the CSR row of node x_j giving the neighbours col_k and their hoppings w_k.
+// Realizations are the fastest index of every array (psi[s][r], eps[i][r],
+// w[k][r]): threadIdx.x walks realizations and threadIdx.y amplitudes, so
+// the CSR lookups of a warp are uniform (broadcast loads) and each neighbour
+// read is one coalesced row.  The first four entries of the rows of all m
+// coordinates are gathered at once (4m neighbour loads in flight per
+// thread), entries past a row's end reading the own amplitude with weight 0.
+#include <algorithm>
+
+#include "graph_internal.cuh"
+#include "stencil.cuh"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int M>
+__device__ __forceinline__ void graph_coords(int s, int N, int (&x)[M], int (&S)[M]) {
+    int stride = 1;
+#pragma unroll
+    for (int j = M - 1; j >= 0; --j) {
+        const int q = s / N;
+        x[j] = s - q * N;
+        s = q;
+        S[j] = stride;
+        stride *= N;
+    }
+}
+
+// Entries k0 + u (u < 4, k0 + u < k1) of one CSR row: weights and
+// neighbour amplitudes.  Past the row end the own amplitude is read with
+// weight 0, so no load depends on a branch.
+template <typename T, int M>
+__device__ __forceinline__ void graph_gather4(const cplx_t<T> *__restrict__ a, int64_t R, int s, int r, int xj,
+                                              int Sj, int k0, int k1, const int32_t *__restrict__ col,
+                                              const T *__restrict__ w, T (&t)[4], cplx_t<T> (&n)[4]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const bool ok = k0 + u < k1;
+        const int c = ok ? col[k0 + u] : xj;
+        t[u] = ok ? w[(int64_t)(k0 + u) * R + r] : T(0);
+        n[u] = a[(int64_t)(s + (c - xj) * Sj) * R + r];
+    }
+}
+
+// (H a)(s) of realization r; R is the realization stride of every array.
+// The first four entries of every coordinate's row are gathered together
+// (all their loads in flight at once); longer rows continue four at a time.
+template <typename T, int M>
+__device__ __forceinline__ cplx_t<T> graph_apply_h(const cplx_t<T> *__restrict__ a, int64_t R, int s, int r,
+                                                    const int (&x)[M], const int (&S)[M],
+                                                    const int32_t *__restrict__ row_ptr,
+                                                    const int32_t *__restrict__ col,
+                                                    const T *__restrict__ w, const T *__restrict__ eps,
+                                                    T U) {
+    int k0[M], k1[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        k0[j] = row_ptr[x[j]];
+        k1[j] = row_ptr[x[j] + 1];
+    }
+    T v = T(0);
+    int pairs = 0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        v += eps[(int64_t)x[j] * R + r];
+#pragma unroll
+        for (int l = j + 1; l < M; ++l) pairs += (x[j] == x[l]);
+    }
+    v += U * T(pairs);
+    T t[M][4];
+    cplx_t<T> n[M][4];
+#pragma unroll
+    for (int j = 0; j < M; ++j) graph_gather4<T, M>(a, R, s, r, x[j], S[j], k0[j], k1[j], col, w, t[j], n[j]);
+    const cplx_t<T> c = a[(int64_t)s * R + r];
+    T yr = v * c.x, yi = v * c.y;
+#pragma unroll
+    for (int j = 0; j < M; ++j)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            yr -= t[j][u] * n[j][u].x;
+            yi -= t[j][u] * n[j][u].y;
+        }
+#pragma unroll
+    for (int j = 0; j < M; ++j)
+        for (int k = k0[j] + 4; k < k1[j]; k += 4) {
+            T tt[4];
+            cplx_t<T> nn[4];
+            graph_gather4<T, M>(a, R, s, r, x[j], S[j], k, k1[j], col, w, tt, nn);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                yr -= tt[u] * nn[u].x;
+                yi -= tt[u] * nn[u].y;
+            }
+        }
+    return mk<T>(yr, yi);
+}
+
+// (amplitude, realization) of this thread, false past the ends.
+__device__ __forceinline__ bool graph_site(const GraphView &g, int &s, int &r) {
+    s = blockIdx.x * blockDim.y + threadIdx.y;
+    r = g.r_begin + blockIdx.y * blockDim.x + threadIdx.x;
+    return s < g.D && r < g.r_end;
+}
+
+__device__ __forceinline__ double graph_param(double mean, double hw, double u, int round_f32) {
+    double v = __dadd_rn(mean, __dmul_rn(hw, __dadd_rn(__dmul_rn(2.0, u), -1.0)));
+    if (round_f32) v = (double)__double2float_rn(v);
+    return v;
+}
+
+__global__ void graph_build_params_kernel(GraphView g, int E, const int32_t *__restrict__ link,
+                                          const double *__restrict__ u_eps,
+                                          const double *__restrict__ u_J, double eps_hw, double J_hw,
+                                          double J0, int round_f32, float *eps32, double *eps64,
+                                          float *w32, double *w64, double *J64) {
+    const int64_t R = g.R;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t t = t0; t < (int64_t)g.N * R; t += stride) {   // eps[i][r] from u_eps[r][i]
+        const int64_t i = t / R, r = t - i * R;
+        const double e = graph_param(0.0, eps_hw, u_eps[r * g.N + i], round_f32);
+        eps64[t] = e;
+        eps32[t] = (float)e;
+    }
+    for (int64_t t = t0; t < (int64_t)E * R; t += stride)      // J[r][e] as drawn
+        J64[t] = graph_param(J0, J_hw, u_J[t], round_f32);
+    for (int64_t t = t0; t < (int64_t)g.nnz * R; t += stride) { // w[k][r] = J[r][link[k]]
+        const int64_t k = t / R, r = t - k * R;
+        const double j = graph_param(J0, J_hw, u_J[r * E + link[k]], round_f32);
+        w64[t] = j;
+        w32[t] = (float)j;
+    }
+}
+
+// Localised initial state of realization r (sum over permutations of the
+// occupied nodes, signed for fermions, normalised); psi zeroed beforehand.
+template <typename T>
+__global__ void graph_init_state_kernel(GraphView g, const int32_t *__restrict__ sites, int stats,
+                                        cplx_t<T> *psi) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= g.R) return;
+    const int m = g.m, N = g.N;
+    const int perms2[2][2] = {{0, 1}, {1, 0}};
+    const int sign2[2] = {1, -1};
+    const int perms3[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    const int sign3[6] = {1, -1, -1, 1, 1, -1};
+    const int nperm = (stats == 0) ? 1 : (m == 2 ? 2 : 6);
+    int64_t idx[6];
+    double amp[6];
+    int n = 0;
+    for (int p = 0; p < nperm; ++p) {
+        int64_t f = 0;
+        for (int j = 0; j < m; ++j) f = f * N + sites[r * m + (m == 2 ? perms2[p][j] : perms3[p][j])];
+        const double sg = (stats == 2) ? (double)(m == 2 ? sign2[p] : sign3[p]) : 1.0;
+        int k = 0;
+        while (k < n && idx[k] != f) ++k;
+        if (k == n) {
+            idx[n] = f;
+            amp[n] = 0.0;
+            ++n;
+        }
+        amp[k] += sg;
+    }
+    double nrm = 0.0;
+    for (int k = 0; k < n; ++k) nrm += amp[k] * amp[k];
+    nrm = sqrt(nrm);
+    for (int k = 0; k < n; ++k) psi[idx[k] * g.R + r] = mk<T>((T)(amp[k] / nrm), T(0));
+}
+
+template <int M>
+__global__ void __launch_bounds__(kThreads) graph_horner_stage_kernel(GraphView g, const float *__restrict__ eps,
+                                                                      const float *__restrict__ w,
+                                                                      const float2 *__restrict__ in,
+                                                                      const float2 *__restrict__ psi,
+                                                                      float2 *__restrict__ out, float coef) {
+    int s, r;
+    if (!graph_site(g, s, r)) return;
+    int x[M], S[M];
+    graph_coords<M>(s, g.N, x, S);
+    const float2 y = graph_apply_h<float, M>(in, g.R, s, r, x, S, g.row_ptr, g.col, w, eps, (float)g.U);
+    const int64_t i = (int64_t)s * g.R + r;
+    const float2 q = psi[i];
+    out[i] = make_float2(fmaf(coef, y.y, q.x), fmaf(-coef, y.x, q.y));   // q + coef (-i) y
+}
+
+template <int M>
+__global__ void __launch_bounds__(kThreads) graph_horner_final_kernel(GraphView g, const float *__restrict__ eps,
+                                                                      const float *__restrict__ w,
+                                                                      const float2 *__restrict__ w2,
+                                                                      float2 *__restrict__ psi,
+                                                                      float2 *__restrict__ lo, float dt) {
+    int s, r;
+    if (!graph_site(g, s, r)) return;
+    int x[M], S[M];
+    graph_coords<M>(s, g.N, x, S);
+    // TwoSum then FastTwoSum per component: the state's rounding error is
+    // carried in lo from step to step
+    auto add = [](float &hi, float &lw, float v) {
+        const float t = __fadd_rn(hi, v);
+        const float bb = __fsub_rn(t, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(v, bb));
+        const float e = __fadd_rn(err, lw);
+        const float h2 = __fadd_rn(t, e);
+        lw = __fsub_rn(e, __fsub_rn(h2, t));
+        hi = h2;
+    };
+    const float2 y = graph_apply_h<float, M>(w2, g.R, s, r, x, S, g.row_ptr, g.col, w, eps, (float)g.U);
+    const int64_t i = (int64_t)s * g.R + r;
+    float2 h = psi[i], l = lo[i];
+    add(h.x, l.x, dt * y.y);    // -i dt H w2
+    add(h.y, l.y, -dt * y.x);
+    psi[i] = h;
+    lo[i] = l;
+}
+
+template <typename T, int M>
+__global__ void __launch_bounds__(kThreads) graph_taylor_term_kernel(GraphView g, const T *__restrict__ eps,
+                                                                     const T *__restrict__ w,
+                                                                     const cplx_t<T> *__restrict__ in,
+                                                                     cplx_t<T> *__restrict__ out,
+                                                                     const cplx_t<T> *__restrict__ psi,
+                                                                     cplx_t<T> *__restrict__ acc, T coef,
+                                                                     int first) {
+    int s, r;
+    if (!graph_site(g, s, r)) return;
+    int x[M], S[M];
+    graph_coords<M>(s, g.N, x, S);
+    const cplx_t<T> y = graph_apply_h<T, M>(in, g.R, s, r, x, S, g.row_ptr, g.col, w, eps, (T)g.U);
+    const int64_t i = (int64_t)s * g.R + r;
+    const cplx_t<T> phi = mk<T>(coef * y.y, -coef * y.x);   // -(i coef) y
+    out[i] = phi;
+    const cplx_t<T> a = first ? psi[i] : acc[i];
+    acc[i] = mk<T>(a.x + phi.x, a.y + phi.y);
+}
+
+template <typename T, int M>
+__global__ void __launch_bounds__(kThreads) graph_rk4_stage_kernel(GraphView g, const T *__restrict__ eps,
+                                                                   const T *__restrict__ w,
+                                                                   const cplx_t<T> *__restrict__ in,
+                                                                   cplx_t<T> *__restrict__ next,
+                                                                   const cplx_t<T> *__restrict__ psi,
+                                                                   cplx_t<T> *__restrict__ acc, T a, T b,
+                                                                   int first) {
+    int s, r;
+    if (!graph_site(g, s, r)) return;
+    int x[M], S[M];
+    graph_coords<M>(s, g.N, x, S);
+    const cplx_t<T> y = graph_apply_h<T, M>(in, g.R, s, r, x, S, g.row_ptr, g.col, w, eps, (T)g.U);
+    const int64_t i = (int64_t)s * g.R + r;
+    const cplx_t<T> k = mk<T>(y.y, -y.x);   // -i H in
+    const cplx_t<T> q = psi[i];
+    if (next) next[i] = mk<T>(q.x + a * k.x, q.y + a * k.y);
+    const cplx_t<T> c = first ? q : acc[i];
+    acc[i] = mk<T>(c.x + b * k.x, c.y + b * k.y);
+}
+
+// Observables of one sample.  Block (32 realizations) x (8 warps) owns
+// kRows rows (fixed x_1..x_{m-1}) of the state; warp y walks the columns
+// x_m = y, y + 8, ...  Column sums of P reduce over the lanes (the
+// realizations) and go out with one atomic per column and block; row sums,
+// norms and energies reduce over the warps in shared memory.  All FP64.
+constexpr int kRows = 8;
+constexpr int kObsWarps = 8;
+
+template <typename T, int M>
+__global__ void __launch_bounds__(32 * kObsWarps) graph_observables_kernel(GraphView g, const T *__restrict__ eps,
+                                                                         const T *__restrict__ w,
+                                                                         const cplx_t<T> *__restrict__ psi,
+                                                                         double *P, double *norm, double *energy) {
+    const int N = g.N;
+    const int n_rows = g.D / N;
+    const int row0 = blockIdx.x * kRows;
+    const int lane = threadIdx.x, wy = threadIdx.y;
+    const int r = g.r_begin + blockIdx.y * 32 + lane;
+    const bool valid = r < g.r_end;
+    const int rr = valid ? r : g.r_begin;   // a valid realization for the loads of idle lanes
+    const double scale = 1.0 / ((double)g.R * M);
+    double rowpart[kRows];
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) rowpart[q] = 0.0;
+    double nrm = 0.0, en = 0.0;
+    for (int c = wy; c < N; c += kObsWarps) {
+        double colacc = 0.0;
+#pragma unroll
+        for (int q = 0; q < kRows; ++q) {
+            const int row = row0 + q;
+            if (row < n_rows) {
+                const int s = row * N + c;
+                const cplx_t<T> v = psi[(int64_t)s * g.R + rr];
+                double p = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+                if (!valid) p = 0.0;
+                colacc += p;
+                rowpart[q] += p;
+                nrm += p;
+                if (energy) {
+                    int x[M], S[M];
+                    graph_coords<M>(s, N, x, S);
+                    const cplx_t<T> y = graph_apply_h<T, M>(psi, g.R, s, rr, x, S, g.row_ptr, g.col, w, eps,
+                                                            (T)g.U);
+                    if (valid) en += (double)v.x * (double)y.x + (double)v.y * (double)y.y;
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) colacc += __shfl_xor_sync(0xffffffffu, colacc, o);
+        if (P && lane == 0) atomicAdd(P + c, colacc * scale);
+    }
+    __shared__ double red_row[kObsWarps][kRows];
+    __shared__ double red_r[2][kObsWarps][32];
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) {
+        double v = rowpart[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red_row[wy][q] = v;
+    }
+    red_r[0][wy][lane] = nrm;
+    red_r[1][wy][lane] = en;
+    __syncthreads();
+    if (wy == 0) {
+        double a = 0.0, b = 0.0;
+        for (int k = 0; k < kObsWarps; ++k) {
+            a += red_r[0][k][lane];
+            b += red_r[1][k][lane];
+        }
+        if (valid && norm) atomicAdd(norm + r, a);
+        if (valid && energy) atomicAdd(energy + r, b);
+    } else if (wy == 1 && lane < kRows && P) {
+        const int row = row0 + lane;
+        if (row < n_rows) {
+            double v = 0.0;
+            for (int k = 0; k < kObsWarps; ++k) v += red_row[k][lane];
+            // coordinates x_1..x_{m-1} of this row
+            int t = row;
+            for (int j = M - 2; j >= 0; --j) {
+                const int qq = t / N;
+                atomicAdd(P + (t - qq * N), v * scale);
+                t = qq;
+            }
+        }
+    }
+}
+
+struct Launch {
+    dim3 grid, block;
+};
+
+// Threads: x over the chunk's realizations (up to 32), y over amplitudes.
+inline Launch graph_launch(const ctqw_graph *g, int rb, int re) {
+    const int n = re - rb;
+    int rx = 1;
+    while (rx < 32 && rx < n) rx <<= 1;
+    const int ry = kThreads / rx;
+    Launch l;
+    l.block = dim3((unsigned)rx, (unsigned)ry);
+    l.grid = dim3((unsigned)((g->D + ry - 1) / ry), (unsigned)((n + rx - 1) / rx));
+    return l;
+}
+
+}  // namespace
+
+int launch_graph_build_params(const ctqw_graph *g, const double *u_eps_d, const double *u_J_d,
+                              cudaStream_t s) {
+    graph_build_params_kernel<<<1024, 256, 0, s>>>(graph_view(g, 0, g->R), g->E, g->link_d, u_eps_d, u_J_d,
+                                                   g->eps_hw, g->J_hw, g->J0, g->round_to_f32, g->eps32,
+                                                   g->eps64, g->w32, g->w64, g->J64);
+    CTQW_CUDA_TRY(cudaGetLastError());
+    return CTQW_OK;
+}
+
+int launch_graph_init_state(const ctqw_graph *g, const int32_t *sites_d, int dtype, void *psi,
+                            cudaStream_t s) {
+    const size_t elem = dtype == CTQW_C64 ? sizeof(float2) : sizeof(double2);
+    CTQW_CUDA_TRY(cudaMemsetAsync(psi, 0, (size_t)g->total_amp * elem, s));
+    const dim3 grid((unsigned)((g->R + 127) / 128));
+    if (dtype == CTQW_C64)
+        graph_init_state_kernel<float><<<grid, 128, 0, s>>>(graph_view(g, 0, g->R), sites_d, g->statistics,
+                                                            (float2 *)psi);
+    else
+        graph_init_state_kernel<double><<<grid, 128, 0, s>>>(graph_view(g, 0, g->R), sites_d, g->statistics,
+                                                             (double2 *)psi);
+    CTQW_CUDA_TRY(cudaGetLastError());
+    return CTQW_OK;
+}
+
+int launch_graph_horner_stage(const ctqw_graph *g, int rb, int re, const void *in, const void *psi,
+                              void *out, double coef, cudaStream_t s) {
+    const Launch l = graph_launch(g, rb, re);
+    auto k = g->m == 2 ? graph_horner_stage_kernel<2> : graph_horner_stage_kernel<3>;
+    k<<<l.grid, l.block, 0, s>>>(graph_view(g, rb, re), g->eps32, g->w32, (const float2 *)in,
+                                 (const float2 *)psi, (float2 *)out, (float)coef);
+    CTQW_CUDA_TRY(cudaGetLastError());
+    return CTQW_OK;
+}
+
+int launch_graph_horner_final(const ctqw_graph *g, int rb, int re, const void *w2, void *psi, void *lo,
+                              double dt, cudaStream_t s) {
+    const Launch l = graph_launch(g, rb, re);
+    auto k = g->m == 2 ? graph_horner_final_kernel<2> : graph_horner_final_kernel<3>;
+    k<<<l.grid, l.block, 0, s>>>(graph_view(g, rb, re), g->eps32, g->w32, (const float2 *)w2, (float2 *)psi,
+                                 (float2 *)lo, (float)dt);
+    CTQW_CUDA_TRY(cudaGetLastError());
+    return CTQW_OK;
+}
+
+int launch_graph_taylor_term(const ctqw_graph *g, int rb, int re, int dtype, const void *in, void *out,
+                             const void *psi, void *acc, double coef, int first, cudaStream_t s) {
+    const Launch l = graph_launch(g, rb, re);
+    if (dtype == CTQW_C64) {
+        auto k = g->m == 2 ? graph_taylor_term_kernel<float, 2> : graph_taylor_term_kernel<float, 3>;
+        k<<<l.grid, l.block, 0, s>>>(graph_view(g, rb, re), g->eps32, g->w32, (const float2 *)in, (float2 *)out,
+                                     (const float2 *)psi, (float2 *)acc, (float)coef, first);
+    } else {
+        auto k = g->m == 2 ? graph_taylor_term_kernel<double, 2> : graph_taylor_term_kernel<double, 3>;
+        k<<<l.grid, l.block, 0, s>>>(graph_view(g, rb, re), g->eps64, g->w64, (const double2 *)in,
+                                     (double2 *)out, (const double2 *)psi, (double2 *)acc, coef, first);
+    }
+    CTQW_CUDA_TRY(cudaGetLastError());
+    return CTQW_OK;
+}
+
+int launch_graph_rk4_stage(const ctqw_graph *g, int rb, int re, int dtype, const void *in, void *next,
+                           const void *psi, void *acc, double a, double b, int first, cudaStream_t s) {
+    const Launch l = graph_launch(g, rb, re);
+    if (dtype == CTQW_C64) {
+        auto k = g->m == 2 ? graph_rk4_stage_kernel<float, 2> : graph_rk4_stage_kernel<float, 3>;
+        k<<<l.grid, l.block, 0, s>>>(graph_view(g, rb, re), g->eps32, g->w32, (const float2 *)in,
+                                     (float2 *)next, (const float2 *)psi, (float2 *)acc, (float)a, (float)b, first);
+    } else {
+        auto k = g->m == 2 ? graph_rk4_stage_kernel<double, 2> : graph_rk4_stage_kernel<double, 3>;
+        k<<<l.grid, l.block, 0, s>>>(graph_view(g, rb, re), g->eps64, g->w64, (const double2 *)in,
+                                     (double2 *)next, (const double2 *)psi, (double2 *)acc, a, b, first);
+    }
+    CTQW_CUDA_TRY(cudaGetLastError());
+    return CTQW_OK;
+}
+
+int launch_graph_observables(const ctqw_graph *g, int rb, int re, int dtype, const void *psi,
+                             double *P_mean, double *norm, double *energy, cudaStream_t s) {
+    if (!P_mean && !norm && !energy) return CTQW_OK;
+    const int n_rows = (int)(g->D / g->N);
+    const dim3 grid((unsigned)((n_rows + kRows - 1) / kRows), (unsigned)((re - rb + 31) / 32));
+    const dim3 block(32, kObsWarps);
+    if (dtype == CTQW_C64) {
+        auto k = g->m == 2 ? graph_observables_kernel<float, 2> : graph_observables_kernel<float, 3>;
+        k<<<grid, block, 0, s>>>(graph_view(g, rb, re), g->eps32, g->w32, (const float2 *)psi, P_mean, norm,
+                                 energy);
+    } else {
+        auto k = g->m == 2 ? graph_observables_kernel<double, 2> : graph_observables_kernel<double, 3>;
+        k<<<grid, block, 0, s>>>(graph_view(g, rb, re), g->eps64, g->w64, (const double2 *)psi, P_mean, norm,
+                                 energy);
+    }
+    CTQW_CUDA_TRY(cudaGetLastError());
+    return CTQW_OK;
+}

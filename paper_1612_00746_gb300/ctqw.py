@@ -49,7 +49,10 @@ EXPORTED = (
     "ctqw_propagate_rk4", "ctqw_ensemble_observables", "ctqw_check_status", "ctqw_last_error",
     "ctqw_version", "ctqw_adjoint_workspace_size", "ctqw_adjoint_grad", "ctqw_taylor_order",
     "ctqw_autotune_order", "ctqw_one_body_density", "ctqw_propagate_taylor_switching",
-    "ctqw_propagate_exact",
+    "ctqw_propagate_exact", "ctqw_graph_build", "ctqw_graph_destroy", "ctqw_graph_get_params",
+    "ctqw_graph_state_size", "ctqw_graph_init_state", "ctqw_graph_workspace_size",
+    "ctqw_graph_propagate_taylor", "ctqw_graph_propagate_rk4", "ctqw_graph_observables",
+    "ctqw_graph_set_chunk",
 )
 
 
@@ -67,6 +70,18 @@ class LatticeDesc(ctypes.Structure):
         ("round_to_f32", ctypes.c_int32), ("J0", ctypes.c_double), ("U", ctypes.c_double),
         ("eps_halfwidth", ctypes.c_double), ("J_halfwidth", ctypes.c_double),
         ("eps_mean", ctypes.POINTER(ctypes.c_double)), ("J_mean", ctypes.POINTER(ctypes.c_double)),
+        ("u_eps_host", ctypes.POINTER(ctypes.c_double)), ("u_J_host", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+class GraphDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_particles", ctypes.c_int32), ("statistics", ctypes.c_int32),
+        ("n_nodes", ctypes.c_int32), ("n_edges", ctypes.c_int32),
+        ("edge_u", ctypes.POINTER(ctypes.c_int32)), ("edge_v", ctypes.POINTER(ctypes.c_int32)),
+        ("n_realizations", ctypes.c_int32), ("round_to_f32", ctypes.c_int32),
+        ("J0", ctypes.c_double), ("U", ctypes.c_double),
+        ("eps_halfwidth", ctypes.c_double), ("J_halfwidth", ctypes.c_double),
         ("u_eps_host", ctypes.POINTER(ctypes.c_double)), ("u_J_host", ctypes.POINTER(ctypes.c_double)),
     ]
 
@@ -108,6 +123,16 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "ctqw_propagate_taylor_switching": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, u32, vp, sz,
                                             ctypes.c_uint64, dbl, vp],
         "ctqw_autotune_order": [vp, i32, dbl, i64, i32, i32, ctypes.POINTER(i32)],
+        "ctqw_graph_build": [ctypes.POINTER(GraphDesc), vp, ctypes.POINTER(vp)],
+        "ctqw_graph_destroy": [vp],
+        "ctqw_graph_get_params": [vp, pd, pd],
+        "ctqw_graph_state_size": [vp, ctypes.POINTER(i64)],
+        "ctqw_graph_init_state": [vp, ctypes.POINTER(i32), i32, vp, vp],
+        "ctqw_graph_workspace_size": [vp, i32, ctypes.POINTER(sz)],
+        "ctqw_graph_propagate_taylor": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, vp, sz, vp],
+        "ctqw_graph_propagate_rk4": [vp, i32, vp, dbl, i64, i32, vp, vp, vp, vp, sz, vp],
+        "ctqw_graph_observables": [vp, i32, vp, vp, vp, vp, vp],
+        "ctqw_graph_set_chunk": [vp, i32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -231,6 +256,122 @@ class Hamiltonian:
 
     def n_obs(self, n_steps: int, obs_every: int) -> int:
         return n_steps // obs_every + 1 if obs_every > 0 else 0
+
+
+class Graph:
+    """Handle of m particles on a q-dimensional lattice or general graph with
+    per-realization disorder (ctqw_graph_build)."""
+
+    def __init__(self, m: int, statistics: int, n_nodes: int, edge_u, edge_v, R: int, J0: float,
+                 U: float, eps_halfwidth: float, J_halfwidth: float, u_eps: np.ndarray,
+                 u_J: np.ndarray, round_to_f32: bool = True, stream=None):
+        lib = load()
+        self.m, self.statistics, self.N, self.R = int(m), int(statistics), int(n_nodes), int(R)
+        self._eu = np.ascontiguousarray(np.asarray(edge_u, dtype=np.int32))
+        self._ev = np.ascontiguousarray(np.asarray(edge_v, dtype=np.int32))
+        self.E = len(self._eu)
+        self._u_eps = np.ascontiguousarray(u_eps, dtype=np.float64)
+        self._u_J = np.ascontiguousarray(u_J, dtype=np.float64)
+        d = GraphDesc()
+        d.n_particles, d.statistics, d.n_nodes, d.n_edges = self.m, self.statistics, self.N, self.E
+        d.edge_u = self._eu.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.edge_v = self._ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        d.n_realizations = self.R
+        d.round_to_f32 = 1 if round_to_f32 else 0
+        d.J0, d.U = float(J0), float(U)
+        d.eps_halfwidth, d.J_halfwidth = float(eps_halfwidth), float(J_halfwidth)
+        d.u_eps_host = _dptr(self._u_eps)
+        d.u_J_host = _dptr(self._u_J)
+        g = ctypes.c_void_p()
+        _check(lib.ctqw_graph_build(ctypes.byref(d), _stream(stream), ctypes.byref(g)))
+        self._g = g
+        total = ctypes.c_int64()
+        _check(lib.ctqw_graph_state_size(g, ctypes.byref(total)))
+        self.total_amplitudes = int(total.value)
+        self.D = self.total_amplitudes // self.R
+
+    @classmethod
+    def from_workload(cls, w, realizations=None, stream=None) -> "Graph":
+        """The handle of a graph workload (its link list and seeded draws)."""
+        import ctqw_workloads as cw
+        realizations = list(range(w.R)) if realizations is None else list(realizations)
+        u, v = w.edges()
+        ue, uj = cw.graph_draws(w, realizations)
+        return cls(w.m, w.statistics, w.n_nodes(), u, v, len(realizations), w.J0, w.U, w.eps_halfwidth,
+                   w.J_halfwidth, ue, uj, stream=stream)
+
+    @property
+    def handle(self):
+        return self._g
+
+    def close(self) -> None:
+        if getattr(self, "_g", None) is not None and self._g.value:
+            load().ctqw_graph_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        """(eps [R][N], J [R][E]) host float64 arrays (ctqw_graph_get_params)."""
+        eps = np.zeros((self.R, self.N))
+        J = np.zeros((self.R, max(self.E, 1)))
+        _check(load().ctqw_graph_get_params(self._g, _dptr(eps), _dptr(J)))
+        return eps, J[:, :self.E]
+
+    def new_state(self, dtype: int, device="cuda") -> torch.Tensor:
+        return torch.zeros(self.total_amplitudes, dtype=torch_dtype(dtype), device=device)
+
+    def workspace(self, dtype: int, device="cuda") -> torch.Tensor:
+        b = ctypes.c_size_t()
+        _check(load().ctqw_graph_workspace_size(self._g, dtype, ctypes.byref(b)))
+        return torch.empty(b.value, dtype=torch.uint8, device=device)
+
+    def n_obs(self, n_steps: int, obs_every: int) -> int:
+        return n_steps // obs_every + 1 if obs_every > 0 else 0
+
+    def states(self, psi: torch.Tensor) -> torch.Tensor:
+        """[R][N^m] view-copy of a graph state (stored amplitude-major, s R + r)."""
+        return psi.reshape(self.D, self.R).t()
+
+
+def ctqw_graph_set_chunk(g: Graph, realizations: int) -> None:
+    _check(load().ctqw_graph_set_chunk(g.handle, int(realizations)))
+
+
+def ctqw_graph_init_state(g: Graph, psi: torch.Tensor, sites, dtype: int, stream=None) -> None:
+    s = np.ascontiguousarray(np.broadcast_to(np.asarray(sites, dtype=np.int32), (g.R, g.m)))
+    _check(load().ctqw_graph_init_state(g.handle, s.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), dtype,
+                                        _ptr(psi), _stream(stream)))
+
+
+def ctqw_graph_propagate_taylor(g: Graph, psi: torch.Tensor, dtype: int, dt: float, K: int, n_steps: int,
+                                obs_every: int = 0, P_mean=None, norm=None, energy=None,
+                                workspace: Optional[torch.Tensor] = None, stream=None):
+    if workspace is None:
+        workspace = g.workspace(dtype, psi.device)
+    _check(load().ctqw_graph_propagate_taylor(g.handle, dtype, _ptr(psi), float(dt), int(K), int(n_steps),
+                                              int(obs_every), _ptr(P_mean), _ptr(norm), _ptr(energy),
+                                              _ptr(workspace), workspace.numel(), _stream(stream)))
+
+
+def ctqw_graph_propagate_rk4(g: Graph, psi: torch.Tensor, dtype: int, dt: float, n_steps: int,
+                             obs_every: int = 0, P_mean=None, norm=None, energy=None,
+                             workspace: Optional[torch.Tensor] = None, stream=None):
+    if workspace is None:
+        workspace = g.workspace(dtype, psi.device)
+    _check(load().ctqw_graph_propagate_rk4(g.handle, dtype, _ptr(psi), float(dt), int(n_steps), int(obs_every),
+                                           _ptr(P_mean), _ptr(norm), _ptr(energy), _ptr(workspace),
+                                           workspace.numel(), _stream(stream)))
+
+
+def ctqw_graph_observables(g: Graph, psi: torch.Tensor, dtype: int, P_mean=None, norm=None, energy=None,
+                           stream=None):
+    _check(load().ctqw_graph_observables(g.handle, dtype, _ptr(psi), _ptr(P_mean), _ptr(norm), _ptr(energy),
+                                         _stream(stream)))
 
 
 def ctqw_init_state(h: Hamiltonian, psi: torch.Tensor, sites, dtype: int, stream=None) -> None:

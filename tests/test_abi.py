@@ -103,3 +103,52 @@ def test_binding_fails_loudly_without_library(tmp_path):
             ctqw.load(str(tmp_path / "nope.so"))
     finally:
         ctqw._lib = saved
+
+
+def _graph_desc(ctqw, **kw):
+    d = ctqw.GraphDesc()
+    eu = np.array(kw.pop("eu", [0, 1, 2]), dtype=np.int32)
+    ev = np.array(kw.pop("ev", [1, 2, 0]), dtype=np.int32)
+    ue = np.full(64, 0.5)
+    d.n_particles, d.statistics, d.n_nodes, d.n_edges = 2, 0, 3, len(eu)
+    d.edge_u = eu.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    d.edge_v = ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    d.n_realizations, d.round_to_f32 = 1, 1
+    d.J0, d.U, d.eps_halfwidth, d.J_halfwidth = 1.0, 0.0, 0.5, 0.1
+    d.u_eps_host = ue.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.u_J_host = ue.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d, (eu, ev, ue)
+
+
+@pytest.mark.parametrize("kw,msg", [
+    ({"eu": [0, 1, 1], "ev": [1, 2, 1]}, "itself"),
+    ({"eu": [0, 1, 2], "ev": [1, 2, 3]}, "out of range"),
+    ({"n_particles": 4}, "n_particles"),
+    ({"n_nodes": 1}, "n_nodes"),
+    ({"n_nodes": 50000}, "2^31"),
+    ({"n_realizations": 0}, "n_realizations"),
+    ({"u_eps_host": None}, "draws"),
+])
+def test_graph_build_rejects_bad_descriptions_before_any_launch(lib, kw, msg):
+    from paper_1612_00746_gb300 import ctqw
+
+    d, keep = _graph_desc(ctqw, **kw)
+    g = ctypes.c_void_p()
+    st = lib.ctqw_graph_build(ctypes.byref(d), None, ctypes.byref(g))
+    assert st == ctqw.CTQW_EINVAL
+    assert msg in lib.ctqw_last_error().decode()
+    assert not g.value
+
+
+def test_graph_entry_points_reject_null_handles(lib):
+    from paper_1612_00746_gb300 import ctqw
+
+    assert lib.ctqw_graph_propagate_taylor(None, 0, None, 0.1, 4, 1, 0, None, None, None, None, 0,
+                                           None) == ctqw.CTQW_EINVAL
+    assert lib.ctqw_graph_propagate_rk4(None, 0, None, 0.1, 1, 0, None, None, None, None, 0,
+                                        None) == ctqw.CTQW_EINVAL
+    assert lib.ctqw_graph_observables(None, 0, None, None, None, None, None) == ctqw.CTQW_EINVAL
+    assert lib.ctqw_graph_init_state(None, None, 0, None, None) == ctqw.CTQW_EINVAL
+    assert lib.ctqw_graph_destroy(None) == ctqw.CTQW_OK
