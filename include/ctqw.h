@@ -387,8 +387,9 @@ int ctqw_check_status(const ctqw_hamiltonian *h, void *stream);
  * over the links e = (u_e, v_e); repeated links add.  All realizations have
  * the same N nodes and P rows have N entries.  State layout: realizations
  * are the fastest index, amplitude s (x_m fastest, as above) of realization
- * r at s R + r, so that the kernels read every neighbour as one coalesced
- * row across realizations.  The topology is stored once as the CSR of the
+ * r at s Rp + r with Rp = R rounded up to a multiple of 4 (the padding
+ * realizations stay zero), so that the kernels read every neighbour as one
+ * coalesced row across realizations, four realizations per thread.  The topology is stored once as the CSR of the
  * one-particle graph; the N^m x (mk + 1) many-particle topology of Sec. 2
  * is regenerated inside the kernels.
  * ------------------------------------------------------------------------ */
@@ -435,7 +436,7 @@ int ctqw_graph_destroy(ctqw_graph *g);
  */
 int ctqw_graph_get_params(const ctqw_graph *g, double *eps_host, double *J_host);
 
-/* Amplitudes of all realizations, R N^m. */
+/* Amplitudes of the state array, Rp N^m (Rp = R rounded up to a multiple of 4). */
 int ctqw_graph_state_size(const ctqw_graph *g, int64_t *amplitudes_total);
 
 /*

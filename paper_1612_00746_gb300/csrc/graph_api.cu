@@ -71,7 +71,7 @@ int sample(const ctqw_graph *g, int rb, int re, int dtype, const void *psi, int6
 
 }  // namespace
 
-int graph_chunk(const ctqw_graph *g) { return g->chunk > 0 ? std::min(g->chunk, g->R) : g->R; }
+int graph_chunk(const ctqw_graph *g) { return g->chunk > 0 ? std::min((g->chunk + 3) / 4 * 4, g->R) : g->R; }
 
 extern "C" {
 
@@ -143,11 +143,12 @@ int ctqw_graph_build(const ctqw_graph_desc *d, void *stream, ctqw_graph **out) {
     g->eps_hw = d->eps_halfwidth;
     g->J_hw = d->J_halfwidth;
     g->D = D;
-    g->total_amp = D * g->R;
+    g->Rp = (g->R + 3) / 4 * 4;
+    g->total_amp = D * g->Rp;
     g->nnz = nnz;
     cudaGetDevice(&g->device);
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t RN = (size_t)g->R * N, RE = (size_t)g->R * E, RK = (size_t)g->R * nnz;
+    const size_t RN = (size_t)g->Rp * N, RE = (size_t)g->R * E, RK = (size_t)g->Rp * nnz;
     double *u_eps_d = nullptr, *u_J_d = nullptr;
     int st = CTQW_OK;
     if (st == CTQW_OK) st = gupload(&g->row_ptr_d, row_ptr.data(), row_ptr.size(), s);
@@ -158,7 +159,7 @@ int ctqw_graph_build(const ctqw_graph_desc *d, void *stream, ctqw_graph **out) {
     if (st == CTQW_OK) st = galloc(&g->w32, RK);
     if (st == CTQW_OK) st = galloc(&g->w64, RK);
     if (st == CTQW_OK) st = galloc(&g->J64, RE);
-    if (st == CTQW_OK) st = gupload(&u_eps_d, d->u_eps_host, RN, s);
+    if (st == CTQW_OK) st = gupload(&u_eps_d, d->u_eps_host, (size_t)g->R * N, s);
     if (st == CTQW_OK) st = gupload(&u_J_d, d->u_J_host, RE, s);
     if (st == CTQW_OK) st = launch_graph_build_params(g, u_eps_d, u_J_d, s);
     // the draws are read by the build only: wait for it before freeing them
@@ -189,11 +190,11 @@ int ctqw_graph_get_params(const ctqw_graph *g, double *eps_host, double *J_host)
     if (!g) { ctqw_set_error("null graph handle"); return CTQW_EINVAL; }
     CTQW_CUDA_TRY(cudaDeviceSynchronize());
     if (eps_host) {
-        // device eps is [N][R]; the caller gets [R][N]
-        std::vector<double> t((size_t)g->R * g->N);
+        // device eps is [N][Rp]; the caller gets [R][N]
+        std::vector<double> t((size_t)g->Rp * g->N);
         CTQW_CUDA_TRY(cudaMemcpy(t.data(), g->eps64, sizeof(double) * t.size(), cudaMemcpyDeviceToHost));
         for (int i = 0; i < g->N; ++i)
-            for (int r = 0; r < g->R; ++r) eps_host[(size_t)r * g->N + i] = t[(size_t)i * g->R + r];
+            for (int r = 0; r < g->R; ++r) eps_host[(size_t)r * g->N + i] = t[(size_t)i * g->Rp + r];
     }
     if (J_host && g->E > 0)
         CTQW_CUDA_TRY(cudaMemcpy(J_host, g->J64, sizeof(double) * g->R * g->E, cudaMemcpyDeviceToHost));

@@ -16,30 +16,34 @@
 // kernels (the Kronecker sum over particles), so nothing of size N^m is
 // stored besides the states.
 //
-// Layout: realizations are the fastest index everywhere.  The states are
-// psi[s][r] (amplitude s of realization r at s R + r), the on-site energies
-// eps[i][r] and the hoppings in CSR order w[k][r] = J_r(link of entry k).
-// A warp covers 32 realizations of one amplitude, so every CSR lookup is
-// uniform across it and every neighbour load is one coalesced row.
+// Layout: realizations are the fastest index everywhere, with the stride Rp
+// = R rounded up to a multiple of 4.  The states are psi[s][r] (amplitude s
+// of realization r at s Rp + r), the on-site energies eps[i][r] and the
+// hoppings in CSR order w[k][r] = J_r(link of entry k); padding realizations
+// carry zero parameters and zero states.  A thread owns four adjacent
+// realizations of one amplitude (16-byte vector loads), a warp 128, so every
+// CSR lookup is uniform across the warp and every neighbour load is one
+// coalesced row.
 struct ctqw_graph {
     int m = 0, statistics = 0, N = 0, E = 0, R = 0, round_to_f32 = 1;
     double J0 = 1.0, U = 0.0, eps_hw = 0.0, J_hw = 0.0;
     int64_t D = 0;            // N^m amplitudes per realization
-    int64_t total_amp = 0;    // R * D
+    int Rp = 0;               // realization stride: R rounded up to a multiple of 4
+    int64_t total_amp = 0;    // Rp * D
     int nnz = 0;              // 2E
     int device = 0;
     int chunk = 0;            // realizations per pass through the steps (0: all)
     int32_t *row_ptr_d = nullptr, *col_d = nullptr, *link_d = nullptr;   // CSR of the one-particle graph
-    float *eps32 = nullptr, *w32 = nullptr;                              // [N][R], [nnz][R]
-    double *eps64 = nullptr, *w64 = nullptr, *J64 = nullptr;             // [N][R], [nnz][R], [R][E]
+    float *eps32 = nullptr, *w32 = nullptr;                              // [N][Rp], [nnz][Rp]
+    double *eps64 = nullptr, *w64 = nullptr, *J64 = nullptr;             // [N][Rp], [nnz][Rp], [R][E]
 };
 
 // Per-launch view of the topology (passed by value to kernels); a launch
-// covers the realizations r_begin <= r < r_end.
+// covers the realizations r_begin <= r < r_end (r_begin a multiple of 4).
 struct GraphView {
     const int32_t *row_ptr;
     const int32_t *col;
-    int N, m, R, nnz;
+    int N, m, R, Rp, nnz;
     int D;        // N^m < 2^31
     int r_begin, r_end;
     double U;
@@ -52,6 +56,7 @@ inline GraphView graph_view(const ctqw_graph *g, int r_begin, int r_end) {
     v.N = g->N;
     v.m = g->m;
     v.R = g->R;
+    v.Rp = g->Rp;
     v.nnz = g->nnz;
     v.D = (int)g->D;
     v.r_begin = r_begin;
@@ -60,8 +65,8 @@ inline GraphView graph_view(const ctqw_graph *g, int r_begin, int r_end) {
     return v;
 }
 
-// Realizations per pass through the steps: g->chunk when set (at most R),
-// else all of them.
+// Realizations per pass through the steps: g->chunk rounded up to a
+// multiple of 4 when set (at most R), else all of them.
 int graph_chunk(const ctqw_graph *g);
 
 // Parameters from the uniform draws u_eps [R][N], u_J [R][E] (device):

@@ -9,11 +9,11 @@
 //   (H a)(s) = (sum_j eps[x_j] + U pairs) a(s) - sum_j sum_{k in row x_j} w_k a(s + (col_k - x_j) S_j),
 // the CSR row of node x_j giving the neighbours col_k and their hoppings w_k.
 // Realizations are the fastest index of every array (psi[s][r], eps[i][r],
-// w[k][r]): threadIdx.x walks realizations and threadIdx.y amplitudes, so
-// the CSR lookups of a warp are uniform (broadcast loads) and each neighbour
-// read is one coalesced row.  The first four entries of the rows of all m
-// coordinates are gathered at once (4m neighbour loads in flight per
-// thread), entries past a row's end reading the own amplitude with weight 0.
+// w[k][r], stride Rp a multiple of 4).  A thread owns four adjacent
+// realizations of one amplitude and moves them with 16-byte loads; threadIdx.x
+// walks realization quads, threadIdx.y amplitudes.  The CSR lookups and the
+// index arithmetic of a neighbour are then shared by four amplitudes and
+// uniform across the warp, and each neighbour read is one coalesced row.
 #include <algorithm>
 
 #include "graph_internal.cuh"
@@ -22,6 +22,44 @@
 namespace {
 
 constexpr int kThreads = 256;
+
+// Four adjacent realizations of one complex amplitude / one real parameter.
+template <typename T> struct C4 { T re[4], im[4]; };
+template <typename T> struct R4 { T v[4]; };
+
+__device__ __forceinline__ C4<float> ld_c4(const float2 *__restrict__ p) {
+    const float4 u = __ldg(reinterpret_cast<const float4 *>(p)), v = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+    return C4<float>{{u.x, u.z, v.x, v.z}, {u.y, u.w, v.y, v.w}};
+}
+__device__ __forceinline__ C4<double> ld_c4(const double2 *__restrict__ p) {
+    const double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
+    return C4<double>{{a.x, b.x, c.x, d.x}, {a.y, b.y, c.y, d.y}};
+}
+// the same through the coherent path (arrays the kernel also writes)
+__device__ __forceinline__ C4<float> ld_c4_rw(const float2 *p) {
+    const float4 u = reinterpret_cast<const float4 *>(p)[0], v = reinterpret_cast<const float4 *>(p)[1];
+    return C4<float>{{u.x, u.z, v.x, v.z}, {u.y, u.w, v.y, v.w}};
+}
+__device__ __forceinline__ C4<double> ld_c4_rw(const double2 *p) {
+    const double2 a = p[0], b = p[1], c = p[2], d = p[3];
+    return C4<double>{{a.x, b.x, c.x, d.x}, {a.y, b.y, c.y, d.y}};
+}
+__device__ __forceinline__ void st_c4(float2 *p, const C4<float> &c) {
+    reinterpret_cast<float4 *>(p)[0] = make_float4(c.re[0], c.im[0], c.re[1], c.im[1]);
+    reinterpret_cast<float4 *>(p)[1] = make_float4(c.re[2], c.im[2], c.re[3], c.im[3]);
+}
+__device__ __forceinline__ void st_c4(double2 *p, const C4<double> &c) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p[q] = make_double2(c.re[q], c.im[q]);
+}
+__device__ __forceinline__ R4<float> ld_r4(const float *__restrict__ p) {
+    const float4 u = __ldg(reinterpret_cast<const float4 *>(p));
+    return R4<float>{{u.x, u.y, u.z, u.w}};
+}
+__device__ __forceinline__ R4<double> ld_r4(const double *__restrict__ p) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return R4<double>{{a.x, a.y, b.x, b.y}};
+}
 
 template <int M>
 __device__ __forceinline__ void graph_coords(int s, int N, int (&x)[M], int (&S)[M]) {
@@ -36,80 +74,59 @@ __device__ __forceinline__ void graph_coords(int s, int N, int (&x)[M], int (&S)
     }
 }
 
-// Entries k0 + u (u < 4, k0 + u < k1) of one CSR row: weights and
-// neighbour amplitudes.  Past the row end the own amplitude is read with
-// weight 0, so no load depends on a branch.
+// (H a)(s) for the four realizations r4..r4+3; Rp is the realization stride.
 template <typename T, int M>
-__device__ __forceinline__ void graph_gather4(const cplx_t<T> *__restrict__ a, int64_t R, int s, int r, int xj,
-                                              int Sj, int k0, int k1, const int32_t *__restrict__ col,
-                                              const T *__restrict__ w, T (&t)[4], cplx_t<T> (&n)[4]) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const bool ok = k0 + u < k1;
-        const int c = ok ? col[k0 + u] : xj;
-        t[u] = ok ? w[(int64_t)(k0 + u) * R + r] : T(0);
-        n[u] = a[(int64_t)(s + (c - xj) * Sj) * R + r];
-    }
-}
-
-// (H a)(s) of realization r; R is the realization stride of every array.
-// The first four entries of every coordinate's row are gathered together
-// (all their loads in flight at once); longer rows continue four at a time.
-template <typename T, int M>
-__device__ __forceinline__ cplx_t<T> graph_apply_h(const cplx_t<T> *__restrict__ a, int64_t R, int s, int r,
-                                                    const int (&x)[M], const int (&S)[M],
-                                                    const int32_t *__restrict__ row_ptr,
-                                                    const int32_t *__restrict__ col,
-                                                    const T *__restrict__ w, const T *__restrict__ eps,
-                                                    T U) {
-    int k0[M], k1[M];
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-        k0[j] = row_ptr[x[j]];
-        k1[j] = row_ptr[x[j] + 1];
-    }
-    T v = T(0);
+__device__ __forceinline__ C4<T> graph_apply_h4(const cplx_t<T> *a, int64_t Rp, int s, int r4,
+                                                const int (&x)[M], const int (&S)[M],
+                                                const int32_t *__restrict__ row_ptr,
+                                                const int32_t *__restrict__ col, const T *__restrict__ w,
+                                                const T *__restrict__ eps, T U) {
     int pairs = 0;
 #pragma unroll
-    for (int j = 0; j < M; ++j) {
-        v += eps[(int64_t)x[j] * R + r];
+    for (int j = 0; j < M; ++j)
 #pragma unroll
         for (int l = j + 1; l < M; ++l) pairs += (x[j] == x[l]);
+    R4<T> v;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v.v[q] = U * T(pairs);
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        const R4<T> e = ld_r4(eps + (int64_t)x[j] * Rp + r4);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v.v[q] += e.v[q];
     }
-    v += U * T(pairs);
-    T t[M][4];
-    cplx_t<T> n[M][4];
+    const C4<T> c = ld_c4(a + (int64_t)s * Rp + r4);
+    C4<T> y;
 #pragma unroll
-    for (int j = 0; j < M; ++j) graph_gather4<T, M>(a, R, s, r, x[j], S[j], k0[j], k1[j], col, w, t[j], n[j]);
-    const cplx_t<T> c = a[(int64_t)s * R + r];
-    T yr = v * c.x, yi = v * c.y;
+    for (int q = 0; q < 4; ++q) {
+        y.re[q] = v.v[q] * c.re[q];
+        y.im[q] = v.v[q] * c.im[q];
+    }
 #pragma unroll
-    for (int j = 0; j < M; ++j)
+    for (int j = 0; j < M; ++j) {
+        const int k0 = row_ptr[x[j]], k1 = row_ptr[x[j] + 1];
+        const int64_t step = (int64_t)S[j] * Rp;                       // one node along coordinate j
+        const cplx_t<T> *base = a + (int64_t)(s - x[j] * S[j]) * Rp + r4;   // coordinate j at node 0
+        const T *wr = w + r4;
+#pragma unroll 4
+        for (int k = k0; k < k1; ++k) {
+            const R4<T> t = ld_r4(wr + (int64_t)k * Rp);
+            const C4<T> n = ld_c4(base + (int64_t)col[k] * step);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            yr -= t[j][u] * n[j][u].x;
-            yi -= t[j][u] * n[j][u].y;
-        }
-#pragma unroll
-    for (int j = 0; j < M; ++j)
-        for (int k = k0[j] + 4; k < k1[j]; k += 4) {
-            T tt[4];
-            cplx_t<T> nn[4];
-            graph_gather4<T, M>(a, R, s, r, x[j], S[j], k, k1[j], col, w, tt, nn);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                yr -= tt[u] * nn[u].x;
-                yi -= tt[u] * nn[u].y;
+            for (int q = 0; q < 4; ++q) {
+                y.re[q] -= t.v[q] * n.re[q];
+                y.im[q] -= t.v[q] * n.im[q];
             }
         }
-    return mk<T>(yr, yi);
+    }
+    return y;
 }
 
-// (amplitude, realization) of this thread, false past the ends.
-__device__ __forceinline__ bool graph_site(const GraphView &g, int &s, int &r) {
+// (amplitude, first realization of the quad) of this thread, false past the ends.
+__device__ __forceinline__ bool graph_site4(const GraphView &g, int &s, int &r4) {
     s = blockIdx.x * blockDim.y + threadIdx.y;
-    r = g.r_begin + blockIdx.y * blockDim.x + threadIdx.x;
-    return s < g.D && r < g.r_end;
+    r4 = g.r_begin + 4 * (blockIdx.y * blockDim.x + threadIdx.x);
+    return s < g.D && r4 < g.r_end;
 }
 
 __device__ __forceinline__ double graph_param(double mean, double hw, double u, int round_f32) {
@@ -123,20 +140,20 @@ __global__ void graph_build_params_kernel(GraphView g, int E, const int32_t *__r
                                           const double *__restrict__ u_J, double eps_hw, double J_hw,
                                           double J0, int round_f32, float *eps32, double *eps64,
                                           float *w32, double *w64, double *J64) {
-    const int64_t R = g.R;
+    const int64_t R = g.R, Rp = g.Rp;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (int64_t t = t0; t < (int64_t)g.N * R; t += stride) {   // eps[i][r] from u_eps[r][i]
-        const int64_t i = t / R, r = t - i * R;
-        const double e = graph_param(0.0, eps_hw, u_eps[r * g.N + i], round_f32);
+    for (int64_t t = t0; t < (int64_t)g.N * Rp; t += stride) {   // eps[i][r] from u_eps[r][i]
+        const int64_t i = t / Rp, r = t - i * Rp;
+        const double e = r < R ? graph_param(0.0, eps_hw, u_eps[r * g.N + i], round_f32) : 0.0;
         eps64[t] = e;
         eps32[t] = (float)e;
     }
-    for (int64_t t = t0; t < (int64_t)E * R; t += stride)      // J[r][e] as drawn
+    for (int64_t t = t0; t < (int64_t)E * R; t += stride)        // J[r][e] as drawn
         J64[t] = graph_param(J0, J_hw, u_J[t], round_f32);
-    for (int64_t t = t0; t < (int64_t)g.nnz * R; t += stride) { // w[k][r] = J[r][link[k]]
-        const int64_t k = t / R, r = t - k * R;
-        const double j = graph_param(J0, J_hw, u_J[r * E + link[k]], round_f32);
+    for (int64_t t = t0; t < (int64_t)g.nnz * Rp; t += stride) {  // w[k][r] = J[r][link[k]]
+        const int64_t k = t / Rp, r = t - k * Rp;
+        const double j = r < R ? graph_param(J0, J_hw, u_J[r * E + link[k]], round_f32) : 0.0;
         w64[t] = j;
         w32[t] = (float)j;
     }
@@ -174,7 +191,7 @@ __global__ void graph_init_state_kernel(GraphView g, const int32_t *__restrict__
     double nrm = 0.0;
     for (int k = 0; k < n; ++k) nrm += amp[k] * amp[k];
     nrm = sqrt(nrm);
-    for (int k = 0; k < n; ++k) psi[idx[k] * g.R + r] = mk<T>((T)(amp[k] / nrm), T(0));
+    for (int k = 0; k < n; ++k) psi[idx[k] * g.Rp + r] = mk<T>((T)(amp[k] / nrm), T(0));
 }
 
 template <int M>
@@ -183,14 +200,20 @@ __global__ void __launch_bounds__(kThreads) graph_horner_stage_kernel(GraphView 
                                                                       const float2 *__restrict__ in,
                                                                       const float2 *__restrict__ psi,
                                                                       float2 *__restrict__ out, float coef) {
-    int s, r;
-    if (!graph_site(g, s, r)) return;
+    int s, r4;
+    if (!graph_site4(g, s, r4)) return;
     int x[M], S[M];
     graph_coords<M>(s, g.N, x, S);
-    const float2 y = graph_apply_h<float, M>(in, g.R, s, r, x, S, g.row_ptr, g.col, w, eps, (float)g.U);
-    const int64_t i = (int64_t)s * g.R + r;
-    const float2 q = psi[i];
-    out[i] = make_float2(fmaf(coef, y.y, q.x), fmaf(-coef, y.x, q.y));   // q + coef (-i) y
+    const C4<float> y = graph_apply_h4<float, M>(in, g.Rp, s, r4, x, S, g.row_ptr, g.col, w, eps, (float)g.U);
+    const int64_t i = (int64_t)s * g.Rp + r4;
+    const C4<float> q = ld_c4(psi + i);
+    C4<float> o;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {   // q + coef (-i) y
+        o.re[k] = fmaf(coef, y.im[k], q.re[k]);
+        o.im[k] = fmaf(-coef, y.re[k], q.im[k]);
+    }
+    st_c4(out + i, o);
 }
 
 template <int M>
@@ -199,8 +222,8 @@ __global__ void __launch_bounds__(kThreads) graph_horner_final_kernel(GraphView 
                                                                       const float2 *__restrict__ w2,
                                                                       float2 *__restrict__ psi,
                                                                       float2 *__restrict__ lo, float dt) {
-    int s, r;
-    if (!graph_site(g, s, r)) return;
+    int s, r4;
+    if (!graph_site4(g, s, r4)) return;
     int x[M], S[M];
     graph_coords<M>(s, g.N, x, S);
     // TwoSum then FastTwoSum per component: the state's rounding error is
@@ -214,13 +237,16 @@ __global__ void __launch_bounds__(kThreads) graph_horner_final_kernel(GraphView 
         lw = __fsub_rn(e, __fsub_rn(h2, t));
         hi = h2;
     };
-    const float2 y = graph_apply_h<float, M>(w2, g.R, s, r, x, S, g.row_ptr, g.col, w, eps, (float)g.U);
-    const int64_t i = (int64_t)s * g.R + r;
-    float2 h = psi[i], l = lo[i];
-    add(h.x, l.x, dt * y.y);    // -i dt H w2
-    add(h.y, l.y, -dt * y.x);
-    psi[i] = h;
-    lo[i] = l;
+    const C4<float> y = graph_apply_h4<float, M>(w2, g.Rp, s, r4, x, S, g.row_ptr, g.col, w, eps, (float)g.U);
+    const int64_t i = (int64_t)s * g.Rp + r4;
+    C4<float> h = ld_c4_rw(psi + i), l = ld_c4_rw(lo + i);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {   // -i dt H w2
+        add(h.re[k], l.re[k], dt * y.im[k]);
+        add(h.im[k], l.im[k], -dt * y.re[k]);
+    }
+    st_c4(psi + i, h);
+    st_c4(lo + i, l);
 }
 
 template <typename T, int M>
@@ -231,16 +257,26 @@ __global__ void __launch_bounds__(kThreads) graph_taylor_term_kernel(GraphView g
                                                                      const cplx_t<T> *__restrict__ psi,
                                                                      cplx_t<T> *__restrict__ acc, T coef,
                                                                      int first) {
-    int s, r;
-    if (!graph_site(g, s, r)) return;
+    int s, r4;
+    if (!graph_site4(g, s, r4)) return;
     int x[M], S[M];
     graph_coords<M>(s, g.N, x, S);
-    const cplx_t<T> y = graph_apply_h<T, M>(in, g.R, s, r, x, S, g.row_ptr, g.col, w, eps, (T)g.U);
-    const int64_t i = (int64_t)s * g.R + r;
-    const cplx_t<T> phi = mk<T>(coef * y.y, -coef * y.x);   // -(i coef) y
-    out[i] = phi;
-    const cplx_t<T> a = first ? psi[i] : acc[i];
-    acc[i] = mk<T>(a.x + phi.x, a.y + phi.y);
+    const C4<T> y = graph_apply_h4<T, M>(in, g.Rp, s, r4, x, S, g.row_ptr, g.col, w, eps, (T)g.U);
+    const int64_t i = (int64_t)s * g.Rp + r4;
+    C4<T> phi;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {   // -(i coef) y
+        phi.re[k] = coef * y.im[k];
+        phi.im[k] = -coef * y.re[k];
+    }
+    st_c4(out + i, phi);
+    C4<T> a = first ? ld_c4_rw(psi + i) : ld_c4_rw(acc + i);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        a.re[k] += phi.re[k];
+        a.im[k] += phi.im[k];
+    }
+    st_c4(acc + i, a);
 }
 
 template <typename T, int M>
@@ -251,24 +287,32 @@ __global__ void __launch_bounds__(kThreads) graph_rk4_stage_kernel(GraphView g, 
                                                                    const cplx_t<T> *__restrict__ psi,
                                                                    cplx_t<T> *__restrict__ acc, T a, T b,
                                                                    int first) {
-    int s, r;
-    if (!graph_site(g, s, r)) return;
+    int s, r4;
+    if (!graph_site4(g, s, r4)) return;
     int x[M], S[M];
     graph_coords<M>(s, g.N, x, S);
-    const cplx_t<T> y = graph_apply_h<T, M>(in, g.R, s, r, x, S, g.row_ptr, g.col, w, eps, (T)g.U);
-    const int64_t i = (int64_t)s * g.R + r;
-    const cplx_t<T> k = mk<T>(y.y, -y.x);   // -i H in
-    const cplx_t<T> q = psi[i];
-    if (next) next[i] = mk<T>(q.x + a * k.x, q.y + a * k.y);
-    const cplx_t<T> c = first ? q : acc[i];
-    acc[i] = mk<T>(c.x + b * k.x, c.y + b * k.y);
+    const C4<T> y = graph_apply_h4<T, M>(in, g.Rp, s, r4, x, S, g.row_ptr, g.col, w, eps, (T)g.U);
+    const int64_t i = (int64_t)s * g.Rp + r4;
+    const C4<T> q = ld_c4_rw(psi + i);
+    C4<T> c = first ? q : ld_c4_rw(acc + i);
+    C4<T> nx;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {   // k = -i H in
+        const T kr = y.im[k], ki = -y.re[k];
+        nx.re[k] = q.re[k] + a * kr;
+        nx.im[k] = q.im[k] + a * ki;
+        c.re[k] += b * kr;
+        c.im[k] += b * ki;
+    }
+    if (next) st_c4(next + i, nx);
+    st_c4(acc + i, c);
 }
 
-// Observables of one sample.  Block (32 realizations) x (8 warps) owns
+// Observables of one sample.  Block (32 realization quads) x (8 warps) owns
 // kRows rows (fixed x_1..x_{m-1}) of the state; warp y walks the columns
-// x_m = y, y + 8, ...  Column sums of P reduce over the lanes (the
-// realizations) and go out with one atomic per column and block; row sums,
-// norms and energies reduce over the warps in shared memory.  All FP64.
+// x_m = y, y + 8, ...  Column sums of P reduce over the lanes and go out with
+// one atomic per column and block; row sums, norms and energies reduce over
+// the warps in shared memory.  All FP64.
 constexpr int kRows = 8;
 constexpr int kObsWarps = 8;
 
@@ -281,14 +325,14 @@ __global__ void __launch_bounds__(32 * kObsWarps) graph_observables_kernel(Graph
     const int n_rows = g.D / N;
     const int row0 = blockIdx.x * kRows;
     const int lane = threadIdx.x, wy = threadIdx.y;
-    const int r = g.r_begin + blockIdx.y * 32 + lane;
-    const bool valid = r < g.r_end;
-    const int rr = valid ? r : g.r_begin;   // a valid realization for the loads of idle lanes
+    const int r4 = g.r_begin + 4 * (blockIdx.y * 32 + lane);
+    const bool valid = r4 < g.r_end;
+    const int rr = valid ? r4 : g.r_begin;   // a valid quad for the loads of idle lanes
     const double scale = 1.0 / ((double)g.R * M);
     double rowpart[kRows];
 #pragma unroll
     for (int q = 0; q < kRows; ++q) rowpart[q] = 0.0;
-    double nrm = 0.0, en = 0.0;
+    double nrm[4] = {0.0, 0.0, 0.0, 0.0}, en[4] = {0.0, 0.0, 0.0, 0.0};
     for (int c = wy; c < N; c += kObsWarps) {
         double colacc = 0.0;
 #pragma unroll
@@ -296,18 +340,21 @@ __global__ void __launch_bounds__(32 * kObsWarps) graph_observables_kernel(Graph
             const int row = row0 + q;
             if (row < n_rows) {
                 const int s = row * N + c;
-                const cplx_t<T> v = psi[(int64_t)s * g.R + rr];
-                double p = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
-                if (!valid) p = 0.0;
-                colacc += p;
-                rowpart[q] += p;
-                nrm += p;
+                const C4<T> v = ld_c4(psi + (int64_t)s * g.Rp + rr);
+                C4<T> y;
                 if (energy) {
                     int x[M], S[M];
                     graph_coords<M>(s, N, x, S);
-                    const cplx_t<T> y = graph_apply_h<T, M>(psi, g.R, s, rr, x, S, g.row_ptr, g.col, w, eps,
-                                                            (T)g.U);
-                    if (valid) en += (double)v.x * (double)y.x + (double)v.y * (double)y.y;
+                    y = graph_apply_h4<T, M>(psi, g.Rp, s, rr, x, S, g.row_ptr, g.col, w, eps, (T)g.U);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    double p = (double)v.re[k] * (double)v.re[k] + (double)v.im[k] * (double)v.im[k];
+                    if (!valid) p = 0.0;
+                    colacc += p;
+                    rowpart[q] += p;
+                    nrm[k] += p;
+                    if (energy && valid) en[k] += (double)v.re[k] * (double)y.re[k] + (double)v.im[k] * (double)y.im[k];
                 }
             }
         }
@@ -315,29 +362,37 @@ __global__ void __launch_bounds__(32 * kObsWarps) graph_observables_kernel(Graph
         if (P && lane == 0) atomicAdd(P + c, colacc * scale);
     }
     __shared__ double red_row[kObsWarps][kRows];
-    __shared__ double red_r[2][kObsWarps][32];
+    __shared__ double red_r[2][kObsWarps][4][32];
 #pragma unroll
     for (int q = 0; q < kRows; ++q) {
         double v = rowpart[q];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) red_row[wy][q] = v;
     }
-    red_r[0][wy][lane] = nrm;
-    red_r[1][wy][lane] = en;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        red_r[0][wy][k][lane] = nrm[k];
+        red_r[1][wy][k][lane] = en[k];
+    }
     __syncthreads();
-    if (wy == 0) {
+    if (wy < 4) {
+        // warp k < 4 reduces realization r4 + k of every lane's quad
+        const int k = wy;
         double a = 0.0, b = 0.0;
-        for (int k = 0; k < kObsWarps; ++k) {
-            a += red_r[0][k][lane];
-            b += red_r[1][k][lane];
+        for (int u = 0; u < kObsWarps; ++u) {
+            a += red_r[0][u][k][lane];
+            b += red_r[1][u][k][lane];
         }
-        if (valid && norm) atomicAdd(norm + r, a);
-        if (valid && energy) atomicAdd(energy + r, b);
-    } else if (wy == 1 && lane < kRows && P) {
+        const int r = r4 + k;
+        if (valid && r < g.R) {
+            if (norm) atomicAdd(norm + r, a);
+            if (energy) atomicAdd(energy + r, b);
+        }
+    } else if (wy == 4 && lane < kRows && P) {
         const int row = row0 + lane;
         if (row < n_rows) {
             double v = 0.0;
-            for (int k = 0; k < kObsWarps; ++k) v += red_row[k][lane];
+            for (int u = 0; u < kObsWarps; ++u) v += red_row[u][lane];
             // coordinates x_1..x_{m-1} of this row
             int t = row;
             for (int j = M - 2; j >= 0; --j) {
@@ -353,9 +408,9 @@ struct Launch {
     dim3 grid, block;
 };
 
-// Threads: x over the chunk's realizations (up to 32), y over amplitudes.
+// Threads: x over the chunk's realization quads (up to 32), y over amplitudes.
 inline Launch graph_launch(const ctqw_graph *g, int rb, int re) {
-    const int n = re - rb;
+    const int n = (re - rb + 3) / 4;
     int rx = 1;
     while (rx < 32 && rx < n) rx <<= 1;
     const int ry = kThreads / rx;
@@ -366,6 +421,7 @@ inline Launch graph_launch(const ctqw_graph *g, int rb, int re) {
 }
 
 }  // namespace
+
 
 int launch_graph_build_params(const ctqw_graph *g, const double *u_eps_d, const double *u_J_d,
                               cudaStream_t s) {
@@ -447,7 +503,7 @@ int launch_graph_observables(const ctqw_graph *g, int rb, int re, int dtype, con
                              double *P_mean, double *norm, double *energy, cudaStream_t s) {
     if (!P_mean && !norm && !energy) return CTQW_OK;
     const int n_rows = (int)(g->D / g->N);
-    const dim3 grid((unsigned)((n_rows + kRows - 1) / kRows), (unsigned)((re - rb + 31) / 32));
+    const dim3 grid((unsigned)((n_rows + kRows - 1) / kRows), (unsigned)((re - rb + 127) / 128));
     const dim3 block(32, kObsWarps);
     if (dtype == CTQW_C64) {
         auto k = g->m == 2 ? graph_observables_kernel<float, 2> : graph_observables_kernel<float, 3>;

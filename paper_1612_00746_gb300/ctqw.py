@@ -288,7 +288,8 @@ class Graph:
         total = ctypes.c_int64()
         _check(lib.ctqw_graph_state_size(g, ctypes.byref(total)))
         self.total_amplitudes = int(total.value)
-        self.D = self.total_amplitudes // self.R
+        self.Rp = (self.R + 3) // 4 * 4
+        self.D = self.total_amplitudes // self.Rp
 
     @classmethod
     def from_workload(cls, w, realizations=None, stream=None) -> "Graph":
@@ -334,8 +335,8 @@ class Graph:
         return n_steps // obs_every + 1 if obs_every > 0 else 0
 
     def states(self, psi: torch.Tensor) -> torch.Tensor:
-        """[R][N^m] view-copy of a graph state (stored amplitude-major, s R + r)."""
-        return psi.reshape(self.D, self.R).t()
+        """[R][N^m] view of a graph state (stored amplitude-major, s Rp + r)."""
+        return psi.reshape(self.D, self.Rp)[:, :self.R].t()
 
 
 def ctqw_graph_set_chunk(g: Graph, realizations: int) -> None:
