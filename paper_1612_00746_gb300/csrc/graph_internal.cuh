@@ -20,10 +20,10 @@
 // = R rounded up to a multiple of 4.  The states are psi[s][r] (amplitude s
 // of realization r at s Rp + r), the on-site energies eps[i][r] and the
 // hoppings in CSR order w[k][r] = J_r(link of entry k); padding realizations
-// carry zero parameters and zero states.  A thread owns four adjacent
-// realizations of one amplitude (16-byte vector loads), a warp 128, so every
-// CSR lookup is uniform across the warp and every neighbour load is one
-// coalesced row.
+// carry zero parameters and zero states.  A thread owns four realizations
+// of one amplitude in two pairs (16-byte loads, each contiguous across the
+// warp), a warp 128, so every CSR lookup is uniform across the warp and
+// every neighbour load is one coalesced row.
 struct ctqw_graph {
     int m = 0, statistics = 0, N = 0, E = 0, R = 0, round_to_f32 = 1;
     double J0 = 1.0, U = 0.0, eps_hw = 0.0, J_hw = 0.0;

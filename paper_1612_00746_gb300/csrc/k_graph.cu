@@ -9,11 +9,12 @@
 //   (H a)(s) = (sum_j eps[x_j] + U pairs) a(s) - sum_j sum_{k in row x_j} w_k a(s + (col_k - x_j) S_j),
 // the CSR row of node x_j giving the neighbours col_k and their hoppings w_k.
 // Realizations are the fastest index of every array (psi[s][r], eps[i][r],
-// w[k][r], stride Rp a multiple of 4).  A thread owns four adjacent
-// realizations of one amplitude and moves them with 16-byte loads; threadIdx.x
-// walks realization quads, threadIdx.y amplitudes.  The CSR lookups and the
-// index arithmetic of a neighbour are then shared by four amplitudes and
-// uniform across the warp, and each neighbour read is one coalesced row.
+// w[k][r], stride Rp a multiple of 4).  A thread owns four realizations of
+// one amplitude in two adjacent pairs, ra = b + 2 l and rb = ra + 2 X (lane
+// l of X lanes, b the first realization of the warp's group of 4X), so each
+// 16-byte complex-pair load is contiguous across the warp; threadIdx.y walks
+// amplitudes.  The CSR lookups and the index arithmetic of a neighbour are
+// shared by four amplitudes and uniform across the warp.
 #include <algorithm>
 
 #include "graph_internal.cuh"
@@ -23,41 +24,59 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Four adjacent realizations of one complex amplitude / one real parameter.
+// Four realizations (pairs ra, ra+1 and rb, rb+1) of one complex amplitude
+// or one real parameter; p points at realization 0 of the row.
 template <typename T> struct C4 { T re[4], im[4]; };
 template <typename T> struct R4 { T v[4]; };
 
-__device__ __forceinline__ C4<float> ld_c4(const float2 *__restrict__ p) {
-    const float4 u = __ldg(reinterpret_cast<const float4 *>(p)), v = __ldg(reinterpret_cast<const float4 *>(p) + 1);
-    return C4<float>{{u.x, u.z, v.x, v.z}, {u.y, u.w, v.y, v.w}};
+// The thread's two pairs: offsets ra, rb and whether the second pair exists.
+struct Pairs {
+    int ra, rb;
+    bool vb;
+};
+
+__device__ __forceinline__ void put2(C4<float> &c, int h, float4 u) {
+    c.re[2 * h] = u.x; c.im[2 * h] = u.y; c.re[2 * h + 1] = u.z; c.im[2 * h + 1] = u.w;
 }
-__device__ __forceinline__ C4<double> ld_c4(const double2 *__restrict__ p) {
-    const double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3);
+__device__ __forceinline__ C4<float> ld_c4(const float2 *__restrict__ p, const Pairs &q) {
+    C4<float> c;
+    put2(c, 0, __ldg(reinterpret_cast<const float4 *>(p + q.ra)));
+    put2(c, 1, __ldg(reinterpret_cast<const float4 *>(p + q.rb)));
+    return c;
+}
+__device__ __forceinline__ C4<double> ld_c4(const double2 *__restrict__ p, const Pairs &q) {
+    const double2 a = __ldg(p + q.ra), b = __ldg(p + q.ra + 1), c = __ldg(p + q.rb), d = __ldg(p + q.rb + 1);
     return C4<double>{{a.x, b.x, c.x, d.x}, {a.y, b.y, c.y, d.y}};
 }
 // the same through the coherent path (arrays the kernel also writes)
-__device__ __forceinline__ C4<float> ld_c4_rw(const float2 *p) {
-    const float4 u = reinterpret_cast<const float4 *>(p)[0], v = reinterpret_cast<const float4 *>(p)[1];
-    return C4<float>{{u.x, u.z, v.x, v.z}, {u.y, u.w, v.y, v.w}};
+__device__ __forceinline__ C4<float> ld_c4_rw(const float2 *p, const Pairs &q) {
+    C4<float> c;
+    put2(c, 0, *reinterpret_cast<const float4 *>(p + q.ra));
+    put2(c, 1, *reinterpret_cast<const float4 *>(p + q.rb));
+    return c;
 }
-__device__ __forceinline__ C4<double> ld_c4_rw(const double2 *p) {
-    const double2 a = p[0], b = p[1], c = p[2], d = p[3];
+__device__ __forceinline__ C4<double> ld_c4_rw(const double2 *p, const Pairs &q) {
+    const double2 a = p[q.ra], b = p[q.ra + 1], c = p[q.rb], d = p[q.rb + 1];
     return C4<double>{{a.x, b.x, c.x, d.x}, {a.y, b.y, c.y, d.y}};
 }
-__device__ __forceinline__ void st_c4(float2 *p, const C4<float> &c) {
-    reinterpret_cast<float4 *>(p)[0] = make_float4(c.re[0], c.im[0], c.re[1], c.im[1]);
-    reinterpret_cast<float4 *>(p)[1] = make_float4(c.re[2], c.im[2], c.re[3], c.im[3]);
+__device__ __forceinline__ void st_c4(float2 *p, const Pairs &q, const C4<float> &c) {
+    *reinterpret_cast<float4 *>(p + q.ra) = make_float4(c.re[0], c.im[0], c.re[1], c.im[1]);
+    if (q.vb) *reinterpret_cast<float4 *>(p + q.rb) = make_float4(c.re[2], c.im[2], c.re[3], c.im[3]);
 }
-__device__ __forceinline__ void st_c4(double2 *p, const C4<double> &c) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) p[q] = make_double2(c.re[q], c.im[q]);
+__device__ __forceinline__ void st_c4(double2 *p, const Pairs &q, const C4<double> &c) {
+    p[q.ra] = make_double2(c.re[0], c.im[0]);
+    p[q.ra + 1] = make_double2(c.re[1], c.im[1]);
+    if (q.vb) {
+        p[q.rb] = make_double2(c.re[2], c.im[2]);
+        p[q.rb + 1] = make_double2(c.re[3], c.im[3]);
+    }
 }
-__device__ __forceinline__ R4<float> ld_r4(const float *__restrict__ p) {
-    const float4 u = __ldg(reinterpret_cast<const float4 *>(p));
-    return R4<float>{{u.x, u.y, u.z, u.w}};
+__device__ __forceinline__ R4<float> ld_r4(const float *__restrict__ p, const Pairs &q) {
+    const float2 a = __ldg(reinterpret_cast<const float2 *>(p + q.ra)), b = __ldg(reinterpret_cast<const float2 *>(p + q.rb));
+    return R4<float>{{a.x, a.y, b.x, b.y}};
 }
-__device__ __forceinline__ R4<double> ld_r4(const double *__restrict__ p) {
-    const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+__device__ __forceinline__ R4<double> ld_r4(const double *__restrict__ p, const Pairs &q) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p + q.ra)), b = __ldg(reinterpret_cast<const double2 *>(p + q.rb));
     return R4<double>{{a.x, a.y, b.x, b.y}};
 }
 
@@ -74,9 +93,9 @@ __device__ __forceinline__ void graph_coords(int s, int N, int (&x)[M], int (&S)
     }
 }
 
-// (H a)(s) for the four realizations r4..r4+3; Rp is the realization stride.
+// (H a)(s) for the thread's four realizations; Rp is the realization stride.
 template <typename T, int M>
-__device__ __forceinline__ C4<T> graph_apply_h4(const cplx_t<T> *a, int64_t Rp, int s, int r4,
+__device__ __forceinline__ C4<T> graph_apply_h4(const cplx_t<T> *a, int64_t Rp, int s, const Pairs &pr,
                                                 const int (&x)[M], const int (&S)[M],
                                                 const int32_t *__restrict__ row_ptr,
                                                 const int32_t *__restrict__ col, const T *__restrict__ w,
@@ -91,11 +110,11 @@ __device__ __forceinline__ C4<T> graph_apply_h4(const cplx_t<T> *a, int64_t Rp, 
     for (int q = 0; q < 4; ++q) v.v[q] = U * T(pairs);
 #pragma unroll
     for (int j = 0; j < M; ++j) {
-        const R4<T> e = ld_r4(eps + (int64_t)x[j] * Rp + r4);
+        const R4<T> e = ld_r4(eps + (int64_t)x[j] * Rp, pr);
 #pragma unroll
         for (int q = 0; q < 4; ++q) v.v[q] += e.v[q];
     }
-    const C4<T> c = ld_c4(a + (int64_t)s * Rp + r4);
+    const C4<T> c = ld_c4(a + (int64_t)s * Rp, pr);
     C4<T> y;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -106,12 +125,11 @@ __device__ __forceinline__ C4<T> graph_apply_h4(const cplx_t<T> *a, int64_t Rp, 
     for (int j = 0; j < M; ++j) {
         const int k0 = row_ptr[x[j]], k1 = row_ptr[x[j] + 1];
         const int64_t step = (int64_t)S[j] * Rp;                       // one node along coordinate j
-        const cplx_t<T> *base = a + (int64_t)(s - x[j] * S[j]) * Rp + r4;   // coordinate j at node 0
-        const T *wr = w + r4;
+        const cplx_t<T> *base = a + (int64_t)(s - x[j] * S[j]) * Rp;   // coordinate j at node 0
 #pragma unroll 4
         for (int k = k0; k < k1; ++k) {
-            const R4<T> t = ld_r4(wr + (int64_t)k * Rp);
-            const C4<T> n = ld_c4(base + (int64_t)col[k] * step);
+            const R4<T> t = ld_r4(w + (int64_t)k * Rp, pr);
+            const C4<T> n = ld_c4(base + (int64_t)col[k] * step, pr);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 y.re[q] -= t.v[q] * n.re[q];
@@ -122,11 +140,17 @@ __device__ __forceinline__ C4<T> graph_apply_h4(const cplx_t<T> *a, int64_t Rp, 
     return y;
 }
 
-// (amplitude, first realization of the quad) of this thread, false past the ends.
-__device__ __forceinline__ bool graph_site4(const GraphView &g, int &s, int &r4) {
+// Amplitude and realization pairs of this thread, false past the ends.  A
+// second pair past the end repeats the first (its loads stay in bounds) and
+// is not stored.
+__device__ __forceinline__ bool graph_site4(const GraphView &g, int &s, Pairs &pr) {
     s = blockIdx.x * blockDim.y + threadIdx.y;
-    r4 = g.r_begin + 4 * (blockIdx.y * blockDim.x + threadIdx.x);
-    return s < g.D && r4 < g.r_end;
+    const int b = g.r_begin + 4 * blockIdx.y * blockDim.x;
+    pr.ra = b + 2 * threadIdx.x;
+    pr.rb = pr.ra + 2 * blockDim.x;
+    pr.vb = pr.rb < g.r_end;
+    if (!pr.vb) pr.rb = pr.ra;
+    return s < g.D && pr.ra < g.r_end;
 }
 
 __device__ __forceinline__ double graph_param(double mean, double hw, double u, int round_f32) {
@@ -200,20 +224,21 @@ __global__ void __launch_bounds__(kThreads) graph_horner_stage_kernel(GraphView 
                                                                       const float2 *__restrict__ in,
                                                                       const float2 *__restrict__ psi,
                                                                       float2 *__restrict__ out, float coef) {
-    int s, r4;
-    if (!graph_site4(g, s, r4)) return;
+    int s;
+    Pairs pr;
+    if (!graph_site4(g, s, pr)) return;
     int x[M], S[M];
     graph_coords<M>(s, g.N, x, S);
-    const C4<float> y = graph_apply_h4<float, M>(in, g.Rp, s, r4, x, S, g.row_ptr, g.col, w, eps, (float)g.U);
-    const int64_t i = (int64_t)s * g.Rp + r4;
-    const C4<float> q = ld_c4(psi + i);
+    const C4<float> y = graph_apply_h4<float, M>(in, g.Rp, s, pr, x, S, g.row_ptr, g.col, w, eps, (float)g.U);
+    const int64_t i = (int64_t)s * g.Rp;
+    const C4<float> q = ld_c4(psi + i, pr);
     C4<float> o;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {   // q + coef (-i) y
         o.re[k] = fmaf(coef, y.im[k], q.re[k]);
         o.im[k] = fmaf(-coef, y.re[k], q.im[k]);
     }
-    st_c4(out + i, o);
+    st_c4(out + i, pr, o);
 }
 
 template <int M>
@@ -222,8 +247,9 @@ __global__ void __launch_bounds__(kThreads) graph_horner_final_kernel(GraphView 
                                                                       const float2 *__restrict__ w2,
                                                                       float2 *__restrict__ psi,
                                                                       float2 *__restrict__ lo, float dt) {
-    int s, r4;
-    if (!graph_site4(g, s, r4)) return;
+    int s;
+    Pairs pr;
+    if (!graph_site4(g, s, pr)) return;
     int x[M], S[M];
     graph_coords<M>(s, g.N, x, S);
     // TwoSum then FastTwoSum per component: the state's rounding error is
@@ -237,16 +263,16 @@ __global__ void __launch_bounds__(kThreads) graph_horner_final_kernel(GraphView 
         lw = __fsub_rn(e, __fsub_rn(h2, t));
         hi = h2;
     };
-    const C4<float> y = graph_apply_h4<float, M>(w2, g.Rp, s, r4, x, S, g.row_ptr, g.col, w, eps, (float)g.U);
-    const int64_t i = (int64_t)s * g.Rp + r4;
-    C4<float> h = ld_c4_rw(psi + i), l = ld_c4_rw(lo + i);
+    const C4<float> y = graph_apply_h4<float, M>(w2, g.Rp, s, pr, x, S, g.row_ptr, g.col, w, eps, (float)g.U);
+    const int64_t i = (int64_t)s * g.Rp;
+    C4<float> h = ld_c4_rw(psi + i, pr), l = ld_c4_rw(lo + i, pr);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {   // -i dt H w2
         add(h.re[k], l.re[k], dt * y.im[k]);
         add(h.im[k], l.im[k], -dt * y.re[k]);
     }
-    st_c4(psi + i, h);
-    st_c4(lo + i, l);
+    st_c4(psi + i, pr, h);
+    st_c4(lo + i, pr, l);
 }
 
 template <typename T, int M>
@@ -257,26 +283,27 @@ __global__ void __launch_bounds__(kThreads) graph_taylor_term_kernel(GraphView g
                                                                      const cplx_t<T> *__restrict__ psi,
                                                                      cplx_t<T> *__restrict__ acc, T coef,
                                                                      int first) {
-    int s, r4;
-    if (!graph_site4(g, s, r4)) return;
+    int s;
+    Pairs pr;
+    if (!graph_site4(g, s, pr)) return;
     int x[M], S[M];
     graph_coords<M>(s, g.N, x, S);
-    const C4<T> y = graph_apply_h4<T, M>(in, g.Rp, s, r4, x, S, g.row_ptr, g.col, w, eps, (T)g.U);
-    const int64_t i = (int64_t)s * g.Rp + r4;
+    const C4<T> y = graph_apply_h4<T, M>(in, g.Rp, s, pr, x, S, g.row_ptr, g.col, w, eps, (T)g.U);
+    const int64_t i = (int64_t)s * g.Rp;
     C4<T> phi;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {   // -(i coef) y
         phi.re[k] = coef * y.im[k];
         phi.im[k] = -coef * y.re[k];
     }
-    st_c4(out + i, phi);
-    C4<T> a = first ? ld_c4_rw(psi + i) : ld_c4_rw(acc + i);
+    st_c4(out + i, pr, phi);
+    C4<T> a = first ? ld_c4_rw(psi + i, pr) : ld_c4_rw(acc + i, pr);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         a.re[k] += phi.re[k];
         a.im[k] += phi.im[k];
     }
-    st_c4(acc + i, a);
+    st_c4(acc + i, pr, a);
 }
 
 template <typename T, int M>
@@ -287,14 +314,15 @@ __global__ void __launch_bounds__(kThreads) graph_rk4_stage_kernel(GraphView g, 
                                                                    const cplx_t<T> *__restrict__ psi,
                                                                    cplx_t<T> *__restrict__ acc, T a, T b,
                                                                    int first) {
-    int s, r4;
-    if (!graph_site4(g, s, r4)) return;
+    int s;
+    Pairs pr;
+    if (!graph_site4(g, s, pr)) return;
     int x[M], S[M];
     graph_coords<M>(s, g.N, x, S);
-    const C4<T> y = graph_apply_h4<T, M>(in, g.Rp, s, r4, x, S, g.row_ptr, g.col, w, eps, (T)g.U);
-    const int64_t i = (int64_t)s * g.Rp + r4;
-    const C4<T> q = ld_c4_rw(psi + i);
-    C4<T> c = first ? q : ld_c4_rw(acc + i);
+    const C4<T> y = graph_apply_h4<T, M>(in, g.Rp, s, pr, x, S, g.row_ptr, g.col, w, eps, (T)g.U);
+    const int64_t i = (int64_t)s * g.Rp;
+    const C4<T> q = ld_c4_rw(psi + i, pr);
+    C4<T> c = first ? q : ld_c4_rw(acc + i, pr);
     C4<T> nx;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {   // k = -i H in
@@ -304,8 +332,8 @@ __global__ void __launch_bounds__(kThreads) graph_rk4_stage_kernel(GraphView g, 
         c.re[k] += b * kr;
         c.im[k] += b * ki;
     }
-    if (next) st_c4(next + i, nx);
-    st_c4(acc + i, c);
+    if (next) st_c4(next + i, pr, nx);
+    st_c4(acc + i, pr, c);
 }
 
 // Observables of one sample.  Block (32 realization quads) x (8 warps) owns
@@ -325,9 +353,14 @@ __global__ void __launch_bounds__(32 * kObsWarps) graph_observables_kernel(Graph
     const int n_rows = g.D / N;
     const int row0 = blockIdx.x * kRows;
     const int lane = threadIdx.x, wy = threadIdx.y;
-    const int r4 = g.r_begin + 4 * (blockIdx.y * 32 + lane);
-    const bool valid = r4 < g.r_end;
-    const int rr = valid ? r4 : g.r_begin;   // a valid quad for the loads of idle lanes
+    // realization pairs as in graph_site4 (32 lanes); idle lanes load a valid pair
+    Pairs pr;
+    pr.ra = g.r_begin + 128 * blockIdx.y + 2 * lane;
+    pr.rb = pr.ra + 64;
+    const bool valid = pr.ra < g.r_end;
+    pr.vb = pr.rb < g.r_end;
+    if (!valid) pr.ra = g.r_begin;
+    if (!pr.vb) pr.rb = pr.ra;
     const double scale = 1.0 / ((double)g.R * M);
     double rowpart[kRows];
 #pragma unroll
@@ -340,21 +373,22 @@ __global__ void __launch_bounds__(32 * kObsWarps) graph_observables_kernel(Graph
             const int row = row0 + q;
             if (row < n_rows) {
                 const int s = row * N + c;
-                const C4<T> v = ld_c4(psi + (int64_t)s * g.Rp + rr);
+                const C4<T> v = ld_c4(psi + (int64_t)s * g.Rp, pr);
                 C4<T> y;
                 if (energy) {
                     int x[M], S[M];
                     graph_coords<M>(s, N, x, S);
-                    y = graph_apply_h4<T, M>(psi, g.Rp, s, rr, x, S, g.row_ptr, g.col, w, eps, (T)g.U);
+                    y = graph_apply_h4<T, M>(psi, g.Rp, s, pr, x, S, g.row_ptr, g.col, w, eps, (T)g.U);
                 }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
+                    const bool vk = valid && (k < 2 || pr.vb);
                     double p = (double)v.re[k] * (double)v.re[k] + (double)v.im[k] * (double)v.im[k];
-                    if (!valid) p = 0.0;
+                    if (!vk) p = 0.0;
                     colacc += p;
                     rowpart[q] += p;
                     nrm[k] += p;
-                    if (energy && valid) en[k] += (double)v.re[k] * (double)y.re[k] + (double)v.im[k] * (double)y.im[k];
+                    if (energy && vk) en[k] += (double)v.re[k] * (double)y.re[k] + (double)v.im[k] * (double)y.im[k];
                 }
             }
         }
@@ -376,15 +410,15 @@ __global__ void __launch_bounds__(32 * kObsWarps) graph_observables_kernel(Graph
     }
     __syncthreads();
     if (wy < 4) {
-        // warp k < 4 reduces realization r4 + k of every lane's quad
+        // warp k < 4 reduces realization k of every lane's two pairs
         const int k = wy;
         double a = 0.0, b = 0.0;
         for (int u = 0; u < kObsWarps; ++u) {
             a += red_r[0][u][k][lane];
             b += red_r[1][u][k][lane];
         }
-        const int r = r4 + k;
-        if (valid && r < g.R) {
+        const int r = (k < 2 ? pr.ra : pr.rb) + (k & 1);
+        if (valid && (k < 2 || pr.vb) && r < g.R) {
             if (norm) atomicAdd(norm + r, a);
             if (energy) atomicAdd(energy + r, b);
         }
