@@ -219,7 +219,7 @@ __global__ void graph_init_state_kernel(GraphView g, const int32_t *__restrict__
 }
 
 template <int M>
-__global__ void __launch_bounds__(kThreads) graph_horner_stage_kernel(GraphView g, const float *__restrict__ eps,
+__global__ void __launch_bounds__(kThreads, 6) graph_horner_stage_kernel(GraphView g, const float *__restrict__ eps,
                                                                       const float *__restrict__ w,
                                                                       const float2 *__restrict__ in,
                                                                       const float2 *__restrict__ psi,
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kThreads) graph_horner_stage_kernel(GraphView 
 }
 
 template <int M>
-__global__ void __launch_bounds__(kThreads) graph_horner_final_kernel(GraphView g, const float *__restrict__ eps,
+__global__ void __launch_bounds__(kThreads, 6) graph_horner_final_kernel(GraphView g, const float *__restrict__ eps,
                                                                       const float *__restrict__ w,
                                                                       const float2 *__restrict__ w2,
                                                                       float2 *__restrict__ psi,
