@@ -71,3 +71,46 @@ def test_combine_means_single_process_is_identity():
     out = combine_means(P, c)
     np.testing.assert_allclose(out[:, :4].numpy(), P[:, :4].numpy())
     assert torch.all(out[:, 4] == 0)
+
+
+def _graph_worker(rank, world, port, q):
+    # each rank propagates its shard of a graph ensemble (the oracle stands in
+    # for the per-rank GPU work) and the ranks combine their P means
+    import ctqw_workloads as cw
+    import oracle
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w = cw.get_graph("graph_small").with_(R=5, n_steps=20, obs_every=10)
+        ids = shard_realizations(w.R, world, rank)
+        out = oracle.graph_ensemble_run(w, realizations=ids)
+        counts = torch.full((w.n_nodes(),), float(len(ids)), dtype=torch.float64)
+        got = combine_means(torch.tensor(out["P"], dtype=torch.float64), counts)
+        q.put((rank, got.numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_graph_ensemble_sharded_over_two_ranks_gloo():
+    """Realization draws depend on the realization id only, so two ranks with
+    disjoint shards reproduce the one-process ensemble mean of a graph
+    workload (5 realizations: shards of 3 and 2)."""
+    import ctqw_workloads as cw
+    import oracle
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_graph_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted([q.get(timeout=180) for _ in procs], key=lambda x: x[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    w = cw.get_graph("graph_small").with_(R=5, n_steps=20, obs_every=10)
+    full = oracle.graph_ensemble_run(w)["P"]
+    for _, got in res:
+        np.testing.assert_allclose(got, full, rtol=0, atol=1e-14)
