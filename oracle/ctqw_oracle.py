@@ -301,11 +301,14 @@ def n_samples(n_steps, obs_every):
 
 
 def propagate(H, psi0, N, m, dt, n_steps, obs_every, method="taylor", K=16,
-              keep_states=False):
+              keep_states=False, renormalize=False):
     """Propagate one realization, sampling P(x), norm and energy.
 
     Samples are taken at steps 0, obs_every, 2*obs_every, ... <= n_steps
     (reading of "averaged every 10 steps": samples in time, not a time mean).
+    With renormalize, the state is divided by its norm after every step: the
+    corrective action that the norm check of Algorithms 2 and 3 calls for
+    (Sec. 2.2: RK4 does not conserve the norm).
     """
     psi = np.array(psi0, dtype=np.complex128)
     P, nr, en, states = [], [], [], [psi.copy()] if keep_states else None
@@ -322,6 +325,8 @@ def propagate(H, psi0, N, m, dt, n_steps, obs_every, method="taylor", K=16,
             psi = rk4_step(H, psi, dt)
         else:
             raise ValueError(method)
+        if renormalize:
+            psi = psi / np.sqrt(norm(psi))
         if keep_states:
             states.append(psi.copy())
     out = {"P": np.array(P), "norm": np.array(nr), "energy": np.array(en), "psi": psi}
@@ -340,7 +345,7 @@ def workload_parameters(w, u_eps, u_J, N, eps_mean=None, J_mean=None, round_to_f
 
 
 def ensemble_run(w, realizations=None, method="taylor", K=None, n_steps=None,
-                 obs_every=None, eps_mean=None, J_mean=None):
+                 obs_every=None, eps_mean=None, J_mean=None, renormalize=False):
     """Propagate the listed realizations of a workload and average P(x).
 
     Algorithm 3 per realization, then the diagonal of <rho> = (1/R) sum_i
@@ -367,7 +372,8 @@ def ensemble_run(w, realizations=None, method="taylor", K=None, n_steps=None,
         eps, J = workload_parameters(w, ue[k], uj[k], N, eps_mean, J_mean)
         H = many_particle_hamiltonian(single_particle_hamiltonian(eps, J, w.periodic), w.m, w.U)
         psi0 = initial_state(N, w.m, w.initial_sites(N), w.statistics)
-        res = propagate(H, psi0, N, w.m, w.dt, n_steps, obs_every, method, K)
+        res = propagate(H, psi0, N, w.m, w.dt, n_steps, obs_every, method, K,
+                        renormalize=renormalize)
         per_P.append(res["P"])
         per_norm.append(res["norm"])
         per_energy.append(res["energy"])

@@ -485,3 +485,22 @@ def test_switching_conserves_norm_and_keeps_bosonic_symmetry():
     static = O.ensemble_run(w)
     assert np.max(np.abs(res["P"][-1] - static["P"][0][-1])) > 1e-6
     assert np.all(np.abs(res["eps"]) <= w.eps_halfwidth)
+
+
+@pytest.mark.parametrize("method", ["rk4", "taylor"])
+def test_renormalized_propagation_is_the_state_over_its_norm(method):
+    # H is linear, so dividing by the norm after every step gives the
+    # unrenormalized state divided by its norm (closed form); a coarse dt
+    # makes RK4 lose norm visibly first
+    rng = np.random.default_rng(11)
+    N, m, dt, steps = 9, 2, 0.3, 40
+    eps, J = _rand_params(rng, N, False)
+    H = O.many_particle_hamiltonian(O.single_particle_hamiltonian(eps, J, False), m, 1.5)
+    psi0 = O.initial_state(N, m, (3, 5), 1)
+    raw = O.propagate(H, psi0, N, m, dt, steps, 1, method, 4, keep_states=True)
+    ren = O.propagate(H, psi0, N, m, dt, steps, 1, method, 4, keep_states=True, renormalize=True)
+    assert abs(raw["norm"][-1] - 1.0) > 1e-6          # the correction has something to correct
+    np.testing.assert_allclose(ren["norm"], 1.0, atol=1e-13)
+    for a, b in zip(raw["states"], ren["states"]):
+        np.testing.assert_allclose(b, a / np.sqrt(O.norm(a)), atol=1e-13)
+    np.testing.assert_allclose(ren["P"], raw["P"] / raw["norm"][:, None], atol=1e-13)
