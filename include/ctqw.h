@@ -57,6 +57,11 @@ extern "C" {
 /* Propagation flags. */
 #define CTQW_FLAG_PLAIN 0x1            /* force the per-term path (one launch per Taylor term) */
 #define CTQW_FLAG_NO_COMPENSATION 0x2  /* c64 fused path: plain FP32 state update (no carried error term) */
+#define CTQW_FLAG_RENORMALIZE 0x4      /* after every step divide each realization's state (and its carried
+                                          error word) by its norm: the corrective action of the norm check of
+                                          Algorithms 2 and 3 (Sec. 2.2: RK4 does not conserve the norm).  Runs
+                                          on the per-term path (workspace as CTQW_FLAG_PLAIN), two extra
+                                          launches per step; sampled norms are then 1 up to rounding */
 #define CTQW_FLAG_TEST_WAIT_TIMEOUT 0x8 /* failure-path test: the fused kernel first waits on an mbarrier that
                                            nothing completes, gives up after 1 ms and flags the handle */
 /* Fused path tuning: CTQW_FUSED_SHAPE(k) selects a compiled CTA/cluster shape

@@ -20,7 +20,7 @@ int64_t n_samples(int64_t n_steps, int obs_every) {
 
 void free_device(ctqw_hamiltonian *h) {
     void *ptrs[] = {h->eps32, h->J32, h->eps64, h->J64, h->sizes_d, h->group_of_d, h->par_off_d,
-                    h->st_off_d, h->group_off_d, h->joint_off_d, h->inv_count_d, h->status_d,
+                    h->st_off_d, h->group_off_d, h->joint_off_d, h->inv_count_d, h->status_d, h->renorm_d,
                     h->by_group_d, h->eps_mean_d, h->J_mean_d, h->eps64_0, h->J64_0};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -258,7 +258,8 @@ int ctqw_build_hamiltonian(const ctqw_lattice_desc *d, void *stream, ctqw_hamilt
         cudaMalloc(&h->J32, sizeof(float) * h->total_par) != cudaSuccess ||
         cudaMalloc(&h->eps64, pb) != cudaSuccess || cudaMalloc(&h->J64, pb) != cudaSuccess ||
         cudaMalloc(&u_eps_d, pb) != cudaSuccess || cudaMalloc(&u_J_d, pb) != cudaSuccess ||
-        cudaMalloc(&h->status_d, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&h->status_d, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&h->renorm_d, sizeof(double) * h->R) != cudaSuccess) {
         ctqw_set_error("cudaMalloc of the parameter arrays failed");
         return fail(CTQW_ENOMEM);
     }
@@ -425,6 +426,7 @@ int ctqw_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t method
     if (!h || !bytes) { ctqw_set_error("null argument"); return CTQW_EINVAL; }
     if (dtype != CTQW_C64 && dtype != CTQW_C128) { ctqw_set_error("dtype %d", dtype); return CTQW_EINVAL; }
     const int shape = (int)((flags >> CTQW_FUSED_SHAPE_SHIFT) & 0xF);
+    if (flags & CTQW_FLAG_RENORMALIZE) flags |= CTQW_FLAG_PLAIN;   // renormalized runs are per-term
     if ((method == 0 || method == 1) && !(flags & CTQW_FLAG_PLAIN) && shape == CTQW_SHAPE_WAVEFRONT &&
         dtype == CTQW_C64) {
         *bytes = wavefront_workspace_bytes(h);
@@ -485,6 +487,7 @@ struct SwitchSpec {
     bool on = false;
     uint64_t seed = 0;
     double p = 0.0;
+    bool renorm = false;   // divide every state by its norm after each step
 };
 
 // One launch per Taylor term (c128, forward order of Algorithm 3) or per
@@ -521,6 +524,7 @@ static int propagate_per_term(const ctqw_hamiltonian *h, int32_t dtype, void *ps
                 out = (out == wa) ? wb : wa;
             }
             CTQW_TRY(launch_horner_final(h, in, psi_dev, lo, dt, s));
+            if (sw.renorm) CTQW_TRY(launch_renormalize(h, dtype, psi_dev, lo, s));
             if (sw.on) CTQW_TRY(launch_switch_params(h, sw.seed, (uint64_t)step, sw.p, s));
         }
         return CTQW_OK;
@@ -543,6 +547,7 @@ static int propagate_per_term(const ctqw_hamiltonian *h, int32_t dtype, void *ps
             out = (out == phi1) ? phi2 : phi1;
         }
         std::swap(cur, acc);
+        if (sw.renorm) CTQW_TRY(launch_renormalize(h, dtype, cur, nullptr, s));
         if (sw.on) CTQW_TRY(launch_switch_params(h, sw.seed, (uint64_t)step, sw.p, s));
     }
     if (cur != psi_dev) CTQW_CUDA_TRY(cudaMemcpyAsync(psi_dev, cur, sb, cudaMemcpyDeviceToDevice, s));
@@ -612,6 +617,19 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
     if (K < 1 || K > 30) { ctqw_set_error("K must be in 1..30, or 0 (got %d)", K); return CTQW_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n_obs = n_samples(n_steps, obs_every);
+    if (flags & CTQW_FLAG_RENORMALIZE) {
+        // the norm correction runs between steps: one launch per term
+        const size_t need = 3 * (size_t)h->total_amp * elem_bytes(dtype);
+        if (!workspace_dev || workspace_bytes < need) {
+            ctqw_set_error("CTQW_FLAG_RENORMALIZE needs a workspace of %zu bytes (got %zu)", need, workspace_bytes);
+            return CTQW_EINVAL;
+        }
+        CTQW_TRY(zero_outputs(h, n_obs, P_mean_dev, norm_dev, energy_dev, s));
+        SwitchSpec sw;
+        sw.renorm = true;
+        return propagate_per_term(h, dtype, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
+                                  energy_dev, workspace_dev, s, sw);
+    }
     const int shape = (int)((flags >> CTQW_FUSED_SHAPE_SHIFT) & 0xF);
     if (!(flags & CTQW_FLAG_PLAIN) && shape == CTQW_SHAPE_WAVEFRONT)
         return propagate_wavefront(h, dtype, psi_dev, dt, K, n_steps, obs_every, P_mean_dev,
@@ -742,7 +760,7 @@ int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, 
     cudaStream_t s = (cudaStream_t)stream;
     // RK4's update map is the order-4 Taylor polynomial of exp(-i H dt)
     // (Sec. 2.3): the fused kernel evaluates it directly
-    if (!(flags & CTQW_FLAG_PLAIN) && fused_rows_supported(h, dtype))
+    if (!(flags & (CTQW_FLAG_PLAIN | CTQW_FLAG_RENORMALIZE)) && fused_rows_supported(h, dtype))
         return ctqw_propagate_taylor(h, dtype, psi_dev, dt, 4, n_steps, obs_every, P_mean_dev,
                                      norm_dev, energy_dev, flags, workspace_dev, workspace_bytes,
                                      stream);
@@ -769,6 +787,8 @@ int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, 
         // K4 = -iH(psi + dt K3): acc += dt/6 K4
         CTQW_TRY(launch_rk4_stage(h, dtype, t1, nullptr, cur, acc, 0.0, dt / 6.0, 0, s));
         std::swap(cur, acc);
+        // the corrective action of the norm check (RK4 does not conserve the norm)
+        if (flags & CTQW_FLAG_RENORMALIZE) CTQW_TRY(launch_renormalize(h, dtype, cur, nullptr, s));
     }
     if (cur != psi_dev) CTQW_CUDA_TRY(cudaMemcpyAsync(psi_dev, cur, sb, cudaMemcpyDeviceToDevice, s));
     return CTQW_OK;

@@ -38,6 +38,7 @@ struct ctqw_hamiltonian {
     double *eps_mean_d = nullptr, *J_mean_d = nullptr;   // [Nmax] or null (0 / J0)
     double *eps64_0 = nullptr, *J64_0 = nullptr;         // [total_par] as built
     int *status_d = nullptr;        // nonzero after a kernel's bounded wait gave up
+    double *renorm_d = nullptr;     // [R] norms of the per-step renormalization
 };
 
 // Per-launch view of the realization table (passed by value to kernels).
@@ -127,6 +128,10 @@ int launch_build_params(const ctqw_hamiltonian *h, const double *u_eps_d, const 
 int launch_switch_params(const ctqw_hamiltonian *h, uint64_t seed, uint64_t step, double p,
                          cudaStream_t s);
 int restore_params(const ctqw_hamiltonian *h, cudaStream_t s);
+
+// Norm correction (CTQW_FLAG_RENORMALIZE): every realization's state (and
+// its carried error word lo, when not null) divided by its norm.
+int launch_renormalize(const ctqw_hamiltonian *h, int dtype, void *psi, void *lo, cudaStream_t s);
 
 // Initial state (a2).  sites_d: [R][m] int32 on the device.
 int launch_init_state(const ctqw_hamiltonian *h, const int32_t *sites_d, int dtype, void *psi,

@@ -92,7 +92,40 @@ __global__ void __launch_bounds__(kThreads) observables_kernel(
     }
 }
 
+// psi (and lo) of realization r times 1 / sqrt(norm[r]).
+template <typename T, int M>
+__global__ void __launch_bounds__(256) renorm_kernel(RealTable tab, const int32_t *__restrict__ list,
+                                                     cplx_t<T> *psi, cplx_t<T> *lo,
+                                                     const double *__restrict__ norm) {
+    Site<M> p;
+    if (!site_of<M>(tab, list, p)) return;
+    const double n = norm[p.r];
+    const T sc = n > 0.0 ? (T)(1.0 / sqrt(n)) : T(1);
+    const int64_t i = tab.st_off[p.r] + p.s;
+    cplx_t<T> v = psi[i];
+    psi[i] = mk<T>(v.x * sc, v.y * sc);
+    if (lo) {
+        v = lo[i];
+        lo[i] = mk<T>(v.x * sc, v.y * sc);
+    }
+}
+
 }  // namespace
+
+int launch_renormalize(const ctqw_hamiltonian *h, int dtype, void *psi, void *lo, cudaStream_t s) {
+    CTQW_CUDA_TRY(cudaMemsetAsync(h->renorm_d, 0, sizeof(double) * h->R, s));
+    CTQW_TRY(launch_observables(h, dtype, psi, nullptr, nullptr, h->renorm_d, nullptr, s));
+    RealTable t = real_table(h);
+    return for_each_group(h, [&](dim3 grid, dim3 block, const int32_t *list) {
+        if (dtype == CTQW_C64) {
+            auto k = h->m == 2 ? renorm_kernel<float, 2> : renorm_kernel<float, 3>;
+            k<<<grid, block, 0, s>>>(t, list, (float2 *)psi, (float2 *)lo, h->renorm_d);
+        } else {
+            auto k = h->m == 2 ? renorm_kernel<double, 2> : renorm_kernel<double, 3>;
+            k<<<grid, block, 0, s>>>(t, list, (double2 *)psi, (double2 *)lo, h->renorm_d);
+        }
+    });
+}
 
 int launch_observables(const ctqw_hamiltonian *h, int dtype, const void *psi, double *P_mean,
                        double *P_joint, double *norm, double *energy, cudaStream_t s) {

@@ -23,6 +23,7 @@ DISTINGUISHABLE, BOSONS, FERMIONS = 0, 1, 2
 C64, C128 = 0, 1
 FLAG_PLAIN = 0x1
 FLAG_NO_COMPENSATION = 0x2
+FLAG_RENORMALIZE = 0x4
 FLAG_TEST_WAIT_TIMEOUT = 0x8
 
 
