@@ -761,7 +761,7 @@ def run_lattice(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "dtype": "c64" if w.dtype == cw.C64 else "c128", "data": "synthetic",
         "config": {"workload": w.name, "shape": list(w.shape), "periodic": w.periodic, "m": w.m,
-                   "chunk": args.chunk or "auto (half of L2)",
+                   "chunk": args.chunk or "all realizations in one pass",
                    "N": w.n_nodes(), "links": int(len(w.edges()[0])), "R": w.R, "K": w.K,
                    "n_steps": w.n_steps, "obs_every": w.obs_every,
                    "l2": "states larger than L2" if g.total_amplitudes * 8 > 129e6 else "L2-resident"},
@@ -856,7 +856,7 @@ def main(argv=None):
     ap.add_argument("--lattice", default=None,
                     help="time a q-dimensional lattice / graph workload (e.g. lattice2d_15x15_m2)")
     ap.add_argument("--chunk", type=int, default=0,
-                    help="--lattice: realizations per pass (0: sized to L2)")
+                    help="--lattice: realizations per pass (0: all in one pass)")
     ap.add_argument("--exact", action="store_true",
                     help="time ctqw_propagate_exact (batched Jacobi, 4096 x N=8 two-particle states)")
     ap.add_argument("--rho1", action="store_true",
