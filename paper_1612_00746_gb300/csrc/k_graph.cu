@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kThreads) graph_rk4_stage_kernel(GraphView g, 
 // x_m = y, y + 8, ...  Column sums of P reduce over the lanes and go out with
 // one atomic per column and block; row sums, norms and energies reduce over
 // the warps in shared memory.  All FP64.
-constexpr int kRows = 8;
+constexpr int kRows = 2;   // rows per block: enough blocks (R/128 x D/(2N)) to fill the GPU
 constexpr int kObsWarps = 8;
 
 template <typename T, int M>
