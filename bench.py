@@ -63,7 +63,9 @@ def _oracle_chunk(args):
 
 
 def oracle_sample(name: str, cores: int, n_steps: int, first: int = 0):
-    """Site-updates/s of the oracle over `cores` realizations run in parallel."""
+    """Site-updates/s of the oracle over `cores` realizations run in parallel,
+    the units, the wall time and the median single-core rate (each worker
+    times its own realization on one core)."""
     ctx = mp.get_context("spawn")
     jobs = [(name, first + k, n_steps) for k in range(cores)]
     with ctx.Pool(cores) as pool:
@@ -72,7 +74,8 @@ def oracle_sample(name: str, cores: int, n_steps: int, first: int = 0):
         out = pool.map(_oracle_chunk, jobs)
         wall = time.perf_counter() - t0
     units = sum(o[0] for o in out)
-    return units / wall, units, wall
+    single = statistics.median(o[0] / o[1] for o in out)
+    return units / wall, units, wall, single
 
 
 def host_cores() -> int:
@@ -264,11 +267,12 @@ def run_reference(args):
     steps_per_sample = args.ref_steps
     for _ in range(args.warmup):
         oracle_sample(w.name, cores, steps_per_sample)
-    vals = []
+    vals, singles = [], []
     t_all = time.perf_counter()
     for _ in range(args.steps):
-        v, units, wall = oracle_sample(w.name, cores, steps_per_sample)
+        v, units, wall, single = oracle_sample(w.name, cores, steps_per_sample)
         vals.append((units, wall))
+        singles.append(single)
     units = sum(u for u, _ in vals)
     wall = sum(t for _, t in vals)
     value = units / wall
@@ -281,7 +285,7 @@ def run_reference(args):
         "data": "synthetic", "config": {"workload": w.name, "m": w.m, "N": w.N, "R": w.R,
                                          "K": w.K, "dt": w.dt, "n_steps": w.n_steps},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "single_core_value": statistics.median(singles), "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": time.perf_counter() - t_all,
     }
@@ -314,10 +318,12 @@ def run_ours(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
-        v, units, wall = oracle_sample(w.name, cores, args.cpu_steps)
+        v, units, wall, single = oracle_sample(w.name, cores, args.cpu_steps)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "single_core_value": single,
                "sample": f"{cores} realizations (one per host core) x {args.cpu_steps} of "
-                         f"{w.n_steps} steps of {w.name}, K={w.K}, FP64 ({wall:.1f} s)"}
+                         f"{w.n_steps} steps of {w.name}, K={w.K}, FP64 ({wall:.1f} s); "
+                         f"single_core_value: median rate of one worker"}
 
     # realizations of this rank: its own block of the (weakly scaled) ensemble
     realizations = list(range(rank * w.R, (rank + 1) * w.R))
