@@ -417,7 +417,8 @@ def run_ours(args):
     ms = t0.elapsed_time(t1) / args.steps
     ms_max = max_over_ranks(ms, dev)
     value = world * units_per_step / (ms_max / 1000.0)
-    kernel_ms = statistics.mean(a.elapsed_time(b) for a, b in prop_events)
+    prop_ms = [a.elapsed_time(b) for a, b in prop_events]
+    kernel_ms = statistics.mean(prop_ms)
 
     # accuracy self-check of this run (rank 0's realizations): norm drift
     norm_drift = float((nr - 1.0).abs().max().item())
@@ -537,6 +538,8 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "propagate_ms": {"best": min(prop_ms), "median": statistics.median(prop_ms),
+                         "mean": kernel_ms, "steps": len(prop_ms)},
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if dtype == ctqw.C64 else "f64",
         "data": "synthetic",
         "config": {"workload": w.name, "m": w.m, "N": w.N, "R_per_gpu": w.R, "K": w.K,
