@@ -426,7 +426,8 @@ typedef struct {
 
 /*
  * Build the topology (CSR, on the host, then copied) and the parameters of
- * every realization (on the device, on `stream`).  Errors: EINVAL for null
+ * every realization (on the device, on `stream`, which is synchronized before
+ * the call returns: the device copies of the draws are then freed).  Errors: EINVAL for null
  * pointers, sizes out of range, a link with a node out of range or with
  * u_e == v_e; ENOMEM; ECUDA.
  */
@@ -447,7 +448,8 @@ int ctqw_graph_state_size(const ctqw_graph *g, int64_t *amplitudes_total);
 /*
  * Localised initial states as ctqw_init_state (in the graph layout):
  * sites_host [R][m] nodes (host, int32).  EINVAL for a node out of range or
- * coinciding fermions.
+ * coinciding fermions.  Synchronizes `stream` before returning (the device
+ * copy of the sites is freed after the kernel has read it).
  */
 int ctqw_graph_init_state(const ctqw_graph *g, const int32_t *sites_host, int32_t dtype,
                           void *psi_dev, void *stream);
