@@ -504,3 +504,78 @@ def test_renormalized_propagation_is_the_state_over_its_norm(method):
     for a, b in zip(raw["states"], ren["states"]):
         np.testing.assert_allclose(b, a / np.sqrt(O.norm(a)), atol=1e-13)
     np.testing.assert_allclose(ren["P"], raw["P"] / raw["norm"][:, None], atol=1e-13)
+
+
+# ---------------------------------------------------------------- energy values
+# The pins above fix energy only through its conservation, which a wrong
+# functional (the imaginary part, a constant factor, the diagonal only) would
+# also satisfy.  These fix its value: <Psi|H|Psi> on states whose energy is
+# known in closed form.
+
+@pytest.mark.parametrize("m,sites,periodic", [(2, (1, 4), False), (2, (3, 3), False),
+                                              (2, (0, 6), True), (3, (2, 2, 5), False),
+                                              (3, (1, 1, 1), True)])
+def test_energy_of_localised_states(m, sites, periodic):
+    """|x_1..x_m> has E = sum_j eps_{x_j} + U #{j<l: x_j = x_l}: hops move
+    amplitude off the site and contribute nothing to the expectation."""
+    N, U = 7, 1.7
+    rng = np.random.default_rng(7 + m)
+    eps, J = _rand_params(rng, N, periodic)
+    H = O.many_particle_hamiltonian(O.single_particle_hamiltonian(eps, J, periodic), m, U)
+    psi = O.initial_state(N, m, sites, 0)
+    pairs = sum(1 for j in range(m) for l in range(j + 1, m) if sites[j] == sites[l])
+    expect = sum(eps[x] for x in sites) + U * pairs
+    assert abs(O.energy(H, psi) - expect) < 1e-14
+    # the same value from the sampled energies of a propagation (conserved)
+    res = O.propagate(H, psi, N, m, 0.02, 30, 10, "taylor", 16)
+    np.testing.assert_allclose(res["energy"], expect, atol=1e-12)
+
+
+def test_energy_of_two_site_hubbard_eigenstates():
+    """Two bosons on two sites: in the basis |+> = (|00> + |11>)/sqrt2,
+    |s> = (|01> + |10>)/sqrt2 the Hamiltonian is [[U, -2J], [-2J, 0]], so
+    (lam |+> - 2J |s>) / sqrt(lam^2 + 4J^2) has energy lam = (U +- sqrt(U^2 + 16 J^2))/2;
+    (|00> - |11>)/sqrt2 has energy U.  A complex global phase leaves E unchanged."""
+    J0, U = 0.8, 2.6
+    H = O.many_particle_hamiltonian(
+        O.single_particle_hamiltonian(np.zeros(2), np.array([J0]), False), 2, U)
+    root = np.sqrt(U ** 2 + 16 * J0 ** 2)
+    s2 = 1 / np.sqrt(2)
+    plus = np.array([s2, 0, 0, s2])
+    sym = np.array([0, s2, s2, 0])
+    for lam in ((U + root) / 2, (U - root) / 2):
+        v = (lam * plus - 2 * J0 * sym) / np.sqrt(lam ** 2 + 4 * J0 ** 2)
+        assert abs(O.energy(H, np.exp(0.7j) * v.astype(complex)) - lam) < 1e-14
+    minus = np.array([s2, 0, 0, -s2], dtype=complex)
+    assert abs(O.energy(H, 1j * minus) - U) < 1e-14
+
+
+@pytest.mark.parametrize("k1,k2,U", [(1, 1, 0.0), (2, 5, 0.0), (3, 7, 1.3)])
+def test_energy_of_clean_chain_sine_mode_products(k1, k2, U):
+    """Clean open chain: phi_k(i) = sqrt(2/(N+1)) sin(pi k (i+1)/(N+1)) has
+    E_k = -2J cos(pi k/(N+1)).  The product phi_k1 x phi_k2 has energy
+    E_k1 + E_k2 + U sum_x phi_k1(x)^2 phi_k2(x)^2 (the interaction acts on
+    the diagonal x1 = x2 only)."""
+    N, J0 = 9, 1.1
+    H = O.many_particle_hamiltonian(
+        O.single_particle_hamiltonian(np.zeros(N), np.full(N - 1, J0), False), 2, U)
+    i = np.arange(N)
+    phi = lambda k: np.sqrt(2 / (N + 1)) * np.sin(np.pi * k * (i + 1) / (N + 1))
+    Ek = lambda k: -2 * J0 * np.cos(np.pi * k / (N + 1))
+    psi = np.kron(phi(k1), phi(k2)).astype(complex)
+    expect = Ek(k1) + Ek(k2) + U * np.sum(phi(k1) ** 2 * phi(k2) ** 2)
+    assert abs(O.energy(H, psi) - expect) < 1e-13
+
+
+def test_energy_of_ring_plane_waves():
+    """Clean ring: e^{i q x}/sqrt(N) with q = 2 pi k / N has E = -2J cos q
+    per particle; the energy of a complex state is real and uses both parts."""
+    N, J0 = 8, 0.9
+    H = O.many_particle_hamiltonian(
+        O.single_particle_hamiltonian(np.zeros(N), np.full(N, J0), True), 2, 0.0)
+    x = np.arange(N)
+    for k1, k2 in ((1, 0), (3, 2), (1, 6)):
+        q1, q2 = 2 * np.pi * k1 / N, 2 * np.pi * k2 / N
+        psi = np.kron(np.exp(1j * q1 * x), np.exp(1j * q2 * x)) / N
+        expect = -2 * J0 * (np.cos(q1) + np.cos(q2))
+        assert abs(O.energy(H, psi) - expect) < 1e-14
