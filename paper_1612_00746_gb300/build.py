@@ -3,6 +3,8 @@
 Each translation unit under csrc/ is compiled in parallel, then linked into
 paper_1612_00746_gb300/libctqw.so.  Objects go to paper_1612_00746_gb300/_build/.
 A source whose object is newer than it and than every header is not rebuilt.
+The FMA-chain microbenchmark of the benchmark's ALU rooflines (peaks/) is
+built alongside as paper_1612_00746_gb300/libfmapeak.so.
 """
 from __future__ import annotations
 
@@ -18,6 +20,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libctqw.so")
+PEAKS_SRC = os.path.join(PKG, "peaks", "fma_peak.cu")
+PEAKS_LIB = os.path.join(PKG, "libfmapeak.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -70,9 +74,22 @@ def build(verbose: bool = False, ptxas_verbose: bool = False) -> str:
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link of libctqw.so failed:\n{res.stdout}\n{res.stderr}")
+    build_peaks()
     if verbose:
         print(f"built {LIB}")
     return LIB
+
+
+def build_peaks() -> str:
+    """Compile and link libfmapeak.so (the FMA-chain microbenchmark)."""
+    if os.path.exists(PEAKS_LIB) and os.path.getmtime(PEAKS_LIB) >= os.path.getmtime(PEAKS_SRC):
+        return PEAKS_LIB
+    cmd = [nvcc()] + ARCH + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", PEAKS_SRC,
+                             "-o", PEAKS_LIB, "-cudart", "static"]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PEAKS_SRC}:\n{res.stdout}\n{res.stderr}")
+    return PEAKS_LIB
 
 
 if __name__ == "__main__":
