@@ -167,7 +167,9 @@ int ctqw_init_state(const ctqw_hamiltonian *h, const int32_t *sites_host, int32_
 
 /*
  * Workspace bytes ctqw_propagate_taylor / ctqw_propagate_rk4 need for the
- * given dtype and flags (method 0 = Taylor, 1 = RK4).  0 means none.
+ * given dtype and flags (method 0 = Taylor, 1 = RK4): 3 states on every path
+ * but the row wavefront (one state).  The fused path also accepts more (see
+ * ctqw_propagate_taylor).
  */
 int ctqw_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t method, uint32_t flags,
                         size_t *bytes);
@@ -207,17 +209,28 @@ int ctqw_autotune_order(const ctqw_hamiltonian *h, int32_t dtype, double dt, int
  *   energy_dev [n_obs][R] FP64:  <Psi_r|H_r|Psi_r>
  * The outputs are overwritten (zeroed on the stream first).  K in 1..30, or
  * 0: the order ctqw_autotune_order picks over 1..30 (host arithmetic only).
- * Precision: CTQW_C128 propagates in FP64; CTQW_C64 propagates in FP32 and,
- * on the fused path, carries the rounding error of every state update in a
- * second FP32 word (compensated summation) kept on chip for the whole call.
+ * Observables (the norm check of Algorithms 2 and 3, and the diagonal of
+ * <rho>) are formed from the state with products in its precision and
+ * exact sums: FP64 for CTQW_C128; for CTQW_C64 64-bit fixed-point integer
+ * sums of the FP32 products (|psi|^2 in units of 2^-48, energy terms of
+ * 2^-44), converted to FP64 per block.  A sample with a non-finite or
+ * out-of-range term (|psi|^2 >= 2^14) gets a NaN norm and energy.
+ * Precision: CTQW_C128 propagates in FP64; CTQW_C64 propagates in FP32 and
+ * carries the rounding error of every state update in a second FP32 word
+ * (compensated summation).
  * Path: m = 2 chains with N a multiple of 64 up to 256 in CTQW_C64 run the
  * fused cluster kernel (every Taylor term of every step on chip; halo rows move between the CTAs
  * of a cluster point to point, see ctqw_check_status); other m = 2 handles
  * in CTQW_C64 (N > 256, ragged sizes) run the temporally blocked tiled
  * kernel with the iterate in registers, ceil(K / 8) launches a step with the
  * stages split evenly between them; everything
- * else, or CTQW_FLAG_PLAIN, runs one launch per Taylor term.  All but the
- * fused kernel need the workspace of ctqw_workspace_size (3 states).  The
+ * else, or CTQW_FLAG_PLAIN, runs one launch per Taylor term.  Every path
+ * needs the workspace of ctqw_workspace_size (3 states).  The fused path
+ * keeps the carried error in the first state and stores the state at
+ * sample points into the others (S = workspace_bytes / state bytes - 1
+ * slots); one launch covers S + 1 sampling intervals, so a larger
+ * workspace means fewer launches.  Given no workspace, the fused path
+ * allocates its 3 states stream-ordered.  The
  * per-term path runs in CTQW_C128 in the order of
  * Algorithm 3 (Phi^(j) from Phi^(j-1), summed forward); in CTQW_C64 as the
  * same polynomial in Horner form (w_j = Psi + (-i dt / j) H w_{j+1}, j = K..2,
@@ -344,7 +357,7 @@ int ctqw_propagate_taylor_noalloc(const ctqw_hamiltonian *h, int32_t dtype, void
 
 /*
  * Workspace bytes of ctqw_adjoint_grad: (ceil(n_steps / checkpoint_every) +
- * checkpoint_every + K + 7) states plus 2 p_width doubles.
+ * checkpoint_every + K + 7) states plus 2 p_width + 2 sum_r N_r doubles.
  */
 int ctqw_adjoint_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t K,
                                 int64_t n_steps, int32_t checkpoint_every, size_t *bytes);
@@ -353,10 +366,16 @@ int ctqw_adjoint_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_
  * Loss on the ensemble-averaged occupations at T = n_steps dt and its exact
  * gradient through the discrete Taylor propagation (Sec. 2.3, Algorithm 3):
  *   loss = sum_x (Pbar(x, T) - P_target(x))^2   (sum over the size groups)
- * grad_eps_dev / grad_J_dev ([sum_r N_r] FP64, laid out like ctqw_get_params)
- * receive dloss/deps_{r,i} and dloss/dJ_{r,b} of every realization; sum them
- * over realizations for the gradient with respect to shared means (the
- * rounding of the disorder to float32 is passed straight through).
+ * Gradient outputs (FP64 device arrays, each may be NULL, not all four):
+ *   grad_eps_dev / grad_J_dev [sum_r N_r], laid out like ctqw_get_params:
+ *     dloss/deps_{r,i} and dloss/dJ_{r,b} of every realization r;
+ *   grad_eps_mean_dev / grad_J_mean_dev [p_width], laid out like a P_mean
+ *     row (size groups back to back, ctqw_output_layout): for group g and
+ *     site (bond) i, the sum over the group's realizations of the gradients
+ *     above, in ascending realization order - the gradient with respect to
+ *     the means eps_mean[i], J_mean[i] the group shares (the rounding of the
+ *     disorder to float32 is passed straight through).  Entry N_g - 1 of the
+ *     J sums of an open chain is 0 (no wrap bond).
  * psi0_dev: initial states (not modified).  P_target_dev: [p_width] FP64.
  * loss_dev: [1] FP64.  P_final_dev: [p_width] FP64 or NULL.
  * Method: forward pass storing psi every checkpoint_every steps, then per
@@ -365,14 +384,17 @@ int ctqw_adjoint_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_
  *   grad += 2 Re sum_{a<K} <mu_a, dH phi_a>,  phi_a = H^a psi_n,
  *   mu_{K-1} = conj(c_K) lambda_{n+1},  mu_a = conj(c_{a+1}) lambda_{n+1} + H mu_{a+1},
  * with c_k = (-i dt)^k / k!.  States in `dtype` (c64: FP32 states), all
- * gradient accumulation in FP64.  Needs the workspace of
- * ctqw_adjoint_workspace_size.  Asynchronous.
+ * gradient accumulation and the sums over realizations in FP64.  Needs the
+ * workspace of ctqw_adjoint_workspace_size.  Errors: EINVAL for a null
+ * target or loss, no gradient output, bad K / checkpoint_every or a short
+ * workspace.  Asynchronous.
  */
 int ctqw_adjoint_grad(const ctqw_hamiltonian *h, int32_t dtype, const void *psi0_dev, double dt,
                       int32_t K, int64_t n_steps, int32_t checkpoint_every,
                       const double *P_target_dev, double *loss_dev, double *grad_eps_dev,
-                      double *grad_J_dev, double *P_final_dev, void *workspace_dev,
-                      size_t workspace_bytes, void *stream);
+                      double *grad_J_dev, double *grad_eps_mean_dev, double *grad_J_mean_dev,
+                      double *P_final_dev, void *workspace_dev, size_t workspace_bytes,
+                      void *stream);
 
 /*
  * Synchronize `stream` and report whether a kernel of an earlier call on this

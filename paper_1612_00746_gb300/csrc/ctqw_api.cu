@@ -109,11 +109,12 @@ int taylor_step_plain(const ctqw_hamiltonian *h, int dtype, const void *in, void
 struct AdjointLayout {
     int64_t n_ck = 0;
     size_t state = 0, total = 0;
-    size_t off_ck = 0, off_seg = 0, off_phi = 0, off_misc = 0, off_dbl = 0;
+    size_t off_ck = 0, off_seg = 0, off_phi = 0, off_misc = 0, off_dbl = 0, off_grad = 0;
 };
 
 // Workspace: checkpoints every M steps, one segment of M replayed states,
-// phi_1..phi_{K-1}, 8 scratch states, then Pbar and diff (FP64).
+// phi_1..phi_{K-1}, 8 scratch states, then Pbar and diff (FP64) and the
+// per-realization gradients (FP64) for calls that want only the sums.
 AdjointLayout adjoint_layout(const ctqw_hamiltonian *h, int dtype, int K, int64_t n_steps, int M) {
     AdjointLayout L;
     L.state = (size_t)h->total_amp * elem_bytes(dtype);
@@ -123,7 +124,8 @@ AdjointLayout adjoint_layout(const ctqw_hamiltonian *h, int dtype, int K, int64_
     L.off_phi = L.off_seg + (size_t)M * L.state;
     L.off_misc = L.off_phi + (size_t)(K > 1 ? K - 1 : 0) * L.state;
     L.off_dbl = L.off_misc + 8 * L.state;
-    L.total = L.off_dbl + 2 * sizeof(double) * (size_t)h->p_width;
+    L.off_grad = L.off_dbl + 2 * sizeof(double) * (size_t)h->p_width;
+    L.total = L.off_grad + 2 * sizeof(double) * (size_t)h->total_par;
     return L;
 }
 
@@ -432,9 +434,7 @@ int ctqw_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t method
         *bytes = wavefront_workspace_bytes(h);
         return CTQW_OK;
     }
-    const bool fused = (method == 0 || method == 1) && !(flags & CTQW_FLAG_PLAIN) &&
-                       shape < CTQW_SHAPE_TILED(0) && fused_rows_supported(h, dtype);
-    *bytes = fused ? 0 : 3 * (size_t)h->total_amp * elem_bytes(dtype);
+    *bytes = 3 * (size_t)h->total_amp * elem_bytes(dtype);
     return CTQW_OK;
 }
 
@@ -608,6 +608,58 @@ static int propagate_tiled(const ctqw_hamiltonian *h, int32_t dtype, void *psi_d
     return CTQW_OK;
 }
 
+// The full-row fused kernel in chunks: the workspace holds the carried
+// rounding error (one state) and S >= 0 snapshot slots.  A launch runs from a
+// sample point over up to S + 1 sampling intervals, storing the state at the
+// S sample points inside it; the observables of every sample are then taken
+// in FP64 by the observables kernel (from psi at the chunk boundaries, from
+// the slots inside).  Without observables it is one launch.  With no
+// workspace, one of 3 states is allocated stream-ordered.
+static int propagate_fused_rows(const ctqw_hamiltonian *h, void *psi_dev, double dt, int32_t K,
+                                int64_t n_steps, int32_t obs_every, double *P_mean_dev,
+                                double *norm_dev, double *energy_dev, uint32_t flags, int shape,
+                                void *workspace_dev, size_t workspace_bytes, cudaStream_t s) {
+    const size_t sb = (size_t)h->total_amp * sizeof(float2);
+    void *ws = workspace_dev;
+    size_t wsb = workspace_bytes;
+    bool own = false;
+    if (!ws) {
+        wsb = 3 * sb;
+        CTQW_CUDA_TRY(cudaMallocAsync(&ws, wsb, s));
+        own = true;
+    } else if (wsb < sb) {
+        ctqw_set_error("fused path needs a workspace of at least %zu bytes (got %zu)", sb, wsb);
+        return CTQW_EINVAL;
+    }
+    char *w = (char *)ws;
+    void *lo = w;
+    const int64_t slots = (int64_t)(wsb / sb) - 1;
+    const int comp = (flags & CTQW_FLAG_NO_COMPENSATION) ? 0 : 1;
+    int test = (flags & CTQW_FLAG_TEST_WAIT_TIMEOUT) ? 1 : 0;
+    int st = CTQW_OK;
+    if (cudaMemsetAsync(lo, 0, sb, s) != cudaSuccess) st = ctqw_cuda_fail(cudaGetLastError(), "memset");
+    auto observe = [&](const void *state, int64_t q) {
+        return launch_observables(h, CTQW_C64, state, P_mean_dev ? P_mean_dev + q * h->p_width : nullptr,
+                                  nullptr, norm_dev ? norm_dev + q * h->R : nullptr,
+                                  energy_dev ? energy_dev + q * h->R : nullptr, s);
+    };
+    for (int64_t s0 = 0; st == CTQW_OK;) {
+        if (obs_every > 0 && s0 % obs_every == 0) st = observe(psi_dev, s0 / obs_every);
+        if (st != CTQW_OK || s0 == n_steps) break;
+        const int64_t chunk = obs_every > 0 ? std::min<int64_t>(n_steps - s0, (slots + 1) * obs_every)
+                                            : n_steps - s0;
+        const int64_t inside = obs_every > 0 ? (chunk - 1) / obs_every : 0;   // snapshots of this launch
+        st = launch_taylor_fused_rows(h, psi_dev, lo, inside > 0 ? w + sb : nullptr, obs_every, dt, K,
+                                      chunk, comp, shape, test, s);
+        test = 0;
+        for (int64_t q = 0; st == CTQW_OK && q < inside; ++q)
+            st = observe(w + (size_t)(q + 1) * sb, s0 / obs_every + q + 1);
+        s0 += chunk;
+    }
+    if (own) cudaFreeAsync(ws, s);
+    return st;
+}
+
 int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
                           int32_t K, int64_t n_steps, int32_t obs_every, double *P_mean_dev,
                           double *norm_dev, double *energy_dev, uint32_t flags,
@@ -663,8 +715,8 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
         const int comp = (flags & CTQW_FLAG_NO_COMPENSATION) ? 0 : 1;
         const int test = (flags & CTQW_FLAG_TEST_WAIT_TIMEOUT) ? 1 : 0;
         if (shape < 4)
-            return launch_taylor_fused_rows(h, psi_dev, dt, K, n_steps, obs_every, P_mean_dev,
-                                            norm_dev, energy_dev, comp, shape, test, s);
+            return propagate_fused_rows(h, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
+                                        energy_dev, flags, shape, workspace_dev, workspace_bytes, s);
         return launch_taylor_fused(h, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
                                    energy_dev, comp, shape - 4, test, s);
     }
@@ -823,13 +875,18 @@ int ctqw_adjoint_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_
 int ctqw_adjoint_grad(const ctqw_hamiltonian *h, int32_t dtype, const void *psi0_dev, double dt,
                       int32_t K, int64_t n_steps, int32_t checkpoint_every,
                       const double *P_target_dev, double *loss_dev, double *grad_eps_dev,
-                      double *grad_J_dev, double *P_final_dev, void *workspace_dev,
-                      size_t workspace_bytes, void *stream) {
+                      double *grad_J_dev, double *grad_eps_mean_dev, double *grad_J_mean_dev,
+                      double *P_final_dev, void *workspace_dev, size_t workspace_bytes,
+                      void *stream) {
     CTQW_TRY(check_common(h, dtype, psi0_dev, dt, n_steps, 0));
     if (K < 1 || K > 30) { ctqw_set_error("K must be in 1..30 (got %d)", K); return CTQW_EINVAL; }
     if (checkpoint_every < 1) { ctqw_set_error("checkpoint_every must be >= 1"); return CTQW_EINVAL; }
-    if (!P_target_dev || !loss_dev || !grad_eps_dev || !grad_J_dev) {
-        ctqw_set_error("null target / loss / gradient pointer");
+    if (!P_target_dev || !loss_dev) {
+        ctqw_set_error("null target / loss pointer");
+        return CTQW_EINVAL;
+    }
+    if (!grad_eps_dev && !grad_J_dev && !grad_eps_mean_dev && !grad_J_mean_dev) {
+        ctqw_set_error("no gradient output (all four gradient pointers are null)");
         return CTQW_EINVAL;
     }
     const int M = checkpoint_every;
@@ -849,6 +906,9 @@ int ctqw_adjoint_grad(const ctqw_hamiltonian *h, int32_t dtype, const void *psi0
     void *lam = misc[4], *lam2 = misc[5], *muA = misc[6], *muB = misc[7];
     double *Pbar = (double *)(ws + L.off_dbl);
     double *diff = Pbar + h->p_width;
+    // per-realization gradients: the caller's arrays, or the workspace's
+    if (!grad_eps_dev) grad_eps_dev = (double *)(ws + L.off_grad);
+    if (!grad_J_dev) grad_J_dev = (double *)(ws + L.off_grad) + h->total_par;
 
     CTQW_CUDA_TRY(cudaMemsetAsync(grad_eps_dev, 0, sizeof(double) * h->total_par, s));
     CTQW_CUDA_TRY(cudaMemsetAsync(grad_J_dev, 0, sizeof(double) * h->total_par, s));
@@ -901,6 +961,10 @@ int ctqw_adjoint_grad(const ctqw_hamiltonian *h, int32_t dtype, const void *psi0
             std::swap(lam, lam2);
         }
     }
+    // gradients with respect to the means shared by a size group: sums over
+    // its realizations, in FP64 and a fixed order
+    if (grad_eps_mean_dev) CTQW_TRY(launch_group_sum(h, grad_eps_dev, grad_eps_mean_dev, s));
+    if (grad_J_mean_dev) CTQW_TRY(launch_group_sum(h, grad_J_dev, grad_J_mean_dev, s));
     return CTQW_OK;
 }
 

@@ -183,13 +183,19 @@ int launch_loss(const double *Pbar, const double *target, int64_t n, double *dif
                 cudaStream_t s);
 int launch_lambda_init(const ctqw_hamiltonian *h, int dtype, const void *psi, const double *diff,
                        void *lam, cudaStream_t s);
+// Per size group g: out[group_off[g] + i] = sum over the group's realizations
+// r (ascending index) of grad[par_off[r] + i], i < N_g (FP64).
+int launch_group_sum(const ctqw_hamiltonian *h, const double *grad, double *out, cudaStream_t s);
 
-// Fused cluster-resident Taylor propagation (m = 2, c64), full-row layout.
+// Fused cluster-resident Taylor propagation (m = 2, c64), full-row layout:
+// n_steps steps on chip; lo (a c64 state, lane-major rows) carries the
+// rounding error in and out; when snap is not null the state after every
+// snap_every-th step before the last is stored to slot q = step/snap_every - 1
+// of snap (consecutive states, the layout of psi).
 bool fused_rows_supported(const ctqw_hamiltonian *h, int dtype);
-int launch_taylor_fused_rows(const ctqw_hamiltonian *h, void *psi, double dt, int K,
-                             int64_t n_steps, int obs_every, double *P_mean, double *norm,
-                             double *energy, int compensated, int shape, int test_timeout,
-                             cudaStream_t s);
+int launch_taylor_fused_rows(const ctqw_hamiltonian *h, void *psi, void *lo, void *snap,
+                             int snap_every, double dt, int K, int64_t n_steps, int compensated,
+                             int shape, int test_timeout, cudaStream_t s);
 
 // Fused row-wavefront Taylor propagation (m = 2, c64, open chains): every
 // Taylor term of a step on chip, psi streamed once per step; lo: the carried

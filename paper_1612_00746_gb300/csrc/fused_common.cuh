@@ -134,5 +134,43 @@ static __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Butterfly sum over the warp in FP64 (every lane gets the total).
+static __device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the warp of V values per lane at once (V a power of two <= 32),
+// in FP64: the first log2 V butterfly steps each halve the values a lane
+// keeps (it sends the half its partner keeps), the remaining steps are a
+// plain butterfly.  Returns, in every lane, the warp total of value
+// (lane >> (5 - log2 V)) & (V - 1); that costs 2V - 1 + (5 - log2 V) adds
+// per lane against 5 V for V separate butterflies.
+template <int V>
+static __device__ __forceinline__ double warp_sum_multi_d(double (&v)[V], int lane) {
+    static_assert(V >= 1 && V <= 32 && (V & (V - 1)) == 0, "V must be a power of two <= 32");
+#pragma unroll
+    for (int o = 16, n = V; n > 1; o >>= 1, n >>= 1) {
+        const bool upper = (lane & o) != 0;   // keeps the upper half of the values
+#pragma unroll
+        for (int q = 0; q < n / 2; ++q) {
+            const double send = upper ? v[q] : v[q + n / 2];
+            const double keep = upper ? v[q + n / 2] : v[q];
+            v[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    double t = v[0];
+#pragma unroll
+    for (int o = 16 / V; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    return t;
+}
+
+// |c|^2 of an FP32 amplitude in FP32 (FP32 products; the sums that use it
+// run in FP64).
+static __device__ __forceinline__ float abs2_f(float2 c) { return fmaf(c.x, c.x, c.y * c.y); }
+
+// Re(conj(c) y) of two FP32 amplitudes in FP32.
+static __device__ __forceinline__ float re_dot_f(float2 c, float2 y) { return fmaf(c.x, y.x, c.y * y.y); }
 
 }  // namespace fused

@@ -269,6 +269,20 @@ __global__ void __launch_bounds__(256) lambda_init_kernel(RealTable tab, const c
     lam[base + s] = mk<T>((T)(w * (double)p.x), (T)(w * (double)p.y));
 }
 
+// out[i] = sum over the group's realizations (in the fixed order of `list`)
+// of grad[par_off[r] + i], i < N: the gradient with respect to parameters
+// shared by the group (the means), deterministic.
+__global__ void __launch_bounds__(256) group_sum_kernel(const int64_t *__restrict__ par_off,
+                                                        const int32_t *__restrict__ list, int cnt, int N,
+                                                        const double *__restrict__ grad,
+                                                        double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double acc = 0.0;
+    for (int q = 0; q < cnt; ++q) acc += grad[par_off[list[q]] + i];
+    out[i] = acc;
+}
+
 dim3 grid_for(const ctqw_hamiltonian *h) {
     int64_t D = 1;
     for (int j = 0; j < h->m; ++j) D *= h->Nmax;
@@ -355,5 +369,17 @@ int launch_lambda_init(const ctqw_hamiltonian *h, int dtype, const void *psi, co
         k<<<g, b, 0, s>>>(t, (const double2 *)psi, diff, (double2 *)lam);
     }
     CTQW_CUDA_TRY(cudaGetLastError());
+    return CTQW_OK;
+}
+
+int launch_group_sum(const ctqw_hamiltonian *h, const double *grad, double *out, cudaStream_t s) {
+    int off = 0;
+    for (size_t g = 0; g < h->group_N.size(); ++g) {
+        const int N = h->group_N[g], cnt = h->group_count[g];
+        group_sum_kernel<<<(N + 255) / 256, 256, 0, s>>>(h->par_off_d, h->by_group_d + off, cnt, N, grad,
+                                                         out + h->group_off[g]);
+        CTQW_CUDA_TRY(cudaGetLastError());
+        off += cnt;
+    }
     return CTQW_OK;
 }

@@ -41,7 +41,7 @@ struct FusedArgs {
     float2 *psi;
     int N;
     double dt;
-    float inv_dt;
+    double inv_dt;
     int K;
     long long n_steps;
     int obs_every;
@@ -76,7 +76,7 @@ __device__ __forceinline__ void stencil_term(float2 (&P)[RL][2], const float2 *_
                                              const float2 (&nJr)[RL + 1], const float2 (&nJc)[3],
                                              float2 up0, float2 up1, float2 dn0, float2 dn1,
                                              const float4 *__restrict__ seam4, int lane,
-                                             float inv_j, float &e) {
+                                             float inv_j, double &e) {
     // "prev" is the old row already passed (above when top-down, below when bottom-up)
     float2 prev0 = REV ? dn0 : up0, prev1 = REV ? dn1 : up1;
     const int from_left = (lane + 31) & 31, from_right = (lane + 1) & 31;
@@ -109,7 +109,7 @@ __device__ __forceinline__ void stencil_term(float2 (&P)[RL][2], const float2 *_
         y1 = __ffma2_rn(nJr[i + 1], b1, y1);
         y1 = __ffma2_rn(nJc[1], c0, y1);
         y1 = __ffma2_rn(nJc[2], rgt, y1);
-        if (ENERGY) e += c0.x * y0.x + c0.y * y0.y + c1.x * y1.x + c1.y * y1.y;
+        if (ENERGY) e += (double)re_dot_f(c0, y0) + (double)re_dot_f(c1, y1);
         if (MODE == kHorner) {
             const float4 q = *reinterpret_cast<const float4 *>(Q + i * N);
             P[i][0] = make_float2(fmaf(inv_j, y0.y, q.x), fmaf(-inv_j, y0.x, q.y));
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
     float2 *edge = halo + 2 * 2 * N;             // [2][BPC][2][N] band edges inside this CTA
     float2 *seamb = edge + 2 * BPC * 2 * N;      // [2][W][2][RL] warp edge columns
     float4 *Vs = reinterpret_cast<float4 *>(seamb + 2 * W * 2 * RL);   // [SR/2][N/2] diagonal of dt H
-    float *pacc = reinterpret_cast<float *>(Vs + (SR / 2) * (N / 2));   // [N]
+    double *pacc = reinterpret_cast<double *>(Vs + (SR / 2) * (N / 2));   // [N] FP64 partials
     __shared__ __align__(8) unsigned long long mbar[2][2];   // [parity][side] halo arrivals
     __shared__ __align__(8) unsigned long long mbar_never;    // failure-path test only
 
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
         *reinterpret_cast<float4 *>(hi + (lrow0 + i) * N + x2_0) = v;
         *reinterpret_cast<float4 *>(lo + (lrow0 + i) * N + x2_0) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (int x = threadIdx.x; x < N; x += blockDim.x) pacc[x] = 0.f;
+    for (int x = threadIdx.x; x < N; x += blockDim.x) pacc[x] = 0.0;
 
     const int rank_up = (rank + C - 1) % C, rank_dn = (rank + 1) % C;
     // band 0 sends its first row into rank_up's "row below" slot, band BPC-1
@@ -238,15 +238,16 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
     for (long long step = 0; step <= n_steps; ++step) {
         const bool sample = a.obs_every > 0 && (step % a.obs_every) == 0;
         if (sample) {
-            // P(x) = (row sums + column sums) / 2, norm = sum |psi|^2 (state = hi)
-            float colp[2] = {0.f, 0.f}, nrm = 0.f;
+            // P(x) = (row sums + column sums) / 2, norm = sum |psi|^2 (state =
+            // hi): FP32 products |psi|^2, every sum in FP64
+            double colp[2] = {0.0, 0.0}, nrm = 0.0;
 #pragma unroll
             for (int i = 0; i < RL; ++i) {
-                const float p0 = P[i][0].x * P[i][0].x + P[i][0].y * P[i][0].y;
-                const float p1 = P[i][1].x * P[i][1].x + P[i][1].y * P[i][1].y;
+                const double p0 = (double)abs2_f(P[i][0]);
+                const double p1 = (double)abs2_f(P[i][1]);
                 colp[0] += p0;
                 colp[1] += p1;
-                const float rs = warp_sum(p0 + p1);
+                const double rs = warp_sum_d(p0 + p1);
                 nrm += rs;
                 if (lane == 0 && Pg) atomicAdd(pacc + x1_0 + i, rs);
             }
@@ -254,13 +255,13 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
                 atomicAdd(pacc + x2_0, colp[0]);
                 atomicAdd(pacc + x2_0 + 1, colp[1]);
             }
-            if (lane == 0 && a.norm) atomicAdd(a.norm + obs * a.tab.R + r, (double)nrm);
+            if (lane == 0 && a.norm) atomicAdd(a.norm + obs * a.tab.R + r, nrm);
             __syncthreads();
             if (Pg) {
                 for (int x = threadIdx.x; x < N; x += blockDim.x) {
-                    const float v = pacc[x];
-                    if (v != 0.f) atomicAdd(Pg + obs * a.p_width + x, (double)v * pscale);
-                    pacc[x] = 0.f;
+                    const double v = pacc[x];
+                    if (v != 0.0) atomicAdd(Pg + obs * a.p_width + x, v * pscale);
+                    pacc[x] = 0.0;
                 }
             }
         }
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
             const float inv_j = a.inv_j[j];
             const bool first = j == K;
             const bool en = first && sample && a.energy;
-            float e = 0.f;
+            double e = 0.0;
             if (last) {
                 stencil_term<kEnergyOnly, true, N, REV>(P, Q, V4, nJr, nJc, up0, up1, dn0, dn1, seam4, lane, inv_j, e);
             } else if (j == 1) {
@@ -336,8 +337,8 @@ __global__ void __launch_bounds__(32 * (N / 64) * BPC, MINB)
                 stencil_term<kHorner, false, N, REV>(P, Q, V4, nJr, nJc, up0, up1, dn0, dn1, seam4, lane, inv_j, e);
             }
             if (en || last) {
-                const float es = warp_sum(e);
-                if (lane == 0) atomicAdd(a.energy + obs * a.tab.R + r, (double)es * (double)a.inv_dt);
+                const double es = warp_sum_d(e);
+                if (lane == 0) atomicAdd(a.energy + obs * a.tab.R + r, es * a.inv_dt);
             }
             ++tc;
         };
@@ -399,7 +400,7 @@ FusedShape make_shape() {
     f.threads = 32 * W;
     f.smem = sizeof(float2) * ((size_t)2 * SR * N + (size_t)2 * 2 * N + (size_t)2 * BPC * 2 * N +
                                (size_t)2 * W * 2 * RL) +
-             sizeof(float) * ((size_t)SR * N + (size_t)N);   // diagonal (as float4 [SR/2][N/2]) + pacc
+             sizeof(float) * (size_t)SR * N + sizeof(double) * (size_t)N;   // diagonal (as float4 [SR/2][N/2]) + pacc
     f.kern = taylor_fused_kernel<N, BPC, MINB>;
     return f;
 }
@@ -449,7 +450,7 @@ int launch_taylor_fused(const ctqw_hamiltonian *h, void *psi, double dt, int K, 
     a.psi = (float2 *)psi;
     a.N = h->Nmax;
     a.dt = dt;
-    a.inv_dt = (float)(1.0 / dt);
+    a.inv_dt = 1.0 / dt;
     a.K = K;
     a.n_steps = n_steps;
     a.obs_every = obs_every;

@@ -1,7 +1,7 @@
 // Fused, cluster-resident Taylor propagation for two particles in complex FP32,
 // full-row layout.
 //
-// One thread-block cluster owns one realization for the whole call (the
+// One thread-block cluster owns one realization for the whole launch (the
 // order-K Taylor polynomial of Algorithm 3, Sec. 2.3, applied n_steps times).
 // The N x N tile is split into row slabs, one per CTA; every warp owns RL
 // whole rows and each lane CL = N/32 adjacent columns of them, so a warp
@@ -21,9 +21,16 @@
 // running sum).  The diagonal dt*(eps_x1 + eps_x2) enters as two FFMA2 with
 // a per-row and a per-column pair; dt*U on x1 = x2 is added for the one lane
 // of a row that owns the diagonal.  The increment A w_2 is added to the state
-// with its rounding error carried in a second FP32 word, kept in the
-// caller's psi buffer during the call (psi is only read at the start and
-// written at the end), so hi + lo holds the state to ~2^-48 relative.
+// with its rounding error carried in a second FP32 word (lo, a state-sized
+// buffer that persists between launches; its per-step reads and writes stay
+// in L2), so hi + lo holds the state to ~2^-48 relative.
+//
+// Observables are not formed here.  At every snap_every-th step inside the
+// launch the kernel stores the state to a snapshot slot (row-major, the
+// layout of psi), and the host reduces the snapshots in FP64 with the
+// observables kernel; a launch covers the steps between a sample and the
+// sample after its last snapshot.  Keeping that work out of the kernel
+// leaves the registers of the Horner loop to the stencil.
 //
 // Row layout in shared memory (and of the carried error in global memory):
 // lane-major, the k-th column pair of lane l at float4 slot (k/2)*32 + l of
@@ -45,15 +52,15 @@ struct RowsArgs {
     const double *eps;
     const double *J;
     RealTable tab;
-    float2 *psi;
+    float2 *psi;            // state in (start of the launch) and out (end)
+    float2 *lo;             // carried rounding error (lane-major rows), in and out
+    float2 *snap;           // snapshot slots (states), or null
     double dt;
-    float inv_dt;
     float dtU;
     int K;
-    long long n_steps;
-    int obs_every;
-    long long p_width;
-    double *P_mean, *norm, *energy;
+    long long n_steps;      // steps of this launch
+    int snap_every;         // snapshot after every snap_every-th step (< n_steps), 0: none
+    long long snap_stride;  // amplitudes per snapshot slot
     int compensated;
     int *status;
     unsigned long long wait_limit_ns;
@@ -61,7 +68,7 @@ struct RowsArgs {
     float inv_j[kMaxK + 1];
 };
 
-enum { kHorner = 0, kFinal = 1, kEnergyOnly = 2 };
+enum { kHorner = 0, kFinal = 1 };
 
 // Register state of one lane: RL rows x CL columns of the Horner iterate and
 // the per-column coefficient pairs (c, c) of dt H.  The per-row pairs are the
@@ -74,7 +81,7 @@ struct Lane {
 };
 
 // One stencil application y = (dt H) P on the lane's block, then
-//   kHorner: P <- Q + (-i/j) y;  kFinal: P <- -i y;  kEnergyOnly: P unchanged.
+//   kHorner: P <- Q + (-i/j) y;  kFinal: P <- -i y.
 // usrc/dsrc: the rows above the first and below the last row in shared memory
 // (this lane's first column), read when needed so they do not hold registers.
 // Q: psi of the step in shared memory (this lane's first element, row stride N).
@@ -85,8 +92,7 @@ template <int MODE, int CL, int RL, int N, int OFF>
 __device__ __forceinline__ void stage(Lane<CL, RL> &L, const float4 *__restrict__ rowc,
                                       const float2 *__restrict__ usrc,
                                       const float2 *__restrict__ dsrc, const float2 *__restrict__ Q,
-                                      int lane, int x1_0, float dtU, float inv_j, bool energy,
-                                      float &e) {
+                                      int lane, int x1_0, float dtU, float inv_j) {
     const int from_left = (lane + 31) & 31, from_right = (lane + 1) & 31;
     const float2 dU = make_float2(dtU, dtU);
     float4 rc = rowc[0];
@@ -136,10 +142,6 @@ __device__ __forceinline__ void stage(Lane<CL, RL> &L, const float4 *__restrict_
             const int kd = (OFF + i) % CL;   // a constant once the row loop is unrolled
             if (lane == (x1_0 + i) / CL) y[kd] = __ffma2_rn(dU, c[kd], y[kd]);
         }
-        if (energy) {
-#pragma unroll
-            for (int k = 0; k < CL; ++k) e += c[k].x * y[k].x + c[k].y * y[k].y;
-        }
         if (MODE == kHorner) {
 #pragma unroll
             for (int k = 0; k < CL; k += 2) {
@@ -168,7 +170,6 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
     float2 *halo = hi + SR * N;                             // [2 parity][2: above, below][N]
     float2 *edge = halo + 2 * 2 * N;                        // [2 parity][W][2: first, last][N]
     float4 *rowc = reinterpret_cast<float4 *>(edge + 2 * W * 2 * N);  // [SR + 1] row coefficient pairs
-    float *pacc = reinterpret_cast<float *>(rowc + SR + 1);           // [N]
     __shared__ __align__(8) unsigned long long mbar[2][2];
     __shared__ __align__(8) unsigned long long mbar_never;
 
@@ -202,38 +203,24 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
         }
     }
 
-    // state in: hi = psi (shared), P = psi (registers), lo = 0 (kept in psi's own buffer)
-    float2 *gpsi = a.psi + a.tab.st_off[r];
+    // state in: hi = psi (shared), P = psi (registers); lo stays in global memory
+    float2 *glo = a.lo + a.tab.st_off[r];
 #pragma unroll
     for (int i = 0; i < RL; ++i) {
 #pragma unroll
         for (int k = 0; k < CL; k += 2) {
-            const float4 v = *reinterpret_cast<const float4 *>(gpsi + (size_t)(x1_0 + i) * N + x2_0 + k);
+            const float4 v = *reinterpret_cast<const float4 *>(a.psi + a.tab.st_off[r] + (size_t)(x1_0 + i) * N + x2_0 + k);
             L.P[i][k] = make_float2(v.x, v.y);
             L.P[i][k + 1] = make_float2(v.z, v.w);
             *reinterpret_cast<float4 *>(hi + (lrow0 + i) * N + lane * 2 + k * 32) = v;
         }
     }
-    // the carried error starts at zero; it lives in this CTA's rows of psi's
-    // buffer (lane-major), which nobody reads until the final write-back
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < RL; ++i) {
-#pragma unroll
-        for (int k = 0; k < CL; k += 2)
-            *reinterpret_cast<float4 *>(gpsi + (size_t)(x1_0 + i) * N + lane * 2 + k * 32) =
-                make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    for (int x = threadIdx.x; x < N; x += blockDim.x) pacc[x] = 0.f;
 
     const int rank_up = (rank + C - 1) % C, rank_dn = (rank + 1) % C;
     const uint32_t send_up = map_rank(smem_u32(halo + N + lane * 2), rank_up);    // their "row below" slot
     const uint32_t send_up_mb = map_rank(smem_u32(&mbar[0][1]), rank_up);
     const uint32_t send_dn = map_rank(smem_u32(halo + lane * 2), rank_dn);        // their "row above" slot
     const uint32_t send_dn_mb = map_rank(smem_u32(&mbar[0][0]), rank_dn);
-    const int g = a.tab.group_of[r];
-    const double pscale = a.tab.inv_count[g] * 0.5;
-    double *Pg = a.P_mean ? a.P_mean + a.tab.group_off[g] : nullptr;
     bool dead = false;
     const float2 *Q = hi + lrow0 * N + lane * 2;
     const int off = x1_0 % CL;
@@ -249,46 +236,9 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
         (void)mbar_wait_bounded(smem_u32(&mbar_never), 0, 1000000ull, a.status);
 
     unsigned tc = 0;
-    long long obs = 0;
     const long long n_steps = a.n_steps;
-    for (long long step = 0; step <= n_steps; ++step) {
-        const bool sample = a.obs_every > 0 && (step % a.obs_every) == 0;
-        if (sample) {
-            // P(x) = (row sums + column sums) / 2, norm = sum |psi|^2 (state = hi = P)
-            float colp[CL], nrm = 0.f;
-#pragma unroll
-            for (int k = 0; k < CL; ++k) colp[k] = 0.f;
-#pragma unroll
-            for (int i = 0; i < RL; ++i) {
-                float rs = 0.f;
-#pragma unroll
-                for (int k = 0; k < CL; ++k) {
-                    const float p = L.P[i][k].x * L.P[i][k].x + L.P[i][k].y * L.P[i][k].y;
-                    colp[k] += p;
-                    rs += p;
-                }
-                rs = warp_sum(rs);
-                nrm += rs;
-                if (lane == 0 && Pg) atomicAdd(pacc + x1_0 + i, rs);
-            }
-            if (Pg) {
-#pragma unroll
-                for (int k = 0; k < CL; ++k) atomicAdd(pacc + x2_0 + k, colp[k]);
-            }
-            if (lane == 0 && a.norm) atomicAdd(a.norm + obs * a.tab.R + r, (double)nrm);
-            __syncthreads();
-            if (Pg) {
-                for (int x = threadIdx.x; x < N; x += blockDim.x) {
-                    const float v = pacc[x];
-                    if (v != 0.f) atomicAdd(Pg + obs * a.p_width + x, (double)v * pscale);
-                    pacc[x] = 0.f;
-                }
-            }
-        }
-        const bool last = step == n_steps;
-        if (last && !(sample && a.energy)) break;
-
-        const int K = a.K;
+    const int K = a.K;
+    for (long long step = 0; step < n_steps; ++step) {
         auto run_stage = [&](const int j) {
             const int parity = tc & 1;
             const uint32_t phase = (tc >> 1) & 1;
@@ -323,16 +273,12 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
                 dsrc = halo + parity * (2 * N) + N + lane * 2;
             }
             const float inv_j = a.inv_j[j];
-            const bool en = (j == K && sample && a.energy) || last;
-            float e = 0.f;
             auto go = [&](auto off_tag) {
                 constexpr int OFF = decltype(off_tag)::value;
-                if (last)
-                    stage<kEnergyOnly, CL, RL, N, OFF>(L, rowc + lrow0, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j, true, e);
-                else if (j == 1)
-                    stage<kFinal, CL, RL, N, OFF>(L, rowc + lrow0, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j, en, e);
+                if (j == 1)
+                    stage<kFinal, CL, RL, N, OFF>(L, rowc + lrow0, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j);
                 else
-                    stage<kHorner, CL, RL, N, OFF>(L, rowc + lrow0, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j, en, e);
+                    stage<kHorner, CL, RL, N, OFF>(L, rowc + lrow0, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j);
             };
             // the first row's offset modulo CL is a multiple of gcd(RL, CL)
             static_assert(CL == 2 || CL == 4 || CL == 6 || CL == 8, "diagonal offsets enumerated for CL <= 8");
@@ -343,27 +289,17 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
                 case 6: if constexpr (CL > 6) go(std::integral_constant<int, 6 % CL>()); break;
                 default: if constexpr (CL % 2 == 1) go(std::integral_constant<int, 1>()); break;
             }
-            if (en) {
-                const float es = warp_sum(e);
-                if (lane == 0) atomicAdd(a.energy + obs * a.tab.R + r, (double)es * (double)a.inv_dt);
-            }
             ++tc;
         };
-        if (last) {
-            run_stage(K);
-        } else {
-            for (int j = K; j >= 1; --j) run_stage(j);
-        }
-        if (sample) ++obs;
-        if (last) break;
+        for (int j = K; j >= 1; --j) run_stage(j);
 
-        // psi(t+dt) = psi + A w_2 (in P); rounding error carried in lo (psi's buffer)
+        // psi(t+dt) = psi + A w_2 (in P); rounding error carried in lo
 #pragma unroll
         for (int i = 0; i < RL; ++i) {
 #pragma unroll
             for (int k = 0; k < CL; k += 2) {
                 float4 *hp = reinterpret_cast<float4 *>(hi + (lrow0 + i) * N + lane * 2 + k * 32);
-                float4 *lp = reinterpret_cast<float4 *>(gpsi + (size_t)(x1_0 + i) * N + lane * 2 + k * 32);
+                float4 *lp = reinterpret_cast<float4 *>(glo + (size_t)(x1_0 + i) * N + lane * 2 + k * 32);
                 float4 h4 = *hp;
                 if (a.compensated) {
                     float4 l4 = *lp;
@@ -384,6 +320,17 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
                 L.P[i][k + 1] = make_float2(h4.z, h4.w);
             }
         }
+        // a snapshot step: the new state (P) to its slot, row-major like psi
+        if (a.snap_every > 0 && step + 1 < n_steps && (step + 1) % a.snap_every == 0) {
+            float2 *gs = a.snap + ((step + 1) / a.snap_every - 1) * a.snap_stride + a.tab.st_off[r];
+#pragma unroll
+            for (int i = 0; i < RL; ++i) {
+#pragma unroll
+                for (int k = 0; k < CL; k += 2)
+                    *reinterpret_cast<float4 *>(gs + (size_t)(x1_0 + i) * N + x2_0 + k) =
+                        make_float4(L.P[i][k].x, L.P[i][k].y, L.P[i][k + 1].x, L.P[i][k + 1].y);
+            }
+        }
     }
 
     // state out (hi; the carried error is below half an ulp of it)
@@ -391,7 +338,7 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
     for (int i = 0; i < RL; ++i) {
 #pragma unroll
         for (int k = 0; k < CL; k += 2)
-            *reinterpret_cast<float4 *>(gpsi + (size_t)(x1_0 + i) * N + x2_0 + k) =
+            *reinterpret_cast<float4 *>(a.psi + a.tab.st_off[r] + (size_t)(x1_0 + i) * N + x2_0 + k) =
                 *reinterpret_cast<const float4 *>(hi + (lrow0 + i) * N + lane * 2 + k * 32);
     }
     cluster_barrier();
@@ -412,7 +359,7 @@ RowsShape rows_shape() {
     f.C = N / SR;
     f.threads = 32 * W;
     f.smem = sizeof(float2) * ((size_t)SR * N + (size_t)2 * 2 * N + (size_t)2 * W * 2 * N) +
-             sizeof(float4) * (size_t)(SR + 1) + sizeof(float) * (size_t)N;
+             sizeof(float4) * (size_t)(SR + 1);
     f.kern = taylor_fused_rows_kernel<CL, RL, W, MINB>;
     return f;
 }
@@ -423,9 +370,9 @@ bool rows_shape_for(int N, int idx, RowsShape &f) {
     RowsShape opts[kRowsShapes];
     switch (N) {
         case 64: opts[0] = rows_shape<2, 8, 8, 2>(); opts[1] = rows_shape<2, 4, 8, 2>(); opts[2] = rows_shape<2, 8, 4, 3>(); break;
-        case 128: opts[0] = rows_shape<4, 8, 4, 2>(); opts[1] = rows_shape<4, 4, 8, 2>(); opts[2] = rows_shape<4, 4, 4, 3>(); break;
+        case 128: opts[0] = rows_shape<4, 4, 8, 2>(); opts[1] = rows_shape<4, 8, 4, 2>(); opts[2] = rows_shape<4, 4, 4, 3>(); break;
         case 192: opts[0] = rows_shape<6, 4, 4, 3>(); opts[1] = rows_shape<6, 4, 8, 1>(); opts[2] = rows_shape<6, 4, 4, 2>(); break;
-        case 256: opts[0] = rows_shape<8, 4, 4, 3>(); opts[1] = rows_shape<8, 4, 8, 1>(); opts[2] = rows_shape<8, 4, 4, 2>(); break;
+        case 256: opts[0] = rows_shape<8, 4, 4, 2>(); opts[1] = rows_shape<8, 4, 8, 1>(); opts[2] = rows_shape<8, 4, 4, 3>(); break;
         default: return false;
     }
     if (idx < 0 || idx >= kRowsShapes) return false;
@@ -440,10 +387,9 @@ bool fused_rows_supported(const ctqw_hamiltonian *h, int dtype) {
     return dtype == CTQW_C64 && h->m == 2 && h->uniform && rows_shape_for(h->Nmax, 0, f);
 }
 
-int launch_taylor_fused_rows(const ctqw_hamiltonian *h, void *psi, double dt, int K,
-                             int64_t n_steps, int obs_every, double *P_mean, double *norm,
-                             double *energy, int compensated, int shape, int test_timeout,
-                             cudaStream_t s) {
+int launch_taylor_fused_rows(const ctqw_hamiltonian *h, void *psi, void *lo, void *snap,
+                             int snap_every, double dt, int K, int64_t n_steps, int compensated,
+                             int shape, int test_timeout, cudaStream_t s) {
     RowsShape f;
     if (!rows_shape_for(h->Nmax, shape, f)) {
         ctqw_set_error("fused path: unsupported size N=%d or shape %d", h->Nmax, shape);
@@ -458,16 +404,14 @@ int launch_taylor_fused_rows(const ctqw_hamiltonian *h, void *psi, double dt, in
     a.J = h->J64;
     a.tab = real_table(h);
     a.psi = (float2 *)psi;
+    a.lo = (float2 *)lo;
+    a.snap = (float2 *)snap;
+    a.snap_every = snap ? snap_every : 0;
+    a.snap_stride = h->total_amp;
     a.dt = dt;
-    a.inv_dt = (float)(1.0 / dt);
     a.dtU = (float)(dt * h->U);
     a.K = K;
     a.n_steps = n_steps;
-    a.obs_every = obs_every;
-    a.p_width = h->p_width;
-    a.P_mean = P_mean;
-    a.norm = norm;
-    a.energy = energy;
     a.compensated = compensated;
     a.status = h->status_d;
     a.test_timeout = test_timeout;

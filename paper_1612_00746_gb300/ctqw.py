@@ -117,7 +117,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "ctqw_ensemble_observables": [vp, i32, vp, vp, vp, vp, vp, vp],
         "ctqw_check_status": [vp, vp],
         "ctqw_adjoint_workspace_size": [vp, i32, i32, i64, i32, ctypes.POINTER(sz)],
-        "ctqw_adjoint_grad": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, vp, vp, vp, sz, vp],
+        "ctqw_adjoint_grad": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp],
         "ctqw_taylor_order": [dbl, i64, dbl, i32, i32, ctypes.POINTER(i32), pd],
         "ctqw_one_body_density": [vp, i32, vp, vp, vp],
         "ctqw_propagate_exact": [vp, i32, vp, dbl, i64, i32, vp, vp, vp, ctypes.POINTER(i32), vp],
@@ -485,26 +485,34 @@ def adjoint_workspace(h: Hamiltonian, dtype: int, K: int, n_steps: int, checkpoi
 
 def ctqw_adjoint_grad(h: Hamiltonian, psi0: torch.Tensor, dtype: int, dt: float, K: int,
                       n_steps: int, checkpoint_every: int, P_target: torch.Tensor, stream=None,
-                      workspace: Optional[torch.Tensor] = None):
-    """Loss on Pbar(x, T) and its gradient w.r.t. every realization's eps and J.
+                      workspace: Optional[torch.Tensor] = None, per_realization: bool = True,
+                      means: bool = True):
+    """Loss on Pbar(x, T) and its gradients (ctqw_adjoint_grad).
 
-    Returns (loss [1], grad_eps [sum N], grad_J [sum N], P_final [p_width]) as
-    FP64 device tensors (ctqw_adjoint_grad).  workspace: from adjoint_workspace
-    (allocated here when None).
+    Returns (loss [1], grad_eps [sum N], grad_J [sum N], P_final [p_width],
+    grad_eps_mean [p_width], grad_J_mean [p_width]) as FP64 device tensors:
+    the gradients w.r.t. every realization's eps and J (None unless
+    per_realization) and their sums over each size group's realizations,
+    the gradients w.r.t. the means the group shares (None unless means).
+    workspace: from adjoint_workspace (allocated here when None).
     """
     dev = psi0.device
     ws = workspace if workspace is not None else adjoint_workspace(h, dtype, K, n_steps,
                                                                    checkpoint_every, dev)
     n = int(h.sizes.sum())
-    loss = torch.empty(1, dtype=torch.float64, device=dev)
-    ge = torch.empty(n, dtype=torch.float64, device=dev)
-    gJ = torch.empty(n, dtype=torch.float64, device=dev)
-    Pf = torch.empty(h.p_width, dtype=torch.float64, device=dev)
+    f64 = dict(dtype=torch.float64, device=dev)
+    loss = torch.empty(1, **f64)
+    ge = torch.empty(n, **f64) if per_realization else None
+    gJ = torch.empty(n, **f64) if per_realization else None
+    gem = torch.empty(h.p_width, **f64) if means else None
+    gJm = torch.empty(h.p_width, **f64) if means else None
+    Pf = torch.empty(h.p_width, **f64)
     tgt = P_target.to(device=dev, dtype=torch.float64).contiguous()
     _check(load().ctqw_adjoint_grad(h.handle, dtype, _ptr(psi0), float(dt), int(K), int(n_steps),
                                     int(checkpoint_every), _ptr(tgt), _ptr(loss), _ptr(ge), _ptr(gJ),
-                                    _ptr(Pf), _ptr(ws), ws.numel(), _stream(stream)))
-    return loss, ge, gJ, Pf
+                                    _ptr(gem), _ptr(gJm), _ptr(Pf), _ptr(ws), ws.numel(),
+                                    _stream(stream)))
+    return loss, ge, gJ, Pf, gem, gJm
 
 
 class EnsembleOccupationLoss(torch.autograd.Function):
@@ -523,11 +531,10 @@ class EnsembleOccupationLoss(torch.autograd.Function):
         h = build_for_workload(w, eps_mean=em, J_mean=jm)
         psi = h.new_state(dtype, P_target.device if P_target.is_cuda else "cuda")
         ctqw_init_state(h, psi, initial_sites(w, h), dtype)
-        loss, ge, gJ, _ = ctqw_adjoint_grad(h, psi, dtype, w.dt, w.K, w.n_steps, checkpoint_every,
-                                            P_target)
-        N = int(h.sizes[0])
-        ctx.save_for_backward(ge.view(h.R, N).sum(0).to(eps_mean.device, eps_mean.dtype),
-                              gJ.view(h.R, N).sum(0).to(J_mean.device, J_mean.dtype))
+        loss, _, _, _, gem, gJm = ctqw_adjoint_grad(h, psi, dtype, w.dt, w.K, w.n_steps,
+                                                    checkpoint_every, P_target, per_realization=False)
+        ctx.save_for_backward(gem.to(eps_mean.device, eps_mean.dtype),
+                              gJm.to(J_mean.device, J_mean.dtype))
         h.close()
         return loss[0].to(eps_mean.device, eps_mean.dtype)
 

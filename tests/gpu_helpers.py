@@ -7,6 +7,30 @@ import ctqw_workloads as cw
 TOL_FP64 = 1e-11
 TOL_FP32 = 2e-6
 TOL_NORM_DRIFT = 1e-6
+U_FP32 = 2.0 ** -24       # unit roundoff of FP32
+
+
+def h_bound(w):
+    """Upper bound of ||H||_2 from the workload's description (Gershgorin on
+    the Kronecker sum): m (max|eps| + 2 max|J|) + |U| m (m - 1) / 2."""
+    eps_max = abs(0.0) + w.eps_halfwidth
+    J_max = abs(w.J0) + w.J_halfwidth
+    return w.m * (eps_max + 2.0 * J_max) + abs(w.U) * w.m * (w.m - 1) / 2.0
+
+
+def energy_tol(w):
+    """Tolerance on an FP32 path's energy, <psi|H|psi>, against the oracle.
+
+    E = sum_s conj(psi_s) (H psi)_s with every quantity that enters it within
+    a few FP32 roundings of exact: storing the state in FP32 moves E by at
+    most u ||H|| (the compensated update keeps the propagated state there),
+    forming H psi and the product in FP32 adds at most 8 u ||H|| (six
+    roundings in the stencil, two in the product, each relative to
+    sum |psi| (|H| |psi|) <= ||H||), and the FP64 (or exact) sums add
+    nothing at this scale.  16 u ||H|| leaves the remaining 7 u ||H|| for
+    the state's drift over the run, which the norm bounds at ~4 u here.
+    """
+    return 16.0 * U_FP32 * h_bound(w)
 
 
 def oracle_params(w, realizations=None, eps_mean=None, J_mean=None):

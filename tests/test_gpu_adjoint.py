@@ -32,8 +32,8 @@ def _gpu(ctqw, w, dtype, target, M=5, eps_mean=None, J_mean=None, round_to_f32=T
     h = ctqw.build_for_workload(w, eps_mean=eps_mean, J_mean=J_mean, round_to_f32=round_to_f32)
     psi = h.new_state(dtype)
     ctqw.ctqw_init_state(h, psi, ctqw.initial_sites(w, h), dtype)
-    loss, ge, gJ, Pf = ctqw.ctqw_adjoint_grad(h, psi, dtype, w.dt, w.K, w.n_steps, M,
-                                              torch.tensor(target))
+    loss, ge, gJ, Pf, _, _ = ctqw.ctqw_adjoint_grad(h, psi, dtype, w.dt, w.K, w.n_steps, M,
+                                                    torch.tensor(target))
     ctqw.ctqw_check_status(h)
     eps, J = h.params()
     h.close()
@@ -112,13 +112,64 @@ def test_adjoint_against_central_differences_of_gpu_loss(ctqw):
 
 
 def test_autograd_function_returns_summed_gradients(ctqw):
+    """EnsembleOccupationLoss takes its gradients from the C call's sums over
+    realizations; they must equal the oracle's per-realization gradients
+    summed (the gradient with respect to the shared means)."""
     w = _workload(N=6, R=3, n_steps=8, K=8)
     em = torch.zeros(w.N, dtype=torch.float64, requires_grad=True)
     jm = torch.ones(w.N, dtype=torch.float64, requires_grad=True)
     target = torch.full((w.N,), 1.0 / w.N, dtype=torch.float64, device="cuda")
     loss = ctqw.EnsembleOccupationLoss.apply(em, jm, w, target, cw.C128, 4)
     loss.backward()
-    _, ge, gJ, *_ = _gpu(ctqw, w, cw.C128, target.cpu().numpy(), M=4,
-                         eps_mean=np.zeros(w.N), J_mean=np.ones(w.N))
-    np.testing.assert_allclose(em.grad.numpy(), ge.sum(0), atol=1e-14)
-    np.testing.assert_allclose(jm.grad.numpy(), gJ.sum(0), atol=1e-14)
+    eps, J = (a.reshape(w.R, w.N) for a in ctqw.build_for_workload(
+        w, eps_mean=np.zeros(w.N), J_mean=np.ones(w.N)).params())
+    lo, ge_o, gJ_o = _oracle(w, eps, J, target.cpu().numpy())
+    assert abs(loss.item() - lo) <= 1e-13 * max(1.0, lo)
+    scale = max(np.max(np.abs(ge_o)), np.max(np.abs(gJ_o)))
+    np.testing.assert_allclose(em.grad.numpy(), ge_o.sum(0), atol=1e-11 * scale)
+    np.testing.assert_allclose(jm.grad.numpy()[:w.N - 1], gJ_o.sum(0), atol=1e-11 * scale)
+    assert jm.grad.numpy()[w.N - 1] == 0.0     # no wrap bond on an open chain
+
+
+@pytest.mark.parametrize("dtype", [cw.C128, cw.C64])
+def test_mean_gradients_are_group_sums_of_realization_gradients(ctqw, dtype):
+    """A ragged batch (three size groups): grad_eps_mean / grad_J_mean hold,
+    per group in ascending N, the sum over the group's realizations of the
+    per-realization gradients, and match the oracle's sums."""
+    w = cw.Workload(name="adj_ragged", m=2, statistics=0, periodic=False, N=7, R=7, J0=1.0,
+                    U=1.0, eps_halfwidth=0.5, J_halfwidth=0.2, sites=(1, 3), dt=0.05, K=8,
+                    n_steps=10, obs_every=0, dtype=dtype, seed=4, ragged_sizes=(5, 6, 7))
+    h = ctqw.build_for_workload(w)
+    psi = h.new_state(dtype)
+    ctqw.ctqw_init_state(h, psi, ctqw.initial_sites(w, h), dtype)
+    groups = [int(g) for g in h.group_sizes]
+    assert groups == [5, 6, 7]
+    rng = np.random.default_rng(3)
+    target = np.concatenate([rng.dirichlet(np.ones(g)) for g in groups])
+    loss, ge, gJ, _, gem, gJm = ctqw.ctqw_adjoint_grad(h, psi, dtype, w.dt, w.K, w.n_steps, 4,
+                                                       torch.tensor(target))
+    ctqw.ctqw_check_status(h)
+    eps, J = h.params()
+    ge, gJ, gem, gJm = (a.cpu().numpy() for a in (ge, gJ, gem, gJm))
+    hsizes = [int(n) for n in h.sizes]
+    h.close()
+    offs = np.concatenate([[0], np.cumsum(hsizes)])
+    tol = 1e-11 if dtype == cw.C128 else 1e-5
+    goff = 0
+    for g in groups:
+        members = [r for r in range(w.R) if hsizes[r] == g]
+        # the C sums are exactly the per-realization outputs summed in order
+        se = sum(ge[offs[r]:offs[r] + g] for r in members)
+        sj = sum(gJ[offs[r]:offs[r] + g] for r in members)
+        np.testing.assert_allclose(gem[goff:goff + g], se, rtol=0, atol=1e-15 * max(1, np.abs(se).max()))
+        np.testing.assert_allclose(gJm[goff:goff + g], sj, rtol=0, atol=1e-15 * max(1, np.abs(sj).max()))
+        # and the oracle's gradients of this group's realizations, summed
+        psi0 = oracle.initial_state(g, 2, w.initial_sites(g), 0)
+        _, ge_o, gJ_o = oracle.loss_and_adjoint_gradient(
+            [eps[offs[r]:offs[r] + g] for r in members], [J[offs[r]:offs[r] + g - 1] for r in members],
+            g, 2, False, w.U, psi0, w.dt, w.K, w.n_steps, target[goff:goff + g])
+        scale = max(np.abs(ge_o).max(), np.abs(gJ_o).max())
+        assert np.max(np.abs(gem[goff:goff + g] - ge_o.sum(0))) <= tol * scale
+        assert np.max(np.abs(gJm[goff:goff + g - 1] - gJ_o.sum(0))) <= tol * scale
+        assert gJm[goff + g - 1] == 0.0
+        goff += g

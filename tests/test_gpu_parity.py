@@ -8,7 +8,7 @@ import pytest
 
 import ctqw_workloads as cw
 import oracle
-from gpu_helpers import TOL_FP32, TOL_FP64, TOL_NORM_DRIFT, oracle_params, per_realization_P
+from gpu_helpers import TOL_FP32, TOL_FP64, TOL_NORM_DRIFT, energy_tol, oracle_params, per_realization_P
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -149,7 +149,7 @@ def test_fused_c64_bosons(ctqw):
     w = cw.get("bosons_small")
     got = ctqw.run_workload(w)
     ref = oracle.ensemble_run(w)
-    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, energy_tol(w))
     assert np.max(np.abs(got["norm"] - 1.0)) <= TOL_NORM_DRIFT
 
 
@@ -160,7 +160,7 @@ def test_fused_c64_shapes(ctqw, N, periodic, K):
                                        sites=(N // 2 - 1, N // 2))
     got = ctqw.run_workload(w)
     ref = oracle.ensemble_run(w)
-    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, energy_tol(w))
     P = per_realization_P(got["psi"], got["st_off"], got["sizes"], 2)
     for r in range(2):
         assert np.max(np.abs(P[r] - ref["P"][r][-1])) <= TOL_FP32
@@ -170,14 +170,14 @@ def test_fused_c64_distinguishable_open(ctqw):
     w = cw.get("fp64_plain_small").with_(dtype=cw.C64, n_steps=300, obs_every=30)
     got = ctqw.run_workload(w)
     ref = oracle.ensemble_run(w)
-    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, energy_tol(w))
 
 
 def test_plain_c64(ctqw):
     w = cw.get("bosons_small").with_(n_steps=100, obs_every=25)
     got = ctqw.run_workload(w, flags=ctqw.FLAG_PLAIN)
     ref = oracle.ensemble_run(w)
-    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, energy_tol(w))
 
 
 @pytest.mark.parametrize("flags", [0, 1])   # fused (order-4 polynomial on chip), plain stages
@@ -185,7 +185,7 @@ def test_rk4_c64(ctqw, flags):
     w = cw.get("bosons_small").with_(R=2, n_steps=100, obs_every=25)
     got = ctqw.run_workload(w, method=ctqw.RK4, flags=flags)
     ref = oracle.ensemble_run(w, method="rk4")
-    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, energy_tol(w))
 
 
 # ------------------------------------------------------------------ edge cases
@@ -261,7 +261,7 @@ def test_fused_c64_alternative_shapes(ctqw, N, shape):
                                        sites=(N // 2 - 1, N // 2))
     got = ctqw.run_workload(w, flags=ctqw.FUSED_SHAPE(shape))
     ref = oracle.ensemble_run(w)
-    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, energy_tol(w))
 
 
 @pytest.mark.parametrize("k", [3, 7])   # no compiled shape at these indices
@@ -287,7 +287,7 @@ def test_fused_bounded_wait_gives_up_and_reports(ctqw):
     ctqw.ctqw_check_status(h)          # the flag is cleared once reported
     got = ctqw.run_workload(w)         # and the device keeps working
     ref = oracle.ensemble_run(w)
-    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, 2e-5)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, energy_tol(w))
     h.close()
 
 

@@ -9,7 +9,7 @@ import pytest
 
 import ctqw_workloads as cw
 import oracle
-from gpu_helpers import TOL_FP32, TOL_FP64
+from gpu_helpers import TOL_FP32, TOL_FP64, energy_tol
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -26,10 +26,10 @@ def ctqw():
     return c
 
 
-def _compare(got, ref, dtype):
+def _compare(got, ref, dtype, w):
     tolP = TOL_FP64 if dtype == cw.C128 else TOL_FP32
     tol_n = 1e-13 if dtype == cw.C128 else 1e-6
-    tol_e = 1e-10 if dtype == cw.C128 else 2e-5
+    tol_e = 1e-10 if dtype == cw.C128 else energy_tol(w)
     assert np.max(np.abs(got["P_mean"] - ref["P_mean"])) <= tolP
     assert np.max(np.abs(got["norm"] - 1.0)) <= tol_n
     assert np.max(np.abs(got["norm"] - ref["norm"].T)) <= tol_n
@@ -44,7 +44,7 @@ def test_renormalized_runs_match_the_oracle(ctqw, name, dtype, method):
     m = ctqw.RK4 if method == "rk4" else ctqw.TAYLOR
     got = ctqw.run_workload(w, method=m, K=4, flags=ctqw.FLAG_RENORMALIZE)
     ref = oracle.ensemble_run(w, method=method, K=4, renormalize=True)
-    _compare(got, ref, dtype)
+    _compare(got, ref, dtype, w)
 
 
 def test_rk4_without_the_flag_drifts(ctqw):

@@ -12,7 +12,7 @@ import pytest
 
 import ctqw_workloads as cw
 import oracle
-from gpu_helpers import TOL_FP32, TOL_NORM_DRIFT, per_realization_P
+from gpu_helpers import TOL_FP32, TOL_NORM_DRIFT, energy_tol, per_realization_P
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -29,13 +29,13 @@ def ctqw():
     return c
 
 
-def _check(got, ref, tol_energy=2e-5):
+def _check(got, ref, w):
     dP = np.max(np.abs(got["P_mean"] - ref["P_mean"]))
     dn = np.max(np.abs(got["norm"] - ref["norm"].T))
     de = np.max(np.abs(got["energy"] - ref["energy"].T))
     assert dP <= TOL_FP32, f"max|dP| = {dP:.3e}"
     assert dn <= TOL_NORM_DRIFT, f"max|dnorm| = {dn:.3e}"
-    assert de <= tol_energy, f"max|dE| = {de:.3e}"
+    assert de <= energy_tol(w), f"max|dE| = {de:.3e}"
 
 
 @pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6])
@@ -46,7 +46,7 @@ def test_tiled_bosons_against_oracle(ctqw, shape, N, periodic, K):
                                        sites=(N // 2 - 1, N // 2))
     got = ctqw.run_workload(w, flags=ctqw.FLAG_TILED(shape))
     ref = oracle.ensemble_run(w)
-    _check(got, ref)
+    _check(got, ref, w)
     P = per_realization_P(got["psi"], got["st_off"], got["sizes"], 2)
     for r in range(w.R):
         assert np.max(np.abs(P[r] - ref["P"][r][-1])) <= TOL_FP32
@@ -57,14 +57,14 @@ def test_tiled_ragged_batch(ctqw, shape):
     w = cw.get("ragged_n128_1024").with_(R=5, ragged_sizes=(64, 130, 200), n_steps=16, obs_every=8)
     got = ctqw.run_workload(w, flags=ctqw.FLAG_TILED(shape))
     ref = oracle.ensemble_run(w)
-    _check(got, ref)
+    _check(got, ref, w)
 
 
 def test_tiled_distinguishable_long_run(ctqw):
     w = cw.get("fp64_plain_small").with_(dtype=cw.C64, N=64, n_steps=300, obs_every=50)
     got = ctqw.run_workload(w, flags=ctqw.FLAG_TILED(0))
     ref = oracle.ensemble_run(w)
-    _check(got, ref)
+    _check(got, ref, w)
 
 
 def test_tiled_agrees_with_fused_kernel_at_n256(ctqw):
@@ -99,4 +99,4 @@ def test_tiled_default_depths(ctqw, K):
                                        sites=(149, 150))
     got = ctqw.run_workload(w)
     ref = oracle.ensemble_run(w)
-    _check(got, ref)
+    _check(got, ref, w)

@@ -11,7 +11,7 @@ import pytest
 
 import ctqw_workloads as cw
 import oracle
-from gpu_helpers import TOL_FP32, TOL_NORM_DRIFT, per_realization_P
+from gpu_helpers import TOL_FP32, TOL_NORM_DRIFT, energy_tol, per_realization_P
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -28,13 +28,13 @@ def ctqw():
     return c
 
 
-def _check(got, ref, tol_energy=2e-5):
+def _check(got, ref, w):
     dP = np.max(np.abs(got["P_mean"] - ref["P_mean"]))
     dn = np.max(np.abs(got["norm"] - ref["norm"].T))
     de = np.max(np.abs(got["energy"] - ref["energy"].T))
     assert dP <= TOL_FP32, f"max|dP| = {dP:.3e}"
     assert dn <= TOL_NORM_DRIFT, f"max|dnorm| = {dn:.3e}"
-    assert de <= tol_energy, f"max|dE| = {de:.3e}"
+    assert de <= energy_tol(w), f"max|dE| = {de:.3e}"
 
 
 @pytest.mark.parametrize("N,K,n_steps,obs_every", [
@@ -50,7 +50,7 @@ def test_wavefront_bosons_against_oracle(ctqw, N, K, n_steps, obs_every):
     got = ctqw.run_workload(w, flags=ctqw.FLAG_WAVEFRONT)
     ref = oracle.ensemble_run(w.with_(obs_every=obs_every if obs_every else n_steps))
     if obs_every:
-        _check(got, ref)
+        _check(got, ref, w)
     if n_steps % (obs_every or n_steps) == 0:
         # the oracle's last sample is the final state
         P = per_realization_P(got["psi"], got["st_off"], got["sizes"], 2)
@@ -73,7 +73,7 @@ def test_wavefront_distinguishable(ctqw):
     w = cw.get("fp64_plain_small").with_(dtype=cw.C64, N=64, n_steps=200, obs_every=25)
     got = ctqw.run_workload(w, flags=ctqw.FLAG_WAVEFRONT)
     ref = oracle.ensemble_run(w)
-    _check(got, ref)
+    _check(got, ref, w)
 
 
 def test_wavefront_ragged_widths(ctqw):
@@ -81,7 +81,7 @@ def test_wavefront_ragged_widths(ctqw):
                                          n_steps=20, obs_every=10)
     got = ctqw.run_workload(w, flags=ctqw.FLAG_WAVEFRONT)
     ref = oracle.ensemble_run(w)
-    _check(got, ref)
+    _check(got, ref, w)
     P = per_realization_P(got["psi"], got["st_off"], got["sizes"], 2)
     for r in range(w.R):
         assert np.max(np.abs(P[r] - ref["P"][r][-1])) <= TOL_FP32
@@ -94,7 +94,7 @@ def test_wavefront_agrees_with_full_row_kernel(ctqw):
     b = ctqw.run_workload(w)
     assert np.max(np.abs(a["P_mean"] - b["P_mean"])) <= TOL_FP32
     assert np.max(np.abs(a["norm"] - 1.0)) <= TOL_NORM_DRIFT
-    assert np.max(np.abs(a["energy"] - a["energy"][0])) <= 2e-5
+    assert np.max(np.abs(a["energy"] - a["energy"][0])) <= energy_tol(w)
 
 
 @pytest.mark.parametrize("kw", [{"periodic": True}, {"N": 96}, {"K": 17}])
