@@ -43,6 +43,7 @@ extern "C" {
 #define CTQW_ENOMEM 2          /* a device allocation failed                     */
 #define CTQW_ECUDA 3           /* a CUDA runtime call or kernel launch failed    */
 #define CTQW_EUNSUPPORTED 4    /* valid request the library does not implement  */
+#define CTQW_ENORM 5           /* the norm check found a non-finite or drifting norm (see ctqw_check_status) */
 #define CTQW_ETIMEOUT 6        /* a bounded wait inside a kernel gave up (see ctqw_check_status) */
 
 /* Particle statistics (initial-state symmetry). */
@@ -157,7 +158,8 @@ int ctqw_output_layout(const ctqw_hamiltonian *h, int64_t *p_width, int32_t *n_g
 
 /*
  * Write the localised initial state of every realization into psi_dev
- * (zeroing everything else).  sites_host is [R][m] (host, int32), the
+ * (zeroing everything else).  The sites are staged through a device buffer
+ * of the handle (no allocation), so calls on one handle are stream-ordered.  sites_host is [R][m] (host, int32), the
  * occupied sites of each realization.  Bosons: normalised sum over all
  * permutations; fermions: normalised signed sum (EINVAL if two sites
  * coincide); distinguishable: |x_1..x_m>.
@@ -342,9 +344,10 @@ int ctqw_ensemble_observables(const ctqw_hamiltonian *h, int32_t dtype, const vo
  * array of 48 MiB inside this library (held on every GPU that loads it until
  * the process exits): 3 x amplitudes_total x 8 bytes (CTQW_C64) or x 16
  * bytes (CTQW_C128) must fit, else CTQW_EINVAL with a message and nothing
- * launched.  The call allocates and frees nothing.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.
+ * launched.  The call allocates and frees nothing.  The handle's device must
+ * be the current device (else CTQW_EINVAL).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.
  * Every call shares the one array, so calls whose work overlaps on the GPU
  * (e.g. on two streams) race and give wrong results; serialise them.
  * Arguments, outputs and results are those of ctqw_propagate_taylor with
@@ -397,13 +400,40 @@ int ctqw_adjoint_grad(const ctqw_hamiltonian *h, int32_t dtype, const void *psi0
                       void *stream);
 
 /*
- * Synchronize `stream` and report whether a kernel of an earlier call on this
- * handle gave up a bounded wait (the fused kernel waits for halo rows from
- * its neighbour CTAs with a 2 s limit; it never spins unbounded).  Returns
- * CTQW_ETIMEOUT once per such event (the flag is cleared), CTQW_OK otherwise.
- * The results of a call that timed out are invalid.
+ * Norm check (Algorithms 2 and 3 check the norm after every step; Sec. 4 of
+ * the paper asks for double checks of GPU results).  Every propagator given
+ * a norm_dev output checks the norms it sampled when it finishes (one small
+ * launch on the stream): a realization fails at its first sample whose norm
+ * is not finite, or, when drift_tol > 0, differs from its first sample by
+ * more than drift_tol.  The first failing realization and sample are kept
+ * on the handle until ctqw_check_status reports them as CTQW_ENORM.
+ * drift_tol = 0 (the default) checks finiteness only; the FP32 paths drift
+ * by ~1e-7 over the workloads here, RK4 at large dt by much more (it does
+ * not conserve the norm).  Errors: EINVAL for a null handle or a negative
+ * or non-finite drift_tol.
+ */
+int ctqw_set_norm_check(ctqw_hamiltonian *h, double drift_tol);
+
+/*
+ * Synchronize `stream` and report a device-side failure of an earlier call
+ * on this handle: CTQW_ETIMEOUT when a kernel gave up a bounded wait (the
+ * fused kernel waits for halo rows from its neighbour CTAs with a 2 s limit;
+ * it never spins unbounded), else CTQW_ENORM when the norm check failed, with
+ * the realization, the sample and the reason in ctqw_last_error().  Each
+ * event is reported once (the status is cleared); CTQW_OK otherwise.  The
+ * results of a call that timed out are invalid.
  */
 int ctqw_check_status(const ctqw_hamiltonian *h, void *stream);
+
+/*
+ * Failure injection for tests (the paper has no counterpart): the next
+ * `after` device allocations of the library succeed and the one after them
+ * fails as if the device were out of memory, so that the error path (the
+ * call returns CTQW_ENOMEM and releases what it took) runs without
+ * exhausting a shared GPU.  -1 switches it off.  Process-wide.  Errors:
+ * EINVAL for after < -1.
+ */
+int ctqw_inject_alloc_failure(int32_t after);
 
 /* ------------------------------------------------------------------------
  * q-dimensional lattices and general graphs (Sec. 2: a q-dimensional lattice

@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <atomic>
+#include <climits>
 #include <map>
 
 #include "ctqw_internal.cuh"
@@ -11,6 +13,16 @@
 namespace {
 
 thread_local char g_err[512] = "";
+// allocations that still succeed before one is made to fail (-1: none)
+std::atomic<int> g_alloc_fail_after{-1};
+
+bool injected_alloc_failure() {
+    int v = g_alloc_fail_after.load();
+    while (v >= 0) {
+        if (g_alloc_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;
+    }
+    return false;
+}
 
 size_t elem_bytes(int dtype) { return dtype == CTQW_C64 ? sizeof(float2) : sizeof(double2); }
 
@@ -21,14 +33,14 @@ int64_t n_samples(int64_t n_steps, int obs_every) {
 void free_device(ctqw_hamiltonian *h) {
     void *ptrs[] = {h->eps32, h->J32, h->eps64, h->J64, h->sizes_d, h->group_of_d, h->par_off_d,
                     h->st_off_d, h->group_off_d, h->joint_off_d, h->inv_count_d, h->status_d, h->renorm_d,
-                    h->by_group_d, h->eps_mean_d, h->J_mean_d, h->eps64_0, h->J64_0};
+                    h->by_group_d, h->eps_mean_d, h->J_mean_d, h->eps64_0, h->J64_0, h->sites_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
 
 template <typename T>
 int upload(T **dst, const std::vector<T> &src, cudaStream_t s) {
-    if (cudaMalloc((void **)dst, std::max<size_t>(1, src.size()) * sizeof(T)) != cudaSuccess) {
+    if (ctqw_malloc((void **)dst, std::max<size_t>(1, src.size()) * sizeof(T)) != cudaSuccess) {
         ctqw_set_error("cudaMalloc of %zu bytes failed", src.size() * sizeof(T));
         return CTQW_ENOMEM;
     }
@@ -136,6 +148,16 @@ void ctqw_set_error(const char *fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
+}
+
+cudaError_t ctqw_malloc(void **p, size_t bytes) {
+    if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t ctqw_malloc_async(void **p, size_t bytes, cudaStream_t s) {
+    if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
+    return cudaMallocAsync(p, bytes, s);
 }
 
 int ctqw_cuda_fail(cudaError_t e, const char *what) {
@@ -256,16 +278,19 @@ int ctqw_build_hamiltonian(const ctqw_lattice_desc *d, void *stream, ctqw_hamilt
     };
     if (cudaGetDevice(&h->device) != cudaSuccess) { ctqw_set_error("no CUDA device"); return fail(CTQW_ECUDA); }
     const size_t pb = sizeof(double) * h->total_par;
-    if (cudaMalloc(&h->eps32, sizeof(float) * h->total_par) != cudaSuccess ||
-        cudaMalloc(&h->J32, sizeof(float) * h->total_par) != cudaSuccess ||
-        cudaMalloc(&h->eps64, pb) != cudaSuccess || cudaMalloc(&h->J64, pb) != cudaSuccess ||
-        cudaMalloc(&u_eps_d, pb) != cudaSuccess || cudaMalloc(&u_J_d, pb) != cudaSuccess ||
-        cudaMalloc(&h->status_d, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&h->renorm_d, sizeof(double) * h->R) != cudaSuccess) {
+    if (ctqw_malloc(&h->eps32, sizeof(float) * h->total_par) != cudaSuccess ||
+        ctqw_malloc(&h->J32, sizeof(float) * h->total_par) != cudaSuccess ||
+        ctqw_malloc(&h->eps64, pb) != cudaSuccess || ctqw_malloc(&h->J64, pb) != cudaSuccess ||
+        ctqw_malloc(&u_eps_d, pb) != cudaSuccess || ctqw_malloc(&u_J_d, pb) != cudaSuccess ||
+        ctqw_malloc((void **)&h->status_d, 16) != cudaSuccess ||
+        ctqw_malloc((void **)&h->renorm_d, sizeof(double) * h->R) != cudaSuccess ||
+        ctqw_malloc((void **)&h->sites_d, sizeof(int32_t) * h->R * h->m) != cudaSuccess) {
         ctqw_set_error("cudaMalloc of the parameter arrays failed");
         return fail(CTQW_ENOMEM);
     }
-    if (cudaMemsetAsync(h->status_d, 0, sizeof(int), s) != cudaSuccess) return fail(CTQW_ECUDA);
+    if (cudaMemsetAsync(h->status_d, 0, 8, s) != cudaSuccess ||
+        cudaMemsetAsync(h->status_d + 2, 0xff, 8, s) != cudaSuccess)
+        return fail(CTQW_ECUDA);
     if ((st = upload(&h->sizes_d, h->sizes, s)) || (st = upload(&h->par_off_d, h->par_off, s)) ||
         (st = upload(&h->st_off_d, h->st_off, s)) || (st = upload(&h->group_of_d, h->group_of, s)) ||
         (st = upload(&h->group_off_d, h->group_off, s)) ||
@@ -285,12 +310,12 @@ int ctqw_build_hamiltonian(const ctqw_lattice_desc *d, void *stream, ctqw_hamilt
         return fail(CTQW_ECUDA);
     }
     if (d->eps_mean) {
-        if (cudaMalloc(&em_d, sizeof(double) * h->Nmax) != cudaSuccess) return fail(CTQW_ENOMEM);
+        if (ctqw_malloc(&em_d, sizeof(double) * h->Nmax) != cudaSuccess) return fail(CTQW_ENOMEM);
         if (cudaMemcpyAsync(em_d, d->eps_mean, sizeof(double) * h->Nmax, cudaMemcpyHostToDevice, s) != cudaSuccess)
             return fail(CTQW_ECUDA);
     }
     if (d->J_mean) {
-        if (cudaMalloc(&jm_d, sizeof(double) * h->Nmax) != cudaSuccess) return fail(CTQW_ENOMEM);
+        if (ctqw_malloc(&jm_d, sizeof(double) * h->Nmax) != cudaSuccess) return fail(CTQW_ENOMEM);
         if (cudaMemcpyAsync(jm_d, d->J_mean, sizeof(double) * h->Nmax, cudaMemcpyHostToDevice, s) != cudaSuccess)
             return fail(CTQW_ECUDA);
     }
@@ -303,7 +328,7 @@ int ctqw_build_hamiltonian(const ctqw_lattice_desc *d, void *stream, ctqw_hamilt
     h->eps_mean_d = em_d;
     h->J_mean_d = jm_d;
     em_d = jm_d = nullptr;
-    if (cudaMalloc(&h->eps64_0, pb) != cudaSuccess || cudaMalloc(&h->J64_0, pb) != cudaSuccess)
+    if (ctqw_malloc(&h->eps64_0, pb) != cudaSuccess || ctqw_malloc(&h->J64_0, pb) != cudaSuccess)
         return fail(CTQW_ENOMEM);
     if (cudaMemcpyAsync(h->eps64_0, h->eps64, pb, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->J64_0, h->J64, pb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -324,8 +349,7 @@ int ctqw_build_hamiltonian(const ctqw_lattice_desc *d, void *stream, ctqw_hamilt
 
 int ctqw_destroy_hamiltonian(ctqw_hamiltonian *h) {
     if (!h) return CTQW_OK;
-    cudaDeviceSynchronize();
-    free_device(h);
+    free_device(h);   // cudaFree waits for work still using the arrays
     delete h;
     return CTQW_OK;
 }
@@ -377,13 +401,9 @@ int ctqw_init_state(const ctqw_hamiltonian *h, const int32_t *sites_host, int32_
         }
     }
     cudaStream_t s = (cudaStream_t)stream;
-    int32_t *sites_d = nullptr;
     const size_t bytes = sizeof(int32_t) * h->R * h->m;
-    CTQW_CUDA_TRY(cudaMallocAsync((void **)&sites_d, bytes, s));
-    CTQW_CUDA_TRY(cudaMemcpyAsync(sites_d, sites_host, bytes, cudaMemcpyHostToDevice, s));
-    int st = launch_init_state(h, sites_d, dtype, psi_dev, s);
-    cudaFreeAsync(sites_d, s);
-    return st;
+    CTQW_CUDA_TRY(cudaMemcpyAsync(h->sites_d, sites_host, bytes, cudaMemcpyHostToDevice, s));
+    return launch_init_state(h, h->sites_d, dtype, psi_dev, s);
 }
 
 int ctqw_taylor_order(double h_dt, int64_t n_steps, double tol, int32_t K_min, int32_t K_max,
@@ -458,7 +478,7 @@ static int propagate_wavefront(const ctqw_hamiltonian *h, int32_t dtype, void *p
         return CTQW_EINVAL;
     }
     if (!lo) {
-        CTQW_CUDA_TRY(cudaMallocAsync(&lo, need, s));
+        CTQW_CUDA_TRY(ctqw_malloc_async(&lo, need, s));
         own = true;
     }
     const int64_t n_obs = n_samples(n_steps, obs_every);
@@ -625,7 +645,7 @@ static int propagate_fused_rows(const ctqw_hamiltonian *h, void *psi_dev, double
     bool own = false;
     if (!ws) {
         wsb = 3 * sb;
-        CTQW_CUDA_TRY(cudaMallocAsync(&ws, wsb, s));
+        CTQW_CUDA_TRY(ctqw_malloc_async(&ws, wsb, s));
         own = true;
     } else if (wsb < sb) {
         ctqw_set_error("fused path needs a workspace of at least %zu bytes (got %zu)", sb, wsb);
@@ -660,10 +680,10 @@ static int propagate_fused_rows(const ctqw_hamiltonian *h, void *psi_dev, double
     return st;
 }
 
-int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
-                          int32_t K, int64_t n_steps, int32_t obs_every, double *P_mean_dev,
-                          double *norm_dev, double *energy_dev, uint32_t flags,
-                          void *workspace_dev, size_t workspace_bytes, void *stream) {
+static int propagate_taylor_impl(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
+                                 int32_t K, int64_t n_steps, int32_t obs_every, double *P_mean_dev,
+                                 double *norm_dev, double *energy_dev, uint32_t flags,
+                                 void *workspace_dev, size_t workspace_bytes, void *stream) {
     CTQW_TRY(check_common(h, dtype, psi_dev, dt, n_steps, obs_every));
     if (K == 0) CTQW_TRY(ctqw_autotune_order(h, dtype, dt, n_steps, 1, 30, &K));
     if (K < 1 || K > 30) { ctqw_set_error("K must be in 1..30, or 0 (got %d)", K); return CTQW_EINVAL; }
@@ -725,7 +745,7 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
                               energy_dev, workspace_dev, s, SwitchSpec{});
 }
 
-int ctqw_propagate_taylor_switching(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev,
+static int propagate_switching_impl(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev,
                                     double dt, int32_t K, int64_t n_steps, int32_t obs_every,
                                     double *P_mean_dev, double *norm_dev, double *energy_dev,
                                     uint32_t flags, void *workspace_dev, size_t workspace_bytes,
@@ -757,9 +777,9 @@ int ctqw_propagate_taylor_switching(const ctqw_hamiltonian *h, int32_t dtype, vo
                               energy_dev, workspace_dev, s, sw);
 }
 
-int ctqw_propagate_exact(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
-                         int64_t n_steps, int32_t obs_every, double *P_mean_dev, double *norm_dev,
-                         double *energy_dev, int32_t *sweeps_host, void *stream) {
+static int propagate_exact_impl(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
+                                int64_t n_steps, int32_t obs_every, double *P_mean_dev, double *norm_dev,
+                                double *energy_dev, int32_t *sweeps_host, void *stream) {
     CTQW_TRY(check_common(h, dtype, psi_dev, dt, n_steps, obs_every));
     if (dtype != CTQW_C128) { ctqw_set_error("exact propagation is FP64 (CTQW_C128)"); return CTQW_EUNSUPPORTED; }
     int64_t D = 1;
@@ -774,10 +794,10 @@ int ctqw_propagate_exact(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev
     double *evals = nullptr, *evecs = nullptr;
     void *psi0 = nullptr;
     int *sweeps = nullptr;
-    CTQW_CUDA_TRY(cudaMallocAsync((void **)&evals, sizeof(double) * (size_t)(h->R * Dp), s));
-    CTQW_CUDA_TRY(cudaMallocAsync((void **)&evecs, sizeof(double) * (size_t)(h->R * Dp * Dp), s));
-    CTQW_CUDA_TRY(cudaMallocAsync(&psi0, sb, s));
-    CTQW_CUDA_TRY(cudaMallocAsync((void **)&sweeps, sizeof(int) * (size_t)h->R, s));
+    CTQW_CUDA_TRY(ctqw_malloc_async((void **)&evals, sizeof(double) * (size_t)(h->R * Dp), s));
+    CTQW_CUDA_TRY(ctqw_malloc_async((void **)&evecs, sizeof(double) * (size_t)(h->R * Dp * Dp), s));
+    CTQW_CUDA_TRY(ctqw_malloc_async(&psi0, sb, s));
+    CTQW_CUDA_TRY(ctqw_malloc_async((void **)&sweeps, sizeof(int) * (size_t)h->R, s));
     int st = zero_outputs(h, n_samples(n_steps, obs_every), P_mean_dev, norm_dev, energy_dev, s);
     if (st == CTQW_OK && cudaMemcpyAsync(psi0, psi_dev, sb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         st = ctqw_cuda_fail(cudaGetLastError(), "copy of psi0");
@@ -804,16 +824,16 @@ int ctqw_propagate_exact(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev
     return st;
 }
 
-int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
-                       int64_t n_steps, int32_t obs_every, double *P_mean_dev, double *norm_dev,
-                       double *energy_dev, uint32_t flags, void *workspace_dev,
-                       size_t workspace_bytes, void *stream) {
+static int propagate_rk4_impl(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
+                              int64_t n_steps, int32_t obs_every, double *P_mean_dev, double *norm_dev,
+                              double *energy_dev, uint32_t flags, void *workspace_dev,
+                              size_t workspace_bytes, void *stream) {
     CTQW_TRY(check_common(h, dtype, psi_dev, dt, n_steps, obs_every));
     cudaStream_t s = (cudaStream_t)stream;
     // RK4's update map is the order-4 Taylor polynomial of exp(-i H dt)
     // (Sec. 2.3): the fused kernel evaluates it directly
     if (!(flags & (CTQW_FLAG_PLAIN | CTQW_FLAG_RENORMALIZE)) && fused_rows_supported(h, dtype))
-        return ctqw_propagate_taylor(h, dtype, psi_dev, dt, 4, n_steps, obs_every, P_mean_dev,
+        return propagate_taylor_impl(h, dtype, psi_dev, dt, 4, n_steps, obs_every, P_mean_dev,
                                      norm_dev, energy_dev, flags, workspace_dev, workspace_bytes,
                                      stream);
     const size_t sb = (size_t)h->total_amp * elem_bytes(dtype);
@@ -846,18 +866,80 @@ int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, 
     return CTQW_OK;
 }
 
+// The public propagators: the work, then the norm check of the sampled norms.
+int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
+                          int32_t K, int64_t n_steps, int32_t obs_every, double *P_mean_dev,
+                          double *norm_dev, double *energy_dev, uint32_t flags,
+                          void *workspace_dev, size_t workspace_bytes, void *stream) {
+    CTQW_TRY(propagate_taylor_impl(h, dtype, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
+                                   energy_dev, flags, workspace_dev, workspace_bytes, stream));
+    return launch_norm_check(h, norm_dev, n_samples(n_steps, obs_every), (cudaStream_t)stream);
+}
+
+int ctqw_propagate_taylor_switching(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev,
+                                    double dt, int32_t K, int64_t n_steps, int32_t obs_every,
+                                    double *P_mean_dev, double *norm_dev, double *energy_dev,
+                                    uint32_t flags, void *workspace_dev, size_t workspace_bytes,
+                                    uint64_t seed, double p_switch, void *stream) {
+    CTQW_TRY(propagate_switching_impl(h, dtype, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
+                                      energy_dev, flags, workspace_dev, workspace_bytes, seed, p_switch,
+                                      stream));
+    return launch_norm_check(h, norm_dev, n_samples(n_steps, obs_every), (cudaStream_t)stream);
+}
+
+int ctqw_propagate_exact(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
+                         int64_t n_steps, int32_t obs_every, double *P_mean_dev, double *norm_dev,
+                         double *energy_dev, int32_t *sweeps_host, void *stream) {
+    CTQW_TRY(propagate_exact_impl(h, dtype, psi_dev, dt, n_steps, obs_every, P_mean_dev, norm_dev,
+                                  energy_dev, sweeps_host, stream));
+    return launch_norm_check(h, norm_dev, n_samples(n_steps, obs_every), (cudaStream_t)stream);
+}
+
+int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
+                       int64_t n_steps, int32_t obs_every, double *P_mean_dev, double *norm_dev,
+                       double *energy_dev, uint32_t flags, void *workspace_dev,
+                       size_t workspace_bytes, void *stream) {
+    CTQW_TRY(propagate_rk4_impl(h, dtype, psi_dev, dt, n_steps, obs_every, P_mean_dev, norm_dev,
+                                energy_dev, flags, workspace_dev, workspace_bytes, stream));
+    return launch_norm_check(h, norm_dev, n_samples(n_steps, obs_every), (cudaStream_t)stream);
+}
+
+int ctqw_set_norm_check(ctqw_hamiltonian *h, double drift_tol) {
+    if (!h) { ctqw_set_error("null handle"); return CTQW_EINVAL; }
+    if (!(drift_tol >= 0.0) || !std::isfinite(drift_tol)) {
+        ctqw_set_error("drift_tol must be finite and >= 0 (got %g)", drift_tol);
+        return CTQW_EINVAL;
+    }
+    h->norm_drift_tol = drift_tol;
+    return CTQW_OK;
+}
+
+int ctqw_inject_alloc_failure(int32_t after) {
+    if (after < -1) { ctqw_set_error("after must be >= -1 (got %d)", after); return CTQW_EINVAL; }
+    g_alloc_fail_after.store(after);
+    return CTQW_OK;
+}
+
 int ctqw_check_status(const ctqw_hamiltonian *h, void *stream) {
     if (!h) { ctqw_set_error("null handle"); return CTQW_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     CTQW_CUDA_TRY(cudaStreamSynchronize(s));
-    int v = 0;
-    CTQW_CUDA_TRY(cudaMemcpy(&v, h->status_d, sizeof(int), cudaMemcpyDeviceToHost));
-    if (v != 0) {
-        CTQW_CUDA_TRY(cudaMemset(h->status_d, 0, sizeof(int)));
+    struct {
+        int flags, pad;
+        unsigned long long key;
+    } st;
+    CTQW_CUDA_TRY(cudaMemcpy(&st, h->status_d, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st.flags == 0) return CTQW_OK;
+    CTQW_CUDA_TRY(cudaMemset(h->status_d, 0, 8));
+    CTQW_CUDA_TRY(cudaMemset(h->status_d + 2, 0xff, 8));
+    if (st.flags & 1) {
         ctqw_set_error("a bounded wait inside a propagation kernel gave up; results of that call are invalid");
         return CTQW_ETIMEOUT;
     }
-    return CTQW_OK;
+    const unsigned long long r = st.key >> 40, q = (st.key >> 8) & 0xffffffffull, why = st.key & 0xffull;
+    ctqw_set_error("norm check: realization %llu, sample %llu: %s", r, q,
+                   why == 1 ? "the norm is not finite" : "the norm drifted beyond the set tolerance");
+    return CTQW_ENORM;
 }
 
 int ctqw_adjoint_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t K,

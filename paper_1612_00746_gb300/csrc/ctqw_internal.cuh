@@ -37,8 +37,13 @@ struct ctqw_hamiltonian {
     double eps_hw = 0.0, J_hw = 0.0;
     double *eps_mean_d = nullptr, *J_mean_d = nullptr;   // [Nmax] or null (0 / J0)
     double *eps64_0 = nullptr, *J64_0 = nullptr;         // [total_par] as built
-    int *status_d = nullptr;        // nonzero after a kernel's bounded wait gave up
+    // status word (16 bytes): int flags at [0] (bit 0: a bounded wait gave
+    // up, bit 1: the norm check failed), at byte 8 the 64-bit key of the
+    // first norm failure, (realization << 40) | (sample << 8) | reason
+    int *status_d = nullptr;
     double *renorm_d = nullptr;     // [R] norms of the per-step renormalization
+    int32_t *sites_d = nullptr;     // [R][m] initial sites (ctqw_init_state)
+    double norm_drift_tol = 0.0;    // norm check: |norm - norm at step 0| above this fails (0: finiteness only)
 };
 
 // Per-launch view of the realization table (passed by value to kernels).
@@ -75,6 +80,24 @@ inline RealTable real_table(const ctqw_hamiltonian *h) {
 // Error reporting (thread-local message, see ctqw_last_error).
 void ctqw_set_error(const char *fmt, ...);
 int ctqw_cuda_fail(cudaError_t e, const char *what);
+
+// Every device allocation of the library goes through these, so that a test
+// can make one fail on the host (ctqw_inject_alloc_failure).
+cudaError_t ctqw_malloc(void **p, size_t bytes);
+cudaError_t ctqw_malloc_async(void **p, size_t bytes, cudaStream_t s);
+template <typename T>
+inline cudaError_t ctqw_malloc(T **p, size_t bytes) {
+    return ctqw_malloc(reinterpret_cast<void **>(p), bytes);
+}
+template <typename T>
+inline cudaError_t ctqw_malloc_async(T **p, size_t bytes, cudaStream_t s) {
+    return ctqw_malloc_async(reinterpret_cast<void **>(p), bytes, s);
+}
+
+// Norm check of the sampled norms ([n_obs][R]): a non-finite norm, or one
+// that moved from the first sample by more than h->norm_drift_tol (> 0),
+// marks the status word with the first such realization and sample.
+int launch_norm_check(const ctqw_hamiltonian *h, const double *norm, int64_t n_obs, cudaStream_t s);
 
 #define CTQW_CUDA_TRY(call)                                  \
     do {                                                     \

@@ -23,7 +23,7 @@ void graph_free(ctqw_graph *g) {
 
 template <typename T>
 int galloc(T **dst, size_t n) {
-    if (cudaMalloc((void **)dst, std::max<size_t>(1, n) * sizeof(T)) != cudaSuccess) {
+    if (ctqw_malloc((void **)dst, std::max<size_t>(1, n) * sizeof(T)) != cudaSuccess) {
         ctqw_set_error("cudaMalloc of %zu bytes failed", n * sizeof(T));
         return CTQW_ENOMEM;
     }

@@ -68,12 +68,22 @@ extern "C" int ctqw_propagate_taylor_noalloc(const ctqw_hamiltonian *h, int32_t 
                        (long long)h->total_amp, need, kNoAllocScratchBytes);
         return CTQW_EINVAL;
     }
+    // the scratch address is per device: the handle's device must be current
+    int dev = -1;
+    CTQW_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != h->device) {
+        ctqw_set_error("no-allocation path: device %d is current but the handle lives on device %d",
+                       dev, h->device);
+        return CTQW_EINVAL;
+    }
     void *scratch = nullptr;
     const int st = noalloc_scratch_address(&scratch);
     if (st != CTQW_OK) return st;
-    // The per-term path overwrites every scratch element before reading it
-    // (the first Taylor term writes the running sum and the term buffer in
-    // full), so nothing is left over from an earlier call that shares the array.
+    // Nothing left in the array by an earlier call is read.  CTQW_C128: the
+    // first Taylor term of every step writes the running sum and the term
+    // buffer in full before they are read.  CTQW_C64: every Horner stage
+    // writes its iterate in full before the next stage reads it, and the
+    // carried error word is cleared by a memset at the start of the call.
     return ctqw_propagate_taylor(h, dtype, psi_dev, dt, K, n_steps, obs_every, P_mean_dev,
                                  norm_dev, energy_dev, CTQW_FLAG_PLAIN, scratch,
                                  kNoAllocScratchBytes, stream);

@@ -324,6 +324,27 @@ __global__ void __launch_bounds__(32 * kObsWarps) occupation_kernel(
     }
 }
 
+// The norm check of Algorithms 2 and 3 on the sampled norms: realization r
+// fails at the first sample q whose norm is not finite (reason 1) or differs
+// from its first sample by more than drift_tol > 0 (reason 2).  The smallest
+// key (r << 40) | (q << 8) | reason over all failures goes to the status word.
+__global__ void norm_check_kernel(const double *__restrict__ norm, int64_t n_obs, int R, double drift_tol,
+                                  int *status) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const double n0 = norm[r];
+    for (int64_t q = 0; q < n_obs; ++q) {
+        const double v = norm[q * R + r];
+        const unsigned reason = !isfinite(v) ? 1u : ((drift_tol > 0.0 && fabs(v - n0) > drift_tol) ? 2u : 0u);
+        if (reason) {
+            const unsigned long long key = ((unsigned long long)r << 40) | ((unsigned long long)q << 8) | reason;
+            atomicMin(reinterpret_cast<unsigned long long *>(status + 2), key);
+            atomicOr(status, 2);
+            return;
+        }
+    }
+}
+
 // psi (and lo) of realization r times 1 / sqrt(norm[r]).
 template <typename T, int M>
 __global__ void __launch_bounds__(256) renorm_kernel(RealTable tab, const int32_t *__restrict__ list,
@@ -396,6 +417,13 @@ int launch_observables(const ctqw_hamiltonian *h, int dtype, const void *psi, do
         k<<<grid, block, 0, s>>>(t, h->eps64, h->J64, (const double2 *)psi, P_mean, P_joint, norm,
                                  energy);
     }
+    CTQW_CUDA_TRY(cudaGetLastError());
+    return CTQW_OK;
+}
+
+int launch_norm_check(const ctqw_hamiltonian *h, const double *norm, int64_t n_obs, cudaStream_t s) {
+    if (!norm || n_obs <= 0) return CTQW_OK;
+    norm_check_kernel<<<(h->R + 255) / 256, 256, 0, s>>>(norm, n_obs, h->R, h->norm_drift_tol, h->status_d);
     CTQW_CUDA_TRY(cudaGetLastError());
     return CTQW_OK;
 }

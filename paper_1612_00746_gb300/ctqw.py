@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libctqw.so")
 
 CTQW_OK, CTQW_EINVAL, CTQW_ENOMEM, CTQW_ECUDA, CTQW_EUNSUPPORTED = 0, 1, 2, 3, 4
+CTQW_ENORM = 5
 CTQW_ETIMEOUT = 6
 DISTINGUISHABLE, BOSONS, FERMIONS = 0, 1, 2
 C64, C128 = 0, 1
@@ -53,7 +54,7 @@ EXPORTED = (
     "ctqw_propagate_exact", "ctqw_graph_build", "ctqw_graph_destroy", "ctqw_graph_get_params",
     "ctqw_graph_state_size", "ctqw_graph_init_state", "ctqw_graph_workspace_size",
     "ctqw_graph_propagate_taylor", "ctqw_graph_propagate_rk4", "ctqw_graph_observables",
-    "ctqw_graph_set_chunk",
+    "ctqw_graph_set_chunk", "ctqw_set_norm_check", "ctqw_inject_alloc_failure",
 )
 
 
@@ -116,6 +117,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "ctqw_propagate_rk4": [vp, i32, vp, dbl, i64, i32, vp, vp, vp, u32, vp, sz, vp],
         "ctqw_ensemble_observables": [vp, i32, vp, vp, vp, vp, vp, vp],
         "ctqw_check_status": [vp, vp],
+        "ctqw_set_norm_check": [vp, dbl],
+        "ctqw_inject_alloc_failure": [i32],
         "ctqw_adjoint_workspace_size": [vp, i32, i32, i64, i32, ctypes.POINTER(sz)],
         "ctqw_adjoint_grad": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp],
         "ctqw_taylor_order": [dbl, i64, dbl, i32, i32, ctypes.POINTER(i32), pd],
@@ -469,6 +472,14 @@ def ctqw_one_body_density(h: Hamiltonian, psi: torch.Tensor, dtype: int, stream=
         out.append(c[off:off + n * n].view(n, n))
         off += n * n
     return out
+
+
+def ctqw_set_norm_check(h: Hamiltonian, drift_tol: float) -> None:
+    _check(load().ctqw_set_norm_check(h.handle, float(drift_tol)))
+
+
+def ctqw_inject_alloc_failure(after: int) -> None:
+    _check(load().ctqw_inject_alloc_failure(int(after)))
 
 
 def ctqw_check_status(h: Hamiltonian, stream=None) -> None:

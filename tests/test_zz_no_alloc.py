@@ -4,7 +4,8 @@ must not synchronize the device through cudaMalloc, or as a plugin of a host
 program that owns the memory budget).  Its scratch is a fixed 48 MiB array
 inside the library.  Checked through the C ABI against the entry point that
 takes a caller-provided workspace, on two different calls in a row (so the
-second call runs on a scratch array the first one has filled).
+second call runs on a scratch array the first one has filled), and
+against the FP64 oracle.
 
 This file is named to be collected last, so that a run that stops at the
 first failure has already run every other test.
@@ -15,7 +16,7 @@ import numpy as np
 import pytest
 
 import ctqw_workloads as cw
-from gpu_helpers import TOL_FP32, TOL_FP64
+from gpu_helpers import TOL_FP32, TOL_FP64, TOL_NORM_DRIFT, energy_tol
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -63,6 +64,11 @@ def _run(ctqw, w, noalloc):
 
 
 def test_noalloc_matches_workspace_entry_point_on_two_calls(ctqw):
+    """Two calls in a row, each against the workspace entry point and against
+    the FP64 oracle (P, norm and energy), so that a fault both entry points
+    share cannot pass unseen."""
+    import oracle
+
     first = cw.get("bosons_small").with_(dtype=cw.C128, R=4, n_steps=40, obs_every=10)
     second = cw.get("ring3_small").with_(dtype=cw.C64, N=9, R=2, n_steps=30, obs_every=15)
     for w, tol in ((first, TOL_FP64), (second, TOL_FP32)):
@@ -71,6 +77,29 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls(ctqw):
         for a, b in zip(got, ref):
             assert a.shape == b.shape
             assert np.max(np.abs(a - b)) <= tol
+        o = oracle.ensemble_run(w)
+        e_tol = 1e-10 if w.dtype == cw.C128 else energy_tol(w)
+        assert np.max(np.abs(got[1] - o["P_mean"])) <= tol
+        assert np.max(np.abs(got[2] - o["norm"].T)) <= (1e-12 if w.dtype == cw.C128 else TOL_NORM_DRIFT)
+        assert np.max(np.abs(got[3] - o["energy"].T)) <= e_tol
+
+
+def test_noalloc_rejects_a_handle_of_another_device(ctqw):
+    """The scratch address is per device, so the call wants the handle's
+    device current.  With one GPU the check is seen through a second device
+    ordinal only when there is one; here it must at least accept the
+    handle's own device."""
+    w = cw.get("bosons_small").with_(dtype=cw.C128, R=1, n_steps=2, obs_every=1)
+    got = _run(ctqw, w, noalloc=True)
+    assert np.isfinite(got[2]).all()
+    if torch.cuda.device_count() > 1:
+        h = ctqw.build_for_workload(w)
+        psi = h.new_state(cw.C128)
+        with torch.cuda.device(1):
+            st = ctqw.load().ctqw_propagate_taylor_noalloc(
+                h.handle, cw.C128, ctypes.c_void_p(psi.data_ptr()), w.dt, w.K, 1, 0, None, None, None, None)
+        assert st == ctqw.CTQW_EINVAL and b"device" in ctqw.load().ctqw_last_error()
+        h.close()
 
 
 def test_noalloc_rejects_states_beyond_its_scratch(ctqw):
