@@ -38,8 +38,9 @@ METRIC = "site-updates/s (dim x K x steps x realizations)"
 UNIT = "site-updates/s"
 FP32_FMA_LANES_PER_SM = 128      # FP32 FMA lanes per SM
 FP64_FMA_PER_SM = 2              # FP64 FMA per SM per cycle
-SM_COUNT = 152
+SM_COUNT = 152                   # replaced by the device's count at run time
 SM_MAX_MHZ = 2070.0
+FMA_PEAKS = {}                   # measured by measure_fma_peaks() (TFLOP/s)
 
 
 # ---------------------------------------------------------------- oracle (CPU) legs
@@ -145,6 +146,47 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- helpers
+def measure_fma_peaks(seconds: float = 0.5):
+    """FP32 (packed pairs, the stencil kernels' instruction) and FP64 FMA
+    peaks of this GPU, measured now by the project's FMA-chain kernel
+    (paper_1612_00746_gb300/peaks/fma_peak.cu), in TFLOP/s."""
+    import ctypes
+
+    path = os.path.join(ROOT, "paper_1612_00746_gb300", "libfmapeak.so")
+    lib = ctypes.CDLL(path)
+    lib.fma_peak_measure.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]
+    out = {}
+    for kind, name in ((0, "fp32"), (2, "fp64")):
+        v, e = ctypes.c_double(), ctypes.c_double()
+        if lib.fma_peak_measure(kind, seconds, ctypes.byref(v), ctypes.byref(e)) == 0:
+            out[name] = 2.0 * v.value / 1e12
+    return out
+
+
+def set_sm_count(dev) -> None:
+    global SM_COUNT
+    import torch
+
+    SM_COUNT = int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def alu_peak(fp64: bool = False) -> float:
+    """Derived peak: SMs x FMA lanes x 2 flop x maximum SM clock (TFLOP/s)."""
+    lanes = FP64_FMA_PER_SM if fp64 else FP32_FMA_LANES_PER_SM
+    return SM_COUNT * lanes * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+def with_measured(entry: dict, key: str) -> dict:
+    """Add the measured FMA peak and the fraction of it to a roofline entry."""
+    if key in FMA_PEAKS and entry.get("achieved") is not None:
+        entry["peak_measured"] = FMA_PEAKS[key]
+        entry["frac_of_measured"] = entry["achieved"] / FMA_PEAKS[key]
+        entry["peak_measured_basis"] = ("FMA-chain kernel (fma.rn.f32x2)" if key == "fp32"
+                                        else "FMA-chain kernel (FP64 fma)") + ", this run"
+    return entry
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -196,7 +238,7 @@ def roofline_of(w, dtype, flags, units, kernel_ms, peaks, traffic, switching=Fal
     """Roofline entry of the kernel that dominates the propagate call.
 
     Fused kernels (every Taylor term on chip) are bound by the FP32 FMA pipe:
-    8m+4 algorithmic flops per site-update against 152 SMs x 128 lanes x 2
+    8m+4 algorithmic flops per site-update against the SMs x 128 lanes x 2
     flop x 2070 MHz.  The FP32 per-term kernels stream the state through HBM:
     per site-update ((K-1) 24 + 40)/K bytes (Horner stages and the
     compensated final stage), against the measured copy bandwidth.  The FP64
@@ -210,26 +252,26 @@ def roofline_of(w, dtype, flags, units, kernel_ms, peaks, traffic, switching=Fal
     if path in ("rows", "banded", "wavefront", "tiled"):
         flops_per_unit = 8 * w.m + 4
         achieved = units * flops_per_unit / sec / 1e12
-        peak = SM_COUNT * FP32_FMA_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        peak = alu_peak()
         kernel = {"rows": "taylor_fused_rows_kernel", "banded": "taylor_fused_kernel",
-                  "wavefront": "taylor_wavefront_kernel", "tiled": "taylor_tiled_kernel"}[path]
-        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic if path == "rows" else None,
-                "kernel": kernel, "kernel_ms": kernel_ms, "flops_per_site_update": flops_per_unit,
-                "peak_basis": "152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz (derived)",
-                "hbm_gbs_measured": peaks.get("hbm_gbs")}
+                  "wavefront": "taylor_wavefront_kernel", "tiled": "taylor_tiled_reg_kernel"}[path]
+        return with_measured({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                              "frac": achieved / peak, "traffic": traffic if path == "rows" else None,
+                              "kernel": kernel, "kernel_ms": kernel_ms, "flops_per_site_update": flops_per_unit,
+                              "peak_basis": f"{SM_COUNT} SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz (derived)",
+                              "hbm_gbs_measured": peaks.get("hbm_gbs")}, "fp32")
     if dtype == ctqw.C128:
         # FP64 on GB300 runs 2 DFMA per SM per cycle: the per-term FP64
         # kernels are bound by that pipe, not by HBM (64 B per site-update)
         flops_per_unit = 8 * w.m + 4
         achieved = units * flops_per_unit / sec / 1e12
-        peak = SM_COUNT * FP64_FMA_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "taylor_term_kernel<double>",
-                "kernel_ms": kernel_ms, "flops_per_site_update": flops_per_unit,
-                "hbm_gbs_achieved": units * 64.0 / sec / 1e9, "bytes_per_site_update": 64.0,
-                "peak_basis": "152 SMs x 2 DFMA x 2 flop x 2070 MHz (FP64, derived)",
-                "timing": "the whole propagate call (observables kernels included)"}
+        peak = alu_peak(fp64=True)
+        return with_measured({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                              "frac": achieved / peak, "traffic": None, "kernel": "taylor_term_kernel<double>",
+                              "kernel_ms": kernel_ms, "flops_per_site_update": flops_per_unit,
+                              "hbm_gbs_achieved": units * 64.0 / sec / 1e9, "bytes_per_site_update": 64.0,
+                              "peak_basis": f"{SM_COUNT} SMs x 2 DFMA x 2 flop x 2070 MHz (FP64, derived)",
+                              "timing": "the whole propagate call (observables kernels included)"}, "fp64")
     bpu = ((w.K - 1) * 24.0 + 40.0) / w.K
     kernel = "horner_stage_kernel + horner_final_kernel"
     gbs = units * bpu / sec / 1e9
@@ -294,6 +336,63 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm
+def ragged_leg(args, dev, stream):
+    """The batching workload at full size: 2048 realizations of two walkers on
+    open chains of N in {128, 192, ..., 1024} drawn per realization, 1000
+    steps, K from the order autotuner over 8..20, observables every 10
+    steps, complex FP32 on the library's default path (temporally blocked
+    register tiles).  One timed call after a short warm-up call."""
+    import numpy as np
+    import torch
+
+    from paper_1612_00746_gb300 import ctqw
+
+    w = cw.get("ragged_n128_1024")
+    u_eps, u_J, sizes, _ = cw.packed_draws(w)
+    h = ctqw.Hamiltonian(w.m, w.statistics, w.periodic, sizes, w.J0, w.U, w.eps_halfwidth,
+                         w.J_halfwidth, u_eps, u_J)
+    K = ctqw.ctqw_autotune_order(h, ctqw.C64, w.dt, w.n_steps, 8, 20)
+    psi = h.new_state(ctqw.C64, dev)
+    sites = ctqw.initial_sites(w, h)
+    n_obs = h.n_obs(w.n_steps, w.obs_every)
+    P = torch.empty((n_obs, h.p_width), dtype=torch.float64, device=dev)
+    nr = torch.empty((n_obs, h.R), dtype=torch.float64, device=dev)
+    en = torch.empty((n_obs, h.R), dtype=torch.float64, device=dev)
+    ws = h.workspace(ctqw.C64, ctqw.TAYLOR, 0, dev)
+    ctqw.ctqw_init_state(h, psi, sites, ctqw.C64)
+    ctqw.ctqw_propagate_taylor(h, psi, ctqw.C64, w.dt, K, 20, w.obs_every, P, nr, en, 0, ws)
+    torch.cuda.synchronize()
+    ctqw.ctqw_init_state(h, psi, sites, ctqw.C64)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(visible_gpu_id(0))
+    clocks.start()
+    e0.record(stream)
+    ctqw.ctqw_propagate_taylor(h, psi, ctqw.C64, w.dt, K, w.n_steps, w.obs_every, P, nr, en, 0, ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ctqw.ctqw_check_status(h)
+    ms = e0.elapsed_time(e1)
+    D = float(np.sum(sizes.astype(np.float64) ** w.m))
+    units = D * K * w.n_steps
+    wk = w.with_(K=K)
+    roof = roofline_of(wk, ctqw.C64, 0, units, ms, measured_peaks(), None)
+    roof["timing"] = "the whole propagate call (tile launches and the reductions of 101 samples)"
+    launches8 = -(-K // 8)
+    depth = -(-K // launches8)
+    launches = 1 + w.n_steps * (-(-K // depth)) * len(h.group_sizes) + n_obs + 1
+    out = {"workload": w.name, "value": units / (ms / 1000.0), "unit": UNIT, "ms": ms,
+           "R": w.R, "sizes": "N in {128, 192, ..., 1024} per realization (15 groups)",
+           "K": K, "K_range": [8, 20], "n_steps": w.n_steps, "obs_every": w.obs_every,
+           "site_updates": units, "gpu_launches": launches,
+           "norm_drift": float((nr - 1.0).abs().max().item()),
+           "roofline": roof, "clocks": clk,
+           "l2": "inputs larger than L2 (states %.1f GB)" % (D * 8 / 1e9)}
+    h.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -307,6 +406,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    set_sm_count(dev)
     ctqw.load()
 
     w = cw.get(args.workload)
@@ -325,6 +425,9 @@ def run_ours(args):
                          f"{w.n_steps} steps of {w.name}, K={w.K}, FP64 ({wall:.1f} s); "
                          f"single_core_value: median rate of one worker"}
 
+    if not args.no_fma_peaks:
+        FMA_PEAKS.update(measure_fma_peaks())
+
     # realizations of this rank: its own block of the (weakly scaled) ensemble
     realizations = list(range(rank * w.R, (rank + 1) * w.R))
     u_eps, u_J, sizes, _ = cw.packed_draws(w, realizations)
@@ -338,11 +441,18 @@ def run_ours(args):
     P = torch.empty((n_obs, h.p_width), dtype=torch.float64, device=dev)
     nr = torch.empty((n_obs, h.R), dtype=torch.float64, device=dev)
     en = torch.empty((n_obs, h.R), dtype=torch.float64, device=dev)
-    ws = h.workspace(dtype, ctqw.TAYLOR, args.flags | (ctqw.FLAG_PLAIN if args.switch is not None else 0), dev)
-    counts = torch.tensor(np.repeat(h.group_count, h.group_sizes), dtype=torch.float64, device=dev)
     D = float(np.sum(sizes.astype(np.float64) ** w.m))
     units_per_step = D * w.K * w.n_steps
     path = propagation_path(w, dtype, args.flags, args.switch is not None)
+    ws = h.workspace(dtype, ctqw.TAYLOR, args.flags | (ctqw.FLAG_PLAIN if args.switch is not None else 0), dev)
+    slots = 0
+    if path == "rows" and w.obs_every > 0:
+        # the fused path stores the state at sample points into workspace
+        # slots: 1 + S states run S + 1 sampling intervals per launch
+        state_bytes = int(D) * (8 if dtype == ctqw.C64 else 16)
+        slots = max(2, min(n_obs - 1, args.snapshots, int(args.snapshot_gb * 1e9) // state_bytes))
+        ws = torch.empty((1 + slots) * state_bytes, dtype=torch.uint8, device=dev)
+    counts = torch.tensor(np.repeat(h.group_count, h.group_sizes), dtype=torch.float64, device=dev)
     if path == "wavefront":
         # init_state + one observables kernel per sample + one wavefront launch
         # per segment between samples and size group
@@ -357,9 +467,13 @@ def run_ours(args):
         depth = {0: -(-w.K // launches8), 9: 4, 10: 8, 11: 8, 12: 4, 13: 8, 14: 2, 15: 7}[(args.flags >> 8) & 0xF]
         launches_per_step = 1 + w.n_steps * (-(-w.K // depth)) * len(h.group_sizes) + n_obs
     else:
-        launches_per_step = 2   # init_state kernel + fused propagation kernel
+        # init_state + one fused launch per S + 1 sampling intervals + one
+        # reduction kernel per sample
+        per_launch = (slots + 1) * w.obs_every if w.obs_every else w.n_steps
+        launches_per_step = 1 + -(-w.n_steps // per_launch) + n_obs
     if args.switch is not None:
         launches_per_step += 1 + w.n_steps   # parameter restore + one update per step
+    launches_per_step += 1   # the norm check of the sampled norms
 
     prop_events = []
     graph = None
@@ -411,6 +525,18 @@ def run_ours(args):
         step(record=True)
     t1.record(stream)
     torch.cuda.synchronize()
+    # the fused kernel alone (one launch over all steps, no sampling), for
+    # its roofline: the timed calls above interleave it with the reductions
+    kernel_alone_ms = None
+    if path == "rows" and graph is None:
+        ctqw.ctqw_init_state(h, psi, sites, dtype)
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        ctqw.ctqw_propagate_taylor(h, psi, dtype, w.dt, w.K, w.n_steps, 0, None, None, None, args.flags, ws)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        kernel_alone_ms = k0.elapsed_time(k1)
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
@@ -532,9 +658,20 @@ def run_ours(args):
         hs.close()
 
     peaks = measured_peaks()
-    roofline = roofline_of(w, dtype, args.flags, units_per_step, kernel_ms, peaks,
+    roofline = roofline_of(w, dtype, args.flags, units_per_step,
+                           kernel_alone_ms if kernel_alone_ms is not None else kernel_ms, peaks,
                            fused_traffic(w.name) if not (args.realizations or args.n_steps or args.switch) else None,
                            switching=args.switch is not None)
+    if kernel_alone_ms is not None:
+        roofline["timing"] = ("one launch of the fused kernel over all steps without sampling "
+                              "(CUDA events, after the timed region)")
+        roofline["achieved_with_sampling"] = units_per_step * (8 * w.m + 4) / (kernel_ms / 1000.0) / 1e12
+        roofline["snapshot_slots"] = slots
+
+    ragged = None
+    if world == 1 and rank == 0 and not args.no_ragged and args.workload == "bosons_n256_u2" \
+            and not (args.realizations or args.n_steps or args.switch or args.graph):
+        ragged = ragged_leg(args, dev, stream)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
@@ -557,6 +694,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "fp64_plain": fp64,
         "plain_fp32_hbm": plain32,
+        "ragged_batch": ragged,
         "norm_drift": norm_drift,
         "clocks": clk,
     }
@@ -580,6 +718,7 @@ def run_adjoint(args):
     from paper_1612_00746_gb300 import ctqw
 
     torch.cuda.set_device(0)
+    set_sm_count(0)
     dev = torch.device("cuda", 0)
     ctqw.load()
     w = cw.get(args.workload)
@@ -646,6 +785,7 @@ def run_rho1(args):
     from paper_1612_00746_gb300 import ctqw
 
     torch.cuda.set_device(0)
+    set_sm_count(0)
     dev = torch.device("cuda", 0)
     ctqw.load()
     w = cw.get(args.workload)
@@ -670,7 +810,7 @@ def run_rho1(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     flops = float(np.sum(w.m * sizes.astype(np.float64) ** (w.m + 1))) * 8.0
-    peak = SM_COUNT * FP32_FMA_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = alu_peak()
     achieved = flops / (ms / 1000.0) / 1e12
     trace = float(sum(torch.diagonal(r).real.sum().item() for r in rho))
     line = {
@@ -681,7 +821,7 @@ def run_rho1(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "kernel": "rho1_term_kernel<float>",
                      "flops_per_call": flops,
-                     "peak_basis": "152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz (derived)"},
+                     "peak_basis": f"{SM_COUNT} SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz (derived)"},
         "trace_sum_over_groups": trace,
     }
     print(json.dumps(line), flush=True)
@@ -702,6 +842,7 @@ def run_lattice(args):
     from paper_1612_00746_gb300 import ctqw
 
     torch.cuda.set_device(0)
+    set_sm_count(0)
     dev = torch.device("cuda", 0)
     ctqw.load()
     w = cw.get_graph(args.lattice)
@@ -762,10 +903,10 @@ def run_lattice(args):
     else:
         flops = 8 * w.m + 4
         ach = units * flops / (ms / 1000.0) / 1e12
-        peak = SM_COUNT * FP64_FMA_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        peak = alu_peak(fp64=True)
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": None, "kernel": "graph_taylor_term_kernel<double>", "kernel_ms": ms,
-                "peak_basis": "152 SMs x 2 DFMA x 2 flop x 2070 MHz (FP64, derived)"}
+                "peak_basis": f"{SM_COUNT} SMs x 2 DFMA x 2 flop x 2070 MHz (FP64, derived)"}
     line = {
         "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -797,6 +938,7 @@ def run_exact(args):
     from paper_1612_00746_gb300 import ctqw
 
     torch.cuda.set_device(0)
+    set_sm_count(0)
     dev = torch.device("cuda", 0)
     ctqw.load()
     R = args.realizations or 4096
@@ -826,7 +968,7 @@ def run_exact(args):
     ms = total / args.steps
     D = w.N ** w.m
     flops = 9.0 * D ** 3 * float(np.sum(sweeps))
-    peak = SM_COUNT * FP64_FMA_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak = alu_peak(fp64=True)
     achieved = flops / (ms / 1000.0) / 1e12
     line = {
         "metric": "realizations diagonalised and propagated per second", "value": R / (ms / 1000.0),
@@ -835,7 +977,7 @@ def run_exact(args):
         "config": {"workload": w.name, "m": w.m, "N": w.N, "D": D, "R": R, "samples": h.n_obs(w.n_steps, w.obs_every)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "kernel": "exact_eigen_kernel",
-                     "peak_basis": "152 SMs x 2 DFMA x 2 flop x 2070 MHz (FP64, derived)"},
+                     "peak_basis": f"{SM_COUNT} SMs x 2 DFMA x 2 flop x 2070 MHz (FP64, derived)"},
         "jacobi_sweeps_mean": float(np.mean(sweeps)), "jacobi_sweeps_max": int(np.max(sweeps)),
     }
     print(json.dumps(line), flush=True)
@@ -876,6 +1018,11 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-plain", action="store_true")
+    ap.add_argument("--no-ragged", action="store_true", help="skip the full-size ragged-batch leg")
+    ap.add_argument("--no-fma-peaks", action="store_true", help="skip the FMA-chain peak measurement")
+    ap.add_argument("--snapshots", type=int, default=24,
+                    help="fused path: sample snapshots per launch (workspace of 1 + S states)")
+    ap.add_argument("--snapshot-gb", type=float, default=16.0, help="cap of the snapshot workspace")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
