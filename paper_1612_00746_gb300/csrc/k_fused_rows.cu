@@ -21,9 +21,14 @@
 // running sum).  The diagonal dt*(eps_x1 + eps_x2) enters as two FFMA2 with
 // a per-row and a per-column pair; dt*U on x1 = x2 is added for the one lane
 // of a row that owns the diagonal.  The increment A w_2 is added to the state
-// with its rounding error carried in a second FP32 word (lo, a state-sized
-// buffer that persists between launches; its per-step reads and writes stay
-// in L2), so hi + lo holds the state to ~2^-48 relative.
+// with its rounding error carried in a second FP32 word (lo), so hi + lo
+// holds the state to ~2^-48 relative.  lo sits in shared memory for the
+// launch (lane-major like hi) and in a state-sized buffer between launches.
+//
+// Control flow: the diagonal offset of a warp's rows is fixed for the
+// kernel, and the Horner stages of a step are K - 1 middle stages and one
+// final one, so the step loop is compiled per offset with the stage mode a
+// compile-time constant: no per-stage dispatch.
 //
 // Observables are not formed here.  At every snap_every-th step inside the
 // launch the kernel stores the state to a snapshot slot (row-major, the
@@ -170,6 +175,7 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
     float2 *halo = hi + SR * N;                             // [2 parity][2: above, below][N]
     float2 *edge = halo + 2 * 2 * N;                        // [2 parity][W][2: first, last][N]
     float4 *rowc = reinterpret_cast<float4 *>(edge + 2 * W * 2 * N);  // [SR + 1] row coefficient pairs
+    float2 *los = reinterpret_cast<float2 *>(rowc + SR + 1);          // [SR][N] carried error, lane-major
     __shared__ __align__(8) unsigned long long mbar[2][2];
     __shared__ __align__(8) unsigned long long mbar_never;
 
@@ -203,8 +209,15 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
         }
     }
 
-    // state in: hi = psi (shared), P = psi (registers); lo stays in global memory
+    // state in: hi = psi (shared), P = psi (registers), lo (shared, lane-major like hi)
     float2 *glo = a.lo + a.tab.st_off[r];
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+#pragma unroll
+        for (int k = 0; k < CL; k += 2)
+            *reinterpret_cast<float4 *>(los + (lrow0 + i) * N + lane * 2 + k * 32) =
+                *reinterpret_cast<const float4 *>(glo + (size_t)(x1_0 + i) * N + lane * 2 + k * 32);
+    }
 #pragma unroll
     for (int i = 0; i < RL; ++i) {
 #pragma unroll
@@ -235,105 +248,111 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
     if (a.test_timeout && threadIdx.x == 0 && blockIdx.x == 0)
         (void)mbar_wait_bounded(smem_u32(&mbar_never), 0, 1000000ull, a.status);
 
-    unsigned tc = 0;
     const long long n_steps = a.n_steps;
     const int K = a.K;
-    for (long long step = 0; step < n_steps; ++step) {
-        auto run_stage = [&](const int j) {
-            const int parity = tc & 1;
-            const uint32_t phase = (tc >> 1) & 1;
-            // publish: this warp's first and last rows (shared memory; the slab
-            // edge rows also into the neighbour CTAs)
-            float2 *eb = edge + parity * (W * 2 * N) + warp * (2 * N) + lane * 2;
+    // the whole step loop, for this warp's (constant) diagonal offset
+    auto main_loop = [&](auto off_tag) {
+        constexpr int OFF = decltype(off_tag)::value;
+        unsigned tc = 0;
+        for (long long step = 0; step < n_steps; ++step) {
+            auto run_stage = [&](const int j, auto mode_tag) {
+                constexpr int MODE = decltype(mode_tag)::value;
+                const int parity = tc & 1;
+                const uint32_t phase = (tc >> 1) & 1;
+                // publish: this warp's first and last rows (shared memory; the slab
+                // edge rows also into the neighbour CTAs)
+                float2 *eb = edge + parity * (W * 2 * N) + warp * (2 * N) + lane * 2;
 #pragma unroll
-            for (int k = 0; k < CL; k += 2) {
-                const float4 t = make_float4(L.P[0][k].x, L.P[0][k].y, L.P[0][k + 1].x, L.P[0][k + 1].y);
-                const float4 b = make_float4(L.P[RL - 1][k].x, L.P[RL - 1][k].y, L.P[RL - 1][k + 1].x,
-                                             L.P[RL - 1][k + 1].y);
-                *reinterpret_cast<float4 *>(eb + k * 32) = t;
-                *reinterpret_cast<float4 *>(eb + N + k * 32) = b;
-                if (warp == 0) st_async16(send_up + parity * (2 * N * 8) + k * 256, t, send_up_mb + parity * 16);
-                if (warp == W - 1) st_async16(send_dn + parity * (2 * N * 8) + k * 256, b, send_dn_mb + parity * 16);
-            }
-            __syncthreads();
-            mbar_expect_tx2_if(smem_u32(&mbar[parity][0]), smem_u32(&mbar[parity][1]), N * 8,
-                               threadIdx.x == 0);
-            // locate the rows above and below this warp's block
-            const float2 *usrc, *dsrc;
-            if (warp > 0) {
-                usrc = edge + parity * (W * 2 * N) + (warp - 1) * (2 * N) + N + lane * 2;
-            } else {
-                if (!dead) dead = !mbar_wait_bounded(smem_u32(&mbar[parity][0]), phase, a.wait_limit_ns, a.status);
-                usrc = halo + parity * (2 * N) + lane * 2;
-            }
-            if (warp < W - 1) {
-                dsrc = edge + parity * (W * 2 * N) + (warp + 1) * (2 * N) + lane * 2;
-            } else {
-                if (!dead) dead = !mbar_wait_bounded(smem_u32(&mbar[parity][1]), phase, a.wait_limit_ns, a.status);
-                dsrc = halo + parity * (2 * N) + N + lane * 2;
-            }
-            const float inv_j = a.inv_j[j];
-            auto go = [&](auto off_tag) {
-                constexpr int OFF = decltype(off_tag)::value;
-                if (j == 1)
-                    stage<kFinal, CL, RL, N, OFF>(L, rowc + lrow0, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j);
-                else
-                    stage<kHorner, CL, RL, N, OFF>(L, rowc + lrow0, usrc, dsrc, Q, lane, x1_0, a.dtU, inv_j);
-            };
-            // the first row's offset modulo CL is a multiple of gcd(RL, CL)
-            static_assert(CL == 2 || CL == 4 || CL == 6 || CL == 8, "diagonal offsets enumerated for CL <= 8");
-            switch (off) {
-                case 0: go(std::integral_constant<int, 0>()); break;
-                case 2: if constexpr (CL > 2) go(std::integral_constant<int, 2 % CL>()); break;
-                case 4: if constexpr (CL > 4) go(std::integral_constant<int, 4 % CL>()); break;
-                case 6: if constexpr (CL > 6) go(std::integral_constant<int, 6 % CL>()); break;
-                default: if constexpr (CL % 2 == 1) go(std::integral_constant<int, 1>()); break;
-            }
-            ++tc;
-        };
-        for (int j = K; j >= 1; --j) run_stage(j);
-
-        // psi(t+dt) = psi + A w_2 (in P); rounding error carried in lo
-#pragma unroll
-        for (int i = 0; i < RL; ++i) {
-#pragma unroll
-            for (int k = 0; k < CL; k += 2) {
-                float4 *hp = reinterpret_cast<float4 *>(hi + (lrow0 + i) * N + lane * 2 + k * 32);
-                float4 *lp = reinterpret_cast<float4 *>(glo + (size_t)(x1_0 + i) * N + lane * 2 + k * 32);
-                float4 h4 = *hp;
-                if (a.compensated) {
-                    float4 l4 = *lp;
-                    float2 h0 = make_float2(h4.x, h4.y), h1 = make_float2(h4.z, h4.w);
-                    float2 l0 = make_float2(l4.x, l4.y), l1 = make_float2(l4.z, l4.w);
-                    compensated_add2(h0, l0, L.P[i][k]);
-                    compensated_add2(h1, l1, L.P[i][k + 1]);
-                    h4 = make_float4(h0.x, h0.y, h1.x, h1.y);
-                    *lp = make_float4(l0.x, l0.y, l1.x, l1.y);
-                } else {
-                    h4.x += L.P[i][k].x;
-                    h4.y += L.P[i][k].y;
-                    h4.z += L.P[i][k + 1].x;
-                    h4.w += L.P[i][k + 1].y;
+                for (int k = 0; k < CL; k += 2) {
+                    const float4 t = make_float4(L.P[0][k].x, L.P[0][k].y, L.P[0][k + 1].x, L.P[0][k + 1].y);
+                    const float4 b = make_float4(L.P[RL - 1][k].x, L.P[RL - 1][k].y, L.P[RL - 1][k + 1].x,
+                                                 L.P[RL - 1][k + 1].y);
+                    *reinterpret_cast<float4 *>(eb + k * 32) = t;
+                    *reinterpret_cast<float4 *>(eb + N + k * 32) = b;
+                    if (warp == 0) st_async16(send_up + parity * (2 * N * 8) + k * 256, t, send_up_mb + parity * 16);
+                    if (warp == W - 1) st_async16(send_dn + parity * (2 * N * 8) + k * 256, b, send_dn_mb + parity * 16);
                 }
-                *hp = h4;
-                L.P[i][k] = make_float2(h4.x, h4.y);
-                L.P[i][k + 1] = make_float2(h4.z, h4.w);
-            }
-        }
-        // a snapshot step: the new state (P) to its slot, row-major like psi
-        if (a.snap_every > 0 && step + 1 < n_steps && (step + 1) % a.snap_every == 0) {
-            float2 *gs = a.snap + ((step + 1) / a.snap_every - 1) * a.snap_stride + a.tab.st_off[r];
-#pragma unroll
+                __syncthreads();
+                mbar_expect_tx2_if(smem_u32(&mbar[parity][0]), smem_u32(&mbar[parity][1]), N * 8,
+                                   threadIdx.x == 0);
+                // the rows above and below this warp's block
+                const float2 *usrc, *dsrc;
+                if (warp > 0) {
+                    usrc = edge + parity * (W * 2 * N) + (warp - 1) * (2 * N) + N + lane * 2;
+                } else {
+                    if (!dead) dead = !mbar_wait_bounded(smem_u32(&mbar[parity][0]), phase, a.wait_limit_ns, a.status);
+                    usrc = halo + parity * (2 * N) + lane * 2;
+                }
+                if (warp < W - 1) {
+                    dsrc = edge + parity * (W * 2 * N) + (warp + 1) * (2 * N) + lane * 2;
+                } else {
+                    if (!dead) dead = !mbar_wait_bounded(smem_u32(&mbar[parity][1]), phase, a.wait_limit_ns, a.status);
+                    dsrc = halo + parity * (2 * N) + N + lane * 2;
+                }
+                stage<MODE, CL, RL, N, OFF>(L, rowc + lrow0, usrc, dsrc, Q, lane, x1_0, a.dtU, a.inv_j[j]);
+                ++tc;
+            };
+            for (int j = K; j >= 2; --j) run_stage(j, std::integral_constant<int, kHorner>());
+            run_stage(1, std::integral_constant<int, kFinal>());
+            // psi(t+dt) = psi + A w_2 (in P); rounding error carried in lo
+    #pragma unroll
             for (int i = 0; i < RL; ++i) {
-#pragma unroll
-                for (int k = 0; k < CL; k += 2)
-                    *reinterpret_cast<float4 *>(gs + (size_t)(x1_0 + i) * N + x2_0 + k) =
-                        make_float4(L.P[i][k].x, L.P[i][k].y, L.P[i][k + 1].x, L.P[i][k + 1].y);
+    #pragma unroll
+                for (int k = 0; k < CL; k += 2) {
+                    float4 *hp = reinterpret_cast<float4 *>(hi + (lrow0 + i) * N + lane * 2 + k * 32);
+                    float4 *lp = reinterpret_cast<float4 *>(los + (lrow0 + i) * N + lane * 2 + k * 32);
+                    float4 h4 = *hp;
+                    if (a.compensated) {
+                        float4 l4 = *lp;
+                        float2 h0 = make_float2(h4.x, h4.y), h1 = make_float2(h4.z, h4.w);
+                        float2 l0 = make_float2(l4.x, l4.y), l1 = make_float2(l4.z, l4.w);
+                        compensated_add2(h0, l0, L.P[i][k]);
+                        compensated_add2(h1, l1, L.P[i][k + 1]);
+                        h4 = make_float4(h0.x, h0.y, h1.x, h1.y);
+                        *lp = make_float4(l0.x, l0.y, l1.x, l1.y);
+                    } else {
+                        h4.x += L.P[i][k].x;
+                        h4.y += L.P[i][k].y;
+                        h4.z += L.P[i][k + 1].x;
+                        h4.w += L.P[i][k + 1].y;
+                    }
+                    *hp = h4;
+                    L.P[i][k] = make_float2(h4.x, h4.y);
+                    L.P[i][k + 1] = make_float2(h4.z, h4.w);
+                }
+            }
+            // a snapshot step: the new state (P) to its slot, row-major like psi
+            if (a.snap_every > 0 && step + 1 < n_steps && (step + 1) % a.snap_every == 0) {
+                float2 *gs = a.snap + ((step + 1) / a.snap_every - 1) * a.snap_stride + a.tab.st_off[r];
+    #pragma unroll
+                for (int i = 0; i < RL; ++i) {
+    #pragma unroll
+                    for (int k = 0; k < CL; k += 2)
+                        *reinterpret_cast<float4 *>(gs + (size_t)(x1_0 + i) * N + x2_0 + k) =
+                            make_float4(L.P[i][k].x, L.P[i][k].y, L.P[i][k + 1].x, L.P[i][k + 1].y);
+                }
             }
         }
+    };
+    // the first row's offset modulo CL: a multiple of gcd(RL, CL); only those are compiled
+    constexpr int GD = RL % CL == 0 ? CL : (CL % RL == 0 ? RL : (RL % 2 == 0 && CL % 2 == 0 ? 2 : 1));
+    static_assert(CL == 2 || CL == 4 || CL == 6 || CL == 8, "diagonal offsets enumerated for CL <= 8");
+    switch (off) {
+        case 0: main_loop(std::integral_constant<int, 0>()); break;
+        case 2: if constexpr (CL > 2 && 2 % GD == 0) main_loop(std::integral_constant<int, 2 % CL>()); break;
+        case 4: if constexpr (CL > 4 && 4 % GD == 0) main_loop(std::integral_constant<int, 4 % CL>()); break;
+        case 6: if constexpr (CL > 6 && 6 % GD == 0) main_loop(std::integral_constant<int, 6 % CL>()); break;
+        default: break;
     }
 
-    // state out (hi; the carried error is below half an ulp of it)
+    // state out (hi, and the carried error for the next launch)
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+#pragma unroll
+        for (int k = 0; k < CL; k += 2)
+            *reinterpret_cast<float4 *>(glo + (size_t)(x1_0 + i) * N + lane * 2 + k * 32) =
+                *reinterpret_cast<const float4 *>(los + (lrow0 + i) * N + lane * 2 + k * 32);
+    }
 #pragma unroll
     for (int i = 0; i < RL; ++i) {
 #pragma unroll
@@ -359,7 +378,7 @@ RowsShape rows_shape() {
     f.C = N / SR;
     f.threads = 32 * W;
     f.smem = sizeof(float2) * ((size_t)SR * N + (size_t)2 * 2 * N + (size_t)2 * W * 2 * N) +
-             sizeof(float4) * (size_t)(SR + 1);
+             sizeof(float4) * (size_t)(SR + 1) + sizeof(float2) * (size_t)SR * N;
     f.kern = taylor_fused_rows_kernel<CL, RL, W, MINB>;
     return f;
 }

@@ -28,9 +28,22 @@ namespace {
 
 using namespace fused;
 
+// One launch for every size group (register tiles): the work items
+// (realization, tile row, tile column) of all groups form one 1D grid,
+// groups in descending N so that the block scheduler starts the largest
+// items first and the small ones fill the tail.
+constexpr int kMaxFlatGroups = 32;
+struct FlatGroups {
+    int n;                              // groups in the launch (0: one launch per group)
+    int64_t item_off[kMaxFlatGroups + 1];   // first item of each group
+    int list_off[kMaxFlatGroups];       // its realizations in by_group (the launch's list)
+    int tiles_y[kMaxFlatGroups], tiles_x[kMaxFlatGroups];
+};
+
 struct TiledArgs {
     RealTable tab;
-    const int32_t *list;     // realizations of this launch's size group
+    FlatGroups flat;
+    const int32_t *list;     // realizations of this launch's size group (all groups when flat.n > 0)
     const float *eps, *J;    // float32 parameters (packed per realization)
     const float2 *w_in;      // input iterate (w_{j0+1}; psi itself when j0 = K)
     const float2 *psi;       // state of the step
@@ -43,6 +56,32 @@ struct TiledArgs {
     int final;               // the launch's last stage is j = 1 (state update)
     int compensated;
 };
+
+
+// The block's work item: its realization and tile (row, column).
+struct TileItem {
+    int r, ty, tx;
+};
+
+__device__ __forceinline__ TileItem tile_item(const TiledArgs &a) {
+    TileItem t;
+    if (a.flat.n == 0) {
+        t.r = a.list[blockIdx.z];
+        t.ty = blockIdx.y;
+        t.tx = blockIdx.x;
+        return t;
+    }
+    const int64_t it = blockIdx.x;
+    int g = 0;
+    while (g + 1 < a.flat.n && it >= a.flat.item_off[g + 1]) ++g;
+    const int64_t local = it - a.flat.item_off[g];
+    const int per_r = a.flat.tiles_y[g] * a.flat.tiles_x[g];
+    const int q = (int)(local / per_r), rem = (int)(local - (int64_t)q * per_r);
+    t.r = a.list[a.flat.list_off[g] + q];
+    t.ty = rem / a.flat.tiles_x[g];
+    t.tx = rem - t.ty * a.flat.tiles_x[g];
+    return t;
+}
 
 // T x T output tile (T <= TMAX, chosen per size group so that the tiles
 // cover N evenly), D halo, blockDim = 256 (warps over rows, lanes over
@@ -215,9 +254,10 @@ __global__ void __launch_bounds__(32 * W, W == 8 ? 3 : 2) taylor_tiled_reg_kerne
     float4 *rowc = zero + 32;                                     // [RS + 1] (dt eps, dt eps, -dt J_up, -dt J_up)
     int *x_row = reinterpret_cast<int *>(rowc + RS + 1);          // [RS]
 
-    const int r = a.list[blockIdx.z];
+    const TileItem item = tile_item(a);
+    const int r = item.r;
     const int N = a.tab.N[r];
-    const int x1_0 = blockIdx.y * T - D, x2_0 = blockIdx.x * T2 - D;
+    const int x1_0 = item.ty * T - D, x2_0 = item.tx * T2 - D;
     const int64_t base = a.tab.st_off[r];
     const int64_t po = a.tab.par_off[r];
     const float dt = a.dt;
@@ -374,9 +414,10 @@ __global__ void __launch_bounds__(256, 2) taylor_tiled_wide_kernel(const __grid_
     float4 *rowc = zero + RC / 2;                                 // [RR + 1]
     int *x_row = reinterpret_cast<int *>(rowc + RR + 1);          // [RR]
 
-    const int r = a.list[blockIdx.z];
+    const TileItem item = tile_item(a);
+    const int r = item.r;
     const int N = a.tab.N[r];
-    const int x1_0 = blockIdx.y * T1 - D, x2_0 = blockIdx.x * T2 - D;
+    const int x1_0 = item.ty * T1 - D, x2_0 = item.tx * T2 - D;
     const int64_t base = a.tab.st_off[r];
     const int64_t po = a.tab.par_off[r];
     const float dt = a.dt;
@@ -669,6 +710,34 @@ int launch_taylor_tiled(const ctqw_hamiltonian *h, int shape, const void *w_in, 
     a.compensated = compensated;
     CTQW_CUDA_TRY(cudaFuncSetAttribute((const void *)f.kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)f.smem));
+    const int G = (int)h->group_N.size();
+    a.flat.n = 0;
+    if (f.fixed_tile && G > 1 && G <= kMaxFlatGroups) {
+        // one launch over every group, largest N first (see FlatGroups)
+        a.flat.n = G;
+        a.list = h->by_group_d;
+        int64_t items = 0;
+        for (int k = 0; k < G; ++k) {
+            const int g = G - 1 - k;   // groups are stored in ascending N
+            int off = 0;
+            for (int q = 0; q < g; ++q) off += h->group_count[q];
+            const int N = h->group_N[g];
+            a.flat.item_off[k] = items;
+            a.flat.list_off[k] = off;
+            a.flat.tiles_y[k] = (N + f.TMAX - 1) / f.TMAX;
+            a.flat.tiles_x[k] = (N + f.TMAX2 - 1) / f.TMAX2;
+            items += (int64_t)h->group_count[g] * a.flat.tiles_y[k] * a.flat.tiles_x[k];
+        }
+        a.flat.item_off[G] = items;
+        a.T = f.TMAX;
+        if (items > 0x7fffffffLL) {
+            ctqw_set_error("tiled path: %lld tiles in one launch", (long long)items);
+            return CTQW_EUNSUPPORTED;
+        }
+        f.kern<<<(unsigned)items, f.threads, f.smem, s>>>(a);
+        CTQW_CUDA_TRY(cudaGetLastError());
+        return CTQW_OK;
+    }
     int off = 0;
     for (size_t g = 0; g < h->group_N.size(); ++g) {
         const int N = h->group_N[g], cnt = h->group_count[g];
