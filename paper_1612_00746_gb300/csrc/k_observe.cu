@@ -390,7 +390,9 @@ int launch_observables(const ctqw_hamiltonian *h, int dtype, const void *psi, do
         const int64_t target = 152 * 8;
         const int64_t per_r = std::max<int64_t>(1, (target + h->R - 1) / h->R);
         int64_t rpb = (rows_max + per_r - 1) / per_r;
-        rpb = std::max<int64_t>(kObsWarps, std::min<int64_t>(rpb, 4096));
+        // a whole number of 8-row groups for every warp, at most 4096 rows
+        constexpr int64_t unit = kObsWarps * kObsRows;
+        rpb = std::min<int64_t>(4096, std::max<int64_t>(unit, (rpb + unit - 1) / unit * unit));
         const dim3 grid((unsigned)((rows_max + rpb - 1) / rpb), (unsigned)h->R);
         const size_t smem = (size_t)rpb * 8;
         if (dtype == CTQW_C64) {
