@@ -381,7 +381,8 @@ def ragged_leg(args, dev, stream):
     roof["timing"] = "the whole propagate call (tile launches and the reductions of 101 samples)"
     launches8 = -(-K // 8)
     depth = -(-K // launches8)
-    launches = 1 + w.n_steps * (-(-K // depth)) * len(h.group_sizes) + n_obs + 1
+    groups_per_launch = 1 if len(h.group_sizes) <= 32 else len(h.group_sizes)   # all groups in one launch
+    launches = 1 + w.n_steps * (-(-K // depth)) * groups_per_launch + n_obs + 1
     out = {"workload": w.name, "value": units / (ms / 1000.0), "unit": UNIT, "ms": ms,
            "R": w.R, "sizes": "N in {128, 192, ..., 1024} per realization (15 groups)",
            "K": K, "K_range": [8, 20], "n_steps": w.n_steps, "obs_every": w.obs_every,
@@ -465,7 +466,10 @@ def run_ours(args):
         # ceil(K / D) launches per step and size group, observables, init
         launches8 = -(-w.K // 8)
         depth = {0: -(-w.K // launches8), 9: 4, 10: 8, 11: 8, 12: 4, 13: 8, 14: 2, 15: 7}[(args.flags >> 8) & 0xF]
-        launches_per_step = 1 + w.n_steps * (-(-w.K // depth)) * len(h.group_sizes) + n_obs
+        # register tiles run every size group in one launch (the shared-memory shapes one per group)
+        shared_mem_shape = ((args.flags >> 8) & 0xF) == 9
+        per_launch_groups = len(h.group_sizes) if shared_mem_shape or len(h.group_sizes) > 32 else 1
+        launches_per_step = 1 + w.n_steps * (-(-w.K // depth)) * per_launch_groups + n_obs
     else:
         # init_state + one fused launch per S + 1 sampling intervals + one
         # reduction kernel per sample

@@ -113,3 +113,18 @@ def tuned_flags(h: ctqw.Hamiltonian, psi: torch.Tensor, dtype: int, dt: float, K
                       "timings": {str(f): ms for f, ms in timings}}
         _store(cache_path, table)
     return best
+
+
+def tune(h: ctqw.Hamiltonian, psi: torch.Tensor, dtype: int, dt: float, n_steps: int,
+         K_min: int = 1, K_max: int = 30, steps: int = 4, cache_path: Optional[str] = DEFAULT_CACHE,
+         candidates: Iterable[int] = CANDIDATES) -> Tuple[int, int]:
+    """(K, flags) for a propagation of n_steps steps of dt on this handle.
+
+    K is the smallest order in K_min..K_max whose summed truncation bound
+    stays within a tenth of the type's tolerance (ctqw_autotune_order; a
+    larger K only costs time), then flags the fastest kernel shape for that
+    K: for a ragged batch the tiled kernels at every compiled depth and
+    region, and the per-term path.
+    """
+    K = ctqw.ctqw_autotune_order(h, dtype, dt, n_steps, K_min, K_max)
+    return K, tuned_flags(h, psi, dtype, dt, K, steps, cache_path, candidates)

@@ -1,5 +1,7 @@
 """Autotuning: the Taylor order from the truncation bound (K = 0) and the
 kernel shape by timing the compiled candidates, through the C ABI."""
+import json
+
 import numpy as np
 import pytest
 
@@ -89,6 +91,36 @@ def test_shape_autotuner_on_a_ragged_batch(ctqw, tmp_path):
     ref = oracle.ensemble_run(w)
     assert np.max(np.abs(got["P_mean"] - ref["P_mean"])) <= TOL_FP32
     assert np.max(np.abs(got["norm"] - ref["norm"].T)) <= TOL_NORM_DRIFT
+
+
+def test_order_and_shape_for_a_ragged_batch(ctqw, tmp_path):
+    """tune() on a ragged batch: K is the bound's order over 8..20 and the
+    flags the fastest timed candidate; propagating with the pair matches
+    the oracle."""
+    import oracle
+    from gpu_helpers import TOL_FP32
+    from paper_1612_00746_gb300 import autotune
+
+    w = cw.get("ragged_n128_1024").with_(R=5, ragged_sizes=(40, 72, 96), n_steps=40, obs_every=20)
+    h = ctqw.build_for_workload(w)
+    psi = h.new_state(cw.C64)
+    ctqw.ctqw_init_state(h, psi, ctqw.initial_sites(w, h), cw.C64)
+    K, flags = autotune.tune(h, psi, cw.C64, w.dt, w.n_steps, 8, 20, steps=2,
+                             cache_path=str(tmp_path / "c.json"))
+    assert K == ctqw.ctqw_autotune_order(h, cw.C64, w.dt, w.n_steps, 8, 20)
+    assert 8 <= K <= 20
+    timed = json.load(open(tmp_path / "c.json"))
+    entry = next(iter(timed.values()))
+    assert int(entry["flags"]) == flags
+    assert entry["ms_per_step"] == min(entry["timings"].values())
+    n_obs = h.n_obs(w.n_steps, w.obs_every)
+    P = torch.empty((n_obs, h.p_width), dtype=torch.float64, device="cuda")
+    ctqw.ctqw_propagate_taylor(h, psi, cw.C64, w.dt, K, w.n_steps, w.obs_every, P, None, None, flags,
+                               h.workspace(cw.C64, ctqw.TAYLOR, flags))
+    ctqw.ctqw_check_status(h)
+    ref = oracle.ensemble_run(w, K=K)
+    assert np.max(np.abs(P.cpu().numpy() - ref["P_mean"])) <= TOL_FP32
+    h.close()
 
 
 def test_per_term_ragged_propagation_replays_from_a_cuda_graph(ctqw):
