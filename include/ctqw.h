@@ -316,12 +316,25 @@ int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, 
  * device, complex128 (interleaved re, im), group g's N_g x N_g block
  * row-major starting at element sum_{g' < g} N_g'^2 (the order of
  * ctqw_output_layout's groups); overwritten (zeroed on the stream first).
- * Products in the state's type (FP32 for CTQW_C64) over chunks of 32
- * (16 in FP64), accumulated in FP64.  m = 2 or 3.  Asynchronous.
- * Errors: EINVAL for null pointers or a bad dtype, ECUDA.
+ * CTQW_C64 with every group's N a multiple of 16 (up to 2048) runs on the
+ * tensor cores (tcgen05, TF32): each FP32 amplitude is split into two TF32
+ * pieces and every product formed from three piece products (~2^-22
+ * relative), accumulated in FP32 in tensor memory over at most 256 k and
+ * then in two-word FP32 totals and FP64 (see ctqw_set_density_method; it
+ * allocates a scratch of 256 KB per CTA stream-ordered).  Otherwise products
+ * in the state's type over chunks of 32 (16 in FP64), accumulated in FP64,
+ * on CUDA cores.  m = 2 or 3.  Asynchronous.  Errors: EINVAL for null
+ * pointers or a bad dtype, ENOMEM, ECUDA.
  */
 int ctqw_one_body_density(const ctqw_hamiltonian *h, int32_t dtype, const void *psi_dev,
                           double *rho_dev, void *stream);
+
+/*
+ * Which units ctqw_one_body_density uses on this handle: 0 (the default)
+ * the tensor cores where supported, 1 the CUDA cores always.  EINVAL for a
+ * null handle or another value.
+ */
+int ctqw_set_density_method(ctqw_hamiltonian *h, int32_t method);
 
 /*
  * One sample of the observables of the current states (the diagonal of

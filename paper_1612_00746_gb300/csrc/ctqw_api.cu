@@ -1056,7 +1056,16 @@ int ctqw_one_body_density(const ctqw_hamiltonian *h, int32_t dtype, const void *
     if (dtype != CTQW_C64 && dtype != CTQW_C128) { ctqw_set_error("dtype %d", dtype); return CTQW_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     CTQW_CUDA_TRY(cudaMemsetAsync(rho_dev, 0, 2 * sizeof(double) * (size_t)h->joint_width, s));
+    if (h->density_method == 0 && one_body_density_tc_supported(h, dtype))
+        return launch_one_body_density_tc(h, psi_dev, rho_dev, s);
     return launch_one_body_density(h, dtype, psi_dev, rho_dev, s);
+}
+
+int ctqw_set_density_method(ctqw_hamiltonian *h, int32_t method) {
+    if (!h) { ctqw_set_error("null handle"); return CTQW_EINVAL; }
+    if (method != 0 && method != 1) { ctqw_set_error("density method must be 0 or 1 (got %d)", method); return CTQW_EINVAL; }
+    h->density_method = method;
+    return CTQW_OK;
 }
 
 int ctqw_ensemble_observables(const ctqw_hamiltonian *h, int32_t dtype, const void *psi_dev,

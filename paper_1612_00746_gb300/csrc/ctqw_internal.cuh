@@ -44,6 +44,7 @@ struct ctqw_hamiltonian {
     double *renorm_d = nullptr;     // [R] norms of the per-step renormalization
     int32_t *sites_d = nullptr;     // [R][m] initial sites (ctqw_init_state)
     double norm_drift_tol = 0.0;    // norm check: |norm - norm at step 0| above this fails (0: finiteness only)
+    int density_method = 0;         // one-body density: 0 tensor cores where supported, 1 CUDA cores
 };
 
 // Per-launch view of the realization table (passed by value to kernels).
@@ -184,6 +185,9 @@ int launch_observables(const ctqw_hamiltonian *h, int dtype, const void *psi, do
 // the caller): [joint_width] complex128 at the pair-distribution offsets.
 int launch_one_body_density(const ctqw_hamiltonian *h, int dtype, const void *psi, double *rho,
                             cudaStream_t s);
+// The same on the tensor cores (c64, every group's N a multiple of 16 up to 2048).
+bool one_body_density_tc_supported(const ctqw_hamiltonian *h, int dtype);
+int launch_one_body_density_tc(const ctqw_hamiltonian *h, const void *psi, double *rho, cudaStream_t s);
 
 // Exact propagation by diagonalisation (FP64, D = N^m <= exact_max_dim()):
 // eigenpairs of every realization (evals [R][Dp], evecs [R][Dp][Dp] with Dp

@@ -1,0 +1,336 @@
+// One-body reduced density matrix on the tensor cores (tcgen05, TF32 with
+// split operands): the dense Hermitian contraction that dominates the
+// paper's post-processing (Sec. 4: cublasCher on <rho>), here for the
+// partial trace over all particles but one,
+//
+//   rho1(x, x') = (1/R_g)(1/m) sum_r sum_j sum_k psi_r(x_j = x, k) conj(psi_r(x_j = x', k)).
+//
+// Per size group it is a real GEMM pair over K = R_g m N^(m-1):
+//   Re rho1 = Ar Ar^T + Ai Ai^T,   Im rho1 = Ai Ar^T - Ar Ai^T
+// with A[x][(r, j, k)] = psi_r(x_j = x, k).  Every FP32 operand is split
+// into TF32 pieces, a = a_hi + a_lo (a_hi = a rounded to TF32, a_lo the
+// rest rounded to TF32), and each product is a_hi b_hi + a_hi b_lo +
+// a_lo b_hi (the dropped a_lo b_lo is ~2^-22 of it).
+//
+// A CTA (256 threads) owns a 128 x 128 tile of (x, x') and a range of
+// (realization, particle) pairs.  All threads stage 16 k at a time into
+// shared memory (two stages, the canonical K-major layout of the MMA: 8-row
+// by 16-byte core matrices), converted to the four TF32 arrays re_hi,
+// re_lo, im_hi, im_lo of the rows x and of the rows x'.  One thread issues
+// 12 MMAs per 8 k (M = 128, N = 128, K = 8, FP32 accumulate in TMEM: 128
+// columns for Re, 128 for Im) and commits them to the stage's mbarrier.
+// Every 256 k (or per pair when N^(m-1) < 256) the FP32 partials in TMEM
+// are added into the CTA's running totals, kept as two FP32 words (TwoSum)
+// in a global slot of its own, so the totals carry ~2^-44 of relative
+// rounding; a second kernel sums the slots of all CTAs in FP64.  All waits
+// are bounded (status word, then the CTA stops).
+#include <cstdint>
+
+#include "ctqw_internal.cuh"
+
+namespace {
+
+constexpr int kM = 128;          // rows x per tile (MMA M)
+constexpr int kNt = 128;         // columns x' per tile (MMA N)
+constexpr int kKc = 16;          // k per shared-memory stage
+constexpr int kThreads = 256;
+constexpr int kArr = kM * kKc;   // floats per operand array of a stage
+constexpr int kBlockK = 256;     // k accumulated in TMEM between two drains
+constexpr long kWaitIters = 1L << 26;
+
+struct TcArgs {
+    RealTable tab;
+    const int32_t *list;     // the group's realizations
+    const float2 *psi;
+    float *slots;            // per CTA: [2 (hi, lo)][2 (re, im)][kNt][kM] FP32
+    int *status;
+    int N, m, pairs;         // pairs = R_g m
+    int pairs_per_split;
+    int64_t n_k;             // N^(m-1)
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// tcgen05 shared-memory descriptor: canonical K-major layout, no swizzle
+// (LBO: bytes between core matrices along K, SBO: along M/N), version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor, kind::tf32: D FP32, A and B TF32, K-major, M x N.
+__host__ __device__ constexpr uint32_t tf32_idesc(int M, int N, bool negate_a) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | (negate_a ? (1u << 13) : 0u) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity) {
+    for (long it = 0; it < kWaitIters; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, q;\n\t}"
+                     : "=r"(done) : "r"(mb), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ float tf32_round(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+// hi + lo + v, rounded back into (hi, lo): TwoSum, then the error into lo.
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v) {
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+// 32 consecutive TMEM columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Offset (floats) of element (row, k) of a [kM x kKc] operand array in the
+// canonical layout: core (row / 8, k / 4) of 8 x 4 floats, cores along K first.
+__device__ __forceinline__ int canon(int row, int k) {
+    return ((row >> 3) * (kKc / 4) + (k >> 2)) * 32 + (row & 7) * 4 + (k & 3);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) rho1_tc_kernel(const __grid_constant__ TcArgs a) {
+    extern __shared__ __align__(1024) float smem[];
+    // stage s: A arrays at smem + s * 8 kArr + q kArr, B arrays at + 4 kArr (q = re_hi, re_lo, im_hi, im_lo)
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int stop;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int N = a.N, m = a.m;
+    const int x0 = blockIdx.y * kM, xp0 = blockIdx.x * kNt;
+    const int p0 = blockIdx.z * a.pairs_per_split;
+    const int p1 = min(a.pairs, p0 + a.pairs_per_split);
+    const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    float *slot = a.slots + (size_t)cta * (2 * 2 * kNt * kM);
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        stop = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;"
+                     ::"r"(smem_u32(&tmem_base)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;   // Re at columns [0, 128), Im at [128, 256)
+
+    const int64_t n_k = a.n_k;
+    const int64_t block_k = n_k < kBlockK ? n_k : kBlockK;
+    const int64_t chunks_per_pair = n_k / kKc;
+    const int64_t n_chunks = (int64_t)(p1 - p0) * chunks_per_pair;
+    const int chunks_per_block = (int)(block_k / kKc);
+    constexpr uint32_t kLbo = 128, kSbo = (kKc / 4) * 128;
+    const uint32_t id_pos = tf32_idesc(kM, kNt, false), id_neg = tf32_idesc(kM, kNt, true);
+
+    for (int64_t c = 0; c < n_chunks; ++c) {
+        const int b = (int)(c & 1);
+        float *st = smem + b * 8 * kArr;
+        // the buffer's previous MMAs (chunk c - 2) must be done before it is overwritten
+        if (c >= 2 && !mbar_wait(smem_u32(&mbar[b]), (uint32_t)(((c - 2) >> 1) & 1))) {
+            if (tid == 0) atomicOr(a.status, 4);
+            stop = 1;
+        }
+        __syncthreads();
+        if (stop) break;
+        // stage 16 k of pair p: rows x0.. (A) and xp0.. (B), TF32 pieces
+        const int64_t pc = c / chunks_per_pair;
+        const int p = p0 + (int)pc;
+        const int64_t k0 = (c - pc * chunks_per_pair) * kKc;
+        const int r = a.list[p / m], j = p - (p / m) * m;
+        int64_t S_x = 1;
+        for (int l = j + 1; l < m; ++l) S_x *= N;
+        const int64_t K_lo = S_x, S_hi = S_x * N;
+        const float2 *ps = a.psi + a.tab.st_off[r];
+        const bool x_contig = S_x == 1;
+        for (int e = tid; e < 2 * kM * kKc; e += kThreads) {
+            const int side = e / (kM * kKc), f = e - side * (kM * kKc);
+            const int row = x_contig ? f % kM : f / kKc, kk = x_contig ? f / kM : f % kKc;
+            const int x = (side ? xp0 : x0) + row;
+            const int64_t k = k0 + kk;
+            float2 v = make_float2(0.f, 0.f);
+            if (x < N) v = ps[(k / K_lo) * S_hi + (int64_t)x * S_x + (k % K_lo)];
+            const float rh = tf32_round(v.x), ih = tf32_round(v.y);
+            const float rl = tf32_round(v.x - rh), il = tf32_round(v.y - ih);
+            float *arr = st + side * 4 * kArr;
+            const int o = canon(row, kk);
+            arr[o] = rh;
+            arr[kArr + o] = rl;
+            arr[2 * kArr + o] = ih;
+            arr[3 * kArr + o] = il;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        const bool block_start = (c % chunks_per_block) == 0;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_u32(st), sb = smem_u32(st + 4 * kArr);
+#pragma unroll
+            for (int ks = 0; ks < kKc / 8; ++ks) {
+                const uint32_t koff = (uint32_t)ks * 2 * kLbo;
+                auto A = [&](int q) { return smem_desc(sa + q * kArr * 4 + koff, kLbo, kSbo); };
+                auto B = [&](int q) { return smem_desc(sb + q * kArr * 4 + koff, kLbo, kSbo); };
+                const uint32_t first = (block_start && ks == 0) ? 0u : 1u;
+                // Re += Ar Br + Ai Bi (three TF32 pieces each)
+                mma_tf32(tmem, A(0), B(0), id_pos, first);
+                mma_tf32(tmem, A(0), B(1), id_pos, 1u);
+                mma_tf32(tmem, A(1), B(0), id_pos, 1u);
+                mma_tf32(tmem, A(2), B(2), id_pos, 1u);
+                mma_tf32(tmem, A(2), B(3), id_pos, 1u);
+                mma_tf32(tmem, A(3), B(2), id_pos, 1u);
+                // Im += Ai Br - Ar Bi
+                mma_tf32(tmem + kNt, A(2), B(0), id_pos, first);
+                mma_tf32(tmem + kNt, A(2), B(1), id_pos, 1u);
+                mma_tf32(tmem + kNt, A(3), B(0), id_pos, 1u);
+                mma_tf32(tmem + kNt, A(0), B(2), id_neg, 1u);
+                mma_tf32(tmem + kNt, A(0), B(3), id_neg, 1u);
+                mma_tf32(tmem + kNt, A(1), B(2), id_neg, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_u32(&mbar[b])) : "memory");
+        }
+        // the end of a block: the FP32 partials into the CTA's two-word totals
+        if ((c + 1) % chunks_per_block == 0 || c + 1 == n_chunks) {
+            if (!mbar_wait(smem_u32(&mbar[b]), (uint32_t)((c >> 1) & 1))) {
+                if (tid == 0) atomicOr(a.status, 4);
+                stop = 1;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (stop) break;
+            // warp w: TMEM lanes 32 (w % 4).. (rows), warpgroup w / 4: Re or Im columns
+            const int row = 32 * (warp & 3) + lane, part = warp >> 2;
+            float *hi = slot + (size_t)part * kNt * kM, *lo = slot + (size_t)(2 + part) * kNt * kM;
+#pragma unroll 1
+            for (int c0 = 0; c0 < kNt; c0 += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(part * kNt + c0), v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const size_t o = (size_t)(c0 + i) * kM + row;
+                    float h = hi[o], l = lo[o];
+                    two_sum_add(h, l, v[i]);
+                    hi[o] = h;
+                    lo[o] = l;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+}
+
+// rho1 tile (x, x') = scale * sum over the splits of (hi + lo), in FP64.
+__global__ void __launch_bounds__(256) rho1_tc_reduce_kernel(const float *__restrict__ slots, int tiles_x,
+                                                             int tiles_y, int splits, int N, double scale,
+                                                             double *__restrict__ rho) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)N * N) return;
+    const int x = (int)(i / N), xp = (int)(i - (int64_t)x * N);
+    const int ty = x / kM, tx = xp / kNt, row = x - ty * kM, col = xp - tx * kNt;
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < splits; ++s) {
+        const float *slot = slots + (size_t)((s * tiles_y + ty) * tiles_x + tx) * (2 * 2 * kNt * kM);
+        const size_t o = (size_t)col * kM + row;
+        re += (double)slot[o] + (double)slot[2 * kNt * kM + o];
+        im += (double)slot[kNt * kM + o] + (double)slot[3 * kNt * kM + o];
+    }
+    rho[2 * i] += scale * re;
+    rho[2 * i + 1] += scale * im;
+}
+
+}  // namespace
+
+bool one_body_density_tc_supported(const ctqw_hamiltonian *h, int dtype) {
+    if (dtype != CTQW_C64) return false;
+    for (int N : h->group_N)
+        if (N % 16 != 0 || N > 2048) return false;
+    return true;
+}
+
+int launch_one_body_density_tc(const ctqw_hamiltonian *h, const void *psi, double *rho, cudaStream_t s) {
+    const size_t smem = sizeof(float) * 2 * 8 * kArr;
+    CTQW_CUDA_TRY(cudaFuncSetAttribute((const void *)rho1_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    int sms = 0, dev = 0;
+    CTQW_CUDA_TRY(cudaGetDevice(&dev));
+    CTQW_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int off = 0;
+    for (size_t g = 0; g < h->group_N.size(); ++g) {
+        const int N = h->group_N[g], cnt = h->group_count[g];
+        int64_t n_k = 1;
+        for (int j = 1; j < h->m; ++j) n_k *= N;
+        const int tiles_x = (N + kNt - 1) / kNt, tiles_y = (N + kM - 1) / kM;
+        const int pairs = cnt * h->m;
+        int splits = std::max(1, sms / (tiles_x * tiles_y));
+        splits = std::min(splits, pairs);
+        const int pps = (pairs + splits - 1) / splits;
+        splits = (pairs + pps - 1) / pps;
+        const size_t slot_floats = (size_t)tiles_x * tiles_y * splits * (2 * 2 * kNt * kM);
+        float *slots = nullptr;
+        CTQW_CUDA_TRY(ctqw_malloc_async((void **)&slots, slot_floats * sizeof(float), s));
+        int st = CTQW_OK;
+        if (cudaMemsetAsync(slots, 0, slot_floats * sizeof(float), s) != cudaSuccess)
+            st = ctqw_cuda_fail(cudaGetLastError(), "memset of the rho1 slots");
+        if (st == CTQW_OK) {
+            TcArgs a;
+            a.tab = real_table(h);
+            a.list = h->by_group_d + off;
+            a.psi = (const float2 *)psi;
+            a.slots = slots;
+            a.status = h->status_d;
+            a.N = N;
+            a.m = h->m;
+            a.pairs = pairs;
+            a.pairs_per_split = pps;
+            a.n_k = n_k;
+            rho1_tc_kernel<<<dim3((unsigned)tiles_x, (unsigned)tiles_y, (unsigned)splits), kThreads, smem, s>>>(a);
+            if (cudaGetLastError() != cudaSuccess) st = ctqw_cuda_fail(cudaGetLastError(), "rho1 tensor-core launch");
+        }
+        if (st == CTQW_OK) {
+            const int64_t n = (int64_t)N * N;
+            rho1_tc_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+                slots, tiles_x, tiles_y, splits, N, 1.0 / ((double)cnt * h->m), rho + 2 * h->joint_off[g]);
+            if (cudaGetLastError() != cudaSuccess) st = ctqw_cuda_fail(cudaGetLastError(), "rho1 reduction launch");
+        }
+        cudaFreeAsync(slots, s);
+        if (st != CTQW_OK) return st;
+        off += cnt;
+    }
+    return CTQW_OK;
+}

@@ -55,6 +55,7 @@ EXPORTED = (
     "ctqw_graph_state_size", "ctqw_graph_init_state", "ctqw_graph_workspace_size",
     "ctqw_graph_propagate_taylor", "ctqw_graph_propagate_rk4", "ctqw_graph_observables",
     "ctqw_graph_set_chunk", "ctqw_set_norm_check", "ctqw_inject_alloc_failure",
+    "ctqw_set_density_method",
 )
 
 
@@ -119,6 +120,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "ctqw_check_status": [vp, vp],
         "ctqw_set_norm_check": [vp, dbl],
         "ctqw_inject_alloc_failure": [i32],
+        "ctqw_set_density_method": [vp, i32],
         "ctqw_adjoint_workspace_size": [vp, i32, i32, i64, i32, ctypes.POINTER(sz)],
         "ctqw_adjoint_grad": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp],
         "ctqw_taylor_order": [dbl, i64, dbl, i32, i32, ctypes.POINTER(i32), pd],
@@ -476,6 +478,11 @@ def ctqw_one_body_density(h: Hamiltonian, psi: torch.Tensor, dtype: int, stream=
 
 def ctqw_set_norm_check(h: Hamiltonian, drift_tol: float) -> None:
     _check(load().ctqw_set_norm_check(h.handle, float(drift_tol)))
+
+
+def ctqw_set_density_method(h: Hamiltonian, method: int) -> None:
+    """0: tensor cores where supported (the default), 1: CUDA cores."""
+    _check(load().ctqw_set_density_method(h.handle, int(method)))
 
 
 def ctqw_inject_alloc_failure(after: int) -> None:

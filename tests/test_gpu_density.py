@@ -92,3 +92,37 @@ def test_null_arguments_rejected(ctqw):
     lib = ctqw.load()
     assert lib.ctqw_one_body_density(h.handle, cw.C64, None, None, None) == ctqw.CTQW_EINVAL
     h.close()
+
+
+@pytest.mark.parametrize("name,kw", [
+    ("bosons_small", {"R": 6, "n_steps": 30, "obs_every": 30}),                            # N = 64
+    ("bosons_small", {"N": 144, "R": 3, "sites": (71, 72), "n_steps": 20, "obs_every": 20}),  # two tile rows, ragged tail
+    ("bosons_small", {"N": 16, "R": 5, "sites": (7, 8), "n_steps": 20, "obs_every": 20}),   # one small tile
+    ("ring3_small", {"N": 16, "R": 3, "sites": (7, 8, 9), "n_steps": 15, "obs_every": 15}),  # m = 3 (k blocks of 256)
+    ("ragged_n128_1024", {"R": 9, "ragged_sizes": (32, 48, 80, 272), "n_steps": 8, "obs_every": 8}),
+])
+def test_tensor_cores_against_oracle_and_cuda_cores(ctqw, name, kw):
+    """The tcgen05 path (TF32, three piece products, FP32 partials over at
+    most 256 k, two-word totals) against the oracle on the same final states
+    and against the CUDA-core kernel, at the FP32 tolerance."""
+    w = cw.get(name).with_(**kw)
+    h = ctqw.build_for_workload(w)
+    assert all(int(n) % 16 == 0 for n in h.group_sizes)
+    psi = h.new_state(cw.C64)
+    ctqw.ctqw_init_state(h, psi, ctqw.initial_sites(w, h), cw.C64)
+    ctqw.ctqw_propagate_taylor(h, psi, cw.C64, w.dt, w.K, w.n_steps, 0, None, None, None, 0,
+                               h.workspace(cw.C64))
+    ctqw.ctqw_set_density_method(h, 0)
+    tc = [r.cpu().numpy() for r in ctqw.ctqw_one_body_density(h, psi, cw.C64)]
+    ctqw.ctqw_check_status(h)
+    ctqw.ctqw_set_density_method(h, 1)
+    cc = [r.cpu().numpy() for r in ctqw.ctqw_one_body_density(h, psi, cw.C64)]
+    ref = _oracle_rho_from(psi.cpu().numpy(), h.st_off, h.sizes, [int(n) for n in h.group_sizes], w.m)
+    for a, c, b in zip(tc, cc, ref):
+        scale = np.max(np.abs(b))
+        assert np.max(np.abs(a - b)) <= TOL_FP32 * scale, np.max(np.abs(a - b)) / scale
+        assert np.max(np.abs(a - c)) <= TOL_FP32 * scale
+        assert np.max(np.abs(a - a.conj().T)) <= TOL_FP32 * scale
+    with pytest.raises(ctqw.CtqwError):
+        ctqw.ctqw_set_density_method(h, 2)
+    h.close()
