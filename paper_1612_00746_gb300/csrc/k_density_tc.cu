@@ -33,7 +33,10 @@ namespace {
 constexpr int kM = 128;          // rows x per tile (MMA M)
 constexpr int kNt = 128;         // columns x' per tile (MMA N)
 constexpr int kKc = 16;          // k per shared-memory stage
-constexpr int kThreads = 256;
+constexpr int kStages = 3;       // shared-memory ring
+constexpr int kProducerWarps = 8;
+constexpr int kMmaWarp = kProducerWarps;           // warp 8 issues the MMAs; warps 9..12 drain TMEM
+constexpr int kThreads = 32 * (kProducerWarps + 1 + 4);
 constexpr int kArr = kM * kKc;   // floats per operand array of a stage
 constexpr int kBlockK = 256;     // k accumulated in TMEM between two drains
 constexpr long kWaitIters = 1L << 26;
@@ -45,6 +48,7 @@ struct TcArgs {
     float *slots;            // per CTA: [2 (hi, lo)][2 (re, im)][kNt][kM] FP32
     int *status;
     int N, m, pairs;         // pairs = R_g m
+    int tiles;               // tiles per side, ceil(N / 128)
     int pairs_per_split;
     int64_t n_k;             // N^(m-1)
 };
@@ -70,15 +74,26 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
                  ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity) {
+// Bounded wait for the phase of parity `parity` to complete; false after
+// kWaitIters tries or once another role has raised `stop`.
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, const volatile int *stop) {
     for (long it = 0; it < kWaitIters; ++it) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, q;\n\t}"
                      : "=r"(done) : "r"(mb), "r"(parity) : "memory");
         if (done) return true;
+        if ((it & 1023) == 1023 && *stop) return false;
     }
     return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mb) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(mb) : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mb) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
 }
 
 __device__ __forceinline__ float tf32_round(float v) {
@@ -120,171 +135,307 @@ __device__ __forceinline__ int canon(int row, int k) {
 __global__ void __launch_bounds__(kThreads, 1) rho1_tc_kernel(const __grid_constant__ TcArgs a) {
     extern __shared__ __align__(1024) float smem[];
     // stage s: A arrays at smem + s * 8 kArr + q kArr, B arrays at + 4 kArr (q = re_hi, re_lo, im_hi, im_lo)
-    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], acc_full[2], acc_empty[2], done;
     __shared__ uint32_t tmem_base;
     __shared__ int stop;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int N = a.N, m = a.m;
-    const int x0 = blockIdx.y * kM, xp0 = blockIdx.x * kNt;
-    const int p0 = blockIdx.z * a.pairs_per_split;
+    // blockIdx.x: a tile (ty <= tx) of the upper triangle, row by row; the
+    // lower one is its conjugate transpose (rho1 is Hermitian)
+    int ty = 0, rest = blockIdx.x;
+    while (rest >= a.tiles - ty) rest -= a.tiles - ty++;
+    const int x0 = ty * kM, xp0 = (ty + rest) * kNt;
+    const int p0 = blockIdx.y * a.pairs_per_split;
     const int p1 = min(a.pairs, p0 + a.pairs_per_split);
-    const int cta = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const int cta = blockIdx.y * gridDim.x + blockIdx.x;
     float *slot = a.slots + (size_t)cta * (2 * 2 * kNt * kM);
 
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        for (int i = 0; i < kStages; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(kProducerWarps));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[i])));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&acc_full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&acc_empty[i])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         stop = 0;
     }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;"
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;"
                      ::"r"(smem_u32(&tmem_base)) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_base;   // Re at columns [0, 128), Im at [128, 256)
+    // accumulator b (0, 1) at columns 256 b: Re at [0, 128), Im at [128, 256) of it
+    const uint32_t tmem = tmem_base;
 
     const int64_t n_k = a.n_k;
     const int64_t block_k = n_k < kBlockK ? n_k : kBlockK;
     const int64_t chunks_per_pair = n_k / kKc;
     const int64_t n_chunks = (int64_t)(p1 - p0) * chunks_per_pair;
-    const int chunks_per_block = (int)(block_k / kKc);
-    constexpr uint32_t kLbo = 128, kSbo = (kKc / 4) * 128;
-    const uint32_t id_pos = tf32_idesc(kM, kNt, false), id_neg = tf32_idesc(kM, kNt, true);
+    const int64_t chunks_per_block = block_k / kKc;
+    const int64_t n_blocks = (n_chunks + chunks_per_block - 1) / chunks_per_block;
+    volatile int *vstop = &stop;
 
-    for (int64_t c = 0; c < n_chunks; ++c) {
-        const int b = (int)(c & 1);
-        float *st = smem + b * 8 * kArr;
-        // the buffer's previous MMAs (chunk c - 2) must be done before it is overwritten
-        if (c >= 2 && !mbar_wait(smem_u32(&mbar[b]), (uint32_t)(((c - 2) >> 1) & 1))) {
-            if (tid == 0) atomicOr(a.status, 4);
-            stop = 1;
-        }
-        __syncthreads();
-        if (stop) break;
-        // stage 16 k of pair p: rows x0.. (A) and xp0.. (B), TF32 pieces
-        const int64_t pc = c / chunks_per_pair;
-        const int p = p0 + (int)pc;
-        const int64_t k0 = (c - pc * chunks_per_pair) * kKc;
-        const int r = a.list[p / m], j = p - (p / m) * m;
-        int64_t S_x = 1;
-        for (int l = j + 1; l < m; ++l) S_x *= N;
-        const int64_t K_lo = S_x, S_hi = S_x * N;
-        const float2 *ps = a.psi + a.tab.st_off[r];
-        const bool x_contig = S_x == 1;
-        for (int e = tid; e < 2 * kM * kKc; e += kThreads) {
-            const int side = e / (kM * kKc), f = e - side * (kM * kKc);
-            const int row = x_contig ? f % kM : f / kKc, kk = x_contig ? f / kM : f % kKc;
-            const int x = (side ? xp0 : x0) + row;
-            const int64_t k = k0 + kk;
-            float2 v = make_float2(0.f, 0.f);
-            if (x < N) v = ps[(k / K_lo) * S_hi + (int64_t)x * S_x + (k % K_lo)];
-            const float rh = tf32_round(v.x), ih = tf32_round(v.y);
-            const float rl = tf32_round(v.x - rh), il = tf32_round(v.y - ih);
-            float *arr = st + side * 4 * kArr;
-            const int o = canon(row, kk);
-            arr[o] = rh;
-            arr[kArr + o] = rl;
-            arr[2 * kArr + o] = ih;
-            arr[3 * kArr + o] = il;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        const bool block_start = (c % chunks_per_block) == 0;
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = smem_u32(st), sb = smem_u32(st + 4 * kArr);
+    if (warp < kProducerWarps) {
+        // ---- producers: global -> TF32 pieces in the stage ring --------------
+        // Each thread stages 4 groups of 4 consecutive k of one row: group q
+        // is g = tid + 256 q, row g % 128 (consecutive over the lanes, so that
+        // a quarter warp writes 128 contiguous bytes of shared memory),
+        // k / 4 = (g / 128) % 4, side g / 512 (0: rows x, 1: rows x').
+        int xq[4], soff[4], k4q[4];
 #pragma unroll
-            for (int ks = 0; ks < kKc / 8; ++ks) {
-                const uint32_t koff = (uint32_t)ks * 2 * kLbo;
-                auto A = [&](int q) { return smem_desc(sa + q * kArr * 4 + koff, kLbo, kSbo); };
-                auto B = [&](int q) { return smem_desc(sb + q * kArr * 4 + koff, kLbo, kSbo); };
-                const uint32_t first = (block_start && ks == 0) ? 0u : 1u;
-                // Re += Ar Br + Ai Bi (three TF32 pieces each)
-                mma_tf32(tmem, A(0), B(0), id_pos, first);
-                mma_tf32(tmem, A(0), B(1), id_pos, 1u);
-                mma_tf32(tmem, A(1), B(0), id_pos, 1u);
-                mma_tf32(tmem, A(2), B(2), id_pos, 1u);
-                mma_tf32(tmem, A(2), B(3), id_pos, 1u);
-                mma_tf32(tmem, A(3), B(2), id_pos, 1u);
-                // Im += Ai Br - Ar Bi
-                mma_tf32(tmem + kNt, A(2), B(0), id_pos, first);
-                mma_tf32(tmem + kNt, A(2), B(1), id_pos, 1u);
-                mma_tf32(tmem + kNt, A(3), B(0), id_pos, 1u);
-                mma_tf32(tmem + kNt, A(0), B(2), id_neg, 1u);
-                mma_tf32(tmem + kNt, A(0), B(3), id_neg, 1u);
-                mma_tf32(tmem + kNt, A(1), B(2), id_neg, 1u);
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(smem_u32(&mbar[b])) : "memory");
+        for (int q = 0; q < 4; ++q) {
+            const int g = tid + 32 * kProducerWarps * q, row = g & (kM - 1), side = g >> 9;
+            k4q[q] = (g >> 7) & 3;
+            xq[q] = (side ? xp0 : x0) + row;
+            soff[q] = side * 4 * kArr + canon(row, 4 * k4q[q]);
         }
-        // the end of a block: the FP32 partials into the CTA's two-word totals
-        if ((c + 1) % chunks_per_block == 0 || c + 1 == n_chunks) {
-            if (!mbar_wait(smem_u32(&mbar[b]), (uint32_t)((c >> 1) & 1))) {
-                if (tid == 0) atomicOr(a.status, 4);
+        // The chunk the next load reads: amplitude (x, k0 + kk) of pair p sits
+        // at base + x S_x + kk S_k.  With the partial trace over particle j,
+        // S_x = N^(m-1-j); k runs over the other coordinates in order, so for
+        // j < m - 1 it is contiguous within blocks of K_lo = S_x (S_k = 1; a
+        // chunk of 16 never straddles two, N being a multiple of 16) and for
+        // j = m - 1 it steps by N (S_k = N).
+        int cp = 0;
+        int64_t cc = 0, base = 0, S_x = 1, S_k = 1, K_lo = 1, S_hi = 1, rem = 0;
+        auto set_pair = [&](int p) {
+            cp = p;
+            cc = 0;
+            const int r = a.list[p / m], j = p - (p / m) * m;
+            int64_t sx = 1;
+            for (int l = j + 1; l < m; ++l) sx *= N;
+            S_x = sx;
+            K_lo = sx;
+            S_hi = sx * N;
+            S_k = (j == m - 1) ? N : 1;
+            base = a.tab.st_off[r];
+            rem = 0;
+        };
+        auto advance = [&]() {
+            if (++cc == chunks_per_pair) {
+                if (cp + 1 < p1) set_pair(cp + 1);
+                return;
+            }
+            if (S_k != 1) {
+                base += kKc * S_k;
+            } else {
+                base += kKc;
+                rem += kKc;
+                if (rem == K_lo) {
+                    rem = 0;
+                    base += S_hi - K_lo;
+                }
+            }
+        };
+        // the 16 amplitudes of the cursor's chunk that this thread stages
+        float2 v[16];
+        auto load_chunk = [&]() {
+            if (S_k == 1) {
+                // offsets are even (N a multiple of 16): two 16-byte loads per group
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float4 u0 = make_float4(0.f, 0.f, 0.f, 0.f), u1 = u0;
+                    if (xq[q] < N) {
+                        const float4 *src = (const float4 *)(a.psi + base + (int64_t)xq[q] * S_x + 4 * k4q[q]);
+                        u0 = __ldg(src);
+                        u1 = __ldg(src + 1);
+                    }
+                    v[4 * q] = make_float2(u0.x, u0.y);
+                    v[4 * q + 1] = make_float2(u0.z, u0.w);
+                    v[4 * q + 2] = make_float2(u1.x, u1.y);
+                    v[4 * q + 3] = make_float2(u1.z, u1.w);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float2 *src = a.psi + base + xq[q] + (int64_t)(4 * k4q[q]) * S_k;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) v[4 * q + t] = xq[q] < N ? __ldg(src + t * S_k) : make_float2(0.f, 0.f);
+                }
+            }
+            advance();
+        };
+        if (n_chunks > 0) {
+            set_pair(p0);
+            load_chunk();
+        }
+        for (int64_t c = 0; c < n_chunks; ++c) {
+            const int s = (int)(c % kStages);
+            const int64_t use = c / kStages;
+            // the stage's previous MMAs (chunk c - kStages) must be done
+            if (use > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((use - 1) & 1), vstop)) {
+                if (lane == 0) atomicOr(a.status, 4);
+                stop = 1;
+                break;
+            }
+            float *st = smem + s * 8 * kArr;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float4 rh, rl, ih, il;
+                float *ph = &rh.x, *pl = &rl.x, *qh = &ih.x, *ql = &il.x;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float2 u = v[4 * q + t];
+                    ph[t] = tf32_round(u.x);
+                    qh[t] = tf32_round(u.y);
+                    pl[t] = tf32_round(u.x - ph[t]);
+                    ql[t] = tf32_round(u.y - qh[t]);
+                }
+                float *dst = st + soff[q];
+                *(float4 *)dst = rh;
+                *(float4 *)(dst + kArr) = rl;
+                *(float4 *)(dst + 2 * kArr) = ih;
+                *(float4 *)(dst + 3 * kArr) = il;
+            }
+            // the stores, seen by the tensor cores' (async) proxy, then one arrival per warp
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&full[s]));
+            if (c + 1 < n_chunks) load_chunk();
+        }
+    } else if (warp == kMmaWarp) {
+        // ---- one thread issues the MMAs -------------------------------------
+        if (lane == 0) {
+            constexpr uint32_t kLbo = 128, kSbo = (kKc / 4) * 128;
+            const uint32_t id_pos = tf32_idesc(kM, kNt, false), id_neg = tf32_idesc(kM, kNt, true);
+            int64_t blk = 0, bi = 0;
+            bool ok = true;
+            for (int64_t c = 0; c < n_chunks && ok; ++c) {
+                const int s = (int)(c % kStages);
+                const int acc = (int)(bi & 1);
+                // a new block: its accumulator must have been drained (block bi - 2)
+                if (blk == 0 && bi >= 2 && !mbar_wait(smem_u32(&acc_empty[acc]), (uint32_t)(((bi >> 1) - 1) & 1), vstop))
+                    ok = false;
+                if (ok && !mbar_wait(smem_u32(&full[s]), (uint32_t)((c / kStages) & 1), vstop)) ok = false;
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(256 * acc);
+                const float *st = smem + s * 8 * kArr;
+                const uint32_t sa = smem_u32(st), sb = smem_u32(st + 4 * kArr);
+#pragma unroll
+                for (int ks = 0; ks < kKc / 8; ++ks) {
+                    const uint32_t koff = (uint32_t)ks * 2 * kLbo;
+                    auto A = [&](int q) { return smem_desc(sa + q * kArr * 4 + koff, kLbo, kSbo); };
+                    auto B = [&](int q) { return smem_desc(sb + q * kArr * 4 + koff, kLbo, kSbo); };
+                    const uint32_t first = (blk == 0 && ks == 0) ? 0u : 1u;
+                    // Re += Ar Br + Ai Bi (three TF32 pieces each)
+                    mma_tf32(d, A(0), B(0), id_pos, first);
+                    mma_tf32(d, A(0), B(1), id_pos, 1u);
+                    mma_tf32(d, A(1), B(0), id_pos, 1u);
+                    mma_tf32(d, A(2), B(2), id_pos, 1u);
+                    mma_tf32(d, A(2), B(3), id_pos, 1u);
+                    mma_tf32(d, A(3), B(2), id_pos, 1u);
+                    // Im += Ai Br - Ar Bi
+                    mma_tf32(d + kNt, A(2), B(0), id_pos, first);
+                    mma_tf32(d + kNt, A(2), B(1), id_pos, 1u);
+                    mma_tf32(d + kNt, A(3), B(0), id_pos, 1u);
+                    mma_tf32(d + kNt, A(0), B(2), id_neg, 1u);
+                    mma_tf32(d + kNt, A(0), B(3), id_neg, 1u);
+                    mma_tf32(d + kNt, A(1), B(2), id_neg, 1u);
+                }
+                mma_commit(smem_u32(&empty[s]));   // the stage is free once these are done
+                if (++blk == chunks_per_block || c + 1 == n_chunks) {
+                    mma_commit(smem_u32(&acc_full[acc]));   // the block's sums are ready
+                    blk = 0;
+                    ++bi;
+                }
+            }
+            if (!ok) {
+                atomicOr(a.status, 4);
                 stop = 1;
             }
+            // every MMA issued has completed before TMEM is released
+            mma_commit(smem_u32(&done));
+            if (!mbar_wait(smem_u32(&done), 0u, vstop) && ok) {
+                atomicOr(a.status, 4);
+                stop = 1;
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- drain: each finished block's FP32 sums into the CTA's two-word totals
+        // warp w reads TMEM lanes 32 (w % 4).. (the tile's rows), all 256 columns
+        const int quarter = warp & 3, row = 32 * quarter + lane;
+        for (int64_t bi = 0; bi < n_blocks; ++bi) {
+            const int acc = (int)(bi & 1);
+            if (!mbar_wait(smem_u32(&acc_full[acc]), (uint32_t)((bi >> 1) & 1), vstop)) {
+                if (lane == 0) atomicOr(a.status, 4);
+                stop = 1;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            __syncthreads();
-            if (stop) break;
-            // warp w: TMEM lanes 32 (w % 4).. (rows), warpgroup w / 4: Re or Im columns
-            const int row = 32 * (warp & 3) + lane, part = warp >> 2;
-            float *hi = slot + (size_t)part * kNt * kM, *lo = slot + (size_t)(2 + part) * kNt * kM;
 #pragma unroll 1
-            for (int c0 = 0; c0 < kNt; c0 += 32) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(part * kNt + c0), v);
+            for (int c0 = 0; c0 < 2 * kNt; c0 += 32) {
+                float tv[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(256 * acc + c0), tv);
+                const int part = c0 / kNt;   // 0: Re, 1: Im
+                float *hi = slot + (size_t)part * kNt * kM, *lo = slot + (size_t)(2 + part) * kNt * kM;
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
-                    const size_t o = (size_t)(c0 + i) * kM + row;
+                    const size_t o = (size_t)(c0 - part * kNt + i) * kM + row;
                     float h = hi[o], l = lo[o];
-                    two_sum_add(h, l, v[i]);
+                    two_sum_add(h, l, tv[i]);
                     hi[o] = h;
                     lo[o] = l;
                 }
             }
+            // this warp's reads of the accumulator are complete: hand it back
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncthreads();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
 
-// rho1 tile (x, x') = scale * sum over the splits of (hi + lo), in FP64.
-__global__ void __launch_bounds__(256) rho1_tc_reduce_kernel(const float *__restrict__ slots, int tiles_x,
-                                                             int tiles_y, int splits, int N, double scale,
-                                                             double *__restrict__ rho) {
+// rho1(x, x') = scale * sum over the splits of (hi + lo), in FP64, read
+// from tile (x / 128, x' / 128) of the upper triangle, or conjugated from
+// its transpose below the diagonal.
+__global__ void __launch_bounds__(256) rho1_tc_reduce_kernel(const float *__restrict__ slots, int tiles, int splits,
+                                                             int N, double scale, double *__restrict__ rho) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)N * N) return;
-    const int x = (int)(i / N), xp = (int)(i - (int64_t)x * N);
+    int x = (int)(i / N), xp = (int)(i - (int64_t)x * N);
+    const bool lower = x / kM > xp / kNt;
+    if (lower) {
+        const int t = x;
+        x = xp;
+        xp = t;
+    }
     const int ty = x / kM, tx = xp / kNt, row = x - ty * kM, col = xp - tx * kNt;
+    const int n_up = tiles * (tiles + 1) / 2;
+    const int id = ty * tiles - ty * (ty - 1) / 2 + (tx - ty);
     double re = 0.0, im = 0.0;
     for (int s = 0; s < splits; ++s) {
-        const float *slot = slots + (size_t)((s * tiles_y + ty) * tiles_x + tx) * (2 * 2 * kNt * kM);
+        const float *slot = slots + (size_t)(s * n_up + id) * (2 * 2 * kNt * kM);
         const size_t o = (size_t)col * kM + row;
         re += (double)slot[o] + (double)slot[2 * kNt * kM + o];
         im += (double)slot[kNt * kM + o] + (double)slot[3 * kNt * kM + o];
     }
     rho[2 * i] += scale * re;
-    rho[2 * i + 1] += scale * im;
+    rho[2 * i + 1] += scale * (lower ? -im : im);
 }
 
 }  // namespace
 
 bool one_body_density_tc_supported(const ctqw_hamiltonian *h, int dtype) {
-    if (dtype != CTQW_C64) return false;
+    if (dtype != CTQW_C64 || h->m < 2) return false;
     for (int N : h->group_N)
         if (N % 16 != 0 || N > 2048) return false;
     return true;
 }
 
 int launch_one_body_density_tc(const ctqw_hamiltonian *h, const void *psi, double *rho, cudaStream_t s) {
-    const size_t smem = sizeof(float) * 2 * 8 * kArr;
+    const size_t smem = sizeof(float) * kStages * 8 * kArr;
     CTQW_CUDA_TRY(cudaFuncSetAttribute((const void *)rho1_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
     int sms = 0, dev = 0;
@@ -295,18 +446,18 @@ int launch_one_body_density_tc(const ctqw_hamiltonian *h, const void *psi, doubl
         const int N = h->group_N[g], cnt = h->group_count[g];
         int64_t n_k = 1;
         for (int j = 1; j < h->m; ++j) n_k *= N;
-        const int tiles_x = (N + kNt - 1) / kNt, tiles_y = (N + kM - 1) / kM;
+        const int tiles = (N + kM - 1) / kM, n_up = tiles * (tiles + 1) / 2;
         const int pairs = cnt * h->m;
-        int splits = std::max(1, sms / (tiles_x * tiles_y));
+        int splits = std::max(1, sms / n_up);
         splits = std::min(splits, pairs);
         const int pps = (pairs + splits - 1) / splits;
         splits = (pairs + pps - 1) / pps;
-        const size_t slot_floats = (size_t)tiles_x * tiles_y * splits * (2 * 2 * kNt * kM);
+        const size_t slot_floats = (size_t)n_up * splits * (2 * 2 * kNt * kM);
         float *slots = nullptr;
         CTQW_CUDA_TRY(ctqw_malloc_async((void **)&slots, slot_floats * sizeof(float), s));
         int st = CTQW_OK;
-        if (cudaMemsetAsync(slots, 0, slot_floats * sizeof(float), s) != cudaSuccess)
-            st = ctqw_cuda_fail(cudaGetLastError(), "memset of the rho1 slots");
+        const cudaError_t em = cudaMemsetAsync(slots, 0, slot_floats * sizeof(float), s);
+        if (em != cudaSuccess) st = ctqw_cuda_fail(em, "memset of the rho1 slots");
         if (st == CTQW_OK) {
             TcArgs a;
             a.tab = real_table(h);
@@ -319,14 +470,17 @@ int launch_one_body_density_tc(const ctqw_hamiltonian *h, const void *psi, doubl
             a.pairs = pairs;
             a.pairs_per_split = pps;
             a.n_k = n_k;
-            rho1_tc_kernel<<<dim3((unsigned)tiles_x, (unsigned)tiles_y, (unsigned)splits), kThreads, smem, s>>>(a);
-            if (cudaGetLastError() != cudaSuccess) st = ctqw_cuda_fail(cudaGetLastError(), "rho1 tensor-core launch");
+            a.tiles = tiles;
+            rho1_tc_kernel<<<dim3((unsigned)n_up, (unsigned)splits), kThreads, smem, s>>>(a);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) st = ctqw_cuda_fail(e, "rho1 tensor-core launch");
         }
         if (st == CTQW_OK) {
             const int64_t n = (int64_t)N * N;
             rho1_tc_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-                slots, tiles_x, tiles_y, splits, N, 1.0 / ((double)cnt * h->m), rho + 2 * h->joint_off[g]);
-            if (cudaGetLastError() != cudaSuccess) st = ctqw_cuda_fail(cudaGetLastError(), "rho1 reduction launch");
+                slots, tiles, splits, N, 1.0 / ((double)cnt * h->m), rho + 2 * h->joint_off[g]);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) st = ctqw_cuda_fail(e, "rho1 reduction launch");
         }
         cudaFreeAsync(slots, s);
         if (st != CTQW_OK) return st;
