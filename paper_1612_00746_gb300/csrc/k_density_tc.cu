@@ -175,26 +175,30 @@ __global__ void __launch_bounds__(kThreads, 1) rho1_tc_kernel(const __grid_const
     const uint32_t tmem = tmem_base;
 
     const int64_t n_k = a.n_k;
-    const int64_t block_k = n_k < kBlockK ? n_k : kBlockK;
     const int64_t chunks_per_pair = n_k / kKc;
     const int64_t n_chunks = (int64_t)(p1 - p0) * chunks_per_pair;
-    const int64_t chunks_per_block = block_k / kKc;
+    const int64_t chunks_per_block = kBlockK / kKc;   // a block may span pairs
     const int64_t n_blocks = (n_chunks + chunks_per_block - 1) / chunks_per_block;
     volatile int *vstop = &stop;
 
     if (warp < kProducerWarps) {
         // ---- producers: global -> TF32 pieces in the stage ring --------------
-        // Each thread stages 4 groups of 4 consecutive k of one row: group q
-        // is g = tid + 256 q, row g % 128 (consecutive over the lanes, so that
-        // a quarter warp writes 128 contiguous bytes of shared memory),
-        // k / 4 = (g / 128) % 4, side g / 512 (0: rows x, 1: rows x').
-        int xq[4], soff[4], k4q[4];
+        // Warps 0-3 stage the rows x, warps 4-7 the rows x'; warp w covers
+        // rows 32 (w % 4) .. + 31 of its side, each thread 4 groups of 4
+        // consecutive k.  Two assignments, chosen per pair by the memory
+        // order of the operand, so that the global loads coalesce and every
+        // quarter warp writes 128 contiguous bytes of shared memory:
+        //   x contiguous (S_k = N): lane = row, group q = k / 4;
+        //   k contiguous (S_k = 1): lane = 8 (k / 4) + row % 8, group q = row / 8 % 4.
+        const int side = warp >> 2, row0 = 32 * (warp & 3);
+        const int xA = (side ? xp0 : x0) + row0 + lane;
+        int xB[4], soffA[4], soffB[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int g = tid + 32 * kProducerWarps * q, row = g & (kM - 1), side = g >> 9;
-            k4q[q] = (g >> 7) & 3;
-            xq[q] = (side ? xp0 : x0) + row;
-            soff[q] = side * 4 * kArr + canon(row, 4 * k4q[q]);
+            const int rowB = row0 + 8 * q + (lane & 7);
+            xB[q] = (side ? xp0 : x0) + rowB;
+            soffA[q] = side * 4 * kArr + canon(row0 + lane, 4 * q);
+            soffB[q] = side * 4 * kArr + canon(rowB, 4 * (lane >> 3));
         }
         // The chunk the next load reads: amplitude (x, k0 + kk) of pair p sits
         // at base + x S_x + kk S_k.  With the partial trace over particle j,
@@ -233,16 +237,18 @@ __global__ void __launch_bounds__(kThreads, 1) rho1_tc_kernel(const __grid_const
                 }
             }
         };
-        // the 16 amplitudes of the cursor's chunk that this thread stages
-        float2 v[16];
-        auto load_chunk = [&]() {
-            if (S_k == 1) {
+        // the 16 amplitudes of the cursor's chunk that this thread stages;
+        // v_kc: they follow the k-contiguous assignment
+        auto load_chunk = [&](float2 (&v)[16], bool &v_kc) {
+            v_kc = S_k == 1;
+            if (v_kc) {
                 // offsets are even (N a multiple of 16): two 16-byte loads per group
+                const int k4 = lane >> 3;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     float4 u0 = make_float4(0.f, 0.f, 0.f, 0.f), u1 = u0;
-                    if (xq[q] < N) {
-                        const float4 *src = (const float4 *)(a.psi + base + (int64_t)xq[q] * S_x + 4 * k4q[q]);
+                    if (xB[q] < N) {
+                        const float4 *src = (const float4 *)(a.psi + base + (int64_t)xB[q] * S_x + 4 * k4);
                         u0 = __ldg(src);
                         u1 = __ldg(src + 1);
                     }
@@ -252,27 +258,25 @@ __global__ void __launch_bounds__(kThreads, 1) rho1_tc_kernel(const __grid_const
                     v[4 * q + 3] = make_float2(u1.z, u1.w);
                 }
             } else {
+                const float2 *src = a.psi + base + xA;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float2 *src = a.psi + base + xq[q] + (int64_t)(4 * k4q[q]) * S_k;
+                for (int q = 0; q < 4; ++q)
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) v[4 * q + t] = xq[q] < N ? __ldg(src + t * S_k) : make_float2(0.f, 0.f);
-                }
+                    for (int t = 0; t < 4; ++t)
+                        v[4 * q + t] = xA < N ? __ldg(src + (int64_t)(4 * q + t) * S_k) : make_float2(0.f, 0.f);
             }
             advance();
         };
-        if (n_chunks > 0) {
-            set_pair(p0);
-            load_chunk();
-        }
-        for (int64_t c = 0; c < n_chunks; ++c) {
+        // stage chunk c from v into its ring slot, then refill v with chunk
+        // c + 2: two chunks of loads stay in flight per thread
+        auto produce = [&](int64_t c, float2 (&v)[16], bool &v_kc) -> bool {
             const int s = (int)(c % kStages);
             const int64_t use = c / kStages;
-            // the stage's previous MMAs (chunk c - kStages) must be done
+            // the slot's previous MMAs (chunk c - kStages) must be done
             if (use > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((use - 1) & 1), vstop)) {
                 if (lane == 0) atomicOr(a.status, 4);
                 stop = 1;
-                break;
+                return false;
             }
             float *st = smem + s * 8 * kArr;
 #pragma unroll
@@ -287,7 +291,7 @@ __global__ void __launch_bounds__(kThreads, 1) rho1_tc_kernel(const __grid_const
                     pl[t] = tf32_round(u.x - ph[t]);
                     ql[t] = tf32_round(u.y - qh[t]);
                 }
-                float *dst = st + soff[q];
+                float *dst = st + (v_kc ? soffB[q] : soffA[q]);
                 *(float4 *)dst = rh;
                 *(float4 *)(dst + kArr) = rl;
                 *(float4 *)(dst + 2 * kArr) = ih;
@@ -297,7 +301,19 @@ __global__ void __launch_bounds__(kThreads, 1) rho1_tc_kernel(const __grid_const
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&full[s]));
-            if (c + 1 < n_chunks) load_chunk();
+            if (c + 2 < n_chunks) load_chunk(v, v_kc);
+            return true;
+        };
+        float2 va[16], vb[16];
+        bool ka = false, kb = false;
+        if (n_chunks > 0) {
+            set_pair(p0);
+            load_chunk(va, ka);
+            if (n_chunks > 1) load_chunk(vb, kb);
+        }
+        for (int64_t c = 0; c < n_chunks; c += 2) {
+            if (!produce(c, va, ka)) break;
+            if (c + 1 < n_chunks && !produce(c + 1, vb, kb)) break;
         }
     } else if (warp == kMmaWarp) {
         // ---- one thread issues the MMAs -------------------------------------
