@@ -12,18 +12,22 @@
 // rest rounded to TF32), and each product is a_hi b_hi + a_hi b_lo +
 // a_lo b_hi (the dropped a_lo b_lo is ~2^-22 of it).
 //
-// A CTA (256 threads) owns a 128 x 128 tile of (x, x') and a range of
-// (realization, particle) pairs.  All threads stage 16 k at a time into
-// shared memory (two stages, the canonical K-major layout of the MMA: 8-row
-// by 16-byte core matrices), converted to the four TF32 arrays re_hi,
-// re_lo, im_hi, im_lo of the rows x and of the rows x'.  One thread issues
-// 12 MMAs per 8 k (M = 128, N = 128, K = 8, FP32 accumulate in TMEM: 128
-// columns for Re, 128 for Im) and commits them to the stage's mbarrier.
-// Every 256 k (or per pair when N^(m-1) < 256) the FP32 partials in TMEM
-// are added into the CTA's running totals, kept as two FP32 words (TwoSum)
-// in a global slot of its own, so the totals carry ~2^-44 of relative
-// rounding; a second kernel sums the slots of all CTAs in FP64.  All waits
-// are bounded (status word, then the CTA stops).
+// Only the 128 x 128 tiles (x, x') with x / 128 <= x' / 128 are computed;
+// the rest of rho1 is their conjugate transpose.  A CTA owns one tile and a
+// range of (realization, particle) pairs, and its warps have three roles:
+//  - warps 0-7 (producers) load 16 k at a time of the tile's 128 + 128 rows,
+//    split them into the four TF32 arrays re_hi, re_lo, im_hi, im_lo and
+//    store them into a three-stage shared-memory ring in the MMA's
+//    canonical K-major layout (8-row by 16-byte core matrices);
+//  - one thread of warp 8 issues 12 MMAs per 8 k (M = 128, N = 128, K = 8,
+//    FP32 accumulate in TMEM: 128 columns for Re, 128 for Im) and commits
+//    them to the stage's mbarrier, which hands the stage back;
+//  - warps 9-12 drain: every 256 k the MMAs switch to the other of two TMEM
+//    accumulators, and the drain warps add the finished FP32 partials into
+//    the CTA's running totals, kept as two FP32 words (TwoSum) in a global
+//    slot of its own, so the totals carry ~2^-44 of relative rounding.
+// A second kernel sums the slots of all CTAs in FP64 and fills the lower
+// triangle.  Every wait is bounded in time (status word, then the CTA stops).
 #include <cstdint>
 
 #include "ctqw_internal.cuh"
@@ -39,7 +43,7 @@ constexpr int kMmaWarp = kProducerWarps;           // warp 8 issues the MMAs; wa
 constexpr int kThreads = 32 * (kProducerWarps + 1 + 4);
 constexpr int kArr = kM * kKc;   // floats per operand array of a stage
 constexpr int kBlockK = 256;     // k accumulated in TMEM between two drains
-constexpr long kWaitIters = 1L << 26;
+constexpr uint64_t kWaitNs = 2000000000ull;   // bound of every wait (2 s)
 
 struct TcArgs {
     RealTable tab;
@@ -74,18 +78,36 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
                  ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
 }
 
-// Bounded wait for the phase of parity `parity` to complete; false after
-// kWaitIters tries or once another role has raised `stop`.
-__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, const volatile int *stop) {
-    for (long it = 0; it < kWaitIters; ++it) {
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase of parity `parity` to complete: false after
+// kWaitNs nanoseconds or once another role has raised `stop`.  Each try may
+// suspend the thread for up to hint_ns (0: the hardware's default), so that
+// idle roles do not spin on the barrier.
+__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity, const volatile int *stop,
+                                          uint32_t hint_ns = 0) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
         uint32_t done;
-        asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, q;\n\t}"
-                     : "=r"(done) : "r"(mb), "r"(parity) : "memory");
+        if (hint_ns)
+            asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, %3;\n\t"
+                         "selp.u32 %0, 1, 0, q;\n\t}"
+                         : "=r"(done) : "r"(mb), "r"(parity), "r"(hint_ns) : "memory");
+        else
+            asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
+                         "selp.u32 %0, 1, 0, q;\n\t}"
+                         : "=r"(done) : "r"(mb), "r"(parity) : "memory");
         if (done) return true;
-        if ((it & 1023) == 1023 && *stop) return false;
+        if ((it & 63) == 0) {
+            const uint64_t t = global_ns();
+            if (it == 0) t0 = t;
+            else if (t - t0 > kWaitNs || *stop) return false;
+        }
     }
-    return false;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mb) {
@@ -273,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1) rho1_tc_kernel(const __grid_const
             const int s = (int)(c % kStages);
             const int64_t use = c / kStages;
             // the slot's previous MMAs (chunk c - kStages) must be done
-            if (use > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((use - 1) & 1), vstop)) {
+            if (use > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((use - 1) & 1), vstop, 500)) {
                 if (lane == 0) atomicOr(a.status, 4);
                 stop = 1;
                 return false;
@@ -380,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1) rho1_tc_kernel(const __grid_const
         const int quarter = warp & 3, row = 32 * quarter + lane;
         for (int64_t bi = 0; bi < n_blocks; ++bi) {
             const int acc = (int)(bi & 1);
-            if (!mbar_wait(smem_u32(&acc_full[acc]), (uint32_t)((bi >> 1) & 1), vstop)) {
+            if (!mbar_wait(smem_u32(&acc_full[acc]), (uint32_t)((bi >> 1) & 1), vstop, 2000)) {
                 if (lane == 0) atomicOr(a.status, 4);
                 stop = 1;
                 break;
