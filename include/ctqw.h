@@ -324,7 +324,9 @@ int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, 
  * allocates a scratch of 256 KB per CTA stream-ordered).  Otherwise products
  * in the state's type over chunks of 32 (16 in FP64), accumulated in FP64,
  * on CUDA cores.  m = 2 or 3.  Asynchronous.  Errors: EINVAL for null
- * pointers or a bad dtype, ENOMEM, ECUDA.
+ * pointers or a bad dtype, ENOMEM, ECUDA.  A wait of the tensor-core
+ * kernel that exceeds 2 s stops it and is reported by ctqw_check_status
+ * (CTQW_ETIMEOUT).
  */
 int ctqw_one_body_density(const ctqw_hamiltonian *h, int32_t dtype, const void *psi_dev,
                           double *rho_dev, void *stream);
