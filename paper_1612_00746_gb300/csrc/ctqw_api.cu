@@ -121,12 +121,14 @@ int taylor_step_plain(const ctqw_hamiltonian *h, int dtype, const void *in, void
 struct AdjointLayout {
     int64_t n_ck = 0;
     size_t state = 0, total = 0;
-    size_t off_ck = 0, off_seg = 0, off_phi = 0, off_misc = 0, off_dbl = 0, off_grad = 0;
+    size_t off_ck = 0, off_seg = 0, off_phi = 0, off_misc = 0, off_dbl = 0, off_grad = 0, off_tg = 0;
+    bool tiled = false;   // the register-tile adjoint (c64, two particles)
 };
 
 // Workspace: checkpoints every M steps, one segment of M replayed states,
-// phi_1..phi_{K-1}, 8 scratch states, then Pbar and diff (FP64) and the
-// per-realization gradients (FP64) for calls that want only the sums.
+// phi_1..phi_{K-1}, 8 scratch states, then Pbar and diff (FP64), the
+// per-realization gradients (FP64) for calls that want only the sums, and
+// on the register-tile path the per-tile gradient slots (FP64).
 AdjointLayout adjoint_layout(const ctqw_hamiltonian *h, int dtype, int K, int64_t n_steps, int M) {
     AdjointLayout L;
     L.state = (size_t)h->total_amp * elem_bytes(dtype);
@@ -137,7 +139,9 @@ AdjointLayout adjoint_layout(const ctqw_hamiltonian *h, int dtype, int K, int64_
     L.off_misc = L.off_phi + (size_t)(K > 1 ? K - 1 : 0) * L.state;
     L.off_dbl = L.off_misc + 8 * L.state;
     L.off_grad = L.off_dbl + 2 * sizeof(double) * (size_t)h->p_width;
-    L.total = L.off_grad + 2 * sizeof(double) * (size_t)h->total_par;
+    L.off_tg = L.off_grad + 2 * sizeof(double) * (size_t)h->total_par;
+    L.tiled = adjoint_tiled_supported(h, dtype, K);
+    L.total = L.off_tg + (L.tiled ? sizeof(double) * adjoint_tiled_slots(h, K) : 0);
     return L;
 }
 
@@ -995,6 +999,8 @@ int ctqw_adjoint_grad(const ctqw_hamiltonian *h, int32_t dtype, const void *psi0
     CTQW_CUDA_TRY(cudaMemsetAsync(grad_eps_dev, 0, sizeof(double) * h->total_par, s));
     CTQW_CUDA_TRY(cudaMemsetAsync(grad_J_dev, 0, sizeof(double) * h->total_par, s));
     CTQW_CUDA_TRY(cudaMemsetAsync(Pbar, 0, sizeof(double) * h->p_width, s));
+    double *tg = (double *)(ws + L.off_tg);
+    if (L.tiled) CTQW_CUDA_TRY(cudaMemsetAsync(tg, 0, L.total - L.off_tg, s));
 
     // forward pass with checkpoints psi_{cM}
     CTQW_CUDA_TRY(cudaMemcpyAsync(X, psi0_dev, L.state, cudaMemcpyDeviceToDevice, s));
@@ -1030,19 +1036,36 @@ int ctqw_adjoint_grad(const ctqw_hamiltonian *h, int32_t dtype, const void *psi0
             CTQW_TRY(taylor_step_plain(h, dtype, k == 1 ? ck(c) : seg(k - 1), seg(k), tA, tB, dt, K, s));
         for (int64_t n = n1 - 1; n >= n0; --n) {
             const void *psi_n = (n == n0) ? ck(c) : seg(n - n0);
+            if (L.tiled) {
+                void *levels[32];
+                levels[0] = const_cast<void *>(psi_n);
+                for (int a = 1; a < K; ++a) levels[a] = phi(a);
+                CTQW_TRY(launch_adjoint_phi_chain(h, K, dt, levels, s));
+                CTQW_TRY(launch_adjoint_mu_chain(h, K, dt, lam, levels, lam2, muA, muB, tg, s));
+                std::swap(lam, lam2);
+                continue;
+            }
             for (int a = 1; a < K; ++a) CTQW_TRY(launch_apply_h(h, dtype, a == 1 ? psi_n : phi(a - 1), phi(a), s));
             // mu_{K-1} = conj(c_K) lambda;  mu_a = conj(c_{a+1}) lambda + H mu_{a+1}
             void *mu = muA, *mu_prev = muB;
             for (int a = K - 1; a >= 0; --a) {
-                CTQW_TRY(launch_mu(h, dtype, mu_prev, lam, mu, cre[a + 1], cim[a + 1], a == K - 1, s));
-                CTQW_TRY(launch_grad(h, dtype, mu, a == 0 ? psi_n : phi(a), grad_eps_dev, grad_J_dev, s));
+                const void *phi_a = a == 0 ? psi_n : phi(a);
+                if (dtype == CTQW_C64 && h->m == 2) {
+                    CTQW_TRY(launch_mu_grad(h, mu_prev, lam, phi_a, mu, cre[a + 1], cim[a + 1], a == K - 1,
+                                            grad_eps_dev, grad_J_dev, s));
+                } else {
+                    CTQW_TRY(launch_mu(h, dtype, mu_prev, lam, mu, cre[a + 1], cim[a + 1], a == K - 1, s));
+                    CTQW_TRY(launch_grad(h, dtype, mu, phi_a, grad_eps_dev, grad_J_dev, s));
+                }
                 std::swap(mu, mu_prev);
             }
-            // lambda_n = T^dagger lambda_{n+1} (the Taylor polynomial of exp(+i H dt))
-            CTQW_TRY(taylor_step_plain(h, dtype, lam, lam2, tA, tB, -dt, K, s));
+            // lambda_n = T^dagger lambda_{n+1} = sum_k conj(c_k) H^k lambda_{n+1}
+            //          = lambda_{n+1} + H mu_0, mu_0 = sum_{b<K} conj(c_{b+1}) H^b lambda_{n+1}
+            CTQW_TRY(launch_mu(h, dtype, mu_prev, lam, lam2, 1.0, 0.0, 0, s));
             std::swap(lam, lam2);
         }
     }
+    if (L.tiled) CTQW_TRY(launch_adjoint_tile_reduce(h, K, dt, tg, grad_eps_dev, grad_J_dev, s));
     // gradients with respect to the means shared by a size group: sums over
     // its realizations, in FP64 and a fixed order
     if (grad_eps_mean_dev) CTQW_TRY(launch_group_sum(h, grad_eps_dev, grad_eps_mean_dev, s));

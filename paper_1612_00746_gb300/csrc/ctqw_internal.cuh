@@ -204,6 +204,21 @@ int launch_exact_propagate(const ctqw_hamiltonian *h, const double *evals, const
 int launch_apply_h(const ctqw_hamiltonian *h, int dtype, const void *in, void *out, cudaStream_t s);
 int launch_mu(const ctqw_hamiltonian *h, int dtype, const void *in, const void *lam, void *out,
               double cre, double cim, int first, cudaStream_t s);
+// Adjoint on register tiles (c64, two particles; k_adjoint_tiled.cu): the
+// phi chain phi_a = (dt H)^a psi into levels[1..K-1] (levels[0] = psi), the
+// mu chain with the gradient contraction into per-tile FP64 slots and
+// lambda_n into lam_out, and the sum of the slots into the gradients.
+bool adjoint_tiled_supported(const ctqw_hamiltonian *h, int dtype, int K);
+size_t adjoint_tiled_slots(const ctqw_hamiltonian *h, int K);
+int launch_adjoint_phi_chain(const ctqw_hamiltonian *h, int K, double dt, void *const *levels, cudaStream_t s);
+int launch_adjoint_mu_chain(const ctqw_hamiltonian *h, int K, double dt, const void *lam, void *const *levels,
+                            void *lam_out, void *bufA, void *bufB, double *tg, cudaStream_t s);
+int launch_adjoint_tile_reduce(const ctqw_hamiltonian *h, int K, double dt, const double *tg, double *grad_eps,
+                               double *grad_J, cudaStream_t s);
+// mu_a = conj(c_{a+1}) lam + H mu_{a+1} and its gradient contribution in one
+// sweep (c64, two particles).
+int launch_mu_grad(const ctqw_hamiltonian *h, const void *mu_in, const void *lam, const void *phi, void *mu_out,
+                   double cre, double cim, int first, double *grad_eps, double *grad_J, cudaStream_t s);
 int launch_grad(const ctqw_hamiltonian *h, int dtype, const void *mu, const void *phi,
                 double *grad_eps, double *grad_J, cudaStream_t s);
 int launch_loss(const double *Pbar, const double *target, int64_t n, double *diff, double *loss,

@@ -1,0 +1,571 @@
+// Adjoint gradient on register tiles: two particles, complex FP32 states.
+//
+// The gradient of Sec. 2.3's Taylor step T = sum_{k<=K} c_k H^k,
+// c_k = (-i dt)^k / k!, with respect to a parameter theta of H is
+//   2 Re <lambda_{n+1}, dT/dtheta psi_n> = 2 Re sum_{a<K} <mu_a, dH/dtheta H^a psi_n>,
+//   mu_a = sum_{b<K-a} conj(c_{a+b+1}) H^b lambda_{n+1}.
+// In the scaled variables of the dt-weighted stencil Hh = dt H,
+//   phi_a = Hh^a psi_n,   mu_a = sum_b (i^(a+b+1) / (a+b+1)!) Hh^b lambda_{n+1},
+// the sum reads dt sum_a 2 Re <mu_a, dH/dtheta phi_a>, with
+//   mu_{K-1} = (i^K / K!) lambda,  mu_a = (i^(a+1) / (a+1)!) lambda + Hh mu_{a+1},
+// and the next adjoint state is lambda_n = T^dagger lambda_{n+1} = lambda + Hh mu_0
+// (the same recurrence one level further, with coefficient i^0 / 0! = 1).
+// Every term stays O(1) in FP32, where the unscaled H^a grows like |H|^a.
+//
+// Two kernels on the register tiles of the forward Taylor kernel (an 8W x 64
+// region per block, 8 rows per warp, 2 adjacent columns per lane, D stages
+// per launch with a D-deep halo):
+//  - the phi chain applies Hh D times per launch and stores every level's
+//    tile;
+//  - the mu chain runs the recurrence from a = K-1 down to -1 with lambda
+//    of the region in shared memory, and at every level a >= 0 contracts mu_a
+//    with phi_a (read from the stored levels, psi_n for a = 0) at the tile's
+//    points.  dH/deps_i counts the particles on site i; dH/dJ_b is minus the
+//    hop across bond b = (b, b+1): a bond collects conj(mu(x)) phi(x') from
+//    both of its end points, so a point needs its own mu and phi at its four
+//    neighbours.  Each lane sums its rows' and columns' terms over the
+//    launch's levels in FP32; at the end of the launch a warp sums its rows
+//    and the block its columns, and adds them in FP64 to per-tile slots (one
+//    owner per slot: no atomics, a fixed order).  A last kernel sums the
+//    slots over the tiles into the per-realization gradients.
+// HBM per step: the phi chain reads psi and writes K-1 levels; the mu chain
+// reads lambda, the K-1 levels and psi, and writes lambda_n: about 16 K
+// bytes per amplitude, against about 56 K for one sweep per level and term.
+#include "ctqw_internal.cuh"
+#include "fused_common.cuh"
+
+namespace {
+
+using namespace fused;
+
+constexpr int kMaxLevels = 31;
+
+struct ChainArgs {
+    RealTable tab;
+    const int32_t *list;              // the group's realizations
+    const float *eps, *J;             // float32 parameters (packed per realization)
+    const float2 *in;                 // input level on the region (null: the mu chain's first level)
+    const float2 *q;                  // mu chain: lambda_{n+1}
+    float2 *out;                      // last level of the launch (tile); lambda_n when final
+    float2 *lev[kMaxLevels];          // phi_a (a = 0: psi_n): written by the phi chain, read by the mu chain
+    float2 co[kMaxLevels + 1];        // i^k / k!
+    double *tg;                       // per-tile gradient slots of the group
+    int64_t tg_per_real;              // doubles per realization
+    int tiles_x;                      // tiles along x2
+    float dt, dtU;
+    int a_in;                         // level of the launch's initial iterate
+    int n_stages;                     // stencil stages of the launch
+    int init;                         // mu chain: the initial iterate is (i^K / K!) lambda
+    int final;                        // mu chain: the last stage is level -1 (lambda_n)
+};
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ float dotf(float2 u, float2 p) { return fmaf(u.x, p.x, u.y * p.y); }
+
+// 32 values summed over the warp: lane l returns the total of value l
+// (the FP32 counterpart of warp_sum_multi_d<32>).
+__device__ __forceinline__ float warp_sum32_f(float (&v)[32], int lane) {
+#pragma unroll
+    for (int o = 16, n = 32; n > 1; o >>= 1, n >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int q = 0; q < n / 2; ++q) {
+            const float send = upper ? v[q] : v[q + n / 2];
+            const float keep = upper ? v[q + n / 2] : v[q];
+            v[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
+// MU = false: the phi chain; MU = true: the mu chain with the contraction.
+template <int D, int W, bool MU>
+__global__ void __launch_bounds__(32 * W, MU ? 2 : 3) adj_chain_kernel(const __grid_constant__ ChainArgs a) {
+    constexpr int RS = 8 * W, T = RS - 2 * D, T2 = 64 - 2 * D, RL = 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *Q = reinterpret_cast<float4 *>(smem_raw);            // mu chain: [RS][32] lambda, (row, lane) -> 2 columns
+    float4 *edge = Q + (MU ? RS * 32 : 0);                        // [2 parity][W warps][2][32]
+    float4 *zero = edge + 2 * W * 2 * 32;                         // [32] a row of zeros
+    float4 *rowc = zero + 32;                                     // [RS + 1] (dt eps, dt eps, -dt J_up, -dt J_up)
+    int *x_row = reinterpret_cast<int *>(rowc + RS + 1);          // [RS]
+    float *colsum = reinterpret_cast<float *>(x_row + RS);        // mu chain: [W][64][3]
+    float4 *phs = reinterpret_cast<float4 *>(colsum + (MU ? W * 64 * 3 : 0));   // mu chain: [2][T + 2][32] phi
+
+    const int r = a.list[blockIdx.z];
+    const int N = a.tab.N[r];
+    const int x1_0 = (int)blockIdx.y * T - D, x2_0 = (int)blockIdx.x * T2 - D;
+    const int64_t base = a.tab.st_off[r];
+    const int64_t po = a.tab.par_off[r];
+    const float dt = a.dt;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = warp * RL;
+
+    for (int i = threadIdx.x; i <= RS; i += blockDim.x) {
+        const int X1 = ((x1_0 + i) % N + N) % N;
+        if (i < RS) x_row[i] = X1;
+        const float e = i < RS ? dt * a.eps[po + X1] : 0.f;
+        const float j = -dt * a.J[po + (X1 + N - 1) % N];
+        rowc[i] = make_float4(e, e, j, j);
+    }
+    if (threadIdx.x < 32) zero[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int X2[2];
+    float2 ec[2], nJc[3];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        X2[k] = ((x2_0 + 2 * lane + k) % N + N) % N;
+        const float v = dt * a.eps[po + X2[k]];
+        ec[k] = make_float2(v, v);
+    }
+#pragma unroll
+    for (int k = 0; k <= 2; ++k) {
+        const int X = ((x2_0 + 2 * lane + k - 1) % N + N) % N;   // bond left of column 2 lane + k
+        const float v = -dt * a.J[po + X];
+        nJc[k] = make_float2(v, v);
+    }
+    __syncthreads();
+
+    // the tile's points among this lane's: rows D .. D + T - 1 and columns
+    // D .. D + T2 - 1 of the region that lie inside the lattice
+    bool col_in[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int ck = 2 * lane + k;
+        col_in[k] = ck >= D && ck < D + T2 && x2_0 + ck < N;
+    }
+    auto row_in = [&](int ri) { return ri >= D && ri < D + T && x1_0 + ri < N; };
+
+    float2 P[RL][2];
+    if (MU) {
+        // lambda of the region into shared memory
+        const float2 *gq = a.q + base;
+        const uint32_t sQ = smem_u32(Q);
+        for (int i = warp; i < RS; i += W) {
+            const int64_t grow = (int64_t)x_row[i] * N;
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sQ + (uint32_t)((i * 32 + lane) * 16 + 8 * k)),
+                             "l"(gq + grow + X2[k])
+                             : "memory");
+        }
+    }
+    if (!MU || !a.init) {
+        const float2 *win = a.in + base;
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            const int64_t grow = (int64_t)x_row[r0 + i] * N;
+            P[i][0] = win[grow + X2[0]];
+            P[i][1] = win[grow + X2[1]];
+        }
+    }
+    if (MU) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+    }
+
+    // mu chain: per-lane sums of the contraction over the launch's levels
+    // (row i: eps, bond below, bond above; column k: eps, bond right, bond left)
+    float racc[RL][3], cacc[2][3];
+#pragma unroll
+    for (int i = 0; i < RL; ++i) racc[i][0] = racc[i][1] = racc[i][2] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) cacc[k][0] = cacc[k][1] = cacc[k][2] = 0.f;
+
+    // phi of the contraction levels through a two-buffer shared-memory ring
+    // (cp.async, rows D - 1 .. D + T of the region, all 64 columns), one
+    // level ahead of its use; the levels run from first_lev down to 0
+    const int first_lev = a.init ? a.a_in : a.a_in - 1;
+    const int last_lev = max(0, a.a_in - a.n_stages);
+    const uint32_t sP = smem_u32(phs);
+    auto prefetch = [&](int lev, int buf) {
+        if (MU && lev >= last_lev && lev <= first_lev) {
+            const float2 *ph = a.lev[lev] + base;
+            for (int i = warp; i < T + 2; i += W) {
+                const int64_t grow = (int64_t)x_row[D - 1 + i] * N;
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
+                                 ::"r"(sP + (uint32_t)(((buf * (T + 2) + i) * 32 + lane) * 16 + 8 * k)),
+                                 "l"(ph + grow + X2[k])
+                                 : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // the contraction of mu_lev (in P) with phi_lev on the tile's points
+    auto contract = [&](int lev) {
+        const int buf = (first_lev - lev) & 1;
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        __syncthreads();
+        const float4 *pb = phs + buf * (T + 2) * 32;
+        const float2 *pb2 = reinterpret_cast<const float2 *>(pb);
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            const int ri = r0 + i;
+            if (!row_in(ri)) continue;
+            const int sr = ri - (D - 1);   // the ring's row of region row ri
+            const float4 c4 = pb[sr * 32 + lane], u4 = pb[(sr - 1) * 32 + lane], d4 = pb[(sr + 1) * 32 + lane];
+            const float2 c[2] = {make_float2(c4.x, c4.y), make_float2(c4.z, c4.w)};
+            const float2 up[2] = {make_float2(u4.x, u4.y), make_float2(u4.z, u4.w)};
+            const float2 dn[2] = {make_float2(d4.x, d4.y), make_float2(d4.z, d4.w)};
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (!col_in[k]) continue;
+                // columns 2 lane - 1 and 2 lane + 2 lie in the region for a tile column
+                const float2 pl = k ? c[0] : pb2[sr * 64 + 2 * lane - 1];
+                const float2 pr = k ? pb2[sr * 64 + 2 * lane + 2] : c[1];
+                const float2 u = P[i][k];
+                const float d = dotf(u, c[k]);
+                racc[i][0] += d;
+                racc[i][1] += dotf(u, dn[k]);
+                racc[i][2] += dotf(u, up[k]);
+                cacc[k][0] += d;
+                cacc[k][1] += dotf(u, pr);
+                cacc[k][2] += dotf(u, pl);
+            }
+        }
+        __syncthreads();
+        prefetch(lev - 2, buf);
+    };
+    prefetch(first_lev, 0);
+    prefetch(first_lev - 1, 1);
+
+    if (MU && a.init) {
+        const float2 co = a.co[a.a_in + 1];
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            const float4 q = Q[(r0 + i) * 32 + lane];
+            P[i][0] = cmulf(co, make_float2(q.x, q.y));
+            P[i][1] = cmulf(co, make_float2(q.z, q.w));
+        }
+        contract(a.a_in);
+    }
+
+    const float2 dU = make_float2(a.dtU, a.dtU);
+    const int from_left = (lane + 31) & 31, from_right = (lane + 1) & 31;
+#pragma unroll 1
+    for (int d = 1; d <= a.n_stages; ++d) {
+        const int par = d & 1;
+        const int lev = MU ? a.a_in - d : a.a_in + d;   // the level this stage forms
+        // publish this warp's first and last rows
+        float4 *eb = edge + (par * W + warp) * 2 * 32;
+        eb[lane] = make_float4(P[0][0].x, P[0][0].y, P[0][1].x, P[0][1].y);
+        eb[32 + lane] = make_float4(P[RL - 1][0].x, P[RL - 1][0].y, P[RL - 1][1].x, P[RL - 1][1].y);
+        __syncthreads();
+        const float4 u4 = warp > 0 ? edge[(par * W + warp - 1) * 2 * 32 + 32 + lane] : zero[lane];
+        const float4 d4 = warp < W - 1 ? edge[(par * W + warp + 1) * 2 * 32 + lane] : zero[lane];
+        float2 prev[2] = {make_float2(u4.x, u4.y), make_float2(u4.z, u4.w)};
+        float4 rc = rowc[r0];
+        const float2 co = MU ? a.co[lev + 1] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            const float2 c0 = P[i][0], c1 = P[i][1];
+            const float2 lft = shfl2(c1, from_left), rgt = shfl2(c0, from_right);
+            const float2 n0 = i < RL - 1 ? P[i + 1][0] : make_float2(d4.x, d4.y);
+            const float2 n1 = i < RL - 1 ? P[i + 1][1] : make_float2(d4.z, d4.w);
+            const float4 rn = rowc[r0 + i + 1];
+            const float2 er = make_float2(rc.x, rc.y), jup = make_float2(rc.z, rc.w), jdn = make_float2(rn.z, rn.w);
+            rc = rn;
+            // y = Hh P: the diagonal (column and row eps), the bonds above and
+            // below, left and right, and dt U where x1 = x2
+            float2 y0 = __fmul2_rn(ec[0], c0), y1 = __fmul2_rn(ec[1], c1);
+            y0 = __ffma2_rn(er, c0, y0);
+            y1 = __ffma2_rn(er, c1, y1);
+            y0 = __ffma2_rn(jup, prev[0], y0);
+            y1 = __ffma2_rn(jup, prev[1], y1);
+            y0 = __ffma2_rn(jdn, n0, y0);
+            y1 = __ffma2_rn(jdn, n1, y1);
+            y0 = __ffma2_rn(nJc[0], lft, y0);
+            y1 = __ffma2_rn(nJc[1], c0, y1);
+            y0 = __ffma2_rn(nJc[1], c1, y0);
+            y1 = __ffma2_rn(nJc[2], rgt, y1);
+            const int X1w = x_row[r0 + i];
+            if (X1w == X2[0]) y0 = __ffma2_rn(dU, c0, y0);
+            if (X1w == X2[1]) y1 = __ffma2_rn(dU, c1, y1);
+            prev[0] = c0;
+            prev[1] = c1;
+            if (MU) {
+                const float4 q = Q[(r0 + i) * 32 + lane];
+                const float2 q0 = cmulf(co, make_float2(q.x, q.y)), q1 = cmulf(co, make_float2(q.z, q.w));
+                P[i][0] = make_float2(q0.x + y0.x, q0.y + y0.y);
+                P[i][1] = make_float2(q1.x + y1.x, q1.y + y1.y);
+            } else {
+                P[i][0] = y0;
+                P[i][1] = y1;
+            }
+        }
+        const bool last = d == a.n_stages;
+        if (!MU || (a.final && last)) {
+            // the phi level, or lambda_n, on the tile
+            float2 *dst = MU ? a.out + base : a.lev[lev] + base;
+#pragma unroll
+            for (int i = 0; i < RL; ++i) {
+                const int ri = r0 + i;
+                if (!row_in(ri)) continue;
+                const int64_t grow = (int64_t)x_row[ri] * N;
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    if (col_in[k]) dst[grow + X2[k]] = P[i][k];
+            }
+        }
+        if (MU && lev >= 0) contract(lev);
+    }
+    if (MU && !a.final) {
+        // the tile of the launch's last level
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            const int ri = r0 + i;
+            if (!row_in(ri)) continue;
+            const int64_t grow = base + (int64_t)x_row[ri] * N;
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+                if (col_in[k]) a.out[grow + X2[k]] = P[i][k];
+        }
+    }
+    if (MU) {
+        // rows: the warp's 8 rows x 3 sums over its 64 columns, value 4 i + q
+        // in lane 4 i + q; then into the tile's FP64 slots (tile column index)
+        double *tg = a.tg + (int64_t)blockIdx.z * a.tg_per_real;
+        float v[32];
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            v[4 * i] = racc[i][0];
+            v[4 * i + 1] = racc[i][1];
+            v[4 * i + 2] = racc[i][2];
+            v[4 * i + 3] = 0.f;
+        }
+        const float tot = warp_sum32_f(v, lane);
+        {
+            const int i = lane >> 2, q = lane & 3, ri = r0 + i;
+            if (q < 3 && row_in(ri)) {
+                double *slot = tg + ((int64_t)blockIdx.x * N + (x1_0 + ri)) * 3 + q;
+                *slot += (double)tot;
+            }
+        }
+        // columns: over the warps through shared memory, then into the tile's
+        // FP64 slots (tile row index)
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) colsum[(warp * 64 + 2 * lane + k) * 3 + q] = cacc[k][q];
+        __syncthreads();
+        for (int t = threadIdx.x; t < 64 * 3; t += blockDim.x) {
+            const int ck = t / 3, q = t - 3 * (t / 3);
+            if (ck < D || ck >= D + T2 || x2_0 + ck >= N) continue;
+            float s = 0.f;
+#pragma unroll
+            for (int w = 0; w < W; ++w) s += colsum[(w * 64 + ck) * 3 + q];
+            double *slot = tg + (int64_t)a.tiles_x * N * 3 + ((int64_t)blockIdx.y * N + (x2_0 + ck)) * 3 + q;
+            *slot += (double)s;
+        }
+    }
+}
+
+// The per-tile slots of a size group summed over the tiles into the
+// per-realization gradients: eps_x from the row and column sums at site x,
+// J_b from the bond-below sum of row b and the bond-above sum of row b + 1
+// (and the same along x2), scaled by 2 dt (eps) and -2 dt (J).  A bond N - 1
+// exists on a ring only.
+__global__ void __launch_bounds__(256) adj_tile_reduce_kernel(RealTable tab, const int32_t *__restrict__ list,
+                                                              const double *__restrict__ tg, int64_t per,
+                                                              int tiles_x, int tiles_y, double dt,
+                                                              double *grad_eps, double *grad_J) {
+    const int z = blockIdx.y;
+    const int r = list[z];
+    const int N = tab.N[r];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    const double *g = tg + (int64_t)z * per;
+    const double *gc = g + (int64_t)tiles_x * N * 3;
+    const int xp = (x + 1 == N) ? 0 : x + 1;
+    double e = 0.0, j = 0.0;
+    for (int t = 0; t < tiles_x; ++t) {
+        e += g[((int64_t)t * N + x) * 3];
+        j += g[((int64_t)t * N + x) * 3 + 1] + g[((int64_t)t * N + xp) * 3 + 2];
+    }
+    for (int t = 0; t < tiles_y; ++t) {
+        e += gc[((int64_t)t * N + x) * 3];
+        j += gc[((int64_t)t * N + x) * 3 + 1] + gc[((int64_t)t * N + xp) * 3 + 2];
+    }
+    const int64_t po = tab.par_off[r];
+    grad_eps[po + x] += 2.0 * dt * e;
+    if (tab.periodic || x < N - 1) grad_J[po + x] += -2.0 * dt * j;
+}
+
+using ChainKernel = void (*)(ChainArgs);
+
+struct ChainShape {
+    int D, T, T2, threads;
+    ChainKernel phi, mu;
+    size_t smem_phi, smem_mu;
+};
+
+template <int D, int W = 8>
+ChainShape chain_shape() {
+    constexpr int RS = 8 * W;
+    ChainShape s;
+    s.D = D;
+    s.T = RS - 2 * D;
+    s.T2 = 64 - 2 * D;
+    s.threads = 32 * W;
+    s.phi = adj_chain_kernel<D, W, false>;
+    s.mu = adj_chain_kernel<D, W, true>;
+    s.smem_phi = sizeof(float4) * (2 * W * 2 * 32 + 32 + RS + 1) + sizeof(int) * RS;
+    s.smem_mu = s.smem_phi + sizeof(float4) * RS * 32 + sizeof(float) * W * 64 * 3 +
+                sizeof(float4) * 2 * (s.T + 2) * 32;
+    return s;
+}
+
+// Depth for K levels: the fewest launches at depth <= 8, the levels split
+// evenly, rounded up to a compiled depth.
+ChainShape chain_shape_for(int K) {
+    const int launches = (K + 7) / 8;
+    const int need = (K + launches - 1) / launches;
+    if (need <= 4) return chain_shape<4>();
+    if (need <= 6) return chain_shape<6>();
+    if (need <= 7) return chain_shape<7>();
+    return chain_shape<8>();
+}
+
+ChainArgs chain_args(const ctqw_hamiltonian *h, double dt) {
+    ChainArgs a;
+    a.tab = real_table(h);
+    a.eps = h->eps32;
+    a.J = h->J32;
+    a.in = nullptr;
+    a.q = nullptr;
+    a.out = nullptr;
+    for (int i = 0; i < kMaxLevels; ++i) a.lev[i] = nullptr;
+    // i^k / k!
+    double mag = 1.0;
+    for (int k = 0; k <= kMaxLevels; ++k) {
+        if (k > 0) mag /= k;
+        const int q = k & 3;
+        a.co[k] = make_float2((float)(q == 0 ? mag : (q == 2 ? -mag : 0.0)),
+                              (float)(q == 1 ? mag : (q == 3 ? -mag : 0.0)));
+    }
+    a.tg = nullptr;
+    a.tg_per_real = 0;
+    a.tiles_x = 0;
+    a.dt = (float)dt;
+    a.dtU = (float)(dt * h->U);
+    a.a_in = 0;
+    a.n_stages = 0;
+    a.init = 0;
+    a.final = 0;
+    return a;
+}
+
+}  // namespace
+
+bool adjoint_tiled_supported(const ctqw_hamiltonian *h, int dtype, int K) {
+    return dtype == CTQW_C64 && h->m == 2 && K >= 1 && K < kMaxLevels;
+}
+
+size_t adjoint_tiled_slots(const ctqw_hamiltonian *h, int K) {
+    const ChainShape f = chain_shape_for(K);
+    size_t n = 0;
+    for (size_t g = 0; g < h->group_N.size(); ++g) {
+        const int N = h->group_N[g];
+        const int tx = (N + f.T2 - 1) / f.T2, ty = (N + f.T - 1) / f.T;
+        n += (size_t)h->group_count[g] * (size_t)(tx + ty) * (size_t)N * 3;
+    }
+    return n;
+}
+
+// phi_a = Hh^a psi for a = 1 .. K - 1 into levels[a] (levels[0] = psi).
+int launch_adjoint_phi_chain(const ctqw_hamiltonian *h, int K, double dt, void *const *levels, cudaStream_t s) {
+    const ChainShape f = chain_shape_for(K);
+    CTQW_CUDA_TRY(cudaFuncSetAttribute((const void *)f.phi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)f.smem_phi));
+    ChainArgs a = chain_args(h, dt);
+    for (int i = 0; i < K; ++i) a.lev[i] = (float2 *)levels[i];
+    for (int a0 = 0; a0 < K - 1;) {
+        const int n = std::min(f.D, K - 1 - a0);
+        a.in = (const float2 *)levels[a0];
+        a.a_in = a0;
+        a.n_stages = n;
+        int off = 0;
+        for (size_t g = 0; g < h->group_N.size(); ++g) {
+            const int N = h->group_N[g], cnt = h->group_count[g];
+            a.list = h->by_group_d + off;
+            const dim3 grid((unsigned)((N + f.T2 - 1) / f.T2), (unsigned)((N + f.T - 1) / f.T), (unsigned)cnt);
+            f.phi<<<grid, f.threads, f.smem_phi, s>>>(a);
+            CTQW_CUDA_TRY(cudaGetLastError());
+            off += cnt;
+        }
+        a0 += n;
+    }
+    return CTQW_OK;
+}
+
+// The mu recurrence from level K - 1 down to -1 with the contraction against
+// levels[a] at every a >= 0, accumulated into the tile slots tg, and
+// lambda_n = T^dagger lambda into lam_out (bufA, bufB: two state-sized
+// buffers for the levels between launches).
+int launch_adjoint_mu_chain(const ctqw_hamiltonian *h, int K, double dt, const void *lam, void *const *levels,
+                            void *lam_out, void *bufA, void *bufB, double *tg, cudaStream_t s) {
+    const ChainShape f = chain_shape_for(K);
+    CTQW_CUDA_TRY(cudaFuncSetAttribute((const void *)f.mu, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)f.smem_mu));
+    ChainArgs a = chain_args(h, dt);
+    for (int i = 0; i < K; ++i) a.lev[i] = (float2 *)levels[i];
+    a.q = (const float2 *)lam;
+    void *bufs[2] = {bufA, bufB};
+    int nb = 0, a_in = K - 1, remaining = K;
+    bool init = true;
+    const void *in = nullptr;
+    while (remaining > 0) {
+        const int n = std::min(f.D, remaining);
+        const bool final = n == remaining;
+        void *out = final ? lam_out : bufs[nb];
+        a.in = (const float2 *)in;
+        a.out = (float2 *)out;
+        a.a_in = a_in;
+        a.n_stages = n;
+        a.init = init ? 1 : 0;
+        a.final = final ? 1 : 0;
+        int off = 0;
+        double *tgg = tg;
+        for (size_t g = 0; g < h->group_N.size(); ++g) {
+            const int N = h->group_N[g], cnt = h->group_count[g];
+            const int tx = (N + f.T2 - 1) / f.T2, ty = (N + f.T - 1) / f.T;
+            a.list = h->by_group_d + off;
+            a.tg = tgg;
+            a.tg_per_real = (int64_t)(tx + ty) * N * 3;
+            a.tiles_x = tx;
+            f.mu<<<dim3((unsigned)tx, (unsigned)ty, (unsigned)cnt), f.threads, f.smem_mu, s>>>(a);
+            CTQW_CUDA_TRY(cudaGetLastError());
+            off += cnt;
+            tgg += (size_t)cnt * a.tg_per_real;
+        }
+        in = out;
+        nb ^= 1;
+        a_in -= n;
+        init = false;
+        remaining -= n;
+    }
+    return CTQW_OK;
+}
+
+// The tile slots into the per-realization gradients (added to grad_*).
+int launch_adjoint_tile_reduce(const ctqw_hamiltonian *h, int K, double dt, const double *tg, double *grad_eps,
+                               double *grad_J, cudaStream_t s) {
+    const ChainShape f = chain_shape_for(K);
+    RealTable t = real_table(h);
+    int off = 0;
+    const double *tgg = tg;
+    for (size_t g = 0; g < h->group_N.size(); ++g) {
+        const int N = h->group_N[g], cnt = h->group_count[g];
+        const int tx = (N + f.T2 - 1) / f.T2, ty = (N + f.T - 1) / f.T;
+        const int64_t per = (int64_t)(tx + ty) * N * 3;
+        adj_tile_reduce_kernel<<<dim3((unsigned)((N + 255) / 256), (unsigned)cnt), 256, 0, s>>>(
+            t, h->by_group_d + off, tgg, per, tx, ty, dt, grad_eps, grad_J);
+        CTQW_CUDA_TRY(cudaGetLastError());
+        off += cnt;
+        tgg += (size_t)cnt * per;
+    }
+    return CTQW_OK;
+}
