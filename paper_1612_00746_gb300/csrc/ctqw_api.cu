@@ -1049,14 +1049,8 @@ int ctqw_adjoint_grad(const ctqw_hamiltonian *h, int32_t dtype, const void *psi0
             // mu_{K-1} = conj(c_K) lambda;  mu_a = conj(c_{a+1}) lambda + H mu_{a+1}
             void *mu = muA, *mu_prev = muB;
             for (int a = K - 1; a >= 0; --a) {
-                const void *phi_a = a == 0 ? psi_n : phi(a);
-                if (dtype == CTQW_C64 && h->m == 2) {
-                    CTQW_TRY(launch_mu_grad(h, mu_prev, lam, phi_a, mu, cre[a + 1], cim[a + 1], a == K - 1,
-                                            grad_eps_dev, grad_J_dev, s));
-                } else {
-                    CTQW_TRY(launch_mu(h, dtype, mu_prev, lam, mu, cre[a + 1], cim[a + 1], a == K - 1, s));
-                    CTQW_TRY(launch_grad(h, dtype, mu, phi_a, grad_eps_dev, grad_J_dev, s));
-                }
+                CTQW_TRY(launch_mu(h, dtype, mu_prev, lam, mu, cre[a + 1], cim[a + 1], a == K - 1, s));
+                CTQW_TRY(launch_grad(h, dtype, mu, a == 0 ? psi_n : phi(a), grad_eps_dev, grad_J_dev, s));
                 std::swap(mu, mu_prev);
             }
             // lambda_n = T^dagger lambda_{n+1} = sum_k conj(c_k) H^k lambda_{n+1}

@@ -215,10 +215,6 @@ int launch_adjoint_mu_chain(const ctqw_hamiltonian *h, int K, double dt, const v
                             void *lam_out, void *bufA, void *bufB, double *tg, cudaStream_t s);
 int launch_adjoint_tile_reduce(const ctqw_hamiltonian *h, int K, double dt, const double *tg, double *grad_eps,
                                double *grad_J, cudaStream_t s);
-// mu_a = conj(c_{a+1}) lam + H mu_{a+1} and its gradient contribution in one
-// sweep (c64, two particles).
-int launch_mu_grad(const ctqw_hamiltonian *h, const void *mu_in, const void *lam, const void *phi, void *mu_out,
-                   double cre, double cim, int first, double *grad_eps, double *grad_J, cudaStream_t s);
 int launch_grad(const ctqw_hamiltonian *h, int dtype, const void *mu, const void *phi,
                 double *grad_eps, double *grad_J, cudaStream_t s);
 int launch_loss(const double *Pbar, const double *target, int64_t n, double *diff, double *loss,

@@ -155,11 +155,7 @@ __global__ void __launch_bounds__(256) grad_kernel(RealTable tab, const cplx_t<T
 // the block adds them to the FP64 gradients with one atomic per site (the
 // time and ensemble sums stay in FP64).
 constexpr int kGradRows = 32;
-constexpr int kMuRows = 32;    // rows per block of mu_grad2_kernel
 
-__device__ __forceinline__ float2 shfl2(float2 v, int src) {
-    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
-}
 
 __global__ void __launch_bounds__(256) grad2_kernel(RealTable tab, const int32_t *__restrict__ list,
                                                     const float2 *__restrict__ mu,
@@ -227,237 +223,6 @@ __global__ void __launch_bounds__(256) grad2_kernel(RealTable tab, const int32_t
         const int x1 = x1_0 + i;
         atomicAdd(grad_eps + po + x1, (double)row_e[i]);
         if (ring || x1 < N - 1) atomicAdd(grad_J + po + x1, (double)row_j[i]);
-    }
-}
-
-// One level of the adjoint recurrence fused with its gradient contribution,
-// for two particles in FP32 states:
-//   mu_a = conj(c_{a+1}) lam + H mu_{a+1}   (first level: without the H term),
-//   grad += 2 Re <mu_a, dH/dtheta phi_a>.
-// A block owns kMuRows rows x1 and up to 256 columns x2 of one realization;
-// each thread walks down its column keeping the rows above and below of
-// mu_{a+1} and phi_a in registers, the next row's loads issued before the
-// current row is used; the neighbours along x2 come from the adjacent
-// lanes.  A bond b = (b, b+1) collects conj(mu(x)) phi(x') from both of its
-// end points x, x', so a point needs its own mu and phi at its four
-// neighbours: mu_a is never read back.  A row's sum is formed in FP32
-// within the block; a column's in FP32 over 32 rows, then in FP64 over the
-// block's rows; then one FP64 atomic per entry.
-__global__ void __launch_bounds__(256) mu_grad2_kernel(RealTable tab, const int32_t *__restrict__ list,
-                                                       const float *__restrict__ eps,
-                                                       const float *__restrict__ J,
-                                                       const float2 *__restrict__ mu_in,
-                                                       const float2 *__restrict__ lam,
-                                                       const float2 *__restrict__ phi,
-                                                       float2 *__restrict__ mu_out, float cre, float cim,
-                                                       int first, double *grad_eps, double *grad_J) {
-    __shared__ float row_e[kMuRows], row_jd[kMuRows], row_ju[kMuRows];
-    __shared__ float3 rowc[kMuRows];   // eps[x1], J[x1 - 1], J[x1] of the block's rows
-    const int r = list[blockIdx.z];
-    const int N = tab.N[r];
-    const int x1_0 = blockIdx.x * kMuRows;
-    const int x2 = blockIdx.y * blockDim.x + threadIdx.x;
-    const bool live = x2 < N;
-    const bool ring = tab.periodic != 0;
-    const int64_t base = tab.st_off[r];
-    const int64_t po = tab.par_off[r];
-    for (int i = threadIdx.x; i < kMuRows; i += blockDim.x) {
-        row_e[i] = row_jd[i] = row_ju[i] = 0.f;
-        const int x1 = min(x1_0 + i, N - 1);
-        rowc[i] = make_float3(eps[po + x1], J[po + ((x1 == 0) ? N - 1 : x1 - 1)], J[po + x1]);
-    }
-    __syncthreads();
-    const float2 *m_ = mu_in + base, *p_ = phi + base, *l_ = lam + base;
-    float2 *o_ = mu_out + base;
-    const float *e_ = eps + po, *j_ = J + po;
-    const float U = (float)tab.U;
-    const int x2l = (x2 == 0) ? N - 1 : x2 - 1, x2r = (x2 + 1 == N) ? 0 : x2 + 1;
-    const bool bond_r = live && (ring || x2 < N - 1), bond_l = live && (ring || x2 > 0);
-    const float e2 = live ? e_[x2] : 0.f, jl2 = live ? j_[x2l] : 0.f, jr2 = live ? j_[x2] : 0.f;
-    const int rows = min(kMuRows, N - x1_0);
-    const float2 z = make_float2(0.f, 0.f);
-    const int lane = threadIdx.x & 31;
-    // the neighbours along x2 come from the adjacent lanes, except at a
-    // warp's ends and across the wrap from N - 1 to 0 (global loads)
-    const bool own_l = lane > 0 && x2 > 0, own_r = lane < 31 && x2 + 1 < N;
-    auto wrap = [N](int x) { return x < 0 ? x + N : (x >= N ? x - N : x); };
-    // rows x1 - 1, x1 and x1 + 1 of mu_{a+1} and phi_a, and lam on row x1:
-    // every iteration loads the next row's values before it uses the current ones
-    float2 mu_up = z, mu_c = z, mu_dn = z, ph_up = z, ph_c = z, ph_dn = z, l_c = z;
-    if (live) {
-        const int64_t rm = (int64_t)wrap(x1_0 - 1) * N + x2, r0 = (int64_t)x1_0 * N + x2,
-                      rp = (int64_t)wrap(x1_0 + 1) * N + x2;
-        if (!first) {
-            mu_up = m_[rm];
-            mu_c = m_[r0];
-            mu_dn = m_[rp];
-        }
-        ph_up = p_[rm];
-        ph_c = p_[r0];
-        ph_dn = p_[rp];
-        l_c = l_[r0];
-    }
-    // column sums: FP32 over 32 rows, then FP64
-    // the x2 neighbours of the warp's end lanes, one row ahead like the rest
-    float2 e_ml = z, e_mr = z, e_pl = z, e_pr = z;
-    auto edge_loads = [&](int64_t row, float2 &ml, float2 &mr, float2 &pl, float2 &pr) {
-        if (!own_l) {
-            if (!first) ml = m_[row + x2l];
-            pl = p_[row + x2l];
-        }
-        if (!own_r) {
-            if (!first) mr = m_[row + x2r];
-            pr = p_[row + x2r];
-        }
-    };
-    if (live) edge_loads((int64_t)x1_0 * N, e_ml, e_mr, e_pl, e_pr);
-    float col_e = 0.f, col_jr = 0.f, col_jl = 0.f;
-    double cd_e = 0.0, cd_jr = 0.0, cd_jl = 0.0;
-    for (int i = 0; i < rows; ++i) {
-        const int x1 = x1_0 + i;
-        const int64_t row = (int64_t)x1 * N;
-        // prefetch row x1 + 2 of mu_{a+1} and phi_a, row x1 + 1 of lam and of the edge values
-        float2 mu_nn = z, ph_nn = z, l_n = z, n_ml = z, n_mr = z, n_pl = z, n_pr = z;
-        if (live && i + 1 < rows) {
-            const int64_t rn = (int64_t)wrap(x1 + 2) * N + x2;
-            if (!first) mu_nn = m_[rn];
-            ph_nn = p_[rn];
-            l_n = l_[row + N + x2];
-            edge_loads(row + N, n_ml, n_mr, n_pl, n_pr);
-        }
-        float2 ml = shfl2(mu_c, (lane + 31) & 31), mr = shfl2(mu_c, (lane + 1) & 31);
-        float2 pl = shfl2(ph_c, (lane + 31) & 31), pr = shfl2(ph_c, (lane + 1) & 31);
-        if (!own_l) {
-            ml = e_ml;
-            pl = e_pl;
-        }
-        if (!own_r) {
-            mr = e_mr;
-            pr = e_pr;
-        }
-        float se = 0.f, sjd = 0.f, sju = 0.f;
-        if (live) {
-            const float3 rc = rowc[i];
-            float ox = cre * l_c.x - cim * l_c.y;
-            float oy = cre * l_c.y + cim * l_c.x;
-            if (!first) {
-                // the stencil of apply_h: diagonal, then particle 2, then particle 1
-                const float v = rc.x + e2 + (x1 == x2 ? U : 0.f);
-                float yr = v * mu_c.x, yi = v * mu_c.y;
-                yr -= jl2 * ml.x + jr2 * mr.x;
-                yi -= jl2 * ml.y + jr2 * mr.y;
-                const float jl1 = rc.y, jr1 = rc.z;
-                yr -= jl1 * mu_up.x + jr1 * mu_dn.x;
-                yi -= jl1 * mu_up.y + jr1 * mu_dn.y;
-                ox += yr;
-                oy += yi;
-            }
-            const float2 u = make_float2(ox, oy);
-            o_[row + x2] = u;
-            const float d = u.x * ph_c.x + u.y * ph_c.y;
-            col_e += 2.f * d;   // particle 2 on site x2
-            if (bond_r) col_jr -= 2.f * (u.x * pr.x + u.y * pr.y);   // particle 2 across bond x2
-            if (bond_l) col_jl -= 2.f * (u.x * pl.x + u.y * pl.y);   // ... across bond x2 - 1
-            se = 2.f * d;       // particle 1 on site x1
-            if (ring || x1 < N - 1) sjd = -2.f * (u.x * ph_dn.x + u.y * ph_dn.y);   // bond x1
-            if (ring || x1 > 0) sju = -2.f * (u.x * ph_up.x + u.y * ph_up.y);       // bond x1 - 1
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            se += __shfl_xor_sync(0xffffffffu, se, o);
-            sjd += __shfl_xor_sync(0xffffffffu, sjd, o);
-            sju += __shfl_xor_sync(0xffffffffu, sju, o);
-        }
-        if (lane == 0) {
-            atomicAdd(row_e + i, se);
-            atomicAdd(row_jd + i, sjd);
-            atomicAdd(row_ju + i, sju);
-        }
-        if ((i & 31) == 31 || i + 1 == rows) {
-            cd_e += (double)col_e;
-            cd_jr += (double)col_jr;
-            cd_jl += (double)col_jl;
-            col_e = col_jr = col_jl = 0.f;
-        }
-        e_ml = n_ml;
-        e_mr = n_mr;
-        e_pl = n_pl;
-        e_pr = n_pr;
-        mu_up = mu_c;
-        mu_c = mu_dn;
-        mu_dn = mu_nn;
-        ph_up = ph_c;
-        ph_c = ph_dn;
-        ph_dn = ph_nn;
-        l_c = l_n;
-    }
-    if (live) {
-        atomicAdd(grad_eps + po + x2, cd_e);
-        if (bond_r) atomicAdd(grad_J + po + x2, cd_jr);
-        if (bond_l) atomicAdd(grad_J + po + x2l, cd_jl);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-        const int x1 = x1_0 + i;
-        atomicAdd(grad_eps + po + x1, (double)row_e[i]);
-        if (ring || x1 < N - 1) atomicAdd(grad_J + po + x1, (double)row_jd[i]);
-        if (ring || x1 > 0) atomicAdd(grad_J + po + ((x1 == 0) ? N - 1 : x1 - 1), (double)row_ju[i]);
-    }
-}
-
-// out = H in for two particles in FP32 states, walking down kGradRows rows
-// per thread like mu_grad2_kernel (next row prefetched, neighbours along x2
-// from the adjacent lanes).
-__global__ void __launch_bounds__(256) apply_h2_kernel(RealTable tab, const int32_t *__restrict__ list,
-                                                       const float *__restrict__ eps,
-                                                       const float *__restrict__ J,
-                                                       const float2 *__restrict__ in,
-                                                       float2 *__restrict__ out) {
-    const int r = list[blockIdx.z];
-    const int N = tab.N[r];
-    const int x1_0 = blockIdx.x * kGradRows;
-    const int x2 = blockIdx.y * blockDim.x + threadIdx.x;
-    const bool live = x2 < N;
-    const int lane = threadIdx.x & 31;
-    const int64_t base = tab.st_off[r];
-    const int64_t po = tab.par_off[r];
-    const float2 *a_ = in + base;
-    float2 *o_ = out + base;
-    const float *e_ = eps + po, *j_ = J + po;
-    const float U = (float)tab.U;
-    const int x2l = (x2 == 0) ? N - 1 : x2 - 1, x2r = (x2 + 1 == N) ? 0 : x2 + 1;
-    const float e2 = live ? e_[x2] : 0.f, jl2 = live ? j_[x2l] : 0.f, jr2 = live ? j_[x2] : 0.f;
-    const int rows = min(kGradRows, N - x1_0);
-    const bool own_l = lane > 0 && x2 > 0, own_r = lane < 31 && x2 + 1 < N;
-    auto wrap = [N](int x) { return x < 0 ? x + N : (x >= N ? x - N : x); };
-    const float2 z = make_float2(0.f, 0.f);
-    float2 a_up = z, a_c = z, a_dn = z;
-    if (live) {
-        a_up = a_[(int64_t)wrap(x1_0 - 1) * N + x2];
-        a_c = a_[(int64_t)x1_0 * N + x2];
-        a_dn = a_[(int64_t)wrap(x1_0 + 1) * N + x2];
-    }
-    for (int i = 0; i < rows; ++i) {
-        const int x1 = x1_0 + i;
-        const int64_t row = (int64_t)x1 * N;
-        float2 a_nn = z;
-        if (live && i + 1 < rows) a_nn = a_[(int64_t)wrap(x1 + 2) * N + x2];
-        float2 al = shfl2(a_c, (lane + 31) & 31), ar = shfl2(a_c, (lane + 1) & 31);
-        if (live) {
-            if (!own_l) al = a_[row + x2l];
-            if (!own_r) ar = a_[row + x2r];
-            const float v = e_[x1] + e2 + (x1 == x2 ? U : 0.f);
-            float yr = v * a_c.x, yi = v * a_c.y;
-            yr -= jl2 * al.x + jr2 * ar.x;
-            yi -= jl2 * al.y + jr2 * ar.y;
-            const float jl1 = j_[(x1 == 0) ? N - 1 : x1 - 1], jr1 = j_[x1];
-            yr -= jl1 * a_up.x + jr1 * a_dn.x;
-            yi -= jl1 * a_up.y + jr1 * a_dn.y;
-            o_[row + x2] = make_float2(yr, yi);
-        }
-        a_up = a_c;
-        a_c = a_dn;
-        a_dn = a_nn;
     }
 }
 
@@ -529,20 +294,6 @@ dim3 grid_for(const ctqw_hamiltonian *h) {
 
 int launch_apply_h(const ctqw_hamiltonian *h, int dtype, const void *in, void *out, cudaStream_t s) {
     RealTable t = real_table(h);
-    if (dtype == CTQW_C64 && h->m == 2) {
-        int off = 0;
-        for (size_t gi = 0; gi < h->group_N.size(); ++gi) {
-            const int N = h->group_N[gi], cnt = h->group_count[gi];
-            const int tx = N >= 256 ? 256 : ((N + 31) / 32) * 32;
-            const dim3 grid((unsigned)((N + kGradRows - 1) / kGradRows), (unsigned)((N + tx - 1) / tx),
-                            (unsigned)cnt);
-            apply_h2_kernel<<<grid, tx, 0, s>>>(t, h->by_group_d + off, h->eps32, h->J32, (const float2 *)in,
-                                                (float2 *)out);
-            CTQW_CUDA_TRY(cudaGetLastError());
-            off += cnt;
-        }
-        return CTQW_OK;
-    }
     return for_each_group(h, [&](dim3 grid, dim3 block, const int32_t *list) {
         if (dtype == CTQW_C64) {
             auto k = h->m == 2 ? apply_h_kernel<float, 2> : apply_h_kernel<float, 3>;
@@ -597,23 +348,6 @@ int launch_grad(const ctqw_hamiltonian *h, int dtype, const void *mu, const void
         k<<<g, b, 0, s>>>(t, (const double2 *)mu, (const double2 *)phi, grad_eps, grad_J);
     }
     CTQW_CUDA_TRY(cudaGetLastError());
-    return CTQW_OK;
-}
-
-int launch_mu_grad(const ctqw_hamiltonian *h, const void *mu_in, const void *lam, const void *phi, void *mu_out,
-                   double cre, double cim, int first, double *grad_eps, double *grad_J, cudaStream_t s) {
-    RealTable t = real_table(h);
-    int off = 0;
-    for (size_t gi = 0; gi < h->group_N.size(); ++gi) {
-        const int N = h->group_N[gi], cnt = h->group_count[gi];
-        const int tx = N >= 256 ? 256 : ((N + 31) / 32) * 32;
-        const dim3 grid((unsigned)((N + kMuRows - 1) / kMuRows), (unsigned)((N + tx - 1) / tx), (unsigned)cnt);
-        mu_grad2_kernel<<<grid, tx, 0, s>>>(t, h->by_group_d + off, h->eps32, h->J32, (const float2 *)mu_in,
-                                            (const float2 *)lam, (const float2 *)phi, (float2 *)mu_out, (float)cre,
-                                            (float)cim, first, grad_eps, grad_J);
-        CTQW_CUDA_TRY(cudaGetLastError());
-        off += cnt;
-    }
     return CTQW_OK;
 }
 
