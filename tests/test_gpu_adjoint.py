@@ -85,6 +85,60 @@ def test_adjoint_fp32_states_fp64_accumulation(ctqw):
     assert np.max(np.abs(gJ[:, :w.N - 1] - gJ_o)) <= 1e-5 * scale
 
 
+@pytest.mark.parametrize("N,periodic,K,n_steps", [(120, False, 14, 5), (110, True, 5, 6), (57, False, 9, 4)])
+def test_adjoint_fp32_register_tiles_span_several_tiles(ctqw, N, periodic, K, n_steps):
+    """The c64 two-particle adjoint runs on register tiles (a 64 x 64 region,
+    a tile of 64 - 2D per side): sizes that need several tiles per side and a
+    ragged last tile, K that needs one and two launches per chain, both
+    boundary conditions, against the FP64 oracle."""
+    w = _workload(N=N, R=2, periodic=periodic, K=K, n_steps=n_steps, dt=0.03)
+    target = np.random.default_rng(5).dirichlet(np.ones(N))
+    loss, ge, gJ, Pf, eps, J = _gpu(ctqw, w, cw.C64, target, M=3)
+    lo, ge_o, gJ_o = _oracle(w, eps, J, target)
+    scale = max(np.max(np.abs(ge_o)), np.max(np.abs(gJ_o)))
+    nb = N if periodic else N - 1
+    assert abs(loss - lo) <= 1e-6 * max(1.0, lo)
+    assert np.max(np.abs(ge - ge_o)) <= 1e-5 * scale
+    assert np.max(np.abs(gJ[:, :nb] - gJ_o)) <= 1e-5 * scale
+    if not periodic:
+        assert np.all(gJ[:, N - 1] == 0.0)
+
+
+def test_adjoint_fp32_ragged_register_tiles(ctqw):
+    """Two size groups of several tiles each: per-realization gradients
+    against the oracle, realization by realization."""
+    w = cw.Workload(name="adj_ragged_tiles", m=2, statistics=1, periodic=True, N=104, R=3, J0=1.0,
+                    U=1.0, eps_halfwidth=0.5, J_halfwidth=0.2, sites=(20, 21), dt=0.03, K=8,
+                    n_steps=4, obs_every=0, dtype=cw.C64, seed=9, ragged_sizes=(56, 104))
+    h = ctqw.build_for_workload(w)
+    psi = h.new_state(cw.C64)
+    ctqw.ctqw_init_state(h, psi, ctqw.initial_sites(w, h), cw.C64)
+    groups = [int(g) for g in h.group_sizes]
+    rng = np.random.default_rng(7)
+    target = np.concatenate([rng.dirichlet(np.ones(g)) for g in groups])
+    loss, ge, gJ, *_ = ctqw.ctqw_adjoint_grad(h, psi, cw.C64, w.dt, w.K, w.n_steps, 2, torch.tensor(target))
+    ctqw.ctqw_check_status(h)
+    eps, J = h.params()
+    ge, gJ = ge.cpu().numpy(), gJ.cpu().numpy()
+    sizes = [int(n) for n in h.sizes]
+    po = np.concatenate([[0], np.cumsum(sizes)])
+    h.close()
+    goff = 0
+    for g in groups:
+        members = [r for r in range(w.R) if sizes[r] == g]
+        psi0 = oracle.initial_state(g, 2, w.sites, w.statistics)
+        e_l = [eps[po[r]:po[r + 1]] for r in members]
+        j_l = [J[po[r]:po[r + 1]] for r in members]
+        # the loss couples the realizations of a group only through its mean
+        _, ge_o, gJ_o = oracle.loss_and_adjoint_gradient(e_l, j_l, g, 2, True, w.U, psi0, w.dt, w.K,
+                                                         w.n_steps, target[goff:goff + g])
+        scale = max(np.max(np.abs(ge_o)), np.max(np.abs(gJ_o)))
+        for q, r in enumerate(members):
+            assert np.max(np.abs(ge[po[r]:po[r + 1]] - ge_o[q])) <= 1e-5 * scale
+            assert np.max(np.abs(gJ[po[r]:po[r + 1]] - gJ_o[q])) <= 1e-5 * scale
+        goff += g
+
+
 def test_adjoint_against_central_differences_of_gpu_loss(ctqw):
     """Gradient w.r.t. shared means (sum over realizations) vs central FD (h = 1e-4)
     of the GPU's own FP64 loss, without float32 rounding of the parameters."""
