@@ -113,6 +113,18 @@ def test_taylor_fp64_three_bosons_ring(ctqw):
     _compare(got, ref, TOL_FP64, 1e-12, 1e-10)
 
 
+@pytest.mark.parametrize("N,periodic,stats", [(40, True, 1), (36, False, 0)])
+def test_taylor_fp32_three_particles_several_slabs(ctqw, N, periodic, stats):
+    """The FP32 three-particle stages walk x1 in slabs of 32 with x3 across
+    the lanes: N = 40 and 36 give a ragged last slab and a partly idle warp,
+    on a ring (bosons) and on an open chain (distinguishable)."""
+    w = cw.get("ring3_small").with_(N=N, periodic=periodic, statistics=stats, R=2,
+                                    sites=(N // 2 - 1, N // 2, N // 2 + 1), n_steps=40, obs_every=20)
+    got = ctqw.run_workload(w)
+    ref = oracle.ensemble_run(w)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, energy_tol(w))
+
+
 def test_taylor_fp64_ragged_sizes_grouped(ctqw):
     w = cw.get("ragged_n128_1024").with_(ragged_sizes=(6, 10, 17), R=7, n_steps=60, obs_every=20,
                                          dtype=cw.C128, K=10)
