@@ -173,64 +173,67 @@ __global__ void __launch_bounds__(32 * W, MU ? 2 : 3) adj_chain_kernel(const __g
 #pragma unroll
     for (int k = 0; k < 2; ++k) cacc[k][0] = cacc[k][1] = cacc[k][2] = 0.f;
 
-    // phi of the contraction levels through a two-buffer shared-memory ring
-    // (cp.async, rows D - 1 .. D + T of the region, all 64 columns), one
-    // level ahead of its use; the levels run from first_lev down to 0
-    const int first_lev = a.init ? a.a_in : a.a_in - 1;
+    // phi of the contraction levels through two shared-memory buffers
+    // (cp.async, rows D - 1 .. D + T of the region, all 64 columns): level
+    // lev sits in buffer lev & 1.  The stage that forms level lev completes
+    // its copy before the stage's barrier, and after that barrier (every
+    // thread is done with level lev + 1) it starts the copy of lev - 1 into
+    // the buffer lev + 1 used: one barrier per stage.
     const int last_lev = max(0, a.a_in - a.n_stages);
     const uint32_t sP = smem_u32(phs);
-    auto prefetch = [&](int lev, int buf) {
-        if (MU && lev >= last_lev && lev <= first_lev) {
-            const float2 *ph = a.lev[lev] + base;
-            for (int i = warp; i < T + 2; i += W) {
-                const int64_t grow = (int64_t)x_row[D - 1 + i] * N;
+    auto prefetch = [&](int lev) {
+        if (!MU || lev < last_lev) return;
+        const float2 *ph = a.lev[lev] + base;
+        const uint32_t sb = sP + (uint32_t)((lev & 1) * (T + 2) * 32 * 16);
+        for (int i = warp; i < T + 2; i += W) {
+            const int32_t grow = x_row[D - 1 + i] * N;
 #pragma unroll
-                for (int k = 0; k < 2; ++k)
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
-                                 ::"r"(sP + (uint32_t)(((buf * (T + 2) + i) * 32 + lane) * 16 + 8 * k)),
-                                 "l"(ph + grow + X2[k])
-                                 : "memory");
-            }
+            for (int k = 0; k < 2; ++k)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
+                             ::"r"(sb + (uint32_t)((i * 32 + lane) * 16 + 8 * k)), "l"(ph + grow + X2[k])
+                             : "memory");
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
     // the contraction of mu_lev (in P) with phi_lev on the tile's points
+    // (the copy of level lev complete and visible)
     auto contract = [&](int lev) {
-        const int buf = (first_lev - lev) & 1;
-        asm volatile("cp.async.wait_group 1;" ::: "memory");
-        __syncthreads();
-        const float4 *pb = phs + buf * (T + 2) * 32;
-        const float2 *pb2 = reinterpret_cast<const float2 *>(pb);
+        const float4 *pb = phs + (lev & 1) * (T + 2) * 32;
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        // ring rows of region rows r0 - 1 .. r0 + RL (ring row = region row - (D - 1))
+        auto ring_row = [&](int ri) { return (ri >= D - 1 && ri <= D + T) ? pb[(ri - (D - 1)) * 32 + lane] : z4; };
+        float4 up4 = ring_row(r0 - 1), c4 = ring_row(r0);
 #pragma unroll
         for (int i = 0; i < RL; ++i) {
-            const int ri = r0 + i;
-            if (!row_in(ri)) continue;
-            const int sr = ri - (D - 1);   // the ring's row of region row ri
-            const float4 c4 = pb[sr * 32 + lane], u4 = pb[(sr - 1) * 32 + lane], d4 = pb[(sr + 1) * 32 + lane];
-            const float2 c[2] = {make_float2(c4.x, c4.y), make_float2(c4.z, c4.w)};
-            const float2 up[2] = {make_float2(u4.x, u4.y), make_float2(u4.z, u4.w)};
-            const float2 dn[2] = {make_float2(d4.x, d4.y), make_float2(d4.z, d4.w)};
+            const float4 dn4 = ring_row(r0 + i + 1);
+            if (row_in(r0 + i)) {
+                // column 2 lane - 1 (lane - 1's second) and 2 lane + 2 (lane + 1's first)
+                const float2 pl = shfl2(make_float2(c4.z, c4.w), (lane + 31) & 31);
+                const float2 pr = shfl2(make_float2(c4.x, c4.y), (lane + 1) & 31);
+                const float2 c[2] = {make_float2(c4.x, c4.y), make_float2(c4.z, c4.w)};
+                const float2 up[2] = {make_float2(up4.x, up4.y), make_float2(up4.z, up4.w)};
+                const float2 dn[2] = {make_float2(dn4.x, dn4.y), make_float2(dn4.z, dn4.w)};
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                if (!col_in[k]) continue;
-                // columns 2 lane - 1 and 2 lane + 2 lie in the region for a tile column
-                const float2 pl = k ? c[0] : pb2[sr * 64 + 2 * lane - 1];
-                const float2 pr = k ? pb2[sr * 64 + 2 * lane + 2] : c[1];
-                const float2 u = P[i][k];
-                const float d = dotf(u, c[k]);
-                racc[i][0] += d;
-                racc[i][1] += dotf(u, dn[k]);
-                racc[i][2] += dotf(u, up[k]);
-                cacc[k][0] += d;
-                cacc[k][1] += dotf(u, pr);
-                cacc[k][2] += dotf(u, pl);
+                for (int k = 0; k < 2; ++k) {
+                    if (!col_in[k]) continue;
+                    const float2 u = P[i][k];
+                    const float d = dotf(u, c[k]);
+                    racc[i][0] += d;
+                    racc[i][1] += dotf(u, dn[k]);
+                    racc[i][2] += dotf(u, up[k]);
+                    cacc[k][0] += d;
+                    cacc[k][1] += dotf(u, k ? pr : c[1]);
+                    cacc[k][2] += dotf(u, k ? c[0] : pl);
+                }
             }
+            up4 = c4;
+            c4 = dn4;
         }
-        __syncthreads();
-        prefetch(lev - 2, buf);
     };
-    prefetch(first_lev, 0);
-    prefetch(first_lev - 1, 1);
+    // the first contraction level (the init level, or the first stage's),
+    // and after the init level the first stage's (the other buffer)
+    prefetch(a.init ? a.a_in : a.a_in - 1);
+    if (a.init) prefetch(a.a_in - 1);
 
     if (MU && a.init) {
         const float2 co = a.co[a.a_in + 1];
@@ -240,6 +243,8 @@ __global__ void __launch_bounds__(32 * W, MU ? 2 : 3) adj_chain_kernel(const __g
             P[i][0] = cmulf(co, make_float2(q.x, q.y));
             P[i][1] = cmulf(co, make_float2(q.z, q.w));
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
         contract(a.a_in);
     }
 
@@ -253,7 +258,9 @@ __global__ void __launch_bounds__(32 * W, MU ? 2 : 3) adj_chain_kernel(const __g
         float4 *eb = edge + (par * W + warp) * 2 * 32;
         eb[lane] = make_float4(P[0][0].x, P[0][0].y, P[0][1].x, P[0][1].y);
         eb[32 + lane] = make_float4(P[RL - 1][0].x, P[RL - 1][0].y, P[RL - 1][1].x, P[RL - 1][1].y);
+        if (MU) asm volatile("cp.async.wait_all;" ::: "memory");   // level lev's phi
         __syncthreads();
+        if (MU) prefetch(lev - 1);
         const float4 u4 = warp > 0 ? edge[(par * W + warp - 1) * 2 * 32 + 32 + lane] : zero[lane];
         const float4 d4 = warp < W - 1 ? edge[(par * W + warp + 1) * 2 * 32 + lane] : zero[lane];
         float2 prev[2] = {make_float2(u4.x, u4.y), make_float2(u4.z, u4.w)};
