@@ -134,6 +134,10 @@ int ctqw_build_hamiltonian(const ctqw_lattice_desc *desc, void *stream, ctqw_ham
 int ctqw_destroy_hamiltonian(ctqw_hamiltonian *h);
 
 /*
+ * Plumbing: the four calls below (parameters, sizes, output layout,
+ * workspace) follow no passage of the paper; they expose the library's own
+ * layouts.
+ *
  * Copy the built parameters back to the host (synchronizes the device).
  * eps_host and J_host are [sum_r N_r] doubles; J entry N_r-1 of an open chain
  * is 0 (the absent wrap bond).  Either pointer may be NULL.
@@ -159,10 +163,11 @@ int ctqw_output_layout(const ctqw_hamiltonian *h, int64_t *p_width, int32_t *n_g
 /*
  * Write the localised initial state of every realization into psi_dev
  * (zeroing everything else).  The sites are staged through a device buffer
- * of the handle (no allocation), so calls on one handle are stream-ordered.  sites_host is [R][m] (host, int32), the
- * occupied sites of each realization.  Bosons: normalised sum over all
- * permutations; fermions: normalised signed sum (EINVAL if two sites
- * coincide); distinguishable: |x_1..x_m>.
+ * of the handle (no allocation), so calls on one handle are stream-ordered.
+ * sites_host is [R][m] (host, int32), the occupied sites of each
+ * realization.  Bosons: normalised sum over all permutations; fermions:
+ * normalised signed sum (EINVAL if two sites coincide); distinguishable:
+ * |x_1..x_m>.
  */
 int ctqw_init_state(const ctqw_hamiltonian *h, const int32_t *sites_host, int32_t dtype,
                     void *psi_dev, void *stream);
