@@ -357,9 +357,8 @@ int ctqw_ensemble_observables(const ctqw_hamiltonian *h, int32_t dtype, const vo
 /*
  * ctqw_propagate_taylor on the per-term path for callers that cannot
  * allocate device memory (the paper has no counterpart).  Such callers
- * include code running while a CUDA graph is captured, loops that must not
- * call cudaMalloc because it can synchronize the device, and plugins whose
- * host program owns the device-memory budget.  Instead of a caller-provided
+ * include loops that must not call cudaMalloc because it can synchronize
+ * the device, and plugins whose host program owns the device-memory budget.  Instead of a caller-provided
  * workspace, the three scratch states live in one statically sized device
  * array of 48 MiB inside this library (held on every GPU that loads it until
  * the process exits): 3 x amplitudes_total x 8 bytes (CTQW_C64) or x 16
@@ -367,7 +366,7 @@ int ctqw_ensemble_observables(const ctqw_hamiltonian *h, int32_t dtype, const vo
  * launched.  The call allocates and frees nothing.  The handle's device must
  * be the current device (else CTQW_EINVAL).  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.
+ * device current.
  * Every call shares the one array, so calls whose work overlaps on the GPU
  * (e.g. on two streams) race and give wrong results; serialise them.
  * Arguments, outputs and results are those of ctqw_propagate_taylor with

@@ -2,10 +2,9 @@
 //
 // ctqw_propagate_taylor's per-term path needs three state-sized scratch
 // buffers that the caller passes in.  Some callers have no way to obtain
-// them: code that runs while a CUDA graph is being captured (cudaMalloc is
-// not allowed there), real-time loops that must never call cudaMalloc
-// because it can synchronize the whole device, and plugins embedded in a
-// host program that owns the device memory budget.  This entry point takes
+// them: real-time loops that must never call cudaMalloc because it can
+// synchronize the whole device, and plugins embedded in a host program that
+// owns the device memory budget.  This entry point takes
 // its scratch from one statically sized device array instead, so it never
 // allocates, frees or calls an allocating library routine.
 #include <mutex>

@@ -1,7 +1,7 @@
 """ctqw_propagate_taylor_noalloc: the per-term Taylor propagation for callers
-that cannot allocate device memory (inside CUDA graph capture, in loops that
-must not synchronize the device through cudaMalloc, or as a plugin of a host
-program that owns the memory budget).  Its scratch is a fixed 48 MiB array
+that cannot allocate device memory (in loops that must not synchronize the
+device through cudaMalloc, or as a plugin of a host program that owns the
+memory budget).  Its scratch is a fixed 48 MiB array
 inside the library.  Checked through the C ABI against the entry point that
 takes a caller-provided workspace, on two different calls in a row (so the
 second call runs on a scratch array the first one has filled), and
