@@ -672,10 +672,23 @@ def run_ours(args):
         roofline["achieved_with_sampling"] = units_per_step * (8 * w.m + 4) / (kernel_ms / 1000.0) / 1e12
         roofline["snapshot_slots"] = slots
 
-    ragged = None
-    if world == 1 and rank == 0 and not args.no_ragged and args.workload == "bosons_n256_u2" \
-            and not (args.realizations or args.n_steps or args.switch or args.graph):
+    ragged = density = adjoint = None
+    full_default = world == 1 and rank == 0 and args.workload == "bosons_n256_u2" \
+        and not (args.realizations or args.n_steps or args.switch or args.graph)
+    if full_default and not args.no_ragged:
         ragged = ragged_leg(args, dev, stream)
+    if full_default and not args.no_extra_legs:
+        # the one-body density matrix on the tensor cores (states of this
+        # workload after 100 steps) and the adjoint gradient at full size
+        import types
+        d = rho1_line(types.SimpleNamespace(workload="bosons_n256_u2", realizations=0, n_steps=0,
+                                            steps=5, warmup=2))
+        density = {k: d[k] for k in ("metric", "value", "unit", "ms_per_step", "roofline", "cuda_cores",
+                                     "speedup_over_cuda_cores", "max_abs_diff_tc_vs_cuda_cores_rel")}
+        a = adjoint_line(types.SimpleNamespace(workload="adjoint_n512", realizations=0, n_steps=0,
+                                               steps=1, warmup=1))
+        adjoint = {k: a[k] for k in ("metric", "value", "unit", "ms_per_step", "config", "forward_ms",
+                                     "adjoint_over_forward")}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
@@ -699,6 +712,8 @@ def run_ours(args):
         "fp64_plain": fp64,
         "plain_fp32_hbm": plain32,
         "ragged_batch": ragged,
+        "density_tensor_cores": density,
+        "adjoint": adjoint,
         "norm_drift": norm_drift,
         "clocks": clk,
     }
@@ -711,6 +726,12 @@ def run_ours(args):
 
 
 def run_adjoint(args):
+    """Print the adjoint_line JSON line."""
+    print(json.dumps(adjoint_line(args)), flush=True)
+    return 0
+
+
+def adjoint_line(args):
     """Time ctqw_adjoint_grad (loss on Pbar(x, T) and its gradient) on one GPU.
 
     Reported as forward-equivalent site-updates/s (N^m K steps R of the
@@ -771,12 +792,19 @@ def run_adjoint(args):
         "forward_ms": fwd_ms, "adjoint_over_forward": ms / fwd_ms,
         "loss": float(loss.item()), "grad_abs_max": float(max(gem.abs().max().item(), gJm.abs().max().item())),
     }
-    print(json.dumps(line), flush=True)
     h.close()
-    return 0
+    del ws, fws, scratch, psi
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_rho1(args):
+    """Print the rho1_line JSON line."""
+    print(json.dumps(rho1_line(args)), flush=True)
+    return 0
+
+
+def rho1_line(args):
     """Time ctqw_one_body_density (ensemble-averaged one-body density matrix)
     on the workload's states after a short propagation, on the tensor cores
     (c64, the default where supported) and on the CUDA cores.
@@ -860,9 +888,10 @@ def run_rho1(args):
         "max_abs_diff_tc_vs_cuda_cores_rel": diff / big if big else None,
         "trace_sum_over_groups": trace,
     }
-    print(json.dumps(line), flush=True)
     h.close()
-    return 0
+    del psi, ws
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_lattice(args):
@@ -1056,6 +1085,8 @@ def main(argv=None):
     ap.add_argument("--no-fp64-plain", action="store_true")
     ap.add_argument("--no-ragged", action="store_true", help="skip the full-size ragged-batch leg")
     ap.add_argument("--no-fma-peaks", action="store_true", help="skip the FMA-chain peak measurement")
+    ap.add_argument("--no-extra-legs", action="store_true",
+                    help="skip the one-body density and adjoint legs of the default line")
     ap.add_argument("--snapshots", type=int, default=24,
                     help="fused path: sample snapshots per launch (workspace of 1 + S states)")
     ap.add_argument("--snapshot-gb", type=float, default=16.0, help="cap of the snapshot workspace")
