@@ -121,14 +121,15 @@ int taylor_step_plain(const ctqw_hamiltonian *h, int dtype, const void *in, void
 struct AdjointLayout {
     int64_t n_ck = 0;
     size_t state = 0, total = 0;
-    size_t off_ck = 0, off_seg = 0, off_phi = 0, off_misc = 0, off_dbl = 0, off_grad = 0, off_tg = 0;
+    size_t off_ck = 0, off_seg = 0, off_phi = 0, off_misc = 0, off_dbl = 0, off_grad = 0, off_tg = 0, off_mu = 0;
     bool tiled = false;   // the register-tile adjoint (c64, two particles)
 };
 
 // Workspace: checkpoints every M steps, one segment of M replayed states,
 // phi_1..phi_{K-1}, 8 scratch states, then Pbar and diff (FP64), the
 // per-realization gradients (FP64) for calls that want only the sums, and
-// on the register-tile path the per-tile gradient slots (FP64).
+// on the register-tile path the per-tile gradient slots (FP64) and the K
+// mu levels of a step.
 AdjointLayout adjoint_layout(const ctqw_hamiltonian *h, int dtype, int K, int64_t n_steps, int M) {
     AdjointLayout L;
     L.state = (size_t)h->total_amp * elem_bytes(dtype);
@@ -141,7 +142,10 @@ AdjointLayout adjoint_layout(const ctqw_hamiltonian *h, int dtype, int K, int64_
     L.off_grad = L.off_dbl + 2 * sizeof(double) * (size_t)h->p_width;
     L.off_tg = L.off_grad + 2 * sizeof(double) * (size_t)h->total_par;
     L.tiled = adjoint_tiled_supported(h, dtype, K);
-    L.total = L.off_tg + (L.tiled ? sizeof(double) * adjoint_tiled_slots(h, K) : 0);
+    L.off_mu = L.off_tg + (L.tiled ? sizeof(double) * adjoint_tiled_slots(h, K) : 0);
+    // the register-tile path keeps the K mu levels of a step
+    L.off_mu = (L.off_mu + 255) / 256 * 256;
+    L.total = L.off_mu + (L.tiled ? (size_t)K * L.state : 0);
     return L;
 }
 
@@ -1000,7 +1004,7 @@ int ctqw_adjoint_grad(const ctqw_hamiltonian *h, int32_t dtype, const void *psi0
     CTQW_CUDA_TRY(cudaMemsetAsync(grad_J_dev, 0, sizeof(double) * h->total_par, s));
     CTQW_CUDA_TRY(cudaMemsetAsync(Pbar, 0, sizeof(double) * h->p_width, s));
     double *tg = (double *)(ws + L.off_tg);
-    if (L.tiled) CTQW_CUDA_TRY(cudaMemsetAsync(tg, 0, L.total - L.off_tg, s));
+    if (L.tiled) CTQW_CUDA_TRY(cudaMemsetAsync(tg, 0, L.off_mu - L.off_tg, s));
 
     // forward pass with checkpoints psi_{cM}
     CTQW_CUDA_TRY(cudaMemcpyAsync(X, psi0_dev, L.state, cudaMemcpyDeviceToDevice, s));
@@ -1037,11 +1041,13 @@ int ctqw_adjoint_grad(const ctqw_hamiltonian *h, int32_t dtype, const void *psi0
         for (int64_t n = n1 - 1; n >= n0; --n) {
             const void *psi_n = (n == n0) ? ck(c) : seg(n - n0);
             if (L.tiled) {
-                void *levels[32];
+                void *levels[32], *mu_levels[32];
                 levels[0] = const_cast<void *>(psi_n);
                 for (int a = 1; a < K; ++a) levels[a] = phi(a);
+                for (int a = 0; a < K; ++a) mu_levels[a] = ws + L.off_mu + (size_t)a * L.state;
                 CTQW_TRY(launch_adjoint_phi_chain(h, K, dt, levels, s));
-                CTQW_TRY(launch_adjoint_mu_chain(h, K, dt, lam, levels, lam2, muA, muB, tg, s));
+                CTQW_TRY(launch_adjoint_mu_chain(h, K, dt, lam, mu_levels, lam2, s));
+                CTQW_TRY(launch_adjoint_contract(h, K, levels, mu_levels, tg, s));
                 std::swap(lam, lam2);
                 continue;
             }

@@ -206,13 +206,16 @@ int launch_mu(const ctqw_hamiltonian *h, int dtype, const void *in, const void *
               double cre, double cim, int first, cudaStream_t s);
 // Adjoint on register tiles (c64, two particles; k_adjoint_tiled.cu): the
 // phi chain phi_a = (dt H)^a psi into levels[1..K-1] (levels[0] = psi), the
-// mu chain with the gradient contraction into per-tile FP64 slots and
-// lambda_n into lam_out, and the sum of the slots into the gradients.
+// mu chain into mu_levels[0..K-1] and lambda_n into lam_out, the contraction
+// of the two into per-tile FP64 slots, and the sum of the slots into the
+// gradients.
 bool adjoint_tiled_supported(const ctqw_hamiltonian *h, int dtype, int K);
 size_t adjoint_tiled_slots(const ctqw_hamiltonian *h, int K);
 int launch_adjoint_phi_chain(const ctqw_hamiltonian *h, int K, double dt, void *const *levels, cudaStream_t s);
-int launch_adjoint_mu_chain(const ctqw_hamiltonian *h, int K, double dt, const void *lam, void *const *levels,
-                            void *lam_out, void *bufA, void *bufB, double *tg, cudaStream_t s);
+int launch_adjoint_mu_chain(const ctqw_hamiltonian *h, int K, double dt, const void *lam, void *const *mu_levels,
+                            void *lam_out, cudaStream_t s);
+int launch_adjoint_contract(const ctqw_hamiltonian *h, int K, void *const *levels, void *const *mu_levels,
+                            double *tg, cudaStream_t s);
 int launch_adjoint_tile_reduce(const ctqw_hamiltonian *h, int K, double dt, const double *tg, double *grad_eps,
                                double *grad_J, cudaStream_t s);
 int launch_grad(const ctqw_hamiltonian *h, int dtype, const void *mu, const void *phi,

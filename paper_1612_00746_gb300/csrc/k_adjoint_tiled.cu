@@ -48,6 +48,7 @@ struct ChainArgs {
     const float2 *q;                  // mu chain: lambda_{n+1}
     float2 *out;                      // last level of the launch (tile); lambda_n when final
     float2 *lev[kMaxLevels];          // phi_a (a = 0: psi_n): written by the phi chain, read by the mu chain
+    float2 *mlev[kMaxLevels];         // mu_a: written by the storing mu chain, read by adj_contract_kernel
     float2 co[kMaxLevels + 1];        // i^k / k!
     double *tg;                       // per-tile gradient slots of the group
     int64_t tg_per_real;              // doubles per realization
@@ -81,9 +82,13 @@ __device__ __forceinline__ float warp_sum32_f(float (&v)[32], int lane) {
     return v[0];
 }
 
-// MU = false: the phi chain; MU = true: the mu chain with the contraction.
-template <int D, int W, bool MU>
-__global__ void __launch_bounds__(32 * W, MU ? 2 : 3) adj_chain_kernel(const __grid_constant__ ChainArgs a) {
+// MODE: kPhi, the phi chain; kMuContract, the mu chain with the contraction;
+// kMuStore, the mu chain storing every level's tile for adj_contract_kernel.
+constexpr int kPhi = 0, kMuContract = 1, kMuStore = 2;
+
+template <int D, int W, int MODE>
+__global__ void __launch_bounds__(32 * W, MODE == kMuContract ? 2 : 3) adj_chain_kernel(const __grid_constant__ ChainArgs a) {
+    constexpr bool MU = MODE != kPhi, CON = MODE == kMuContract;
     constexpr int RS = 8 * W, T = RS - 2 * D, T2 = 64 - 2 * D, RL = 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *Q = reinterpret_cast<float4 *>(smem_raw);            // mu chain: [RS][32] lambda, (row, lane) -> 2 columns
@@ -92,7 +97,7 @@ __global__ void __launch_bounds__(32 * W, MU ? 2 : 3) adj_chain_kernel(const __g
     float4 *rowc = zero + 32;                                     // [RS + 1] (dt eps, dt eps, -dt J_up, -dt J_up)
     int *x_row = reinterpret_cast<int *>(rowc + RS + 1);          // [RS]
     float *colsum = reinterpret_cast<float *>(x_row + RS);        // mu chain: [W][64][3]
-    float4 *phs = reinterpret_cast<float4 *>(colsum + (MU ? W * 64 * 3 : 0));   // mu chain: [2][T + 2][32] phi
+    float4 *phs = reinterpret_cast<float4 *>(colsum + (CON ? W * 64 * 3 : 0));  // contraction: [2][T + 2][32] phi
 
     const int r = a.list[blockIdx.z];
     const int N = a.tab.N[r];
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(32 * W, MU ? 2 : 3) adj_chain_kernel(const __g
     const int last_lev = max(0, a.a_in - a.n_stages);
     const uint32_t sP = smem_u32(phs);
     auto prefetch = [&](int lev) {
-        if (!MU || lev < last_lev) return;
+        if (!CON || lev < last_lev) return;
         const float2 *ph = a.lev[lev] + base;
         const uint32_t sb = sP + (uint32_t)((lev & 1) * (T + 2) * 32 * 16);
         for (int i = warp; i < T + 2; i += W) {
@@ -245,7 +250,21 @@ __global__ void __launch_bounds__(32 * W, MU ? 2 : 3) adj_chain_kernel(const __g
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
-        contract(a.a_in);
+        if (CON) {
+            contract(a.a_in);
+        } else {
+            // the first level's tile
+            float2 *dst = a.mlev[a.a_in] + base;
+#pragma unroll
+            for (int i = 0; i < RL; ++i) {
+                const int ri = r0 + i;
+                if (!row_in(ri)) continue;
+                const int64_t grow = (int64_t)x_row[ri] * N;
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    if (col_in[k]) dst[grow + X2[k]] = P[i][k];
+            }
+        }
     }
 
     const float2 dU = make_float2(a.dtU, a.dtU);
@@ -258,9 +277,9 @@ __global__ void __launch_bounds__(32 * W, MU ? 2 : 3) adj_chain_kernel(const __g
         float4 *eb = edge + (par * W + warp) * 2 * 32;
         eb[lane] = make_float4(P[0][0].x, P[0][0].y, P[0][1].x, P[0][1].y);
         eb[32 + lane] = make_float4(P[RL - 1][0].x, P[RL - 1][0].y, P[RL - 1][1].x, P[RL - 1][1].y);
-        if (MU) asm volatile("cp.async.wait_all;" ::: "memory");   // level lev's phi
+        if (CON) asm volatile("cp.async.wait_all;" ::: "memory");   // level lev's phi
         __syncthreads();
-        if (MU) prefetch(lev - 1);
+        if (CON) prefetch(lev - 1);
         const float4 u4 = warp > 0 ? edge[(par * W + warp - 1) * 2 * 32 + 32 + lane] : zero[lane];
         const float4 d4 = warp < W - 1 ? edge[(par * W + warp + 1) * 2 * 32 + lane] : zero[lane];
         float2 prev[2] = {make_float2(u4.x, u4.y), make_float2(u4.z, u4.w)};
@@ -304,9 +323,9 @@ __global__ void __launch_bounds__(32 * W, MU ? 2 : 3) adj_chain_kernel(const __g
             }
         }
         const bool last = d == a.n_stages;
-        if (!MU || (a.final && last)) {
-            // the phi level, or lambda_n, on the tile
-            float2 *dst = MU ? a.out + base : a.lev[lev] + base;
+        if (!MU || (a.final && last) || (MODE == kMuStore && lev >= 0)) {
+            // the phi level, lambda_n, or the stored mu level, on the tile
+            float2 *dst = !MU ? a.lev[lev] + base : (lev < 0 ? a.out + base : a.mlev[lev] + base);
 #pragma unroll
             for (int i = 0; i < RL; ++i) {
                 const int ri = r0 + i;
@@ -317,9 +336,9 @@ __global__ void __launch_bounds__(32 * W, MU ? 2 : 3) adj_chain_kernel(const __g
                     if (col_in[k]) dst[grow + X2[k]] = P[i][k];
             }
         }
-        if (MU && lev >= 0) contract(lev);
+        if (CON && lev >= 0) contract(lev);
     }
-    if (MU && !a.final) {
+    if (CON && !a.final) {
         // the tile of the launch's last level
 #pragma unroll
         for (int i = 0; i < RL; ++i) {
@@ -331,7 +350,7 @@ __global__ void __launch_bounds__(32 * W, MU ? 2 : 3) adj_chain_kernel(const __g
                 if (col_in[k]) a.out[grow + X2[k]] = P[i][k];
         }
     }
-    if (MU) {
+    if (CON) {
         // rows: the warp's 8 rows x 3 sums over its 64 columns, value 4 i + q
         // in lane 4 i + q; then into the tile's FP64 slots (tile column index)
         double *tg = a.tg + (int64_t)blockIdx.z * a.tg_per_real;
@@ -401,6 +420,137 @@ __global__ void __launch_bounds__(256) adj_tile_reduce_kernel(RealTable tab, con
     if (tab.periodic || x < N - 1) grad_J[po + x] += -2.0 * dt * j;
 }
 
+// The contraction of every level a < K, streamed: mu_a (stored by the mu
+// chain) against phi_a (stored by the phi chain; psi_n for a = 0).  A block
+// owns a tile of kCtRows x kCtCols points (4 warps x 4 rows, 2 columns a
+// lane); every point sums its five terms over the levels in registers, and
+// at the end a warp sums its rows and the block its columns into the
+// per-tile FP64 slots (one owner each).  Per level and point it reads 8 B
+// of mu and 8 B of phi from HBM (the neighbour rows and the lanes' edge
+// columns from L1/L2).
+constexpr int kCtRows = 16, kCtCols = 64, kCtWarps = 4, kCtRL = 4;
+
+struct ContractArgs {
+    RealTable tab;
+    const int32_t *list;
+    const float2 *lev[kMaxLevels];    // phi_a
+    const float2 *mlev[kMaxLevels];   // mu_a
+    int K;
+    double *tg;
+    int64_t tg_per_real;
+    int tiles_x;                      // column tiles (kCtCols wide)
+};
+
+__global__ void __launch_bounds__(32 * kCtWarps, 4) adj_contract_kernel(const __grid_constant__ ContractArgs a) {
+    __shared__ float colsum[kCtWarps][kCtCols][3];
+    const int r = a.list[blockIdx.z];
+    const int N = a.tab.N[r];
+    const int x1_0 = (int)blockIdx.y * kCtRows, x2_0 = (int)blockIdx.x * kCtCols;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t base = a.tab.st_off[r];
+    auto wrap = [N](int x) { return x < 0 ? x + N : (x >= N ? x - N : x); };
+    int x2[2];
+    bool col_ok[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        x2[k] = x2_0 + 2 * lane + k;
+        col_ok[k] = x2[k] < N;
+    }
+    const int xl = wrap(x2[0] - 1), xr = wrap(x2[1] + 1);
+    // the neighbours along x2 come from the adjacent lane unless the lane is
+    // at the warp's end or the neighbour wraps around the lattice
+    const bool own_l = lane > 0 && x2[0] > 0, own_r = lane < 31 && x2[1] + 1 < N;
+    int x1[kCtRL + 2];   // rows r0 - 1 .. r0 + kCtRL (wrapped)
+#pragma unroll
+    for (int i = 0; i < kCtRL + 2; ++i) x1[i] = wrap(x1_0 + warp * kCtRL + i - 1);
+    const float2 z = make_float2(0.f, 0.f);
+    float sd[kCtRL][2], sdn[kCtRL][2], sup[kCtRL][2], srt[kCtRL][2], slf[kCtRL][2];
+#pragma unroll
+    for (int i = 0; i < kCtRL; ++i)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) sd[i][k] = sdn[i][k] = sup[i][k] = srt[i][k] = slf[i][k] = 0.f;
+#pragma unroll 1
+    for (int lv = 0; lv < a.K; ++lv) {
+        const float2 *mu = a.mlev[lv] + base, *ph = a.lev[lv] + base;
+        float2 u[kCtRL][2], p[kCtRL + 2][2], pl[kCtRL], pr[kCtRL];
+#pragma unroll
+        for (int i = 0; i < kCtRL + 2; ++i) {
+            const int64_t rb = (int64_t)x1[i] * N;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) p[i][k] = col_ok[k] ? ph[rb + x2[k]] : z;
+            if (i >= 1 && i <= kCtRL) {
+#pragma unroll
+                for (int k = 0; k < 2; ++k) u[i - 1][k] = col_ok[k] ? mu[rb + x2[k]] : z;
+                pl[i - 1] = (!own_l && col_ok[0]) ? ph[rb + xl] : z;
+                pr[i - 1] = (!own_r && col_ok[1]) ? ph[rb + xr] : z;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kCtRL; ++i) {
+            const float2 l = shfl2(p[i + 1][1], (lane + 31) & 31), rr = shfl2(p[i + 1][0], (lane + 1) & 31);
+            const float2 left = own_l ? l : pl[i], right = own_r ? rr : pr[i];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const float2 uu = u[i][k];
+                sd[i][k] += dotf(uu, p[i + 1][k]);
+                sdn[i][k] += dotf(uu, p[i + 2][k]);
+                sup[i][k] += dotf(uu, p[i][k]);
+                srt[i][k] += dotf(uu, k ? right : p[i + 1][1]);
+                slf[i][k] += dotf(uu, k ? p[i + 1][0] : left);
+            }
+        }
+    }
+    double *tg = a.tg + (int64_t)blockIdx.z * a.tg_per_real;
+    // rows: 4 rows x 3 sums over the warp's 64 columns; value 4 i + q (16 of
+    // the 32 slots used) ends in lane 4 i + q
+    float v[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = 0.f;
+#pragma unroll
+    for (int i = 0; i < kCtRL; ++i) {
+        float e = 0.f, dn = 0.f, up = 0.f;
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            if (col_ok[k]) {
+                e += sd[i][k];
+                dn += sdn[i][k];
+                up += sup[i][k];
+            }
+        v[4 * i] = e;
+        v[4 * i + 1] = dn;
+        v[4 * i + 2] = up;
+    }
+    const float tot = warp_sum32_f(v, lane);
+    {
+        const int i = lane >> 2, q = lane & 3, row = x1_0 + warp * kCtRL + i;
+        if (i < kCtRL && q < 3 && row < N) tg[((int64_t)blockIdx.x * N + row) * 3 + q] += (double)tot;
+    }
+    // columns: over the warp's rows in registers, over the warps in shared memory
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        float e = 0.f, rt = 0.f, lf = 0.f;
+#pragma unroll
+        for (int i = 0; i < kCtRL; ++i)
+            if (x1_0 + warp * kCtRL + i < N) {
+                e += sd[i][k];
+                rt += srt[i][k];
+                lf += slf[i][k];
+            }
+        colsum[warp][2 * lane + k][0] = e;
+        colsum[warp][2 * lane + k][1] = rt;
+        colsum[warp][2 * lane + k][2] = lf;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kCtCols * 3; t += blockDim.x) {
+        const int c = t / 3, q = t - 3 * (t / 3);
+        if (x2_0 + c >= N) continue;
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < kCtWarps; ++w) sum += colsum[w][c][q];
+        tg[(int64_t)a.tiles_x * N * 3 + ((int64_t)blockIdx.y * N + (x2_0 + c)) * 3 + q] += (double)sum;
+    }
+}
+
 using ChainKernel = void (*)(ChainArgs);
 
 struct ChainShape {
@@ -417,11 +567,10 @@ ChainShape chain_shape() {
     s.T = RS - 2 * D;
     s.T2 = 64 - 2 * D;
     s.threads = 32 * W;
-    s.phi = adj_chain_kernel<D, W, false>;
-    s.mu = adj_chain_kernel<D, W, true>;
+    s.phi = adj_chain_kernel<D, W, kPhi>;
+    s.mu = adj_chain_kernel<D, W, kMuStore>;
     s.smem_phi = sizeof(float4) * (2 * W * 2 * 32 + 32 + RS + 1) + sizeof(int) * RS;
-    s.smem_mu = s.smem_phi + sizeof(float4) * RS * 32 + sizeof(float) * W * 64 * 3 +
-                sizeof(float4) * 2 * (s.T + 2) * 32;
+    s.smem_mu = s.smem_phi + sizeof(float4) * RS * 32;
     return s;
 }
 
@@ -444,7 +593,7 @@ ChainArgs chain_args(const ctqw_hamiltonian *h, double dt) {
     a.in = nullptr;
     a.q = nullptr;
     a.out = nullptr;
-    for (int i = 0; i < kMaxLevels; ++i) a.lev[i] = nullptr;
+    for (int i = 0; i < kMaxLevels; ++i) a.lev[i] = a.mlev[i] = nullptr;
     // i^k / k!
     double mag = 1.0;
     for (int k = 0; k <= kMaxLevels; ++k) {
@@ -472,11 +621,11 @@ bool adjoint_tiled_supported(const ctqw_hamiltonian *h, int dtype, int K) {
 }
 
 size_t adjoint_tiled_slots(const ctqw_hamiltonian *h, int K) {
-    const ChainShape f = chain_shape_for(K);
+    (void)K;
     size_t n = 0;
     for (size_t g = 0; g < h->group_N.size(); ++g) {
         const int N = h->group_N[g];
-        const int tx = (N + f.T2 - 1) / f.T2, ty = (N + f.T - 1) / f.T;
+        const int tx = (N + kCtCols - 1) / kCtCols, ty = (N + kCtRows - 1) / kCtRows;
         n += (size_t)h->group_count[g] * (size_t)(tx + ty) * (size_t)N * 3;
     }
     return n;
@@ -508,48 +657,36 @@ int launch_adjoint_phi_chain(const ctqw_hamiltonian *h, int K, double dt, void *
     return CTQW_OK;
 }
 
-// The mu recurrence from level K - 1 down to -1 with the contraction against
-// levels[a] at every a >= 0, accumulated into the tile slots tg, and
-// lambda_n = T^dagger lambda into lam_out (bufA, bufB: two state-sized
-// buffers for the levels between launches).
-int launch_adjoint_mu_chain(const ctqw_hamiltonian *h, int K, double dt, const void *lam, void *const *levels,
-                            void *lam_out, void *bufA, void *bufB, double *tg, cudaStream_t s) {
+// The mu recurrence from level K - 1 down to -1: every level a >= 0 into
+// mu_levels[a], lambda_n = T^dagger lambda into lam_out.
+int launch_adjoint_mu_chain(const ctqw_hamiltonian *h, int K, double dt, const void *lam, void *const *mu_levels,
+                            void *lam_out, cudaStream_t s) {
     const ChainShape f = chain_shape_for(K);
     CTQW_CUDA_TRY(cudaFuncSetAttribute((const void *)f.mu, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)f.smem_mu));
     ChainArgs a = chain_args(h, dt);
-    for (int i = 0; i < K; ++i) a.lev[i] = (float2 *)levels[i];
+    for (int i = 0; i < K; ++i) a.mlev[i] = (float2 *)mu_levels[i];
     a.q = (const float2 *)lam;
-    void *bufs[2] = {bufA, bufB};
-    int nb = 0, a_in = K - 1, remaining = K;
+    int a_in = K - 1, remaining = K;
     bool init = true;
-    const void *in = nullptr;
     while (remaining > 0) {
         const int n = std::min(f.D, remaining);
         const bool final = n == remaining;
-        void *out = final ? lam_out : bufs[nb];
-        a.in = (const float2 *)in;
-        a.out = (float2 *)out;
+        a.in = init ? nullptr : (const float2 *)mu_levels[a_in];
+        a.out = final ? (float2 *)lam_out : nullptr;
         a.a_in = a_in;
         a.n_stages = n;
         a.init = init ? 1 : 0;
         a.final = final ? 1 : 0;
         int off = 0;
-        double *tgg = tg;
         for (size_t g = 0; g < h->group_N.size(); ++g) {
             const int N = h->group_N[g], cnt = h->group_count[g];
             const int tx = (N + f.T2 - 1) / f.T2, ty = (N + f.T - 1) / f.T;
             a.list = h->by_group_d + off;
-            a.tg = tgg;
-            a.tg_per_real = (int64_t)(tx + ty) * N * 3;
-            a.tiles_x = tx;
             f.mu<<<dim3((unsigned)tx, (unsigned)ty, (unsigned)cnt), f.threads, f.smem_mu, s>>>(a);
             CTQW_CUDA_TRY(cudaGetLastError());
             off += cnt;
-            tgg += (size_t)cnt * a.tg_per_real;
         }
-        in = out;
-        nb ^= 1;
         a_in -= n;
         init = false;
         remaining -= n;
@@ -557,16 +694,44 @@ int launch_adjoint_mu_chain(const ctqw_hamiltonian *h, int K, double dt, const v
     return CTQW_OK;
 }
 
+// The contraction of mu_levels[a] with levels[a] over a < K into the tile
+// slots tg.
+int launch_adjoint_contract(const ctqw_hamiltonian *h, int K, void *const *levels, void *const *mu_levels,
+                            double *tg, cudaStream_t s) {
+    ContractArgs a;
+    a.tab = real_table(h);
+    for (int i = 0; i < kMaxLevels; ++i) {
+        a.lev[i] = i < K ? (const float2 *)levels[i] : nullptr;
+        a.mlev[i] = i < K ? (const float2 *)mu_levels[i] : nullptr;
+    }
+    a.K = K;
+    int off = 0;
+    double *tgg = tg;
+    for (size_t g = 0; g < h->group_N.size(); ++g) {
+        const int N = h->group_N[g], cnt = h->group_count[g];
+        const int tx = (N + kCtCols - 1) / kCtCols, ty = (N + kCtRows - 1) / kCtRows;
+        a.list = h->by_group_d + off;
+        a.tg = tgg;
+        a.tg_per_real = (int64_t)(tx + ty) * N * 3;
+        a.tiles_x = tx;
+        adj_contract_kernel<<<dim3((unsigned)tx, (unsigned)ty, (unsigned)cnt), 32 * kCtWarps, 0, s>>>(a);
+        CTQW_CUDA_TRY(cudaGetLastError());
+        off += cnt;
+        tgg += (size_t)cnt * a.tg_per_real;
+    }
+    return CTQW_OK;
+}
+
 // The tile slots into the per-realization gradients (added to grad_*).
 int launch_adjoint_tile_reduce(const ctqw_hamiltonian *h, int K, double dt, const double *tg, double *grad_eps,
                                double *grad_J, cudaStream_t s) {
-    const ChainShape f = chain_shape_for(K);
+    (void)K;
     RealTable t = real_table(h);
     int off = 0;
     const double *tgg = tg;
     for (size_t g = 0; g < h->group_N.size(); ++g) {
         const int N = h->group_N[g], cnt = h->group_count[g];
-        const int tx = (N + f.T2 - 1) / f.T2, ty = (N + f.T - 1) / f.T;
+        const int tx = (N + kCtCols - 1) / kCtCols, ty = (N + kCtRows - 1) / kCtRows;
         const int64_t per = (int64_t)(tx + ty) * N * 3;
         adj_tile_reduce_kernel<<<dim3((unsigned)((N + 255) / 256), (unsigned)cnt), 256, 0, s>>>(
             t, h->by_group_d + off, tgg, per, tx, ty, dt, grad_eps, grad_J);
