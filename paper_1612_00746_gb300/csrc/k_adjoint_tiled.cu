@@ -12,25 +12,26 @@
 // (the same recurrence one level further, with coefficient i^0 / 0! = 1).
 // Every term stays O(1) in FP32, where the unscaled H^a grows like |H|^a.
 //
-// Two kernels on the register tiles of the forward Taylor kernel (an 8W x 64
-// region per block, 8 rows per warp, 2 adjacent columns per lane, D stages
-// per launch with a D-deep halo):
-//  - the phi chain applies Hh D times per launch and stores every level's
-//    tile;
-//  - the mu chain runs the recurrence from a = K-1 down to -1 with lambda
-//    of the region in shared memory, and at every level a >= 0 contracts mu_a
-//    with phi_a (read from the stored levels, psi_n for a = 0) at the tile's
-//    points.  dH/deps_i counts the particles on site i; dH/dJ_b is minus the
+// Three kernels per step:
+//  - the phi chain applies Hh on the register tiles of the forward Taylor
+//    kernel (an 8W x 64 region per block, 8 rows per warp, 2 adjacent
+//    columns per lane, D stages per launch with a D-deep halo) and stores
+//    every level's tile;
+//  - the mu chain runs the recurrence from a = K-1 down to -1 on the same
+//    tiles, with lambda of the region in shared memory, stores every level
+//    a >= 0 and writes lambda_n;
+//  - the contraction streams mu_a and phi_a (psi_n for a = 0) for every
+//    level.  dH/deps_i counts the particles on site i; dH/dJ_b is minus the
 //    hop across bond b = (b, b+1): a bond collects conj(mu(x)) phi(x') from
 //    both of its end points, so a point needs its own mu and phi at its four
-//    neighbours.  Each lane sums its rows' and columns' terms over the
-//    launch's levels in FP32; at the end of the launch a warp sums its rows
-//    and the block its columns, and adds them in FP64 to per-tile slots (one
-//    owner per slot: no atomics, a fixed order).  A last kernel sums the
-//    slots over the tiles into the per-realization gradients.
-// HBM per step: the phi chain reads psi and writes K-1 levels; the mu chain
-// reads lambda, the K-1 levels and psi, and writes lambda_n: about 16 K
-// bytes per amplitude, against about 56 K for one sweep per level and term.
+//    neighbours.  Every point sums its terms over the levels in FP32; a warp
+//    sums its rows and the block its columns, and adds them in FP64 to
+//    per-tile slots (one owner per slot: no atomics, a fixed order).  A last
+//    kernel sums the slots over the tiles into the per-realization
+//    gradients.
+// HBM per step: the chains write 2K - 1 levels and lambda_n, the contraction
+// reads 2K levels: about 32 K bytes per amplitude, all of it streamed, where
+// one sweep per level and term moves about 56 K with neighbour re-reads.
 #include "ctqw_internal.cuh"
 #include "fused_common.cuh"
 
@@ -50,9 +51,6 @@ struct ChainArgs {
     float2 *lev[kMaxLevels];          // phi_a (a = 0: psi_n): written by the phi chain, read by the mu chain
     float2 *mlev[kMaxLevels];         // mu_a: written by the storing mu chain, read by adj_contract_kernel
     float2 co[kMaxLevels + 1];        // i^k / k!
-    double *tg;                       // per-tile gradient slots of the group
-    int64_t tg_per_real;              // doubles per realization
-    int tiles_x;                      // tiles along x2
     float dt, dtU;
     int a_in;                         // level of the launch's initial iterate
     int n_stages;                     // stencil stages of the launch
@@ -82,13 +80,10 @@ __device__ __forceinline__ float warp_sum32_f(float (&v)[32], int lane) {
     return v[0];
 }
 
-// MODE: kPhi, the phi chain; kMuContract, the mu chain with the contraction;
-// kMuStore, the mu chain storing every level's tile for adj_contract_kernel.
-constexpr int kPhi = 0, kMuContract = 1, kMuStore = 2;
-
-template <int D, int W, int MODE>
-__global__ void __launch_bounds__(32 * W, MODE == kMuContract ? 2 : 3) adj_chain_kernel(const __grid_constant__ ChainArgs a) {
-    constexpr bool MU = MODE != kPhi, CON = MODE == kMuContract;
+// MU = false: the phi chain; MU = true: the mu chain, storing every level's
+// tile for adj_contract_kernel.
+template <int D, int W, bool MU>
+__global__ void __launch_bounds__(32 * W, 3) adj_chain_kernel(const __grid_constant__ ChainArgs a) {
     constexpr int RS = 8 * W, T = RS - 2 * D, T2 = 64 - 2 * D, RL = 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *Q = reinterpret_cast<float4 *>(smem_raw);            // mu chain: [RS][32] lambda, (row, lane) -> 2 columns
@@ -96,8 +91,6 @@ __global__ void __launch_bounds__(32 * W, MODE == kMuContract ? 2 : 3) adj_chain
     float4 *zero = edge + 2 * W * 2 * 32;                         // [32] a row of zeros
     float4 *rowc = zero + 32;                                     // [RS + 1] (dt eps, dt eps, -dt J_up, -dt J_up)
     int *x_row = reinterpret_cast<int *>(rowc + RS + 1);          // [RS]
-    float *colsum = reinterpret_cast<float *>(x_row + RS);        // mu chain: [W][64][3]
-    float4 *phs = reinterpret_cast<float4 *>(colsum + (CON ? W * 64 * 3 : 0));  // contraction: [2][T + 2][32] phi
 
     const int r = a.list[blockIdx.z];
     const int N = a.tab.N[r];
@@ -170,76 +163,6 @@ __global__ void __launch_bounds__(32 * W, MODE == kMuContract ? 2 : 3) adj_chain
         __syncthreads();
     }
 
-    // mu chain: per-lane sums of the contraction over the launch's levels
-    // (row i: eps, bond below, bond above; column k: eps, bond right, bond left)
-    float racc[RL][3], cacc[2][3];
-#pragma unroll
-    for (int i = 0; i < RL; ++i) racc[i][0] = racc[i][1] = racc[i][2] = 0.f;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) cacc[k][0] = cacc[k][1] = cacc[k][2] = 0.f;
-
-    // phi of the contraction levels through two shared-memory buffers
-    // (cp.async, rows D - 1 .. D + T of the region, all 64 columns): level
-    // lev sits in buffer lev & 1.  The stage that forms level lev completes
-    // its copy before the stage's barrier, and after that barrier (every
-    // thread is done with level lev + 1) it starts the copy of lev - 1 into
-    // the buffer lev + 1 used: one barrier per stage.
-    const int last_lev = max(0, a.a_in - a.n_stages);
-    const uint32_t sP = smem_u32(phs);
-    auto prefetch = [&](int lev) {
-        if (!CON || lev < last_lev) return;
-        const float2 *ph = a.lev[lev] + base;
-        const uint32_t sb = sP + (uint32_t)((lev & 1) * (T + 2) * 32 * 16);
-        for (int i = warp; i < T + 2; i += W) {
-            const int32_t grow = x_row[D - 1 + i] * N;
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
-                             ::"r"(sb + (uint32_t)((i * 32 + lane) * 16 + 8 * k)), "l"(ph + grow + X2[k])
-                             : "memory");
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    // the contraction of mu_lev (in P) with phi_lev on the tile's points
-    // (the copy of level lev complete and visible)
-    auto contract = [&](int lev) {
-        const float4 *pb = phs + (lev & 1) * (T + 2) * 32;
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        // ring rows of region rows r0 - 1 .. r0 + RL (ring row = region row - (D - 1))
-        auto ring_row = [&](int ri) { return (ri >= D - 1 && ri <= D + T) ? pb[(ri - (D - 1)) * 32 + lane] : z4; };
-        float4 up4 = ring_row(r0 - 1), c4 = ring_row(r0);
-#pragma unroll
-        for (int i = 0; i < RL; ++i) {
-            const float4 dn4 = ring_row(r0 + i + 1);
-            if (row_in(r0 + i)) {
-                // column 2 lane - 1 (lane - 1's second) and 2 lane + 2 (lane + 1's first)
-                const float2 pl = shfl2(make_float2(c4.z, c4.w), (lane + 31) & 31);
-                const float2 pr = shfl2(make_float2(c4.x, c4.y), (lane + 1) & 31);
-                const float2 c[2] = {make_float2(c4.x, c4.y), make_float2(c4.z, c4.w)};
-                const float2 up[2] = {make_float2(up4.x, up4.y), make_float2(up4.z, up4.w)};
-                const float2 dn[2] = {make_float2(dn4.x, dn4.y), make_float2(dn4.z, dn4.w)};
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    if (!col_in[k]) continue;
-                    const float2 u = P[i][k];
-                    const float d = dotf(u, c[k]);
-                    racc[i][0] += d;
-                    racc[i][1] += dotf(u, dn[k]);
-                    racc[i][2] += dotf(u, up[k]);
-                    cacc[k][0] += d;
-                    cacc[k][1] += dotf(u, k ? pr : c[1]);
-                    cacc[k][2] += dotf(u, k ? c[0] : pl);
-                }
-            }
-            up4 = c4;
-            c4 = dn4;
-        }
-    };
-    // the first contraction level (the init level, or the first stage's),
-    // and after the init level the first stage's (the other buffer)
-    prefetch(a.init ? a.a_in : a.a_in - 1);
-    if (a.init) prefetch(a.a_in - 1);
-
     if (MU && a.init) {
         const float2 co = a.co[a.a_in + 1];
 #pragma unroll
@@ -248,22 +171,16 @@ __global__ void __launch_bounds__(32 * W, MODE == kMuContract ? 2 : 3) adj_chain
             P[i][0] = cmulf(co, make_float2(q.x, q.y));
             P[i][1] = cmulf(co, make_float2(q.z, q.w));
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();
-        if (CON) {
-            contract(a.a_in);
-        } else {
-            // the first level's tile
-            float2 *dst = a.mlev[a.a_in] + base;
+        // the first level's tile
+        float2 *dst = a.mlev[a.a_in] + base;
 #pragma unroll
-            for (int i = 0; i < RL; ++i) {
-                const int ri = r0 + i;
-                if (!row_in(ri)) continue;
-                const int64_t grow = (int64_t)x_row[ri] * N;
+        for (int i = 0; i < RL; ++i) {
+            const int ri = r0 + i;
+            if (!row_in(ri)) continue;
+            const int64_t grow = (int64_t)x_row[ri] * N;
 #pragma unroll
-                for (int k = 0; k < 2; ++k)
-                    if (col_in[k]) dst[grow + X2[k]] = P[i][k];
-            }
+            for (int k = 0; k < 2; ++k)
+                if (col_in[k]) dst[grow + X2[k]] = P[i][k];
         }
     }
 
@@ -277,9 +194,7 @@ __global__ void __launch_bounds__(32 * W, MODE == kMuContract ? 2 : 3) adj_chain
         float4 *eb = edge + (par * W + warp) * 2 * 32;
         eb[lane] = make_float4(P[0][0].x, P[0][0].y, P[0][1].x, P[0][1].y);
         eb[32 + lane] = make_float4(P[RL - 1][0].x, P[RL - 1][0].y, P[RL - 1][1].x, P[RL - 1][1].y);
-        if (CON) asm volatile("cp.async.wait_all;" ::: "memory");   // level lev's phi
         __syncthreads();
-        if (CON) prefetch(lev - 1);
         const float4 u4 = warp > 0 ? edge[(par * W + warp - 1) * 2 * 32 + 32 + lane] : zero[lane];
         const float4 d4 = warp < W - 1 ? edge[(par * W + warp + 1) * 2 * 32 + lane] : zero[lane];
         float2 prev[2] = {make_float2(u4.x, u4.y), make_float2(u4.z, u4.w)};
@@ -323,7 +238,7 @@ __global__ void __launch_bounds__(32 * W, MODE == kMuContract ? 2 : 3) adj_chain
             }
         }
         const bool last = d == a.n_stages;
-        if (!MU || (a.final && last) || (MODE == kMuStore && lev >= 0)) {
+        if (!MU || lev >= 0 || (a.final && last)) {
             // the phi level, lambda_n, or the stored mu level, on the tile
             float2 *dst = !MU ? a.lev[lev] + base : (lev < 0 ? a.out + base : a.mlev[lev] + base);
 #pragma unroll
@@ -335,56 +250,6 @@ __global__ void __launch_bounds__(32 * W, MODE == kMuContract ? 2 : 3) adj_chain
                 for (int k = 0; k < 2; ++k)
                     if (col_in[k]) dst[grow + X2[k]] = P[i][k];
             }
-        }
-        if (CON && lev >= 0) contract(lev);
-    }
-    if (CON && !a.final) {
-        // the tile of the launch's last level
-#pragma unroll
-        for (int i = 0; i < RL; ++i) {
-            const int ri = r0 + i;
-            if (!row_in(ri)) continue;
-            const int64_t grow = base + (int64_t)x_row[ri] * N;
-#pragma unroll
-            for (int k = 0; k < 2; ++k)
-                if (col_in[k]) a.out[grow + X2[k]] = P[i][k];
-        }
-    }
-    if (CON) {
-        // rows: the warp's 8 rows x 3 sums over its 64 columns, value 4 i + q
-        // in lane 4 i + q; then into the tile's FP64 slots (tile column index)
-        double *tg = a.tg + (int64_t)blockIdx.z * a.tg_per_real;
-        float v[32];
-#pragma unroll
-        for (int i = 0; i < RL; ++i) {
-            v[4 * i] = racc[i][0];
-            v[4 * i + 1] = racc[i][1];
-            v[4 * i + 2] = racc[i][2];
-            v[4 * i + 3] = 0.f;
-        }
-        const float tot = warp_sum32_f(v, lane);
-        {
-            const int i = lane >> 2, q = lane & 3, ri = r0 + i;
-            if (q < 3 && row_in(ri)) {
-                double *slot = tg + ((int64_t)blockIdx.x * N + (x1_0 + ri)) * 3 + q;
-                *slot += (double)tot;
-            }
-        }
-        // columns: over the warps through shared memory, then into the tile's
-        // FP64 slots (tile row index)
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-#pragma unroll
-            for (int q = 0; q < 3; ++q) colsum[(warp * 64 + 2 * lane + k) * 3 + q] = cacc[k][q];
-        __syncthreads();
-        for (int t = threadIdx.x; t < 64 * 3; t += blockDim.x) {
-            const int ck = t / 3, q = t - 3 * (t / 3);
-            if (ck < D || ck >= D + T2 || x2_0 + ck >= N) continue;
-            float s = 0.f;
-#pragma unroll
-            for (int w = 0; w < W; ++w) s += colsum[(w * 64 + ck) * 3 + q];
-            double *slot = tg + (int64_t)a.tiles_x * N * 3 + ((int64_t)blockIdx.y * N + (x2_0 + ck)) * 3 + q;
-            *slot += (double)s;
         }
     }
 }
@@ -567,8 +432,8 @@ ChainShape chain_shape() {
     s.T = RS - 2 * D;
     s.T2 = 64 - 2 * D;
     s.threads = 32 * W;
-    s.phi = adj_chain_kernel<D, W, kPhi>;
-    s.mu = adj_chain_kernel<D, W, kMuStore>;
+    s.phi = adj_chain_kernel<D, W, false>;
+    s.mu = adj_chain_kernel<D, W, true>;
     s.smem_phi = sizeof(float4) * (2 * W * 2 * 32 + 32 + RS + 1) + sizeof(int) * RS;
     s.smem_mu = s.smem_phi + sizeof(float4) * RS * 32;
     return s;
@@ -602,9 +467,6 @@ ChainArgs chain_args(const ctqw_hamiltonian *h, double dt) {
         a.co[k] = make_float2((float)(q == 0 ? mag : (q == 2 ? -mag : 0.0)),
                               (float)(q == 1 ? mag : (q == 3 ? -mag : 0.0)));
     }
-    a.tg = nullptr;
-    a.tg_per_real = 0;
-    a.tiles_x = 0;
     a.dt = (float)dt;
     a.dtU = (float)(dt * h->U);
     a.a_in = 0;
