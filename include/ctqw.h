@@ -379,7 +379,10 @@ int ctqw_propagate_taylor_noalloc(const ctqw_hamiltonian *h, int32_t dtype, void
 
 /*
  * Workspace bytes of ctqw_adjoint_grad: (ceil(n_steps / checkpoint_every) +
- * checkpoint_every + K + 7) states plus 2 p_width + 2 sum_r N_r doubles.
+ * checkpoint_every + K + 7) states plus 2 p_width + 2 sum_r N_r doubles; in
+ * CTQW_C64 with two particles (the register-tile path) also K states for the
+ * mu levels of a step and sum_r (ceil(N_r / 64) + ceil(N_r / 16)) N_r 3
+ * doubles of per-tile gradient sums.
  */
 int ctqw_adjoint_workspace_size(const ctqw_hamiltonian *h, int32_t dtype, int32_t K,
                                 int64_t n_steps, int32_t checkpoint_every, size_t *bytes);
