@@ -106,7 +106,7 @@ typedef struct {
     int32_t n_particles;        /* m: 2 or 3                                        */
     int32_t statistics;         /* CTQW_DISTINGUISHABLE / BOSONS / FERMIONS          */
     int32_t periodic;           /* 0 open chain, 1 ring                              */
-    int32_t n_realizations;     /* R >= 1                                           */
+    int32_t n_realizations;     /* 1 <= R <= 65535                                  */
     const int32_t *n_sites;     /* host [R] sites per realization, or NULL           */
     int32_t n_sites_uniform;    /* used when n_sites is NULL                         */
     int32_t round_to_f32;       /* nonzero: round disorder to float32 values         */
