@@ -47,9 +47,9 @@ struct ChainArgs {
     const float *eps, *J;             // float32 parameters (packed per realization)
     const float2 *in;                 // input level on the region (null: the mu chain's first level)
     const float2 *q;                  // mu chain: lambda_{n+1}
-    float2 *out;                      // last level of the launch (tile); lambda_n when final
-    float2 *lev[kMaxLevels];          // phi_a (a = 0: psi_n): written by the phi chain, read by the mu chain
-    float2 *mlev[kMaxLevels];         // mu_a: written by the storing mu chain, read by adj_contract_kernel
+    float2 *out;                      // mu chain: lambda_n (the final launch's last stage)
+    float2 *lev[kMaxLevels];          // phi_a (a = 0: psi_n), written by the phi chain
+    float2 *mlev[kMaxLevels];         // mu_a, written by the mu chain
     float2 co[kMaxLevels + 1];        // i^k / k!
     float dt, dtU;
     int a_in;                         // level of the launch's initial iterate
