@@ -9,6 +9,17 @@ TOL_FP32 = 2e-6
 TOL_NORM_DRIFT = 1e-6
 U_FP32 = 2.0 ** -24       # unit roundoff of FP32
 
+# The tensor-core one-body density (Sec. 4 builds <rho> with a single-
+# precision Hermitian update): each real product from three TF32 piece
+# products (the dropped and rounded pieces at most ~2^-21 of it), summed in
+# FP32 in tensor memory over blocks of 256 k, then in two-word FP32 and FP64.
+# The tensor cores' FP32 accumulation may round every add toward zero (a
+# dense random state at N = 2048 shows a one-sided 4.6e-6 on the diagonal),
+# so a block carries up to 256 ulp = 256 * 2^-23 of its sum of |terms|,
+# itself at most the largest element of rho1 (Cauchy-Schwarz on the
+# diagonal).
+TOL_TC = 256 * 2.0 ** -23
+
 
 def h_bound(w):
     """Upper bound of ||H||_2 from the workload's description (Gershgorin on

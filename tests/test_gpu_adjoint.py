@@ -85,7 +85,8 @@ def test_adjoint_fp32_states_fp64_accumulation(ctqw):
     assert np.max(np.abs(gJ[:, :w.N - 1] - gJ_o)) <= 1e-5 * scale
 
 
-@pytest.mark.parametrize("N,periodic,K,n_steps", [(120, False, 14, 5), (110, True, 5, 6), (57, False, 9, 4)])
+@pytest.mark.parametrize("N,periodic,K,n_steps", [(120, False, 14, 5), (110, True, 5, 6), (57, False, 9, 4),
+                                                   (57, False, 1, 3), (57, True, 2, 3)])
 def test_adjoint_fp32_register_tiles_span_several_tiles(ctqw, N, periodic, K, n_steps):
     """The c64 two-particle adjoint runs on register tiles (a 64 x 64 region,
     a tile of 64 - 2D per side): sizes that need several tiles per side and a

@@ -8,7 +8,7 @@ import pytest
 
 import ctqw_workloads as cw
 import oracle
-from gpu_helpers import TOL_FP32
+from gpu_helpers import TOL_FP32, TOL_TC
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -104,7 +104,8 @@ def test_null_arguments_rejected(ctqw):
 def test_tensor_cores_against_oracle_and_cuda_cores(ctqw, name, kw):
     """The tcgen05 path (TF32, three piece products, FP32 partials over at
     most 256 k, two-word totals) against the oracle on the same final states
-    and against the CUDA-core kernel, at the FP32 tolerance."""
+    and against the CUDA-core kernel, at the bound of its FP32 partial
+    sums (TOL_TC); the CUDA-core kernel at the FP32 tolerance."""
     w = cw.get(name).with_(**kw)
     h = ctqw.build_for_workload(w)
     assert all(int(n) % 16 == 0 for n in h.group_sizes)
@@ -120,9 +121,34 @@ def test_tensor_cores_against_oracle_and_cuda_cores(ctqw, name, kw):
     ref = _oracle_rho_from(psi.cpu().numpy(), h.st_off, h.sizes, [int(n) for n in h.group_sizes], w.m)
     for a, c, b in zip(tc, cc, ref):
         scale = np.max(np.abs(b))
-        assert np.max(np.abs(a - b)) <= TOL_FP32 * scale, np.max(np.abs(a - b)) / scale
-        assert np.max(np.abs(a - c)) <= TOL_FP32 * scale
-        assert np.max(np.abs(a - a.conj().T)) <= TOL_FP32 * scale
+        assert np.max(np.abs(c - b)) <= TOL_FP32 * scale   # the CUDA cores (FP64 sums)
+        assert np.max(np.abs(a - b)) <= TOL_TC * scale, np.max(np.abs(a - b)) / scale
+        assert np.max(np.abs(a - c)) <= TOL_TC * scale
+        assert np.max(np.abs(a - a.conj().T)) <= TOL_TC * scale
     with pytest.raises(ctqw.CtqwError):
         ctqw.ctqw_set_density_method(h, 2)
+    h.close()
+
+
+def test_tensor_cores_at_the_largest_size(ctqw):
+    """N = 2048, the largest size of the tcgen05 path (16 x 16 tiles, 136 of
+    them computed), on a dense seeded random state, against the oracle at
+    the bound of the FP32 partial sums (TOL_TC): every block of 256 k then
+    carries terms of one size, the case that shows the accumulation's
+    rounding most."""
+    w = cw.get("bosons_small").with_(N=2048, R=1, statistics=cw.DISTINGUISHABLE, sites=(1000, 1001),
+                                     n_steps=1, obs_every=1)
+    h = ctqw.build_for_workload(w)
+    rng = np.random.default_rng(11)
+    v = (rng.standard_normal(2048 * 2048) + 1j * rng.standard_normal(2048 * 2048)).astype(np.complex64)
+    v /= np.sqrt(np.sum(np.abs(v.astype(np.complex128)) ** 2))
+    psi = h.new_state(cw.C64)
+    psi.copy_(torch.from_numpy(v).to(psi.device))
+    ctqw.ctqw_set_density_method(h, 0)
+    got = ctqw.ctqw_one_body_density(h, psi, cw.C64)[0].cpu().numpy()
+    ctqw.ctqw_check_status(h)
+    ref = oracle.one_body_density(v.astype(np.complex128), 2048, 2)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) <= TOL_TC * scale, np.max(np.abs(got - ref)) / scale
+    assert np.max(np.abs(got - got.conj().T)) <= TOL_TC * scale
     h.close()
