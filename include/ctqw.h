@@ -325,7 +325,9 @@ int ctqw_propagate_rk4(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, 
  * tensor cores (tcgen05, TF32): each FP32 amplitude is split into two TF32
  * pieces and every product formed from three piece products (~2^-22
  * relative), accumulated in FP32 in tensor memory over at most 256 k and
- * then in two-word FP32 totals and FP64 (see ctqw_set_density_method; it
+ * then in two-word FP32 totals and FP64: within 256 x 2^-23 of the largest
+ * element (the tensor cores' FP32 adds may round toward zero; the CUDA-core
+ * kernel sums in FP64) (see ctqw_set_density_method; it
  * allocates a scratch of 256 KB per CTA stream-ordered).  Otherwise products
  * in the state's type over chunks of 32 (16 in FP64), accumulated in FP64,
  * on CUDA cores.  m = 2 or 3.  Asynchronous.  Errors: EINVAL for null

@@ -25,7 +25,10 @@
 //  - warps 9-12 drain: every 256 k the MMAs switch to the other of two TMEM
 //    accumulators, and the drain warps add the finished FP32 partials into
 //    the CTA's running totals, kept as two FP32 words (TwoSum) in a global
-//    slot of its own, so the totals carry ~2^-44 of relative rounding.
+//    slot of its own, so the totals carry ~2^-44 of relative rounding.  A
+//    block's FP32 sum in TMEM can be off by up to 256 ulp of its sum of
+//    |terms| (the adds may round toward zero): at most 256 x 2^-23 of the
+//    largest element of rho1.
 // A second kernel sums the slots of all CTAs in FP64 and fills the lower
 // triangle.  Every wait is bounded in time (status word, then the CTA stops).
 #include <cstdint>
