@@ -178,6 +178,22 @@ def test_fused_c64_shapes(ctqw, N, periodic, K):
         assert np.max(np.abs(P[r] - ref["P"][r][-1])) <= TOL_FP32
 
 
+@pytest.mark.parametrize("name,kw", [
+    ("bosons_small", {"K": 1}), ("bosons_small", {"K": 2}), ("bosons_small", {"K": 30}),     # fused, N = 64
+    ("bosons_small", {"N": 96, "sites": (47, 48), "K": 1}),                                   # register tiles
+    ("bosons_small", {"N": 96, "sites": (47, 48), "K": 30}),
+    ("ring3_small", {"K": 1}), ("ring3_small", {"K": 30}),                                    # m = 3 stages
+])
+def test_c64_orders_at_the_ends_of_the_range(ctqw, name, kw):
+    """K = 1 (one final stage), K = 2 and K = 30 (the largest order) on each
+    FP32 path against the oracle (the order-1 map is not unitary: both sides
+    follow the same norm)."""
+    w = cw.get(name).with_(R=2, n_steps=10, obs_every=5, **kw)
+    got = ctqw.run_workload(w)
+    ref = oracle.ensemble_run(w)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, energy_tol(w))
+
+
 def test_fused_c64_distinguishable_open(ctqw):
     w = cw.get("fp64_plain_small").with_(dtype=cw.C64, n_steps=300, obs_every=30)
     got = ctqw.run_workload(w)
