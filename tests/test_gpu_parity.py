@@ -194,6 +194,27 @@ def test_c64_orders_at_the_ends_of_the_range(ctqw, name, kw):
     _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, energy_tol(w))
 
 
+@pytest.mark.parametrize("name,kw", [
+    ("bosons_small", {"sites": (20, 41)}),                                        # fused, N = 64
+    ("bosons_small", {"N": 96, "sites": (30, 61)}),                               # register tiles
+    ("ring3_small", {"sites": (2, 5, 9)}),                                        # m = 3 stages
+])
+def test_c64_fermions_stay_antisymmetric(ctqw, name, kw):
+    """Fermions (an antisymmetrised initial state) on each FP32 path: the
+    oracle's P, norm and energy, and psi odd under every exchange of two
+    particles (zero where two coordinates coincide)."""
+    w = cw.get(name).with_(statistics=cw.FERMIONS, R=2, n_steps=30, obs_every=10, **kw)
+    got = ctqw.run_workload(w)
+    ref = oracle.ensemble_run(w)
+    _compare(got, ref, TOL_FP32, TOL_NORM_DRIFT, energy_tol(w))
+    N, m = w.N, w.m
+    psi = got["psi"][got["st_off"][0]:got["st_off"][1]].reshape((N,) * m)
+    scale = np.max(np.abs(psi))
+    perms = [(1, 0)] if m == 2 else [(1, 0, 2), (0, 2, 1), (2, 1, 0)]
+    for perm in perms:
+        assert np.max(np.abs(psi + np.transpose(psi, perm))) <= 1e-6 * scale
+
+
 def test_fused_c64_distinguishable_open(ctqw):
     w = cw.get("fp64_plain_small").with_(dtype=cw.C64, n_steps=300, obs_every=30)
     got = ctqw.run_workload(w)
