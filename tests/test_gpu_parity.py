@@ -215,6 +215,37 @@ def test_c64_fermions_stay_antisymmetric(ctqw, name, kw):
         assert np.max(np.abs(psi + np.transpose(psi, perm))) <= 1e-6 * scale
 
 
+def test_fused_snapshot_slots_do_not_change_the_result(ctqw):
+    """The fused path runs S + 1 sampling intervals per launch with S
+    snapshot slots in the workspace (S = bytes / state - 1): S = 0, 2 and 7
+    on 47 steps sampled every 3 (launches that end mid-interval and a last
+    short one) give the same state bit for bit, the same samples up to the
+    order of the FP64 atomics that combine blocks, and match the oracle."""
+    w = cw.get("bosons_small").with_(R=3, n_steps=47, obs_every=3)
+    ref = oracle.ensemble_run(w)
+    outs = []
+    for S in (0, 2, 7):
+        h = ctqw.build_for_workload(w)
+        psi = h.new_state(cw.C64)
+        ctqw.ctqw_init_state(h, psi, ctqw.initial_sites(w, h), cw.C64)
+        n_obs = h.n_obs(w.n_steps, w.obs_every)
+        P = torch.empty((n_obs, h.p_width), dtype=torch.float64, device="cuda")
+        nr = torch.empty((n_obs, h.R), dtype=torch.float64, device="cuda")
+        en = torch.empty((n_obs, h.R), dtype=torch.float64, device="cuda")
+        ws = torch.empty((S + 1) * psi.numel() * 8, dtype=torch.uint8, device="cuda")
+        ctqw.ctqw_propagate_taylor(h, psi, cw.C64, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en, 0, ws)
+        ctqw.ctqw_check_status(h)
+        outs.append([t.cpu().numpy() for t in (psi, P, nr, en)])
+        h.close()
+    for other in outs[1:]:
+        assert np.array_equal(outs[0][0], other[0])          # the state, bit for bit
+        for a, b in zip(outs[0][1:], other[1:]):             # FP64 sums (atomic order)
+            assert np.max(np.abs(a - b)) <= 1e-13
+    assert np.max(np.abs(outs[0][1] - ref["P_mean"])) <= TOL_FP32
+    assert np.max(np.abs(outs[0][2] - ref["norm"].T)) <= TOL_NORM_DRIFT
+    assert np.max(np.abs(outs[0][3] - ref["energy"].T)) <= energy_tol(w)
+
+
 def test_fused_c64_distinguishable_open(ctqw):
     w = cw.get("fp64_plain_small").with_(dtype=cw.C64, n_steps=300, obs_every=30)
     got = ctqw.run_workload(w)
