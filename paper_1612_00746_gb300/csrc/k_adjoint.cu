@@ -148,84 +148,6 @@ __global__ void __launch_bounds__(256) grad_kernel(RealTable tab, const cplx_t<T
     }
 }
 
-// The same gradient for two particles in FP32 states: a block owns kGradRows
-// rows x1 and up to 256 columns x2 of one realization.  Products are formed
-// in FP32 (operands are FP32); each thread sums its column's contributions
-// over the block's rows in FP32 registers and each warp its rows' sums, and
-// the block adds them to the FP64 gradients with one atomic per site (the
-// time and ensemble sums stay in FP64).
-constexpr int kGradRows = 32;
-
-
-__global__ void __launch_bounds__(256) grad2_kernel(RealTable tab, const int32_t *__restrict__ list,
-                                                    const float2 *__restrict__ mu,
-                                                    const float2 *__restrict__ phi,
-                                                    double *grad_eps, double *grad_J) {
-    __shared__ float row_e[kGradRows], row_j[kGradRows];
-    const int r = list[blockIdx.z];
-    const int N = tab.N[r];
-    const int x1_0 = blockIdx.x * kGradRows;
-    const int x2 = blockIdx.y * blockDim.x + threadIdx.x;
-    const bool live = x2 < N;
-    const bool ring = tab.periodic != 0;
-    for (int i = threadIdx.x; i < kGradRows; i += blockDim.x) row_e[i] = row_j[i] = 0.f;
-    __syncthreads();
-    const int64_t base = tab.st_off[r];
-    const float2 *u_ = mu + base, *p_ = phi + base;
-    const int x2n = (x2 + 1 == N) ? 0 : x2 + 1;
-    const bool bond2 = live && (ring || x2 < N - 1);
-    float col_e = 0.f, col_j = 0.f;
-    const int rows = min(kGradRows, N - x1_0);
-    float2 u = make_float2(0.f, 0.f), p = u;
-    if (live) {
-        u = u_[(int64_t)x1_0 * N + x2];
-        p = p_[(int64_t)x1_0 * N + x2];
-    }
-    for (int i = 0; i < rows; ++i) {
-        const int x1 = x1_0 + i;
-        const int x1n = (x1 + 1 == N) ? 0 : x1 + 1;
-        const bool bond1 = ring || x1 < N - 1;
-        float2 un = make_float2(0.f, 0.f), pn = un;   // row x1+1 (next iteration's row)
-        float d = 0.f, h1 = 0.f, h2 = 0.f;
-        if (live) {
-            un = u_[(int64_t)x1n * N + x2];
-            pn = p_[(int64_t)x1n * N + x2];
-            d = u.x * p.x + u.y * p.y;
-            if (bond1) h1 = u.x * pn.x + u.y * pn.y + un.x * p.x + un.y * p.y;
-            if (bond2) {
-                const float2 ur = u_[(int64_t)x1 * N + x2n], pr = p_[(int64_t)x1 * N + x2n];
-                h2 = u.x * pr.x + u.y * pr.y + ur.x * p.x + ur.y * p.y;
-            }
-        }
-        col_e += 2.f * d;      // particle 2 on site x2
-        col_j -= 2.f * h2;     // particle 2 across bond x2
-        // particle 1 on site x1 / across bond x1: the row's sum
-        float se = 2.f * d, sj = -2.f * h1;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            se += __shfl_xor_sync(0xffffffffu, se, o);
-            sj += __shfl_xor_sync(0xffffffffu, sj, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(row_e + i, se);
-            atomicAdd(row_j + i, sj);
-        }
-        u = un;
-        p = pn;
-    }
-    const int64_t po = tab.par_off[r];
-    if (live) {
-        atomicAdd(grad_eps + po + x2, (double)col_e);
-        if (bond2) atomicAdd(grad_J + po + x2, (double)col_j);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-        const int x1 = x1_0 + i;
-        atomicAdd(grad_eps + po + x1, (double)row_e[i]);
-        if (ring || x1 < N - 1) atomicAdd(grad_J + po + x1, (double)row_j[i]);
-    }
-}
-
 // loss = sum_x (Pbar - P*)^2 over all groups; diff = Pbar - P*.  One block.
 __global__ void loss_kernel(const double *__restrict__ Pbar, const double *__restrict__ target,
                             int64_t n, double *diff, double *loss) {
@@ -325,21 +247,6 @@ int launch_grad(const ctqw_hamiltonian *h, int dtype, const void *mu, const void
                 double *grad_eps, double *grad_J, cudaStream_t s) {
     dim3 g = grid_for(h), b(256);
     RealTable t = real_table(h);
-    if (dtype == CTQW_C64 && h->m == 2) {
-        // one launch per size group: (row blocks, column blocks, realizations)
-        int off = 0;
-        for (size_t gi = 0; gi < h->group_N.size(); ++gi) {
-            const int N = h->group_N[gi], cnt = h->group_count[gi];
-            const int tx = N >= 256 ? 256 : ((N + 31) / 32) * 32;
-            const dim3 grid((unsigned)((N + kGradRows - 1) / kGradRows), (unsigned)((N + tx - 1) / tx),
-                            (unsigned)cnt);
-            grad2_kernel<<<grid, tx, 0, s>>>(t, h->by_group_d + off, (const float2 *)mu,
-                                             (const float2 *)phi, grad_eps, grad_J);
-            CTQW_CUDA_TRY(cudaGetLastError());
-            off += cnt;
-        }
-        return CTQW_OK;
-    }
     if (dtype == CTQW_C64) {
         auto k = h->m == 2 ? grad_kernel<float, 2> : grad_kernel<float, 3>;
         k<<<g, b, 0, s>>>(t, (const float2 *)mu, (const float2 *)phi, grad_eps, grad_J);
