@@ -270,9 +270,8 @@ int launch_horner_stage(const ctqw_hamiltonian *h, const void *in, const void *p
     if (h->m == 3) return launch_horner3_rows<false>(h, in, psi, out, nullptr, coef, s);
     RealTable t = real_table(h);
     return for_each_group(h, [&](dim3 grid, dim3 block, const int32_t *list) {
-        auto k = h->m == 2 ? horner_stage_kernel<2> : horner_stage_kernel<3>;
-        k<<<grid, block, 0, s>>>(t, list, h->eps32, h->J32, (const float2 *)in, (const float2 *)psi,
-                                 (float2 *)out, (float)coef);
+        horner_stage_kernel<2><<<grid, block, 0, s>>>(t, list, h->eps32, h->J32, (const float2 *)in,
+                                                      (const float2 *)psi, (float2 *)out, (float)coef);
     });
 }
 
@@ -281,8 +280,7 @@ int launch_horner_final(const ctqw_hamiltonian *h, const void *w2, void *psi, vo
     if (h->m == 3) return launch_horner3_rows<true>(h, w2, nullptr, psi, lo, dt, s);
     RealTable t = real_table(h);
     return for_each_group(h, [&](dim3 grid, dim3 block, const int32_t *list) {
-        auto k = h->m == 2 ? horner_final_kernel<2> : horner_final_kernel<3>;
-        k<<<grid, block, 0, s>>>(t, list, h->eps32, h->J32, (const float2 *)w2, (float2 *)psi,
-                                 (float2 *)lo, (float)dt);
+        horner_final_kernel<2><<<grid, block, 0, s>>>(t, list, h->eps32, h->J32, (const float2 *)w2,
+                                                      (float2 *)psi, (float2 *)lo, (float)dt);
     });
 }
