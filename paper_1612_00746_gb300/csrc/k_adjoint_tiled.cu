@@ -229,9 +229,9 @@ __global__ void __launch_bounds__(32 * W, 3) adj_chain_kernel(const __grid_const
             prev[1] = c1;
             if (MU) {
                 const float4 q = Q[(r0 + i) * 32 + lane];
-                const float2 q0 = cmulf(co, make_float2(q.x, q.y)), q1 = cmulf(co, make_float2(q.z, q.w));
-                P[i][0] = make_float2(q0.x + y0.x, q0.y + y0.y);
-                P[i][1] = make_float2(q1.x + y1.x, q1.y + y1.y);
+                // co lambda + y as four fused multiply-adds per amplitude
+                P[i][0] = make_float2(fmaf(co.x, q.x, fmaf(-co.y, q.y, y0.x)), fmaf(co.x, q.y, fmaf(co.y, q.x, y0.y)));
+                P[i][1] = make_float2(fmaf(co.x, q.z, fmaf(-co.y, q.w, y1.x)), fmaf(co.x, q.w, fmaf(co.y, q.z, y1.y)));
             } else {
                 P[i][0] = y0;
                 P[i][1] = y1;
