@@ -475,6 +475,12 @@ def run_ours(args):
         # reduction kernel per sample
         per_launch = (slots + 1) * w.obs_every if w.obs_every else w.n_steps
         launches_per_step = 1 + -(-w.n_steps // per_launch) + n_obs
+    # the fused path's second stream: register tiles for the last realizations
+    # (ceil(K / D) launches a step) and their own reduction per sample
+    split = ctqw.ctqw_fused_split(h, w.K, args.flags) if path == "rows" and slots >= 2 else 0
+    if split:
+        tile_depth = -(-w.K // -(-w.K // 8))   # the stages split evenly over ceil(K / 8) launches
+        launches_per_step += w.n_steps * -(-w.K // tile_depth) + n_obs
     if args.switch is not None:
         launches_per_step += 1 + w.n_steps   # parameter restore + one update per step
     launches_per_step += 1   # the norm check of the sampled norms
@@ -529,18 +535,32 @@ def run_ours(args):
         step(record=True)
     t1.record(stream)
     torch.cuda.synchronize()
-    # the fused kernel alone (one launch over all steps, no sampling), for
-    # its roofline: the timed calls above interleave it with the reductions
+    # the fused kernel alone (one launch over all steps and realizations, no
+    # sampling, no second stream), for its roofline: the timed calls above
+    # interleave it with the reductions and the second stream's tiles
     kernel_alone_ms = None
+    one_stream = None
     if path == "rows" and graph is None:
         ctqw.ctqw_init_state(h, psi, sites, dtype)
         k0 = torch.cuda.Event(enable_timing=True)
         k1 = torch.cuda.Event(enable_timing=True)
         k0.record(stream)
-        ctqw.ctqw_propagate_taylor(h, psi, dtype, w.dt, w.K, w.n_steps, 0, None, None, None, args.flags, ws)
+        ctqw.ctqw_propagate_taylor(h, psi, dtype, w.dt, w.K, w.n_steps, 0, None, None, None,
+                                   args.flags | ctqw.FLAG_ONE_STREAM, ws)
         k1.record(stream)
         torch.cuda.synchronize()
         kernel_alone_ms = k0.elapsed_time(k1)
+        if split:
+            # the same bench step with every realization on the clusters
+            ctqw.ctqw_init_state(h, psi, sites, dtype)
+            k0.record(stream)
+            ctqw.ctqw_propagate_taylor(h, psi, dtype, w.dt, w.K, w.n_steps, w.obs_every, P, nr, en,
+                                       args.flags | ctqw.FLAG_ONE_STREAM, ws)
+            k1.record(stream)
+            torch.cuda.synchronize()
+            one_ms = k0.elapsed_time(k1)
+            one_stream = {"value": world * units_per_step / (one_ms / 1000.0), "ms": one_ms,
+                          "what": "the same step, every realization on the clusters (CTQW_FLAG_ONE_STREAM)"}
     clk = clocks.stop()
     if world > 1:
         dist.barrier()
@@ -706,6 +726,10 @@ def run_ours(args):
                    "launch": "cuda graph replay" if args.graph else "eager",
                    "switching_noise_p": args.switch},
         "gpu_launches": launches_per_step * args.steps,
+        "fused_split": ({"clusters_realizations": w.R - split, "tiles_realizations": split,
+                         "what": "the last realizations on the register tiles on a second stream, "
+                                 "on the SMs no 16-CTA cluster can hold"} if path == "rows" else None),
+        "one_stream": one_stream,
         "roofline": roofline,
         "e2e": e2e,
         "cpu_baseline": cpu,

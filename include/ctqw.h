@@ -65,6 +65,8 @@ extern "C" {
                                           launches per step; sampled norms are then 1 up to rounding */
 #define CTQW_FLAG_TEST_WAIT_TIMEOUT 0x8 /* failure-path test: the fused kernel first waits on an mbarrier that
                                            nothing completes, gives up after 1 ms and flags the handle */
+#define CTQW_FLAG_ONE_STREAM 0x10      /* fused path: run every realization on the clusters, on the caller's
+                                          stream alone (see ctqw_fused_split) */
 /* Fused path tuning: CTQW_FUSED_SHAPE(k) selects a compiled CTA/cluster shape
  * for the lattice size.  k = 0..2: full-row kernel (each warp owns whole rows;
  * 0 = default, the fastest measured for the size; 1 and 2 = other splits of
@@ -237,7 +239,12 @@ int ctqw_autotune_order(const ctqw_hamiltonian *h, int32_t dtype, double dt, int
  * sample points into the others (S = workspace_bytes / state bytes - 1
  * slots); one launch covers S + 1 sampling intervals, so a larger
  * workspace means fewer launches.  Given no workspace, the fused path
- * allocates its 3 states stream-ordered.  The
+ * allocates its 3 states stream-ordered.  With S >= 2 and enough
+ * realizations, the fused path also runs the last ctqw_fused_split
+ * realizations on the register tiles, on a second stream of the handle that
+ * it forks from and joins back to `stream` (so the call stays ordered on
+ * `stream`, also under graph capture): those tiles fill the SMs that no
+ * cluster can hold.  Overlapping calls on one handle share that stream.  The
  * per-term path runs in CTQW_C128 in the order of
  * Algorithm 3 (Phi^(j) from Phi^(j-1), summed forward); in CTQW_C64 as the
  * same polynomial in Horner form (w_j = Psi + (-i dt / j) H w_{j+1}, j = K..2,
@@ -249,6 +256,22 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
                           int32_t K, int64_t n_steps, int32_t obs_every, double *P_mean_dev,
                           double *norm_dev, double *energy_dev, uint32_t flags,
                           void *workspace_dev, size_t workspace_bytes, void *stream);
+
+/*
+ * How many realizations the fused path of ctqw_propagate_taylor (and of
+ * ctqw_propagate_rk4, at K = 4) hands to the register tiles on the handle's
+ * second stream, given a workspace of at least 3 states: the last *R_tiled
+ * realizations.  A 16-CTA cluster (two particles, N = 256) needs 8 SMs of
+ * one GPC, so the SMs left over in each GPC hold no cluster; the tiles get
+ * the share of realizations that their throughput on those SMs can finish
+ * in the time the clusters take for the rest (whole rounds of the resident
+ * clusters).  0 when fewer than 1/16 of the SMs are left over, when the
+ * handle has no fused path, with CTQW_FLAG_ONE_STREAM, CTQW_FLAG_PLAIN or
+ * CTQW_FLAG_RENORMALIZE, or with a shape flag.  Queries the device's
+ * occupancy; launches nothing.  Errors: CTQW_EINVAL for a null handle or
+ * pointer or K outside 1..30.
+ */
+int ctqw_fused_split(const ctqw_hamiltonian *h, int32_t K, uint32_t flags, int32_t *R_tiled);
 
 /*
  * ctqw_propagate_taylor with switching noise (Sec. 2: the stochastic terms

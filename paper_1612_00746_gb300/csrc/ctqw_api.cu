@@ -36,6 +36,11 @@ void free_device(ctqw_hamiltonian *h) {
                     h->by_group_d, h->eps_mean_d, h->J_mean_d, h->eps64_0, h->J64_0, h->sites_d};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
+    h->side = nullptr;
+    h->fork_ev = h->join_ev = nullptr;
 }
 
 template <typename T>
@@ -290,7 +295,7 @@ int ctqw_build_hamiltonian(const ctqw_lattice_desc *d, void *stream, ctqw_hamilt
         ctqw_malloc(&h->J32, sizeof(float) * h->total_par) != cudaSuccess ||
         ctqw_malloc(&h->eps64, pb) != cudaSuccess || ctqw_malloc(&h->J64, pb) != cudaSuccess ||
         ctqw_malloc(&u_eps_d, pb) != cudaSuccess || ctqw_malloc(&u_J_d, pb) != cudaSuccess ||
-        ctqw_malloc((void **)&h->status_d, 16) != cudaSuccess ||
+        ctqw_malloc((void **)&h->status_d, 32) != cudaSuccess ||
         ctqw_malloc((void **)&h->renorm_d, sizeof(double) * h->R) != cudaSuccess ||
         ctqw_malloc((void **)&h->sites_d, sizeof(int32_t) * h->R * h->m) != cudaSuccess) {
         ctqw_set_error("cudaMalloc of the parameter arrays failed");
@@ -341,6 +346,18 @@ int ctqw_build_hamiltonian(const ctqw_lattice_desc *d, void *stream, ctqw_hamilt
     if (cudaMemcpyAsync(h->eps64_0, h->eps64, pb, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(h->J64_0, h->J64, pb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return fail(CTQW_ECUDA);
+    if (fused_rows_supported(h, CTQW_C64)) {
+        // the fused path's second stream, at the lowest priority so that the
+        // clusters go first when both have work waiting
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, least) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+            ctqw_cuda_fail(cudaGetLastError(), "side stream");
+            return fail(CTQW_ECUDA);
+        }
+    }
     cudaError_t e = cudaStreamSynchronize(s);
     for (void *p : {(void *)u_eps_d, (void *)u_J_d})
         if (p) cudaFree(p);
@@ -582,10 +599,53 @@ static int propagate_per_term(const ctqw_hamiltonian *h, int32_t dtype, void *ps
     return CTQW_OK;
 }
 
-// The temporally blocked tiled kernels: ceil(K / D) launches per step.  The
-// state rotates through psi and the two iterate buffers of the workspace
-// (the new state cannot overwrite the one other tiles read as halo); the
-// carried rounding error stays in the third workspace state.
+// The step loop of the temporally blocked tiled kernels (c64) over
+// realizations r0 .. r0 + R_run - 1: ceil(K / D) launches per step.  The
+// state rotates through bufs[0] (psi) and the iterate buffers bufs[1],
+// bufs[2] (the new state cannot overwrite the one other tiles read as halo);
+// lo carries the rounding error.  The caller zeroes the outputs and lo.
+static int tiled_steps(const ctqw_hamiltonian *h, void *const bufs[3], void *lo, double dt, int32_t K,
+                       int64_t n_steps, int32_t obs_every, double *P_mean_dev, double *norm_dev,
+                       double *energy_dev, int comp, int shape, const SwitchSpec &sw, int r0, int R_run,
+                       cudaStream_t s) {
+    const int D = tiled_depth(shape);
+    int cur = 0;
+    int64_t obs = 0;
+    for (int64_t step = 0; step <= n_steps; ++step) {
+        if (obs_every > 0 && step % obs_every == 0) {
+            CTQW_TRY(launch_observables_range(h, CTQW_C64, bufs[cur], r0, R_run,
+                                              P_mean_dev ? P_mean_dev + obs * h->p_width : nullptr,
+                                              norm_dev ? norm_dev + obs * h->R : nullptr,
+                                              energy_dev ? energy_dev + obs * h->R : nullptr, s));
+            ++obs;
+        }
+        if (step == n_steps) break;
+        const int o1 = (cur + 1) % 3, o2 = (cur + 2) % 3;
+        int win = cur;
+        for (int j0 = K; j0 >= 1;) {
+            const int nst = j0 < D ? j0 : D;
+            const int final = (j0 - nst + 1 == 1) ? 1 : 0;
+            const int wout = (win == o1) ? o2 : o1;   // neither the state nor the input iterate
+            CTQW_TRY(launch_taylor_tiled_range(h, shape, bufs[win], bufs[cur], bufs[wout], lo, dt, j0, nst,
+                                               final, comp, r0, R_run, s));
+            win = wout;
+            j0 -= nst;
+            if (final) cur = wout;
+        }
+        if (sw.on) CTQW_TRY(launch_switch_params(h, sw.seed, (uint64_t)step, sw.p, s));
+    }
+    if (cur != 0) {
+        const size_t a0 = (size_t)h->st_off[r0] * sizeof(float2);
+        const size_t a1 = (size_t)h->st_off[r0 + R_run] * sizeof(float2);
+        CTQW_CUDA_TRY(cudaMemcpyAsync((char *)bufs[0] + a0, (const char *)bufs[cur] + a0, a1 - a0,
+                                      cudaMemcpyDeviceToDevice, s));
+    }
+    return CTQW_OK;
+}
+
+// The temporally blocked tiled kernels on the whole handle, with psi and the
+// two iterate buffers of the workspace; the carried rounding error stays in
+// the third workspace state.
 static int propagate_tiled(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev, double dt,
                            int32_t K, int64_t n_steps, int32_t obs_every, double *P_mean_dev,
                            double *norm_dev, double *energy_dev, uint32_t flags, int shape,
@@ -607,33 +667,8 @@ static int propagate_tiled(const ctqw_hamiltonian *h, int32_t dtype, void *psi_d
     void *lo = ws + 2 * sb;
     CTQW_CUDA_TRY(cudaMemsetAsync(lo, 0, sb, s));
     const int comp = (flags & CTQW_FLAG_NO_COMPENSATION) ? 0 : 1;
-    const int D = tiled_depth(shape);
-    int cur = 0;
-    int64_t obs = 0;
-    for (int64_t step = 0; step <= n_steps; ++step) {
-        if (obs_every > 0 && step % obs_every == 0) {
-            CTQW_TRY(launch_observables(h, dtype, bufs[cur], P_mean_dev ? P_mean_dev + obs * h->p_width : nullptr,
-                                        nullptr, norm_dev ? norm_dev + obs * h->R : nullptr,
-                                        energy_dev ? energy_dev + obs * h->R : nullptr, s));
-            ++obs;
-        }
-        if (step == n_steps) break;
-        const int o1 = (cur + 1) % 3, o2 = (cur + 2) % 3;
-        int win = cur;
-        for (int j0 = K; j0 >= 1;) {
-            const int nst = j0 < D ? j0 : D;
-            const int final = (j0 - nst + 1 == 1) ? 1 : 0;
-            const int wout = (win == o1) ? o2 : o1;   // neither the state nor the input iterate
-            CTQW_TRY(launch_taylor_tiled(h, shape, bufs[win], bufs[cur], bufs[wout], lo, dt, j0, nst,
-                                         final, comp, s));
-            win = wout;
-            j0 -= nst;
-            if (final) cur = wout;
-        }
-        if (sw.on) CTQW_TRY(launch_switch_params(h, sw.seed, (uint64_t)step, sw.p, s));
-    }
-    if (cur != 0) CTQW_CUDA_TRY(cudaMemcpyAsync(psi_dev, bufs[cur], sb, cudaMemcpyDeviceToDevice, s));
-    return CTQW_OK;
+    return tiled_steps(h, bufs, lo, dt, K, n_steps, obs_every, P_mean_dev, norm_dev, energy_dev, comp, shape,
+                       sw, 0, h->R, s);
 }
 
 // The full-row fused kernel in chunks: the workspace holds the carried
@@ -643,6 +678,13 @@ static int propagate_tiled(const ctqw_hamiltonian *h, int32_t dtype, void *psi_d
 // in FP64 by the observables kernel (from psi at the chunk boundaries, from
 // the slots inside).  Without observables it is one launch.  With no
 // workspace, one of 3 states is allocated stream-ordered.
+//
+// A 16-CTA cluster needs 8 SMs of one GPC, so some SMs hold no cluster.
+// With S >= 2 the last realizations (fused_rows_split) run meanwhile on the
+// register tiles on the handle's side stream, forked from and joined to the
+// caller's stream: the tiles use slots 1 and 2 of their own realizations as
+// iterate buffers, the clusters' snapshots only touch theirs, and both add
+// into the same zeroed P_mean rows.
 static int propagate_fused_rows(const ctqw_hamiltonian *h, void *psi_dev, double dt, int32_t K,
                                 int64_t n_steps, int32_t obs_every, double *P_mean_dev,
                                 double *norm_dev, double *energy_dev, uint32_t flags, int shape,
@@ -666,10 +708,22 @@ static int propagate_fused_rows(const ctqw_hamiltonian *h, void *psi_dev, double
     int test = (flags & CTQW_FLAG_TEST_WAIT_TIMEOUT) ? 1 : 0;
     int st = CTQW_OK;
     if (cudaMemsetAsync(lo, 0, sb, s) != cudaSuccess) st = ctqw_cuda_fail(cudaGetLastError(), "memset");
+    int R_t = 0;
+    if (st == CTQW_OK && h->side && slots >= 2 && shape == 0 && !(flags & CTQW_FLAG_ONE_STREAM))
+        st = fused_rows_split(h, shape, K, &R_t);
+    const int R_f = h->R - R_t;
+    cudaStream_t side = s;
+    if (st == CTQW_OK && R_t > 0) {
+        if (cudaEventRecord(h->fork_ev, s) != cudaSuccess || cudaStreamWaitEvent(h->side, h->fork_ev, 0) != cudaSuccess)
+            st = ctqw_cuda_fail(cudaGetLastError(), "fork of the side stream");
+        else
+            side = h->side;
+    }
     auto observe = [&](const void *state, int64_t q) {
-        return launch_observables(h, CTQW_C64, state, P_mean_dev ? P_mean_dev + q * h->p_width : nullptr,
-                                  nullptr, norm_dev ? norm_dev + q * h->R : nullptr,
-                                  energy_dev ? energy_dev + q * h->R : nullptr, s);
+        return launch_observables_range(h, CTQW_C64, state, 0, R_f,
+                                        P_mean_dev ? P_mean_dev + q * h->p_width : nullptr,
+                                        norm_dev ? norm_dev + q * h->R : nullptr,
+                                        energy_dev ? energy_dev + q * h->R : nullptr, s);
     };
     for (int64_t s0 = 0; st == CTQW_OK;) {
         if (obs_every > 0 && s0 % obs_every == 0) st = observe(psi_dev, s0 / obs_every);
@@ -678,11 +732,23 @@ static int propagate_fused_rows(const ctqw_hamiltonian *h, void *psi_dev, double
                                             : n_steps - s0;
         const int64_t inside = obs_every > 0 ? (chunk - 1) / obs_every : 0;   // snapshots of this launch
         st = launch_taylor_fused_rows(h, psi_dev, lo, inside > 0 ? w + sb : nullptr, obs_every, dt, K,
-                                      chunk, comp, shape, test, s);
+                                      chunk, comp, shape, test, 0, R_f, s);
         test = 0;
         for (int64_t q = 0; st == CTQW_OK && q < inside; ++q)
             st = observe(w + (size_t)(q + 1) * sb, s0 / obs_every + q + 1);
         s0 += chunk;
+    }
+    if (side != s) {
+        // enqueued after the clusters' work, so a full launch queue on the
+        // side stream cannot hold the clusters back
+        if (st == CTQW_OK) {
+            void *const bufs[3] = {psi_dev, w + sb, w + 2 * sb};
+            st = tiled_steps(h, bufs, lo, dt, K, n_steps, obs_every, P_mean_dev, norm_dev, energy_dev, comp,
+                             tiled_default_shape(K), SwitchSpec{}, R_f, R_t, side);
+        }
+        // joined even after an error: nothing of this call stays behind the caller's stream
+        if (cudaEventRecord(h->join_ev, side) != cudaSuccess || cudaStreamWaitEvent(s, h->join_ev, 0) != cudaSuccess)
+            if (st == CTQW_OK) st = ctqw_cuda_fail(cudaGetLastError(), "join of the side stream");
     }
     if (own) cudaFreeAsync(ws, s);
     return st;
@@ -882,6 +948,19 @@ int ctqw_propagate_taylor(const ctqw_hamiltonian *h, int32_t dtype, void *psi_de
     CTQW_TRY(propagate_taylor_impl(h, dtype, psi_dev, dt, K, n_steps, obs_every, P_mean_dev, norm_dev,
                                    energy_dev, flags, workspace_dev, workspace_bytes, stream));
     return launch_norm_check(h, norm_dev, n_samples(n_steps, obs_every), (cudaStream_t)stream);
+}
+
+int ctqw_fused_split(const ctqw_hamiltonian *h, int32_t K, uint32_t flags, int32_t *R_tiled) {
+    if (!h || !R_tiled) { ctqw_set_error("null handle or output"); return CTQW_EINVAL; }
+    if (K < 1 || K > 30) { ctqw_set_error("K must be in 1..30 (got %d)", K); return CTQW_EINVAL; }
+    *R_tiled = 0;
+    const int shape = (int)((flags >> CTQW_FUSED_SHAPE_SHIFT) & 0xF);
+    if ((flags & (CTQW_FLAG_PLAIN | CTQW_FLAG_RENORMALIZE | CTQW_FLAG_ONE_STREAM)) || shape != 0 || !h->side)
+        return CTQW_OK;
+    int r = 0;
+    CTQW_TRY(fused_rows_split(h, 0, K, &r));
+    *R_tiled = r;
+    return CTQW_OK;
 }
 
 int ctqw_propagate_taylor_switching(const ctqw_hamiltonian *h, int32_t dtype, void *psi_dev,

@@ -40,11 +40,15 @@ struct ctqw_hamiltonian {
     // status word (16 bytes): int flags at [0] (bit 0: a bounded wait gave
     // up, bit 1: the norm check failed), at byte 8 the 64-bit key of the
     // first norm failure, (realization << 40) | (sample << 8) | reason
-    int *status_d = nullptr;
+    int *status_d = nullptr;        // 32 bytes: the status word, then at int [4] the fused kernel's ticket counter
     double *renorm_d = nullptr;     // [R] norms of the per-step renormalization
     int32_t *sites_d = nullptr;     // [R][m] initial sites (ctqw_init_state)
     double norm_drift_tol = 0.0;    // norm check: |norm - norm at step 0| above this fails (0: finiteness only)
     int density_method = 0;         // one-body density: 0 tensor cores where supported, 1 CUDA cores
+    // second stream of the fused path (the realizations on the SMs that hold
+    // no cluster) and the events that fork it from and join it to the caller's
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
 
 // Per-launch view of the realization table (passed by value to kernels).
@@ -61,6 +65,8 @@ struct RealTable {
     int periodic;
     double U;
 };
+
+inline int *work_counter(const ctqw_hamiltonian *h) { return h->status_d + 4; }
 
 inline RealTable real_table(const ctqw_hamiltonian *h) {
     RealTable t;
@@ -180,6 +186,11 @@ int launch_rk4_stage(const ctqw_hamiltonian *h, int dtype, const void *in, void 
 // energy [R], P_joint [joint_width]; any may be null.  Outputs must be zeroed.
 int launch_observables(const ctqw_hamiltonian *h, int dtype, const void *psi, double *P_mean,
                        double *P_joint, double *norm, double *energy, cudaStream_t s);
+// The same without P_joint for realizations r0 .. r0 + R_run - 1 only: their
+// P terms are added into P_mean with the group's full 1/R_g weight, and
+// norm/energy are indexed by the absolute realization.
+int launch_observables_range(const ctqw_hamiltonian *h, int dtype, const void *psi, int r0, int R_run,
+                             double *P_mean, double *norm, double *energy, cudaStream_t s);
 
 // One-body reduced density matrix per size group (adds into rho, zeroed by
 // the caller): [joint_width] complex128 at the pair-distribution offsets.
@@ -232,11 +243,19 @@ int launch_group_sum(const ctqw_hamiltonian *h, const double *grad, double *out,
 // n_steps steps on chip; lo (a c64 state, lane-major rows) carries the
 // rounding error in and out; when snap is not null the state after every
 // snap_every-th step before the last is stored to slot q = step/snap_every - 1
-// of snap (consecutive states, the layout of psi).
+// of snap (consecutive states, the layout of psi).  The launch covers
+// realizations r0 .. r0 + R_run - 1 with one cluster per resident slot; the
+// clusters take the realizations one at a time from the handle's ticket
+// counter (work_counter), which the launch zeroes on its stream.
 bool fused_rows_supported(const ctqw_hamiltonian *h, int dtype);
+// How many realizations (the last ones) to run on the register tiles on the
+// handle's side stream while the clusters run the rest: the SMs that hold no
+// cluster (a 16-CTA cluster needs 8 SMs of one GPC) take a share matched to
+// their throughput.  0 when under 1/16 of the SMs would be idle.
+int fused_rows_split(const ctqw_hamiltonian *h, int shape, int K, int *R_tiled);
 int launch_taylor_fused_rows(const ctqw_hamiltonian *h, void *psi, void *lo, void *snap,
                              int snap_every, double dt, int K, int64_t n_steps, int compensated,
-                             int shape, int test_timeout, cudaStream_t s);
+                             int shape, int test_timeout, int r0, int R_run, cudaStream_t s);
 
 // Fused row-wavefront Taylor propagation (m = 2, c64, open chains): every
 // Taylor term of a step on chip, psi streamed once per step; lo: the carried
@@ -256,6 +275,10 @@ int tiled_default_shape(int K);   // register tiles at the depth that needs the 
 int launch_taylor_tiled(const ctqw_hamiltonian *h, int shape, const void *w_in, const void *psi,
                         void *w_out, void *lo, double dt, int j0, int n_stages, int final,
                         int compensated, cudaStream_t s);
+// The same for realizations r0 .. r0 + R_run - 1 of a handle with one size group.
+int launch_taylor_tiled_range(const ctqw_hamiltonian *h, int shape, const void *w_in, const void *psi,
+                              void *w_out, void *lo, double dt, int j0, int n_stages, int final,
+                              int compensated, int r0, int R_run, cudaStream_t s);
 
 // Fused cluster-resident Taylor propagation (m = 2, c64), multi-warp bands.
 bool fused_taylor_supported(const ctqw_hamiltonian *h, int dtype);

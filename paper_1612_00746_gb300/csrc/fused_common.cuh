@@ -18,7 +18,8 @@ static __device__ __forceinline__ unsigned cluster_rank() {
     return r;
 }
 
-// Full cluster barrier (used at the start and the end of the kernel only).
+// Full cluster barrier (outside the stage loop: at the start and the end of a
+// kernel, and around a realization hand-out).
 static __device__ __forceinline__ void cluster_barrier() {
     __syncwarp();
     asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
@@ -34,6 +35,13 @@ static __device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank
     uint32_t r;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
     return r;
+}
+
+// 32-bit load from the shared memory of a CTA of the cluster (a map_rank address).
+static __device__ __forceinline__ int ld_shared_cluster_s32(uint32_t raddr) {
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(raddr) : "memory");
+    return v;
 }
 
 static __device__ __forceinline__ void mbar_init(uint32_t mb, uint32_t count) {

@@ -1,8 +1,11 @@
 // Fused, cluster-resident Taylor propagation for two particles in complex FP32,
 // full-row layout.
 //
-// One thread-block cluster owns one realization for the whole launch (the
-// order-K Taylor polynomial of Algorithm 3, Sec. 2.3, applied n_steps times).
+// One thread-block cluster owns one realization at a time for all steps of
+// the launch (the order-K Taylor polynomial of Algorithm 3, Sec. 2.3, applied
+// n_steps times).  The grid holds only as many clusters as are resident at
+// once, and each takes realization after realization from a ticket counter,
+// so the SMs a cluster holds stay its own until the launch ends.
 // The N x N tile is split into row slabs, one per CTA; every warp owns RL
 // whole rows and each lane CL = N/32 adjacent columns of them, so a warp
 // covers full rows: neighbours along x2 are in the lane's registers or one
@@ -42,6 +45,7 @@
 // the row, so that every 16-byte access of a warp touches 32 consecutive
 // slots (a plain row-major layout puts lanes CL*8 bytes apart, a 4-way bank
 // conflict for CL = 8).  Every reader uses the writer's lane mapping.
+#include <algorithm>
 #include <type_traits>
 
 #include "ctqw_internal.cuh"
@@ -70,6 +74,8 @@ struct RowsArgs {
     int *status;
     unsigned long long wait_limit_ns;
     int test_timeout;
+    int r0, R_run;          // realizations r0 .. r0 + R_run - 1, handed out one at a time
+    int *work;              // ticket counter of the hand-out, zero at the launch
     float inv_j[kMaxK + 1];
 };
 
@@ -178,16 +184,18 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
     float2 *los = reinterpret_cast<float2 *>(rowc + SR + 1);          // [SR][N] carried error, lane-major
     __shared__ __align__(8) unsigned long long mbar[2][2];
     __shared__ __align__(8) unsigned long long mbar_never;
+    __shared__ int next_r;
 
     const int rank = (int)cluster_rank();
-    const int r = blockIdx.x / C;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lrow0 = warp * RL;
     const int x1_0 = rank * SR + lrow0;
     const int x2_0 = lane * CL;
 
     Lane<CL, RL> L;
-    {
+    // coefficients and state of realization r (every warp reads rowc, so the
+    // caller orders this behind the previous realization's last stage)
+    auto load_realization = [&](const int r) {
         const int64_t po = a.tab.par_off[r];
         const double *eps = a.eps + po, *J = a.J + po;
         const double dt = a.dt;
@@ -207,27 +215,45 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
             const float v = (float)(-dt * J[(x2_0 + k - 1 + N) % N]);
             L.nJc[k] = make_float2(v, v);
         }
-    }
-
-    // state in: hi = psi (shared), P = psi (registers), lo (shared, lane-major like hi)
-    float2 *glo = a.lo + a.tab.st_off[r];
+        // state in: hi = psi (shared), P = psi (registers), lo (shared, lane-major like hi)
+        const float2 *glo = a.lo + a.tab.st_off[r];
 #pragma unroll
-    for (int i = 0; i < RL; ++i) {
+        for (int i = 0; i < RL; ++i) {
 #pragma unroll
-        for (int k = 0; k < CL; k += 2)
-            *reinterpret_cast<float4 *>(los + (lrow0 + i) * N + lane * 2 + k * 32) =
-                *reinterpret_cast<const float4 *>(glo + (size_t)(x1_0 + i) * N + lane * 2 + k * 32);
-    }
-#pragma unroll
-    for (int i = 0; i < RL; ++i) {
-#pragma unroll
-        for (int k = 0; k < CL; k += 2) {
-            const float4 v = *reinterpret_cast<const float4 *>(a.psi + a.tab.st_off[r] + (size_t)(x1_0 + i) * N + x2_0 + k);
-            L.P[i][k] = make_float2(v.x, v.y);
-            L.P[i][k + 1] = make_float2(v.z, v.w);
-            *reinterpret_cast<float4 *>(hi + (lrow0 + i) * N + lane * 2 + k * 32) = v;
+            for (int k = 0; k < CL; k += 2)
+                *reinterpret_cast<float4 *>(los + (lrow0 + i) * N + lane * 2 + k * 32) =
+                    *reinterpret_cast<const float4 *>(glo + (size_t)(x1_0 + i) * N + lane * 2 + k * 32);
         }
-    }
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+#pragma unroll
+            for (int k = 0; k < CL; k += 2) {
+                const float4 v = *reinterpret_cast<const float4 *>(a.psi + a.tab.st_off[r] + (size_t)(x1_0 + i) * N + x2_0 + k);
+                L.P[i][k] = make_float2(v.x, v.y);
+                L.P[i][k + 1] = make_float2(v.z, v.w);
+                *reinterpret_cast<float4 *>(hi + (lrow0 + i) * N + lane * 2 + k * 32) = v;
+            }
+        }
+    };
+    // state out (hi, and the carried error for the next launch); each thread
+    // reads back only the shared words it wrote
+    auto store_realization = [&](const int r) {
+        float2 *glo = a.lo + a.tab.st_off[r];
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+#pragma unroll
+            for (int k = 0; k < CL; k += 2)
+                *reinterpret_cast<float4 *>(glo + (size_t)(x1_0 + i) * N + lane * 2 + k * 32) =
+                    *reinterpret_cast<const float4 *>(los + (lrow0 + i) * N + lane * 2 + k * 32);
+        }
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+#pragma unroll
+            for (int k = 0; k < CL; k += 2)
+                *reinterpret_cast<float4 *>(a.psi + a.tab.st_off[r] + (size_t)(x1_0 + i) * N + x2_0 + k) =
+                    *reinterpret_cast<const float4 *>(hi + (lrow0 + i) * N + lane * 2 + k * 32);
+        }
+    };
 
     const int rank_up = (rank + C - 1) % C, rank_dn = (rank + 1) % C;
     const uint32_t send_up = map_rank(smem_u32(halo + N + lane * 2), rank_up);    // their "row below" slot
@@ -250,10 +276,27 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
 
     const long long n_steps = a.n_steps;
     const int K = a.K;
+    // the next realization of this cluster: CTA 0 takes a ticket, the others
+    // read it from CTA 0's shared memory between two cluster barriers
+    auto grab = [&]() -> int {
+        if (rank == 0 && threadIdx.x == 0) next_r = a.r0 + atomicAdd(a.work, 1);
+        cluster_barrier();
+        const int r = ld_shared_cluster_s32(map_rank(smem_u32(&next_r), 0));
+        cluster_barrier();
+        return r;
+    };
     // the whole step loop, for this warp's (constant) diagonal offset
     auto main_loop = [&](auto off_tag) {
         constexpr int OFF = decltype(off_tag)::value;
+        // the stage counter runs on across realizations: the halo slots and
+        // their mbarrier phases continue without a reset, and a neighbour can
+        // never be more than one stage ahead
         unsigned tc = 0;
+        // realizations are handed out one at a time, so a cluster that runs
+        // faster takes more of them
+        for (int r = grab(); r < a.r0 + a.R_run; r = grab()) {
+        __syncthreads();
+        load_realization(r);
         for (long long step = 0; step < n_steps; ++step) {
             auto run_stage = [&](const int j, auto mode_tag) {
                 constexpr int MODE = decltype(mode_tag)::value;
@@ -333,6 +376,8 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
                 }
             }
         }
+        store_realization(r);
+        }
     };
     // the first row's offset modulo CL: a multiple of gcd(RL, CL); only those are compiled
     constexpr int GD = RL % CL == 0 ? CL : (CL % RL == 0 ? RL : (RL % 2 == 0 && CL % 2 == 0 ? 2 : 1));
@@ -344,23 +389,7 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
         case 6: if constexpr (CL > 6 && 6 % GD == 0) main_loop(std::integral_constant<int, 6 % CL>()); break;
         default: break;
     }
-
-    // state out (hi, and the carried error for the next launch)
-#pragma unroll
-    for (int i = 0; i < RL; ++i) {
-#pragma unroll
-        for (int k = 0; k < CL; k += 2)
-            *reinterpret_cast<float4 *>(glo + (size_t)(x1_0 + i) * N + lane * 2 + k * 32) =
-                *reinterpret_cast<const float4 *>(los + (lrow0 + i) * N + lane * 2 + k * 32);
-    }
-#pragma unroll
-    for (int i = 0; i < RL; ++i) {
-#pragma unroll
-        for (int k = 0; k < CL; k += 2)
-            *reinterpret_cast<float4 *>(a.psi + a.tab.st_off[r] + (size_t)(x1_0 + i) * N + x2_0 + k) =
-                *reinterpret_cast<const float4 *>(hi + (lrow0 + i) * N + lane * 2 + k * 32);
-    }
-    cluster_barrier();
+    cluster_barrier();   // no CTA leaves while a neighbour may still push into it
 }
 
 using RowsKernel = void (*)(RowsArgs);
@@ -389,8 +418,8 @@ bool rows_shape_for(int N, int idx, RowsShape &f) {
     RowsShape opts[kRowsShapes];
     switch (N) {
         case 64: opts[0] = rows_shape<2, 8, 8, 2>(); opts[1] = rows_shape<2, 4, 8, 2>(); opts[2] = rows_shape<2, 8, 4, 3>(); break;
-        case 128: opts[0] = rows_shape<4, 4, 8, 2>(); opts[1] = rows_shape<4, 8, 4, 2>(); opts[2] = rows_shape<4, 4, 4, 3>(); break;
-        case 192: opts[0] = rows_shape<6, 4, 4, 3>(); opts[1] = rows_shape<6, 4, 8, 1>(); opts[2] = rows_shape<6, 4, 4, 2>(); break;
+        case 128: opts[0] = rows_shape<4, 8, 4, 2>(); opts[1] = rows_shape<4, 4, 8, 2>(); opts[2] = rows_shape<4, 4, 4, 3>(); break;
+        case 192: opts[0] = rows_shape<6, 4, 8, 1>(); opts[1] = rows_shape<6, 4, 4, 3>(); opts[2] = rows_shape<6, 4, 4, 2>(); break;
         case 256: opts[0] = rows_shape<8, 4, 4, 2>(); opts[1] = rows_shape<8, 4, 8, 1>(); opts[2] = rows_shape<8, 4, 4, 3>(); break;
         default: return false;
     }
@@ -406,9 +435,66 @@ bool fused_rows_supported(const ctqw_hamiltonian *h, int dtype) {
     return dtype == CTQW_C64 && h->m == 2 && h->uniform && rows_shape_for(h->Nmax, 0, f);
 }
 
+namespace {
+
+int set_rows_attributes(const RowsShape &f) {
+    CTQW_CUDA_TRY(cudaFuncSetAttribute((const void *)f.kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)f.smem));
+    if (f.C > 8)
+        CTQW_CUDA_TRY(cudaFuncSetAttribute((const void *)f.kern,
+                                           cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    return CTQW_OK;
+}
+
+int rows_clusters(const RowsShape &f, int *clusters) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)f.C);
+    cfg.blockDim = dim3((unsigned)f.threads);
+    cfg.dynamicSmemBytes = f.smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)f.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CTQW_CUDA_TRY(cudaOccupancyMaxActiveClusters(clusters, (const void *)f.kern, &cfg));
+    return CTQW_OK;
+}
+
+}  // namespace
+
+// Tiled-to-fused throughput ratio per SM, measured on two bosons at N = 256,
+// K = 16 (register tiles at depth 8 against the full-row clusters).
+static constexpr double kTiledPerSmRatio = 0.25;
+
+int fused_rows_split(const ctqw_hamiltonian *h, int shape, int K, int *R_tiled) {
+    *R_tiled = 0;
+    RowsShape f;
+    if (!fused_rows_supported(h, CTQW_C64) || !rows_shape_for(h->Nmax, shape, f) ||
+        !tiled_supported(h, CTQW_C64, tiled_default_shape(K)) || h->group_N.size() != 1)
+        return CTQW_OK;
+    CTQW_TRY(set_rows_attributes(f));
+    int clusters = 0, per_sm = 0, n_sm = 0;
+    CTQW_TRY(rows_clusters(f, &clusters));
+    CTQW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)f.kern, f.threads, f.smem));
+    CTQW_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, h->device));
+    if (clusters < 1 || per_sm < 1) return CTQW_OK;
+    const int used = std::min(n_sm, (clusters * f.C + per_sm - 1) / per_sm);
+    const int idle = n_sm - used;
+    if (idle * 16 < n_sm) return CTQW_OK;   // under 1/16 of the SMs idle: not worth a second stream
+    // both parts end together when each one's share of the realizations
+    // matches its share of the throughput; the fused part gets whole rounds
+    const double share = used / (used + kTiledPerSmRatio * idle);
+    const int rounds = std::max(1, (int)std::lround(h->R * share / clusters));
+    const int R_f = std::min(h->R, rounds * clusters);
+    *R_tiled = h->R - R_f;
+    return CTQW_OK;
+}
+
 int launch_taylor_fused_rows(const ctqw_hamiltonian *h, void *psi, void *lo, void *snap,
                              int snap_every, double dt, int K, int64_t n_steps, int compensated,
-                             int shape, int test_timeout, cudaStream_t s) {
+                             int shape, int test_timeout, int r0, int R_run, cudaStream_t s) {
     RowsShape f;
     if (!rows_shape_for(h->Nmax, shape, f)) {
         ctqw_set_error("fused path: unsupported size N=%d or shape %d", h->Nmax, shape);
@@ -418,6 +504,11 @@ int launch_taylor_fused_rows(const ctqw_hamiltonian *h, void *psi, void *lo, voi
         ctqw_set_error("fused path: K=%d above %d", K, kMaxK);
         return CTQW_EUNSUPPORTED;
     }
+    if (r0 < 0 || R_run < 0 || r0 + R_run > h->R) {
+        ctqw_set_error("fused path: realizations %d..%d outside 0..%d", r0, r0 + R_run, h->R);
+        return CTQW_EINVAL;
+    }
+    if (R_run == 0) return CTQW_OK;
     RowsArgs a;
     a.eps = h->eps64;
     a.J = h->J64;
@@ -435,15 +526,14 @@ int launch_taylor_fused_rows(const ctqw_hamiltonian *h, void *psi, void *lo, voi
     a.status = h->status_d;
     a.test_timeout = test_timeout;
     a.wait_limit_ns = 2000000000ull;
+    a.r0 = r0;
+    a.R_run = R_run;
+    a.work = work_counter(h);
     a.inv_j[0] = 0.f;
     for (int j = 1; j <= kMaxK; ++j) a.inv_j[j] = (float)(1.0 / j);
-    CTQW_CUDA_TRY(cudaFuncSetAttribute((const void *)f.kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)f.smem));
-    if (f.C > 8)
-        CTQW_CUDA_TRY(cudaFuncSetAttribute((const void *)f.kern,
-                                           cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    CTQW_TRY(set_rows_attributes(f));
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(h->R * f.C));
+    cfg.gridDim = dim3((unsigned)f.C);
     cfg.blockDim = dim3((unsigned)f.threads);
     cfg.dynamicSmemBytes = f.smem;
     cfg.stream = s;
@@ -460,6 +550,9 @@ int launch_taylor_fused_rows(const ctqw_hamiltonian *h, void *psi, void *lo, voi
         ctqw_set_error("fused path: no cluster of %d CTAs x %d threads fits", f.C, f.threads);
         return CTQW_EUNSUPPORTED;
     }
+    // one cluster per resident slot, each taking realizations until none is left
+    cfg.gridDim = dim3((unsigned)(std::min(R_run, clusters) * f.C));
+    CTQW_CUDA_TRY(cudaMemsetAsync(a.work, 0, sizeof(int), s));
     CTQW_CUDA_TRY(cudaLaunchKernelEx(&cfg, f.kern, a));
     return CTQW_OK;
 }

@@ -178,7 +178,7 @@ constexpr int kObsWarps = 8;
 constexpr int kObsRows = 8;   // rows a warp takes at once (one multi-value reduction)
 
 // P(x), norm and energy of one sample; see the file comment.  Block
-// (blockIdx.x, r) owns rows_per_block rows of realization r; warp w takes
+// (blockIdx.x, r - r0) owns rows_per_block rows of realization r; warp w takes
 // groups of kObsRows consecutive rows (group w, w + 8, ...), lane l column
 // c0 + l of each 32-column tile.  <psi|H|psi> = sum_s V(s)|psi(s)|^2 -
 // 2 sum_bonds J Re(conj(psi(s)) psi(s')), every bond taken once, by the
@@ -188,7 +188,7 @@ template <typename T, int M>
 __global__ void __launch_bounds__(32 * kObsWarps) occupation_kernel(
     RealTable tab, const T *__restrict__ eps, const T *__restrict__ J,
     const cplx_t<T> *__restrict__ psi, int rows_per_block, double *P_mean, double *norm,
-    double *energy) {
+    double *energy, int r0) {
     using S = ObsSum<T>;
     using A = typename S::A;
     extern __shared__ __align__(16) unsigned char obs_smem[];
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(32 * kObsWarps) occupation_kernel(
     __shared__ A colred[kObsWarps][32];
     __shared__ A red[kObsWarps][2];
     __shared__ unsigned red_bad;
-    const int r = blockIdx.y;
+    const int r = r0 + (int)blockIdx.y;
     const int N = tab.N[r];
     const int n_rows = M == 2 ? N : N * N;
     const int row0 = blockIdx.x * rows_per_block;
@@ -380,33 +380,42 @@ int launch_renormalize(const ctqw_hamiltonian *h, int dtype, void *psi, void *lo
     });
 }
 
+int launch_observables_range(const ctqw_hamiltonian *h, int dtype, const void *psi, int r0, int R_run,
+                             double *P_mean, double *norm, double *energy, cudaStream_t s) {
+    if ((!P_mean && !norm && !energy) || R_run <= 0) return CTQW_OK;
+    if (r0 < 0 || r0 + R_run > h->R) {
+        ctqw_set_error("observables: realizations %d..%d outside 0..%d", r0, r0 + R_run, h->R);
+        return CTQW_EINVAL;
+    }
+    RealTable t = real_table(h);
+    // rows per block: about one wave of 8 blocks per SM over the realizations
+    const int64_t rows_max = h->m == 2 ? (int64_t)h->Nmax : (int64_t)h->Nmax * h->Nmax;
+    const int64_t target = 152 * 8;
+    const int64_t per_r = std::max<int64_t>(1, (target + R_run - 1) / R_run);
+    int64_t rpb = (rows_max + per_r - 1) / per_r;
+    // a whole number of 8-row groups for every warp, at most 4096 rows
+    constexpr int64_t unit = kObsWarps * kObsRows;
+    rpb = std::min<int64_t>(4096, std::max<int64_t>(unit, (rpb + unit - 1) / unit * unit));
+    const dim3 grid((unsigned)((rows_max + rpb - 1) / rpb), (unsigned)R_run);
+    const size_t smem = (size_t)rpb * 8;
+    if (dtype == CTQW_C64) {
+        auto k = h->m == 2 ? occupation_kernel<float, 2> : occupation_kernel<float, 3>;
+        k<<<grid, 32 * kObsWarps, smem, s>>>(t, h->eps32, h->J32, (const float2 *)psi, (int)rpb, P_mean,
+                                             norm, energy, r0);
+    } else {
+        auto k = h->m == 2 ? occupation_kernel<double, 2> : occupation_kernel<double, 3>;
+        k<<<grid, 32 * kObsWarps, smem, s>>>(t, h->eps64, h->J64, (const double2 *)psi, (int)rpb, P_mean,
+                                             norm, energy, r0);
+    }
+    CTQW_CUDA_TRY(cudaGetLastError());
+    return CTQW_OK;
+}
+
 int launch_observables(const ctqw_hamiltonian *h, int dtype, const void *psi, double *P_mean,
                        double *P_joint, double *norm, double *energy, cudaStream_t s) {
     if (!P_mean && !P_joint && !norm && !energy) return CTQW_OK;
+    if (!P_joint) return launch_observables_range(h, dtype, psi, 0, h->R, P_mean, norm, energy, s);
     RealTable t = real_table(h);
-    if (!P_joint) {
-        // rows per block: about one wave of 8 blocks per SM over all realizations
-        const int64_t rows_max = h->m == 2 ? (int64_t)h->Nmax : (int64_t)h->Nmax * h->Nmax;
-        const int64_t target = 152 * 8;
-        const int64_t per_r = std::max<int64_t>(1, (target + h->R - 1) / h->R);
-        int64_t rpb = (rows_max + per_r - 1) / per_r;
-        // a whole number of 8-row groups for every warp, at most 4096 rows
-        constexpr int64_t unit = kObsWarps * kObsRows;
-        rpb = std::min<int64_t>(4096, std::max<int64_t>(unit, (rpb + unit - 1) / unit * unit));
-        const dim3 grid((unsigned)((rows_max + rpb - 1) / rpb), (unsigned)h->R);
-        const size_t smem = (size_t)rpb * 8;
-        if (dtype == CTQW_C64) {
-            auto k = h->m == 2 ? occupation_kernel<float, 2> : occupation_kernel<float, 3>;
-            k<<<grid, 32 * kObsWarps, smem, s>>>(t, h->eps32, h->J32, (const float2 *)psi, (int)rpb, P_mean,
-                                                 norm, energy);
-        } else {
-            auto k = h->m == 2 ? occupation_kernel<double, 2> : occupation_kernel<double, 3>;
-            k<<<grid, 32 * kObsWarps, smem, s>>>(t, h->eps64, h->J64, (const double2 *)psi, (int)rpb, P_mean,
-                                                 norm, energy);
-        }
-        CTQW_CUDA_TRY(cudaGetLastError());
-        return CTQW_OK;
-    }
     int64_t rows = 1;
     for (int j = 1; j < h->m; ++j) rows *= h->Nmax;
     dim3 grid((unsigned)((rows + kRows - 1) / kRows), (unsigned)h->R), block(kThreads);

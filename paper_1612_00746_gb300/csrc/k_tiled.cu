@@ -682,9 +682,16 @@ int tiled_default_shape(int K) {
     return by_depth[D < 1 ? 1 : (D > 8 ? 8 : D)];
 }
 
-int launch_taylor_tiled(const ctqw_hamiltonian *h, int shape, const void *w_in, const void *psi,
-                        void *w_out, void *lo, double dt, int j0, int n_stages, int final,
-                        int compensated, cudaStream_t s) {
+int launch_taylor_tiled_range(const ctqw_hamiltonian *h, int shape, const void *w_in, const void *psi,
+                              void *w_out, void *lo, double dt, int j0, int n_stages, int final,
+                              int compensated, int r0, int R_run, cudaStream_t s) {
+    const bool whole = r0 == 0 && R_run == h->R;
+    if (!whole && (h->group_N.size() != 1 || r0 < 0 || R_run < 0 || r0 + R_run > h->R)) {
+        ctqw_set_error("tiled path: realizations %d..%d of %d (a range needs one size group)", r0,
+                       r0 + R_run, h->R);
+        return CTQW_EINVAL;
+    }
+    if (R_run == 0) return CTQW_OK;
     TiledShape f;
     if (!tiled_shape_for(shape, f)) {
         ctqw_set_error("tiled path: unknown shape %d", shape);
@@ -738,9 +745,10 @@ int launch_taylor_tiled(const ctqw_hamiltonian *h, int shape, const void *w_in, 
         CTQW_CUDA_TRY(cudaGetLastError());
         return CTQW_OK;
     }
-    int off = 0;
+    // one size group: a range is a slice of its (ascending) realization list
+    int off = whole ? 0 : r0;
     for (size_t g = 0; g < h->group_N.size(); ++g) {
-        const int N = h->group_N[g], cnt = h->group_count[g];
+        const int N = h->group_N[g], cnt = whole ? h->group_count[g] : R_run;
         // as few tiles per side as the compiled maximum allows, of equal size
         const int tiles = (N + f.TMAX - 1) / f.TMAX;             // along x1 (and x2 if square)
         const int tiles2 = (N + f.TMAX2 - 1) / f.TMAX2;          // along x2
@@ -751,4 +759,11 @@ int launch_taylor_tiled(const ctqw_hamiltonian *h, int shape, const void *w_in, 
         off += cnt;
     }
     return CTQW_OK;
+}
+
+int launch_taylor_tiled(const ctqw_hamiltonian *h, int shape, const void *w_in, const void *psi,
+                        void *w_out, void *lo, double dt, int j0, int n_stages, int final,
+                        int compensated, cudaStream_t s) {
+    return launch_taylor_tiled_range(h, shape, w_in, psi, w_out, lo, dt, j0, n_stages, final, compensated, 0,
+                                     h->R, s);
 }

@@ -26,6 +26,7 @@ FLAG_PLAIN = 0x1
 FLAG_NO_COMPENSATION = 0x2
 FLAG_RENORMALIZE = 0x4
 FLAG_TEST_WAIT_TIMEOUT = 0x8
+FLAG_ONE_STREAM = 0x10
 
 
 def FUSED_SHAPE(k: int) -> int:
@@ -55,7 +56,7 @@ EXPORTED = (
     "ctqw_graph_state_size", "ctqw_graph_init_state", "ctqw_graph_workspace_size",
     "ctqw_graph_propagate_taylor", "ctqw_graph_propagate_rk4", "ctqw_graph_observables",
     "ctqw_graph_set_chunk", "ctqw_set_norm_check", "ctqw_inject_alloc_failure",
-    "ctqw_set_density_method",
+    "ctqw_set_density_method", "ctqw_fused_split",
 )
 
 
@@ -121,6 +122,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "ctqw_set_norm_check": [vp, dbl],
         "ctqw_inject_alloc_failure": [i32],
         "ctqw_set_density_method": [vp, i32],
+        "ctqw_fused_split": [vp, i32, u32, ctypes.POINTER(i32)],
         "ctqw_adjoint_workspace_size": [vp, i32, i32, i64, i32, ctypes.POINTER(sz)],
         "ctqw_adjoint_grad": [vp, i32, vp, dbl, i32, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp],
         "ctqw_taylor_order": [dbl, i64, dbl, i32, i32, ctypes.POINTER(i32), pd],
@@ -487,6 +489,14 @@ def ctqw_set_density_method(h: Hamiltonian, method: int) -> None:
 
 def ctqw_inject_alloc_failure(after: int) -> None:
     _check(load().ctqw_inject_alloc_failure(int(after)))
+
+
+def ctqw_fused_split(h: Hamiltonian, K: int, flags: int = 0) -> int:
+    """Realizations (the last ones) the fused path runs on the register tiles
+    on its second stream."""
+    r = ctypes.c_int32()
+    _check(load().ctqw_fused_split(h.handle, int(K), int(flags), ctypes.byref(r)))
+    return r.value
 
 
 def ctqw_check_status(h: Hamiltonian, stream=None) -> None:

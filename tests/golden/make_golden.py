@@ -11,6 +11,8 @@ oracle on the GPU machine.
 bosons_n256_u2_r0-3.json: realizations 0..3 of the 2-boson N=256 workload,
 full 2500 steps (t = 50), K = 16: per-realization P_r(x) at steps 500, 1250,
 2500 and the norm and energy at those steps.
+bosons_n256_u2_r1020-1023.json: the same for the last four realizations
+(the ones the fused path runs on its second stream).
 """
 import json
 import multiprocessing as mp
@@ -46,21 +48,24 @@ def _bosons_realization(r):
     return r, out
 
 
-def make_bosons():
+def make_bosons(first=0):
+    reals = list(range(first, first + 4))
     ctx = mp.get_context("spawn")
     with ctx.Pool(4) as pool:
-        res = dict(pool.map(_bosons_realization, range(4)))
+        res = dict(pool.map(_bosons_realization, reals))
     doc = {
-        "what": "oracle FP64 Taylor (K=16) on realizations 0..3 of bosons_n256_u2",
+        "what": f"oracle FP64 Taylor (K=16) on realizations {reals[0]}..{reals[-1]} of bosons_n256_u2",
         "writer": "tests/golden/make_golden.py (oracle only)",
         "steps": [500, 1250, 2500],
-        "realizations": {str(r): res[r] for r in range(4)},
+        "realizations": {str(r): res[r] for r in reals},
     }
-    with open(os.path.join(HERE, "bosons_n256_u2_r0-3.json"), "w") as f:
+    with open(os.path.join(HERE, f"bosons_n256_u2_r{reals[0]}-{reals[-1]}.json"), "w") as f:
         json.dump(doc, f)
 
 
 if __name__ == "__main__":
-    which = sys.argv[1:] or ["bosons"]
+    which = sys.argv[1:] or ["bosons", "bosons_last"]
     if "bosons" in which:
-        make_bosons()
+        make_bosons(0)
+    if "bosons_last" in which:
+        make_bosons(1020)
