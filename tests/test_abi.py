@@ -90,6 +90,8 @@ def test_entry_points_reject_null_handles(lib):
     assert lib.ctqw_state_size(None, None, None) == E
     assert lib.ctqw_get_params(None, None, None) == E
     assert lib.ctqw_init_state(None, None, 0, None, None) == E
+    r = ctypes.c_int32(-1)
+    assert lib.ctqw_fused_split(None, 16, 0, ctypes.byref(r)) == E
     assert lib.ctqw_destroy_hamiltonian(None) == ctqw.CTQW_OK
 
 
