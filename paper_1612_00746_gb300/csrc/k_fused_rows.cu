@@ -295,88 +295,88 @@ __global__ void __launch_bounds__(32 * W, MINB) taylor_fused_rows_kernel(const _
         // realizations are handed out one at a time, so a cluster that runs
         // faster takes more of them
         for (int r = grab(); r < a.r0 + a.R_run; r = grab()) {
-        __syncthreads();
-        load_realization(r);
-        for (long long step = 0; step < n_steps; ++step) {
-            auto run_stage = [&](const int j, auto mode_tag) {
-                constexpr int MODE = decltype(mode_tag)::value;
-                const int parity = tc & 1;
-                const uint32_t phase = (tc >> 1) & 1;
-                // publish: this warp's first and last rows (shared memory; the slab
-                // edge rows also into the neighbour CTAs)
-                float2 *eb = edge + parity * (W * 2 * N) + warp * (2 * N) + lane * 2;
-#pragma unroll
-                for (int k = 0; k < CL; k += 2) {
-                    const float4 t = make_float4(L.P[0][k].x, L.P[0][k].y, L.P[0][k + 1].x, L.P[0][k + 1].y);
-                    const float4 b = make_float4(L.P[RL - 1][k].x, L.P[RL - 1][k].y, L.P[RL - 1][k + 1].x,
-                                                 L.P[RL - 1][k + 1].y);
-                    *reinterpret_cast<float4 *>(eb + k * 32) = t;
-                    *reinterpret_cast<float4 *>(eb + N + k * 32) = b;
-                    if (warp == 0) st_async16(send_up + parity * (2 * N * 8) + k * 256, t, send_up_mb + parity * 16);
-                    if (warp == W - 1) st_async16(send_dn + parity * (2 * N * 8) + k * 256, b, send_dn_mb + parity * 16);
-                }
-                __syncthreads();
-                mbar_expect_tx2_if(smem_u32(&mbar[parity][0]), smem_u32(&mbar[parity][1]), N * 8,
-                                   threadIdx.x == 0);
-                // the rows above and below this warp's block
-                const float2 *usrc, *dsrc;
-                if (warp > 0) {
-                    usrc = edge + parity * (W * 2 * N) + (warp - 1) * (2 * N) + N + lane * 2;
-                } else {
-                    if (!dead) dead = !mbar_wait_bounded(smem_u32(&mbar[parity][0]), phase, a.wait_limit_ns, a.status);
-                    usrc = halo + parity * (2 * N) + lane * 2;
-                }
-                if (warp < W - 1) {
-                    dsrc = edge + parity * (W * 2 * N) + (warp + 1) * (2 * N) + lane * 2;
-                } else {
-                    if (!dead) dead = !mbar_wait_bounded(smem_u32(&mbar[parity][1]), phase, a.wait_limit_ns, a.status);
-                    dsrc = halo + parity * (2 * N) + N + lane * 2;
-                }
-                stage<MODE, CL, RL, N, OFF>(L, rowc + lrow0, usrc, dsrc, Q, lane, x1_0, a.dtU, a.inv_j[j]);
-                ++tc;
-            };
-            for (int j = K; j >= 2; --j) run_stage(j, std::integral_constant<int, kHorner>());
-            run_stage(1, std::integral_constant<int, kFinal>());
-            // psi(t+dt) = psi + A w_2 (in P); rounding error carried in lo
+            __syncthreads();
+            load_realization(r);
+            for (long long step = 0; step < n_steps; ++step) {
+                auto run_stage = [&](const int j, auto mode_tag) {
+                    constexpr int MODE = decltype(mode_tag)::value;
+                    const int parity = tc & 1;
+                    const uint32_t phase = (tc >> 1) & 1;
+                    // publish: this warp's first and last rows (shared memory; the slab
+                    // edge rows also into the neighbour CTAs)
+                    float2 *eb = edge + parity * (W * 2 * N) + warp * (2 * N) + lane * 2;
     #pragma unroll
-            for (int i = 0; i < RL; ++i) {
-    #pragma unroll
-                for (int k = 0; k < CL; k += 2) {
-                    float4 *hp = reinterpret_cast<float4 *>(hi + (lrow0 + i) * N + lane * 2 + k * 32);
-                    float4 *lp = reinterpret_cast<float4 *>(los + (lrow0 + i) * N + lane * 2 + k * 32);
-                    float4 h4 = *hp;
-                    if (a.compensated) {
-                        float4 l4 = *lp;
-                        float2 h0 = make_float2(h4.x, h4.y), h1 = make_float2(h4.z, h4.w);
-                        float2 l0 = make_float2(l4.x, l4.y), l1 = make_float2(l4.z, l4.w);
-                        compensated_add2(h0, l0, L.P[i][k]);
-                        compensated_add2(h1, l1, L.P[i][k + 1]);
-                        h4 = make_float4(h0.x, h0.y, h1.x, h1.y);
-                        *lp = make_float4(l0.x, l0.y, l1.x, l1.y);
-                    } else {
-                        h4.x += L.P[i][k].x;
-                        h4.y += L.P[i][k].y;
-                        h4.z += L.P[i][k + 1].x;
-                        h4.w += L.P[i][k + 1].y;
+                    for (int k = 0; k < CL; k += 2) {
+                        const float4 t = make_float4(L.P[0][k].x, L.P[0][k].y, L.P[0][k + 1].x, L.P[0][k + 1].y);
+                        const float4 b = make_float4(L.P[RL - 1][k].x, L.P[RL - 1][k].y, L.P[RL - 1][k + 1].x,
+                                                     L.P[RL - 1][k + 1].y);
+                        *reinterpret_cast<float4 *>(eb + k * 32) = t;
+                        *reinterpret_cast<float4 *>(eb + N + k * 32) = b;
+                        if (warp == 0) st_async16(send_up + parity * (2 * N * 8) + k * 256, t, send_up_mb + parity * 16);
+                        if (warp == W - 1) st_async16(send_dn + parity * (2 * N * 8) + k * 256, b, send_dn_mb + parity * 16);
                     }
-                    *hp = h4;
-                    L.P[i][k] = make_float2(h4.x, h4.y);
-                    L.P[i][k + 1] = make_float2(h4.z, h4.w);
-                }
-            }
-            // a snapshot step: the new state (P) to its slot, row-major like psi
-            if (a.snap_every > 0 && step + 1 < n_steps && (step + 1) % a.snap_every == 0) {
-                float2 *gs = a.snap + ((step + 1) / a.snap_every - 1) * a.snap_stride + a.tab.st_off[r];
-    #pragma unroll
+                    __syncthreads();
+                    mbar_expect_tx2_if(smem_u32(&mbar[parity][0]), smem_u32(&mbar[parity][1]), N * 8,
+                                       threadIdx.x == 0);
+                    // the rows above and below this warp's block
+                    const float2 *usrc, *dsrc;
+                    if (warp > 0) {
+                        usrc = edge + parity * (W * 2 * N) + (warp - 1) * (2 * N) + N + lane * 2;
+                    } else {
+                        if (!dead) dead = !mbar_wait_bounded(smem_u32(&mbar[parity][0]), phase, a.wait_limit_ns, a.status);
+                        usrc = halo + parity * (2 * N) + lane * 2;
+                    }
+                    if (warp < W - 1) {
+                        dsrc = edge + parity * (W * 2 * N) + (warp + 1) * (2 * N) + lane * 2;
+                    } else {
+                        if (!dead) dead = !mbar_wait_bounded(smem_u32(&mbar[parity][1]), phase, a.wait_limit_ns, a.status);
+                        dsrc = halo + parity * (2 * N) + N + lane * 2;
+                    }
+                    stage<MODE, CL, RL, N, OFF>(L, rowc + lrow0, usrc, dsrc, Q, lane, x1_0, a.dtU, a.inv_j[j]);
+                    ++tc;
+                };
+                for (int j = K; j >= 2; --j) run_stage(j, std::integral_constant<int, kHorner>());
+                run_stage(1, std::integral_constant<int, kFinal>());
+                // psi(t+dt) = psi + A w_2 (in P); rounding error carried in lo
+        #pragma unroll
                 for (int i = 0; i < RL; ++i) {
-    #pragma unroll
-                    for (int k = 0; k < CL; k += 2)
-                        *reinterpret_cast<float4 *>(gs + (size_t)(x1_0 + i) * N + x2_0 + k) =
-                            make_float4(L.P[i][k].x, L.P[i][k].y, L.P[i][k + 1].x, L.P[i][k + 1].y);
+        #pragma unroll
+                    for (int k = 0; k < CL; k += 2) {
+                        float4 *hp = reinterpret_cast<float4 *>(hi + (lrow0 + i) * N + lane * 2 + k * 32);
+                        float4 *lp = reinterpret_cast<float4 *>(los + (lrow0 + i) * N + lane * 2 + k * 32);
+                        float4 h4 = *hp;
+                        if (a.compensated) {
+                            float4 l4 = *lp;
+                            float2 h0 = make_float2(h4.x, h4.y), h1 = make_float2(h4.z, h4.w);
+                            float2 l0 = make_float2(l4.x, l4.y), l1 = make_float2(l4.z, l4.w);
+                            compensated_add2(h0, l0, L.P[i][k]);
+                            compensated_add2(h1, l1, L.P[i][k + 1]);
+                            h4 = make_float4(h0.x, h0.y, h1.x, h1.y);
+                            *lp = make_float4(l0.x, l0.y, l1.x, l1.y);
+                        } else {
+                            h4.x += L.P[i][k].x;
+                            h4.y += L.P[i][k].y;
+                            h4.z += L.P[i][k + 1].x;
+                            h4.w += L.P[i][k + 1].y;
+                        }
+                        *hp = h4;
+                        L.P[i][k] = make_float2(h4.x, h4.y);
+                        L.P[i][k + 1] = make_float2(h4.z, h4.w);
+                    }
+                }
+                // a snapshot step: the new state (P) to its slot, row-major like psi
+                if (a.snap_every > 0 && step + 1 < n_steps && (step + 1) % a.snap_every == 0) {
+                    float2 *gs = a.snap + ((step + 1) / a.snap_every - 1) * a.snap_stride + a.tab.st_off[r];
+        #pragma unroll
+                    for (int i = 0; i < RL; ++i) {
+        #pragma unroll
+                        for (int k = 0; k < CL; k += 2)
+                            *reinterpret_cast<float4 *>(gs + (size_t)(x1_0 + i) * N + x2_0 + k) =
+                                make_float4(L.P[i][k].x, L.P[i][k].y, L.P[i][k + 1].x, L.P[i][k + 1].y);
+                    }
                 }
             }
-        }
-        store_realization(r);
+            store_realization(r);
         }
     };
     // the first row's offset modulo CL: a multiple of gcd(RL, CL); only those are compiled
